@@ -1,0 +1,155 @@
+/*
+ * diffsim.h - C ABI of the batched differentiable contact-simulation step (sm_103a).
+ *
+ * One call advances B independent environments (a kinematic-tree robot touching a ground plane)
+ * by one time step and, on request, differentiates the step.  The method is that of
+ * "Highly-Efficient Differentiable Simulation for Robotics" (arXiv 2409.07107):
+ *   - the symplectic-Euler impulse step  v+ = v + dt (vdot_f + M^-1 J_c^T lambda)   (Sec. 2.3, Eq. 3)
+ *     with lambda read as an impulse, so that sigma = J_c v+ = G lambda + g          (Eq. 4);
+ *   - the Coulomb-cone NCP with the De Saxce correction                            (Sec. 2.2, Eq. 1),
+ *     solved by ADMM (Sec. 2.2) followed by Newton steps on the identified modes;
+ *   - implicit differentiation of the NCP with breaking / sticking / sliding modes
+ *     (Sec. 3.2, Eq. 8-10, App. A), the reduced system A X = -B(dG lambda + dg)   (Sec. 3.3, App. B),
+ *     chained with the rigid-body derivatives and the contact-point terms           (Sec. 3.1, 3.4, App. C, D).
+ *
+ * Conventions (all arrays are caller-owned DEVICE memory unless stated; no call allocates):
+ *   - state and outputs are structure-of-arrays with the environment index fastest:
+ *       element (r, e) of an [R][B] array is at r * B + e;
+ *   - q [nq_max][B], v and tau [nv_max][B] (FP64); rows beyond a model's nq / nv are ignored;
+ *   - free-flyer q = (x, y, z, qw, qx, qy, qz), its velocity (linear, angular) in its own frame;
+ *     derivatives w.r.t. q are taken w.r.t. the tangent perturbation q (+) dq (nv columns);
+ *   - contact slot k of env e: body c_link[k*B+e] (-1 = unused), reference point
+ *     c_point[(k*3+i)*B+e] in the body frame, sphere radius c_radius[k*B+e] (0 = corner),
+ *     friction c_mu[k*B+e]; ground plane plane[i*B+e] = (nx, ny, nz, d): points x with n.x = d.
+ *     A slot is active iff n.x - d - r <= 0 (x = reference point in world coordinates);
+ *   - contact triplets are ordered (T1, T2, N) in the contact frame t1 = normalize(e_x - (n.e_x) n)
+ *     (e_y instead of e_x when |n_x| > 0.9), t2 = n x t1, normal last;
+ *   - lambda [3*ncmax][B]: contact IMPULSES per slot (0 for inactive slots);
+ *   - modes [ncmax][B]: DS_MODE_* per slot;
+ *   - Jacobians dv_dq, dv_dv, dv_dtau [nv][nv][B]: element (row i, col j) at (i*nv + j)*B + e.
+ * All calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL = default
+ * stream).  The return code reports argument and launch errors only; per-environment numerical
+ * outcomes go to env_status.  Inputs are never modified.
+ */
+#ifndef DIFFSIM_H
+#define DIFFSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DS_OK = 0,
+  DS_EINVAL = -1,        /* a NULL pointer, a size out of range, an unsupported model shape   */
+  DS_ECUDA = -2,         /* a CUDA runtime call or kernel launch failed                         */
+  DS_ENOMEM = -3,        /* ds_model_create could not allocate the model's device copy          */
+  DS_EUNSUPPORTED = -4   /* no compiled kernel for this (bodies, dofs, contact slots) shape     */
+} ds_status;
+
+typedef enum { DS_FP64 = 0, DS_MIXED = 1 } ds_precision;
+/* DS_MIXED: kinematics, contact detection, the NCP polish, the residual check and the reduced
+ * implicit system in FP64; dynamics, Delassus matrix, ADMM iterations and derivative passes in FP32. */
+
+enum { DS_MODE_BREAKING = 0, DS_MODE_STICKING = 1, DS_MODE_SLIDING = 2, DS_MODE_INACTIVE = 3 };
+
+/* per-environment status bits (env_status[e]) */
+#define DS_ENV_NOT_CONVERGED 1u  /* the NCP residual check failed after all ADMM stages          */
+#define DS_ENV_NONFINITE     2u  /* NaN/Inf in the inputs or the results of this env            */
+#define DS_ENV_SINGULAR      4u  /* the reduced implicit system was rank deficient (basic solution used) */
+#define DS_ENV_NEAR_SWITCH   8u  /* mode-classification margin below margin_delta               */
+
+/* Host description of a kinematic tree; copied by ds_model_create (the caller keeps ownership).
+ * Bodies are numbered in depth-first preorder (parent[i] < i and every subtree is a contiguous
+ * index range).  Body 0 may have a free-flyer joint (joint_type 1); all others are revolute (0). */
+typedef struct {
+  int32_t nbodies;
+  const int32_t* parent;      /* [nbodies], -1 = world                                        */
+  const int32_t* joint_type;  /* [nbodies], 0 revolute, 1 free-flyer                           */
+  const double* axis;         /* [nbodies][3] unit rotation axis in the joint frame (revolute)   */
+  const double* joint_rot;    /* [nbodies][9] row-major rotation of the joint frame in the parent */
+  const double* joint_pos;    /* [nbodies][3] origin of the joint frame in the parent            */
+  const double* mass;         /* [nbodies]                                                      */
+  const double* com;          /* [nbodies][3] centre of mass in the body frame                   */
+  const double* inertia;      /* [nbodies][6] (xx, yy, zz, xy, xz, yz) about the centre of mass  */
+} ds_model_desc;
+
+typedef struct ds_model ds_model; /* opaque; holds a device copy of the description */
+
+/* Validate and copy a model to the current device.  Errors: DS_EINVAL (bad description),
+ * DS_ENOMEM / DS_ECUDA (device copy).  The handle is destroyed with ds_model_destroy.          */
+ds_status ds_model_create(const ds_model_desc* desc, ds_model** out);
+ds_status ds_model_destroy(ds_model* model);
+ds_status ds_model_dims(const ds_model* model, int32_t* nbodies, int32_t* nq, int32_t* nv);
+
+typedef struct {
+  int32_t B;                 /* number of environments (>= 0)                                */
+  int32_t ncmax;             /* contact slots per environment (0..16)                        */
+  const int32_t* model_id;   /* [B] index into the models array, or NULL = every env uses models[0] */
+  const double* q;           /* [nq_max][B] */
+  const double* v;           /* [nv_max][B] */
+  const double* tau;         /* [nv_max][B] */
+  const int32_t* c_link;     /* [ncmax][B]  */
+  const double* c_point;     /* [ncmax][3][B] */
+  const double* c_radius;    /* [ncmax][B]  */
+  const double* c_mu;        /* [ncmax][B]  */
+  const double* plane;       /* [4][B]      */
+} ds_batch;
+
+typedef struct {
+  double dt;                 /* time step (s) */
+  double gravity[3];         /* m/s^2, world frame */
+  int32_t admm_max_iter;     /* total ADMM iteration cap per env over all stages               */
+  double admm_eps;           /* first (loose) ADMM stage tolerance; later stages tighten it     */
+  int32_t polish_iters;      /* Newton steps per stage on the identified mode equations         */
+  double ncp_tol;            /* accepted NCP residual, relative to max(1, ||g||_inf)            */
+  double eps_sigma;          /* mode test: contact-velocity threshold, relative                */
+  double eps_lambda;         /* mode test: impulse threshold, relative                         */
+  double margin_delta;       /* DS_ENV_NEAR_SWITCH below this classification margin             */
+  int32_t precision;         /* ds_precision */
+} ds_options;
+
+/* Fill *opt with the defaults used by the tests and the benchmark. */
+void ds_options_default(ds_options* opt);
+
+typedef struct {
+  double* v_next;            /* [nv_max][B]  required */
+  double* q_next;            /* [nq_max][B]  may be NULL */
+  double* lambda;            /* [3*ncmax][B] may be NULL */
+  uint8_t* modes;            /* [ncmax][B]   may be NULL */
+  uint32_t* env_status;      /* [B]          may be NULL */
+  int32_t* iters;            /* [B] ADMM iterations used, may be NULL */
+} ds_step_out;
+
+/* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e. */
+ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                   const ds_options* opt, const ds_step_out* out, void* stream);
+
+/* One step plus the full Jacobians dv+/dq (tangent), dv+/dv, dv+/dtau (Sec. 3, App. D; each
+ * [nv][nv][B]).  Envs of different models must all have nv equal to the row count of the arrays:
+ * element (i, j) of env e is at (i*nv_e + j)*B + e with nv_e the env's own nv. */
+ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                       const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
+                       double* dv_dtau, void* stream);
+
+/* Vector-Jacobian product (reverse mode, the OptNet-style adjoint of Sec. 3.1): given
+ * v_next_bar [nv_max][B], writes q_bar (tangent), v_bar, tau_bar [nv_max][B] =
+ * (dv+/d(q, v, tau))^T v_next_bar without forming the Jacobians.  Also fills *out like sim_step. */
+ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                       const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
+                       double* q_bar, double* v_bar, double* tau_bar, void* stream);
+
+const char* ds_status_string(ds_status s);
+
+/* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
+ * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per
+ * thread to out[blocks*256] (device, FP64).  Used to measure the CUDA-core FMA peak that bounds
+ * this ALU-bound path; 2 * 8 * iters * blocks * 256 flops per launch. */
+ds_status ds_fma_peak(double* out, int32_t blocks, int32_t iters, int32_t fp64, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFFSIM_H */

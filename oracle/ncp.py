@@ -45,62 +45,120 @@ def proj_K(x, mu):
     return np.concatenate([proj_cone(x[3 * i:3 * i + 3], mu[i]) for i in range(len(mu))]) if len(mu) else x.copy()
 
 
+RHO_SCALE = 0.3      # rho = RHO_SCALE * mean diagonal of G
+RELAX = 1.6          # over-relaxation of the x-step
+
+
 def admm_rho(G):
-    """Penalty parameter: mean diagonal of G (scale of the Delassus operator)."""
+    """Penalty parameter: 0.3 x the mean diagonal of G (the scale of the Delassus operator)."""
     m = G.shape[0]
-    return max(np.trace(G) / m, 1e-12)
+    return max(RHO_SCALE * np.trace(G) / m, 1e-12)
 
 
-def admm(G, g, mu, eps=1e-12, max_iter=20000, rho=None, lam0=None):
-    """ADMM iteration for Eq. 1 (reading stated in the module docstring; the De Saxce term is taken
-    at the most recent primal iterate x).  Stops when ||x - z||_inf <= eps max(1, ||z||_inf) and
-    rho ||z - z_prev||_inf <= eps max(1, ||g||_inf).  Returns (lambda, iterations, converged)."""
+class AdmmState:
+    def __init__(self, m):
+        self.x = np.zeros(m)
+        self.z = np.zeros(m)
+        self.y = np.zeros(m)
+        self.iters = 0
+
+
+def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
+    """ADMM iteration for Eq. 1 (reading stated in the module docstring): the De Saxce term is taken
+    at the most recent primal iterate x, and the x-step is over-relaxed,
+    xh = RELAX x + (1 - RELAX) z, before the z-step and the dual step (the fixed points are
+    unchanged).  Stops when ||x - z||_inf <= eps max(1, ||z||_inf) and
+    rho ||z - z_prev||_inf <= eps max(1, ||g||_inf), or when the state has done max_iter iterations
+    in total.  Continues from ``state`` when given.  Returns (lambda, iterations, converged, state)."""
     m = len(g)
+    st = state or AdmmState(m)
     if m == 0:
-        return np.zeros(0), 0, True
-    if rho is None:
-        rho = admm_rho(G)
+        return np.zeros(0), 0, True, st
+    rho = admm_rho(G)
     L = cholesky(G + rho * np.eye(m))
-    z = np.zeros(m) if lam0 is None else lam0.copy()
-    x = z.copy()
-    y = np.zeros(m)
     gs = max(1.0, np.max(np.abs(g)))
-    for k in range(1, max_iter + 1):
+    x, z, y = st.x, st.z, st.y
+    conv = False
+    while st.iters < max_iter:
+        st.iters += 1
         s = desaxce(G @ x + g, mu)
         x = chol_solve(L, rho * z - y - g - s)
+        xh = RELAX * x + (1.0 - RELAX) * z
         z_prev = z
-        z = proj_K(x + y / rho, mu)
-        y = y + rho * (x - z)
+        z = proj_K(xh + y / rho, mu)
+        y = y + rho * (xh - z)
         rp = np.max(np.abs(x - z))
         rd = rho * np.max(np.abs(z - z_prev))
         if rp <= eps * max(1.0, np.max(np.abs(z))) and rd <= eps * gs:
-            return z, k, True
-    return z, max_iter, False
+            conv = True
+            break
+    st.x, st.z, st.y = x, z, y
+    return z.copy(), st.iters, conv, st
+
+
+def reclassify(G, g, mu, lam, modes, es, el, delta):
+    """Active-set update after a Newton polish that did not give an NCP solution: a breaking
+    contact that penetrates becomes sticking; a sticking or sliding contact that pulls
+    (lambda_N < 0) becomes breaking; a sticking contact whose impulse leaves the cone becomes
+    sliding; a sliding contact that stops (||sigma_T|| below threshold) becomes sticking."""
+    sig = G @ lam + g
+    new = np.array(modes).copy()
+    for i, md in enumerate(modes):
+        l, s = lam[3 * i:3 * i + 3], sig[3 * i:3 * i + 3]
+        if md == BRK:
+            if s[2] < -es:
+                new[i] = STK
+        elif md == STK:
+            if l[2] < -el:
+                new[i] = BRK
+            elif mu[i] * l[2] - np.sqrt(l[:2] @ l[:2]) < -delta:
+                new[i] = SLD
+        else:
+            if l[2] < -el:
+                new[i] = BRK
+            elif np.sqrt(s[:2] @ s[:2]) < es:
+                new[i] = STK
+    return new
 
 
 def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4, 1e-6, 1e-9, 1e-12),
-              max_iter=50000):
-    """Staged solve of Eq. 1: ADMM to a loose tolerance, identification of the contact modes,
-    Newton on the mode equations, and acceptance when the NCP residual is <= tol max(1, ||g||);
-    otherwise ADMM continues from scratch to the next, tighter tolerance.
-    Returns (lambda, admm_iterations, converged)."""
+              rounds=4, max_iter=50000):
+    """Staged solve of Eq. 1.  Each stage continues the ADMM iteration to a tolerance, identifies
+    the contact modes, and runs up to ``rounds`` active-set rounds of Newton on the mode equations
+    (reclassify + retry from the cone projection of the last iterate).  The first candidate whose
+    NCP residual is <= tol max(1, ||g||_inf) is accepted.  Returns (lambda, admm_iterations, converged)."""
     m = len(g)
     if m == 0:
         return np.zeros(0), 0, True
     scale = max(1.0, np.max(np.abs(g)))
-    best, best_r, total = None, np.inf, 0
+    best, best_r = None, np.inf
+    state = None
     for eps in stages:
-        lam, it, _ = admm(G, g, mu, eps=eps, max_iter=max_iter)
-        total += it
-        modes, _ = classify(G, g, mu, lam, max(eps_sigma, 10 * eps), max(eps_lambda, 10 * eps))
-        lp = polish(G, g, mu, lam, modes)
-        for cand in (lp, lam):
-            r = ncp_residual(G, g, mu, cand)
+        lam, it, _, state = admm(G, g, mu, eps=eps, max_iter=max_iter, state=state)
+        lscale = max(1.0, np.max(np.abs(lam)))
+        es, el = max(eps_sigma, 10 * eps), max(eps_lambda, 10 * eps)
+        modes, _ = classify(G, g, mu, lam, es, el)
+        start = lam
+        cands = [lam]
+        for _ in range(rounds):
+            x = newton_modes(G, g, mu, start, modes, sat_delta=10 * eps * lscale)
+            cands.append(x)
+            if ncp_residual(G, g, mu, x) <= tol * scale:
+                break
+            new = reclassify(G, g, mu, x, modes, es * scale, el * lscale, 10 * eps * lscale)
+            if (new == modes).all():
+                break
+            modes = new
+            start = proj_K(x, mu)
+        for c in cands:
+            r = ncp_residual(G, g, mu, c)
             if r < best_r:
-                best, best_r = cand, r
+                best, best_r = c, r
         if best_r <= tol * scale:
-            return best, total, True
-    return best, total, False
+            return best, state.iters, True
+        if state.iters >= max_iter:
+            break
+    return best, state.iters, False
 
 
 def ncp_residual(G, g, mu, lam):
@@ -180,23 +238,41 @@ def cs_jacobian(f, x, h=1e-30):
     return np.stack(cols, axis=1)
 
 
-def polish(G, g, mu, lam, modes, iters=20, tol=1e-15):
-    """Newton on the mode equations with minimum-norm steps (the system is singular when the
-    contact set is redundant).  Returns the polished lambda, or the input if it does not improve
-    the NCP residual."""
+def saturated(lam, mu, modes, delta):
+    """Sticking contacts whose impulse lies within delta of the cone boundary (||l_T|| = mu l_N)."""
+    out = []
+    for i, md in enumerate(modes):
+        l = lam[3 * i:3 * i + 3]
+        if md == STK and mu[i] * l[2] - np.sqrt(l[:2] @ l[:2]) <= delta:
+            out.append(i)
+    return out
+
+
+def polish_equations(lam, G, g, mu, modes, sat):
+    """Mode equations plus, for each saturated sticking contact, mu lambda_N - ||lambda_T|| = 0.
+    With redundant contacts the sticking impulses are only defined up to internal forces; this
+    extra equation picks the member of that family that keeps a boundary impulse on the boundary."""
+    e = mode_equations(lam, G, g, mu, modes)
+    extra = [mu[i] * lam[3 * i + 2] - np.sqrt(lam[3 * i:3 * i + 2] @ lam[3 * i:3 * i + 2]) for i in sat]
+    return np.concatenate([e, np.array(extra)]) if extra else e
+
+
+def newton_modes(G, g, mu, lam, modes, iters=20, tol=1e-15, sat_delta=0.0):
+    """Newton on the mode equations (plus the saturation equations of the sticking contacts whose
+    impulse is within sat_delta of the cone boundary) with minimum-norm least-squares steps (the
+    system is singular when the contact set is redundant)."""
     if len(g) == 0:
         return lam
+    sat = saturated(lam, mu, modes, sat_delta)
     x = lam.copy()
     scale = max(1.0, np.max(np.abs(g)))
     for _ in range(iters):
-        F = mode_equations(x, G, g, mu, modes)
+        F = polish_equations(x, G, g, mu, modes, sat)
         if np.max(np.abs(F)) <= tol * scale:
             break
-        J = cs_jacobian(lambda z: mode_equations(z, G, g, mu, modes), x)
+        J = cs_jacobian(lambda z: polish_equations(z, G, g, mu, modes, sat), x)
         x = x - np.linalg.lstsq(J, F, rcond=1e-13)[0]
-    if ncp_residual(G, g, mu, x) <= ncp_residual(G, g, mu, lam):
-        return x
-    return lam
+    return x
 
 
 def brute_force_single(G, g, mu, n_angles=720):

@@ -56,7 +56,7 @@ def step(model, env, opt, do_polish=True):
     if do_polish:
         lam, iters, conv = solve_ncp(G, g, mu, es, el)
     else:
-        lam, iters, conv = admm(G, g, mu, eps=1e-12, max_iter=50000)
+        lam, iters, conv, _ = admm(G, g, mu, eps=1e-12, max_iter=50000)
     modes, margin = classify(G, g, mu, lam, es, el)
     v_next = ufd_velocity(model, env, opt, slots, q, v, tau, lam)
     q_next = rigid.integrate(model, q, dt * v_next)

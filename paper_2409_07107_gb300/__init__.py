@@ -1,0 +1,237 @@
+"""GB300-native batched differentiable contact-simulation step (Python binding of libdiffsim.so).
+
+The library computes, for B independent environments at once, one time step of frictional-contact
+multibody simulation and its implicit derivatives (arXiv 2409.07107, Sec. 2-3, App. A-D).  This
+module only marshals arguments: every step of the computation runs in the CUDA kernels behind the
+C ABI declared in include/diffsim.h.  There is no CPU fallback: if the library is missing the calls
+raise.
+
+    from paper_2409_07107_gb300 import scenes, Simulator
+    sim = Simulator(scenes.arm_cube(4096), precision="fp64")
+    out = sim.step_jac()          # v_next, q_next, lambda, modes, status, dv_dq, dv_dv, dv_dtau
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdiffsim.so")
+
+DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED = 0, -1, -2, -3, -4
+DS_FP64, DS_MIXED = 0, 1
+MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
+ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH = 1, 2, 4, 8
+
+EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
+           "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak")
+
+
+class ds_model_desc(ctypes.Structure):
+    _fields_ = [("nbodies", ctypes.c_int32), ("parent", ctypes.c_void_p), ("joint_type", ctypes.c_void_p),
+                ("axis", ctypes.c_void_p), ("joint_rot", ctypes.c_void_p), ("joint_pos", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("com", ctypes.c_void_p), ("inertia", ctypes.c_void_p)]
+
+
+class ds_batch(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("ncmax", ctypes.c_int32), ("model_id", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("v", ctypes.c_void_p), ("tau", ctypes.c_void_p),
+                ("c_link", ctypes.c_void_p), ("c_point", ctypes.c_void_p), ("c_radius", ctypes.c_void_p),
+                ("c_mu", ctypes.c_void_p), ("plane", ctypes.c_void_p)]
+
+
+class ds_options(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("admm_max_iter", ctypes.c_int32),
+                ("admm_eps", ctypes.c_double), ("polish_iters", ctypes.c_int32), ("ncp_tol", ctypes.c_double),
+                ("eps_sigma", ctypes.c_double), ("eps_lambda", ctypes.c_double),
+                ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32)]
+
+
+class ds_step_out(ctypes.Structure):
+    _fields_ = [("v_next", ctypes.c_void_p), ("q_next", ctypes.c_void_p), ("lambda_", ctypes.c_void_p),
+                ("modes", ctypes.c_void_p), ("env_status", ctypes.c_void_p), ("iters", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libdiffsim.so (built in-tree by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdiffsim.so is not built (run paper_2409_07107_gb300.build.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32 = ctypes.c_void_p, ctypes.c_int32
+        L.ds_model_create.argtypes = [ctypes.POINTER(ds_model_desc), ctypes.POINTER(vp)]
+        L.ds_model_destroy.argtypes = [vp]
+        L.ds_model_dims.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.ds_options_default.argtypes = [ctypes.POINTER(ds_options)]
+        L.ds_options_default.restype = None
+        L.ds_status_string.argtypes = [ctypes.c_int]
+        L.ds_status_string.restype = ctypes.c_char_p
+        common = [vp, i32, ctypes.POINTER(ds_batch), ctypes.POINTER(ds_options)]
+        L.sim_step.argtypes = common + [ctypes.POINTER(ds_step_out), vp]
+        L.sim_step_jac.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
+        L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
+        L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
+        for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
+                  "ds_fma_peak"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class DiffsimError(RuntimeError):
+    pass
+
+
+def _check(status):
+    if status != DS_OK:
+        raise DiffsimError("diffsim: %s (%d)" % (lib().ds_status_string(status).decode(), status))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class DeviceModel:
+    """A model copied to the current CUDA device (ds_model_create)."""
+
+    def __init__(self, model):
+        self._keep = [np.ascontiguousarray(model.parent, np.int32), np.ascontiguousarray(model.jtype, np.int32),
+                      np.ascontiguousarray(model.axis, np.float64), np.ascontiguousarray(model.jrot, np.float64),
+                      np.ascontiguousarray(model.jpos, np.float64), np.ascontiguousarray(model.mass, np.float64),
+                      np.ascontiguousarray(model.com, np.float64), np.ascontiguousarray(model.inertia, np.float64)]
+        k = self._keep
+        d = ds_model_desc(model.nb, *[a.ctypes.data for a in k])
+        h = ctypes.c_void_p()
+        _check(lib().ds_model_create(ctypes.byref(d), ctypes.byref(h)))
+        self.handle = h
+        self.nb, self.nq, self.nv = model.nb, model.nq, model.nv
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ds_model_destroy(self.handle)
+            self.handle = None
+
+
+def make_options(precision="fp64", **kw):
+    o = ds_options()
+    lib().ds_options_default(ctypes.byref(o))
+    o.precision = DS_MIXED if precision in ("mixed", DS_MIXED) else DS_FP64
+    for k, v in kw.items():
+        if k == "gravity":
+            o.gravity[:] = list(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _models_array(models):
+    arr = (ctypes.c_void_p * len(models))(*[m.handle.value for m in models])
+    return arr
+
+
+def _batch_struct(t):
+    return ds_batch(t["q"].shape[1], t["c_link"].shape[0], _ptr(t.get("model_id")), _ptr(t["q"]), _ptr(t["v"]),
+                    _ptr(t["tau"]), _ptr(t["c_link"]), _ptr(t["c_point"]), _ptr(t["c_radius"]), _ptr(t["c_mu"]),
+                    _ptr(t["plane"]))
+
+
+def _out_struct(o):
+    return ds_step_out(_ptr(o["v_next"]), _ptr(o.get("q_next")), _ptr(o.get("lambda")), _ptr(o.get("modes")),
+                       _ptr(o.get("status")), _ptr(o.get("iters")))
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def sim_step(models, batch, opt, out, stream=None):
+    """C-ABI sim_step on device tensors (dicts of torch tensors, see Simulator)."""
+    b, o = _batch_struct(batch), _out_struct(out)
+    _check(lib().sim_step(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                          ctypes.byref(o), _stream(stream)))
+
+
+def sim_step_jac(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, stream=None):
+    b, o = _batch_struct(batch), _out_struct(out)
+    _check(lib().sim_step_jac(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                              ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), _stream(stream)))
+
+
+def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, stream=None):
+    b, o = _batch_struct(batch), _out_struct(out)
+    _check(lib().sim_step_vjp(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                              _ptr(v_next_bar), ctypes.byref(o), _ptr(q_bar), _ptr(v_bar), _ptr(tau_bar),
+                              _stream(stream)))
+
+
+def fma_peak(out, blocks, iters, fp64, stream=None):
+    """Launch the FMA-throughput probe (2 * 8 * iters * blocks * 256 flops)."""
+    _check(lib().ds_fma_peak(_ptr(out), blocks, iters, 1 if fp64 else 0, _stream(stream)))
+
+
+def batch_to_device(batch, device="cuda"):
+    import torch
+    f64 = dict(dtype=torch.float64, device=device)
+    i32 = dict(dtype=torch.int32, device=device)
+    t = dict(q=torch.as_tensor(batch.q, **f64).contiguous(), v=torch.as_tensor(batch.v, **f64).contiguous(),
+             tau=torch.as_tensor(batch.tau, **f64).contiguous(), c_link=torch.as_tensor(batch.c_link, **i32).contiguous(),
+             c_point=torch.as_tensor(batch.c_point, **f64).contiguous(),
+             c_radius=torch.as_tensor(batch.c_radius, **f64).contiguous(),
+             c_mu=torch.as_tensor(batch.c_mu, **f64).contiguous(), plane=torch.as_tensor(batch.plane, **f64).contiguous())
+    if batch.model_id is not None:
+        t["model_id"] = torch.as_tensor(batch.model_id, **i32).contiguous()
+    return t
+
+
+class Simulator:
+    """Device-resident batch + outputs for one workload; thin wrapper over the three C-ABI calls."""
+
+    def __init__(self, workload, precision=None, device="cuda", **opt):
+        import torch
+        self.workload = workload
+        self.models = [DeviceModel(m) for m in workload.models]
+        self.batch = batch_to_device(workload.batch, device)
+        prec = precision or workload.precision
+        self.opt = make_options(prec, dt=workload.options.dt, gravity=workload.options.gravity, **opt)
+        B = workload.batch.B
+        nq = workload.batch.q.shape[0]
+        nv = workload.batch.v.shape[0]
+        nc = workload.batch.ncmax
+        f64 = dict(dtype=torch.float64, device=device)
+        self.nv = nv
+        self.out = dict(v_next=torch.zeros(nv, B, **f64), q_next=torch.zeros(nq, B, **f64),
+                        **{"lambda": torch.zeros(3 * nc, B, **f64)},
+                        modes=torch.zeros(nc, B, dtype=torch.uint8, device=device),
+                        status=torch.zeros(B, dtype=torch.int32, device=device),
+                        iters=torch.zeros(B, dtype=torch.int32, device=device))
+        self.jac = None
+        self.vjp_out = None
+
+    def step(self, stream=None):
+        sim_step(self.models, self.batch, self.opt, self.out, stream)
+        return self.out
+
+    def step_jac(self, stream=None):
+        import torch
+        B = self.workload.batch.B
+        if self.jac is None:
+            n = self.nv
+            self.jac = [torch.zeros(n, n, B, dtype=torch.float64, device=self.out["v_next"].device) for _ in range(3)]
+        sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, stream=stream)
+        return dict(self.out, dv_dq=self.jac[0], dv_dv=self.jac[1], dv_dtau=self.jac[2])
+
+    def step_vjp(self, v_next_bar, stream=None):
+        import torch
+        if self.vjp_out is None:
+            self.vjp_out = [torch.zeros_like(self.out["v_next"]) for _ in range(3)]
+        sim_step_vjp(self.models, self.batch, self.opt, v_next_bar.contiguous(), self.out, *self.vjp_out, stream=stream)
+        return dict(self.out, q_bar=self.vjp_out[0], v_bar=self.vjp_out[1], tau_bar=self.vjp_out[2])

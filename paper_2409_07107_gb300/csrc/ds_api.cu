@@ -1,0 +1,193 @@
+// C ABI of the batched contact step: argument checks, model upload, kernel dispatch.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ds_common.cuh"
+
+struct ds_model {
+  DevModel host;       // host copy (dims, preorder data)
+  DevModel* dev;       // device copy
+  int device;
+};
+
+extern "C" void ds_options_default(ds_options* o) {
+  if (!o) return;
+  o->dt = 1e-3;
+  o->gravity[0] = 0.0; o->gravity[1] = 0.0; o->gravity[2] = -9.81;
+  o->admm_max_iter = 2000;
+  o->admm_eps = 1e-4;
+  o->polish_iters = 10;
+  o->ncp_tol = 1e-12;
+  o->eps_sigma = 1e-8;
+  o->eps_lambda = 1e-8;
+  o->margin_delta = 1e-3;
+  o->precision = DS_FP64;
+}
+
+extern "C" const char* ds_status_string(ds_status s) {
+  switch (s) {
+    case DS_OK: return "ok";
+    case DS_EINVAL: return "invalid argument";
+    case DS_ECUDA: return "CUDA error";
+    case DS_ENOMEM: return "out of device memory";
+    case DS_EUNSUPPORTED: return "no compiled kernel for this model shape";
+  }
+  return "unknown status";
+}
+
+extern "C" ds_status ds_model_create(const ds_model_desc* d, ds_model** out) {
+  if (!d || !out) return DS_EINVAL;
+  *out = nullptr;
+  const int nb = d->nbodies;
+  if (nb <= 0 || nb > DS_MAXB || !d->parent || !d->joint_type || !d->axis || !d->joint_rot ||
+      !d->joint_pos || !d->mass || !d->com || !d->inertia)
+    return DS_EINVAL;
+  DevModel h;
+  std::memset(&h, 0, sizeof(h));
+  h.nb = nb;
+  int nq = 0, nv = 0;
+  for (int i = 0; i < nb; ++i) {
+    const int p = d->parent[i];
+    const int jt = d->joint_type[i];
+    if (p >= i || p < -1) return DS_EINVAL;                 // topological order
+    if (jt != 0 && jt != 1) return DS_EINVAL;
+    if (jt == 1 && p != -1) return DS_EINVAL;                // free-flyer only at a root
+    if (!(d->mass[i] > 0.0) || !std::isfinite(d->mass[i])) return DS_EINVAL;
+    h.parent[i] = p;
+    h.jtype[i] = jt;
+    h.iq[i] = nq;
+    h.iv[i] = nv;
+    h.nd[i] = jt == 1 ? 6 : 1;
+    nq += jt == 1 ? 7 : 1;
+    nv += h.nd[i];
+    if (nv > DS_MAXNV) return DS_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+      h.axis[i][k] = d->axis[3 * i + k];
+      h.jpos[i][k] = d->joint_pos[3 * i + k];
+      h.com[i][k] = d->com[3 * i + k];
+    }
+    for (int k = 0; k < 9; ++k) h.jrot[i][k] = d->joint_rot[9 * i + k];
+    for (int k = 0; k < 6; ++k) h.inertia[i][k] = d->inertia[6 * i + k];
+    h.mass[i] = d->mass[i];
+    if (jt == 0) {
+      const double n2 = h.axis[i][0] * h.axis[i][0] + h.axis[i][1] * h.axis[i][1] + h.axis[i][2] * h.axis[i][2];
+      if (!(std::fabs(n2 - 1.0) < 1e-9)) return DS_EINVAL;   // unit axis
+    }
+  }
+  h.nq = nq;
+  h.nv = nv;
+  // subtree ranges; preorder means every subtree is a contiguous index range
+  for (int i = 0; i < nb; ++i) {
+    int e = i + 1;
+    while (e < nb) {
+      int b = e;
+      while (b > i) b = h.parent[b];
+      if (b != i) break;
+      ++e;
+    }
+    h.sub_end[i] = e;
+    for (int k = e; k < nb; ++k) {
+      int b = k;
+      while (b > i) b = h.parent[b];
+      if (b == i) return DS_EINVAL;                          // not depth-first preorder
+    }
+    for (int dd = h.iv[i]; dd < h.iv[i] + h.nd[i]; ++dd) h.dof_body[dd] = i;
+  }
+  ds_model* m = new (std::nothrow) ds_model;
+  if (!m) return DS_ENOMEM;
+  m->host = h;
+  if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return DS_ECUDA; }
+  if (cudaMalloc(&m->dev, sizeof(DevModel)) != cudaSuccess) { delete m; return DS_ENOMEM; }
+  if (cudaMemcpy(m->dev, &h, sizeof(DevModel), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->dev);
+    delete m;
+    return DS_ECUDA;
+  }
+  *out = m;
+  return DS_OK;
+}
+
+extern "C" ds_status ds_model_destroy(ds_model* m) {
+  if (!m) return DS_EINVAL;
+  cudaFree(m->dev);
+  delete m;
+  return DS_OK;
+}
+
+extern "C" ds_status ds_model_dims(const ds_model* m, int32_t* nb, int32_t* nq, int32_t* nv) {
+  if (!m) return DS_EINVAL;
+  if (nb) *nb = m->host.nb;
+  if (nq) *nq = m->host.nq;
+  if (nv) *nv = m->host.nv;
+  return DS_OK;
+}
+
+static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
+                     const ds_step_out* out, int mode, double* dq, double* dv, double* dtau, const double* vbar,
+                     double* qb, double* vb, double* tb, void* stream) {
+  if (!models || nmodels <= 0 || nmodels > 64 || !b || !o || !out) return DS_EINVAL;
+  if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
+  if (!out->v_next) return DS_EINVAL;
+  if (b->B == 0) return DS_OK;
+  if (!b->q || !b->v || !b->tau || !b->plane) return DS_EINVAL;
+  if (b->ncmax > 0 && (!b->c_link || !b->c_point || !b->c_radius || !b->c_mu)) return DS_EINVAL;
+  if (nmodels > 1 && !b->model_id) return DS_EINVAL;
+  if (!(o->dt > 0.0) || o->admm_max_iter < 1 || o->polish_iters < 0 || !(o->admm_eps > 0.0) || !(o->ncp_tol > 0.0))
+    return DS_EINVAL;
+  if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
+  if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
+  if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
+  for (int k = 0; k < nmodels; ++k) {
+    if (!models[k]) return DS_EINVAL;
+    if (!ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision)) return DS_EUNSUPPORTED;
+  }
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.B = b->B; a.ncmax = b->ncmax;
+  a.q = b->q; a.v = b->v; a.tau = b->tau;
+  a.c_link = b->c_link; a.c_point = b->c_point; a.c_radius = b->c_radius; a.c_mu = b->c_mu; a.plane = b->plane;
+  a.dt = o->dt; a.gx = o->gravity[0]; a.gy = o->gravity[1]; a.gz = o->gravity[2];
+  a.admm_max_iter = o->admm_max_iter; a.polish_iters = o->polish_iters;
+  a.admm_eps = o->admm_eps; a.ncp_tol = o->ncp_tol;
+  a.eps_sigma = o->eps_sigma; a.eps_lambda = o->eps_lambda; a.margin_delta = o->margin_delta;
+  a.v_next = out->v_next; a.q_next = out->q_next; a.lambda = out->lambda; a.modes = out->modes;
+  a.status = out->env_status; a.iters = out->iters;
+  a.dv_dq = dq; a.dv_dv = dv; a.dv_dtau = dtau;
+  a.vbar = vbar; a.q_bar = qb; a.v_bar = vb; a.tau_bar = tb;
+  a.run = mode;
+  a.env_list = nullptr;
+  a.n_env = b->B;
+  a.model_id = nmodels > 1 ? b->model_id : nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < nmodels; ++k) {
+    const ds_kernel_entry* ke = ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision);
+    a.model = models[k]->dev;
+    a.model_index = k;
+    ke->fn(a, s);
+    if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
+  }
+  return DS_OK;
+}
+
+extern "C" ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                              const ds_options* opt, const ds_step_out* out, void* stream) {
+  return run(models, nmodels, batch, opt, out, DS_RUN_STEP, nullptr, nullptr, nullptr, nullptr, nullptr,
+             nullptr, nullptr, stream);
+}
+
+extern "C" ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                                  const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
+                                  double* dv_dtau, void* stream) {
+  return run(models, nmodels, batch, opt, out, DS_RUN_JAC, dv_dq, dv_dv, dv_dtau, nullptr, nullptr, nullptr,
+             nullptr, stream);
+}
+
+extern "C" ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                                  const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
+                                  double* q_bar, double* v_bar, double* tau_bar, void* stream) {
+  return run(models, nmodels, batch, opt, out, DS_RUN_VJP, nullptr, nullptr, nullptr, v_next_bar, q_bar, v_bar,
+             tau_bar, stream);
+}

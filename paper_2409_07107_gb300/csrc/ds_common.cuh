@@ -1,0 +1,239 @@
+// Shared device-side definitions of the batched contact-step kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+#include "diffsim.h"
+
+#define DS_MAXB 32       // bodies per model
+#define DS_MAXNV 36      // velocity dofs per model
+#define DS_MAXSLOTS 16   // contact slots per env
+
+// Device copy of a model.  Bodies are in depth-first preorder: the subtree of body i is the index
+// range [i, sub_end[i]).  A dof is a column of a joint's motion subspace; the dofs of body i are
+// iv[i] .. iv[i] + nd[i] - 1.
+struct DevModel {
+  int nb, nq, nv, pad;
+  int parent[DS_MAXB], jtype[DS_MAXB], iq[DS_MAXB], iv[DS_MAXB], nd[DS_MAXB], sub_end[DS_MAXB];
+  int dof_body[DS_MAXNV];
+  double axis[DS_MAXB][3], jrot[DS_MAXB][9], jpos[DS_MAXB][3];
+  double mass[DS_MAXB], com[DS_MAXB][3], inertia[DS_MAXB][6];
+};
+
+enum { DS_RUN_STEP = 0, DS_RUN_JAC = 1, DS_RUN_VJP = 2 };
+
+// Everything a launch needs; passed by value.
+struct KArgs {
+  const DevModel* model;
+  const int32_t* env_list;   // envs handled by this launch (NULL: 0 .. n_env-1)
+  const int32_t* model_id;   // [B] or NULL; a launch only handles envs with model_id == model_index
+  int model_index;
+  int n_env;
+  int B, ncmax;
+  const double *q, *v, *tau;
+  const int32_t* c_link;
+  const double *c_point, *c_radius, *c_mu, *plane;
+  double dt, gx, gy, gz;
+  int admm_max_iter, polish_iters;
+  double admm_eps, ncp_tol, eps_sigma, eps_lambda, margin_delta;
+  double *v_next, *q_next, *lambda;
+  uint8_t* modes;
+  uint32_t* status;
+  int32_t* iters;
+  double *dv_dq, *dv_dv, *dv_dtau;
+  const double* vbar;
+  double *q_bar, *v_bar, *tau_bar;
+  int run;
+};
+
+typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);
+
+// Registry of compiled shapes: (bodies, dofs, contact slots, precision) -> launcher.
+struct ds_kernel_entry {
+  int nb, nv, ns, precision;
+  ds_launch_fn fn;
+};
+extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
+
+// ------------------------------------------------------------------------------ small algebra
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T* a, const T* b, T* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T* a, const T* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+template <typename T>
+__device__ __forceinline__ T dot6(const T* a, const T* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3] + a[4] * b[4] + a[5] * b[5];
+}
+
+// Spatial vectors are (linear, angular), expressed in world axes at the world origin.
+// o = a x b (motion cross product); o must not alias a or b.
+template <typename T>
+__device__ __forceinline__ void mcross(const T* a, const T* b, T* o) {
+  T t1[3], t2[3];
+  cross3(a + 3, b, t1);
+  cross3(a, b + 3, t2);
+  o[0] = t1[0] + t2[0];
+  o[1] = t1[1] + t2[1];
+  o[2] = t1[2] + t2[2];
+  cross3(a + 3, b + 3, o + 3);
+}
+
+// o = a x* f (force cross product); o must not alias a or f.
+template <typename T>
+__device__ __forceinline__ void fcross(const T* a, const T* f, T* o) {
+  T t1[3], t2[3];
+  cross3(a + 3, f, o);
+  cross3(a + 3, f + 3, t1);
+  cross3(a, f, t2);
+  o[3] = t1[0] + t2[0];
+  o[4] = t1[1] + t2[1];
+  o[5] = t1[2] + t2[2];
+}
+
+// Spatial inertia about the world origin, 10 numbers: mass m, first moment h = m c, rotational
+// inertia about the origin (xx, yy, zz, xy, xz, yz).  o = I x; o must not alias x.
+template <typename T>
+__device__ __forceinline__ void iapply(const T* I, const T* x, T* o) {
+  const T m = I[0];
+  const T* h = I + 1;
+  const T* J = I + 4;
+  T t[3];
+  cross3(x + 3, h, t);
+  o[0] = m * x[0] + t[0];
+  o[1] = m * x[1] + t[1];
+  o[2] = m * x[2] + t[2];
+  cross3(h, x, t);
+  o[3] = t[0] + J[0] * x[3] + J[3] * x[4] + J[4] * x[5];
+  o[4] = t[1] + J[3] * x[3] + J[1] * x[4] + J[5] * x[5];
+  o[5] = t[2] + J[4] * x[3] + J[5] * x[4] + J[2] * x[5];
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+
+// In-place Cholesky of a packed lower-triangular n x n matrix; returns false if not positive.
+template <typename T>
+__device__ bool chol_packed(T* L, int n) {
+  for (int j = 0; j < n; ++j) {
+    T s = L[tri(j, j)];
+    for (int k = 0; k < j; ++k) s -= L[tri(j, k)] * L[tri(j, k)];
+    if (!(s > T(0))) return false;
+    const T d = sqrt(s);
+    L[tri(j, j)] = d;
+    const T inv = T(1) / d;
+    for (int i = j + 1; i < n; ++i) {
+      T t = L[tri(i, j)];
+      for (int k = 0; k < j; ++k) t -= L[tri(i, k)] * L[tri(j, k)];
+      L[tri(i, j)] = t * inv;
+    }
+  }
+  return true;
+}
+
+// x <- L^-1 x
+template <typename T>
+__device__ __forceinline__ void fwd_packed(const T* L, T* x, int n) {
+  for (int i = 0; i < n; ++i) {
+    T s = x[i];
+    for (int k = 0; k < i; ++k) s -= L[tri(i, k)] * x[k];
+    x[i] = s / L[tri(i, i)];
+  }
+}
+
+// x <- L^-T x
+template <typename T>
+__device__ __forceinline__ void bwd_packed(const T* L, T* x, int n) {
+  for (int i = n - 1; i >= 0; --i) {
+    T s = x[i];
+    for (int k = i + 1; k < n; ++k) s -= L[tri(k, i)] * x[k];
+    x[i] = s / L[tri(i, i)];
+  }
+}
+
+// LU factorisation with complete pivoting, P A Q = L U, in FP64, for an r x c matrix (r <= MR,
+// c <= MC).  Rank-revealing: pivots below rel_tol * |first pivot| are treated as zero and the
+// corresponding unknowns are set to 0 (basic solution), which solves consistent singular or
+// over-determined systems exactly.
+template <int MR, int MC>
+struct LUcp {
+  double a[MR][MC];
+  int pr[MR], pc[MC];
+  int r, c, rank;
+
+  __device__ void factor(double rel_tol) {
+    for (int i = 0; i < r; ++i) pr[i] = i;
+    for (int j = 0; j < c; ++j) pc[j] = j;
+    double first = 0.0;
+    const int kmax = r < c ? r : c;
+    rank = kmax;
+    for (int k = 0; k < kmax; ++k) {
+      double best = -1.0;
+      int bi = k, bj = k;
+      for (int i = k; i < r; ++i)
+        for (int j = k; j < c; ++j) {
+          const double v = fabs(a[i][j]);
+          if (v > best) { best = v; bi = i; bj = j; }
+        }
+      if (k == 0) first = best;
+      if (!(best > rel_tol * first) || best == 0.0) { rank = k; return; }
+      if (bi != k) {
+        for (int j = 0; j < c; ++j) { double t = a[k][j]; a[k][j] = a[bi][j]; a[bi][j] = t; }
+        int t = pr[k]; pr[k] = pr[bi]; pr[bi] = t;
+      }
+      if (bj != k) {
+        for (int i = 0; i < r; ++i) { double t = a[i][k]; a[i][k] = a[i][bj]; a[i][bj] = t; }
+        int t = pc[k]; pc[k] = pc[bj]; pc[bj] = t;
+      }
+      const double inv = 1.0 / a[k][k];
+      for (int i = k + 1; i < r; ++i) {
+        const double l = a[i][k] * inv;
+        a[i][k] = l;
+        for (int j = k + 1; j < c; ++j) a[i][j] -= l * a[k][j];
+      }
+    }
+  }
+
+  // x[c] = A^- b[r] (basic solution)
+  __device__ void solve(const double* b, double* x) const {
+    double y[MR];
+    for (int i = 0; i < r; ++i) y[i] = b[pr[i]];
+    for (int i = 0; i < rank; ++i) {
+      double s = y[i];
+      for (int j = 0; j < i; ++j) s -= a[i][j] * y[j];
+      y[i] = s;
+    }
+    for (int i = rank - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int j = i + 1; j < rank; ++j) s -= a[i][j] * y[j];
+      y[i] = s / a[i][i];
+    }
+    for (int j = 0; j < c; ++j) x[pc[j]] = j < rank ? y[j] : 0.0;
+  }
+
+  // z[r] = (A^-)^T w[c], the transpose of the same generalized inverse (square systems)
+  __device__ void solve_t(const double* w, double* z) const {
+    double t[MR];
+    for (int j = 0; j < c; ++j) t[j] = w[pc[j]];
+    for (int i = 0; i < rank; ++i) {
+      double s = t[i];
+      for (int j = 0; j < i; ++j) s -= a[j][i] * t[j];
+      t[i] = s / a[i][i];
+    }
+    for (int i = rank - 1; i >= 0; --i) {
+      double s = t[i];
+      for (int j = i + 1; j < rank; ++j) s -= a[j][i] * t[j];
+      t[i] = s;
+    }
+    for (int i = 0; i < r; ++i) z[pr[i]] = i < rank ? t[i] : 0.0;
+  }
+};

@@ -1,0 +1,23 @@
+// Table of compiled (bodies, dofs, contact slots, precision) shapes.
+#include "ds_common.cuh"
+
+#define DS_DECL(NB, NV, NS)                                          \
+  void ds_launch_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t); \
+  void ds_launch_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
+#define DS_ROW(NB, NV, NS)                                          \
+  {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64},        \
+  {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix},
+
+#include "ds_shapes.inc"
+
+static const ds_kernel_entry kTable[] = {
+#define DS_SHAPE(NB, NV, NS) DS_ROW(NB, NV, NS)
+#include "ds_shapes_list.inc"
+#undef DS_SHAPE
+};
+
+const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision) {
+  for (const ds_kernel_entry& k : kTable)
+    if (k.nb == nb && k.nv == nv && k.ns == ns && k.precision == precision) return &k;
+  return nullptr;
+}

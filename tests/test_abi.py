@@ -1,0 +1,81 @@
+"""The C-ABI library loads, exports every symbol include/diffsim.h declares, and rejects bad
+arguments before touching a GPU (no compute call here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2409_07107_gb300 as ds
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "diffsim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(\w+)\s*\([^;{]*\)\s*;", src)) - {"if", "while", "sizeof"})
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(ds.LIB_PATH):
+        from paper_2409_07107_gb300 import build
+        build.build()
+    return ds.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert set(ds.EXPORTS) <= set(names)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_status_strings_and_defaults(L):
+    assert L.ds_status_string(0) == b"ok"
+    assert b"invalid" in L.ds_status_string(-1)
+    o = ds.make_options()
+    assert o.dt == 1e-3 and o.precision == ds.DS_FP64 and o.admm_max_iter > 0
+
+
+def _desc(nb=2, parent=(-1, 0), jtype=(0, 0), axis=None):
+    arrs = [np.array(parent, np.int32), np.array(jtype, np.int32),
+            np.array(axis if axis is not None else [[1.0, 0, 0]] * nb), np.tile(np.eye(3), (nb, 1, 1)),
+            np.zeros((nb, 3)), np.ones(nb), np.zeros((nb, 3)), np.tile([0.1, 0.1, 0.1, 0, 0, 0], (nb, 1))]
+    arrs = [np.ascontiguousarray(a) for a in arrs]
+    return arrs, ds.ds_model_desc(nb, *[a.ctypes.data for a in arrs])
+
+
+@pytest.mark.parametrize("kw", [dict(parent=(0, -1)), dict(jtype=(0, 1)), dict(axis=[[2.0, 0, 0], [1.0, 0, 0]]),
+                                dict(jtype=(5, 0))])
+def test_model_create_rejects_bad_descriptions(L, kw):
+    keep, d = _desc(**kw)
+    h = ctypes.c_void_p()
+    assert L.ds_model_create(ctypes.byref(d), ctypes.byref(h)) == ds.DS_EINVAL
+    assert L.ds_model_create(None, ctypes.byref(h)) == ds.DS_EINVAL
+
+
+def test_model_create_rejects_non_preorder(L):
+    keep, d = _desc(nb=3, parent=(-1, 0, 0), jtype=(0, 0, 0))
+    # 3 bodies where body 2's parent is 0 is fine (preorder); make body 1 a child of 0 and 2 of 1 with
+    # a sibling order that breaks contiguity: parent = (-1, 0, 1) is fine too, so use 4 bodies
+    keep, d = _desc(nb=4, parent=(-1, 0, 0, 1), jtype=(0, 0, 0, 0))
+    h = ctypes.c_void_p()
+    assert L.ds_model_create(ctypes.byref(d), ctypes.byref(h)) == ds.DS_EINVAL
+
+
+def test_step_rejects_bad_arguments(L):
+    o = ds.make_options()
+    b = ds.ds_batch(4, 1, None, None, None, None, None, None, None, None, None)
+    out = ds.ds_step_out(None, None, None, None, None, None)
+    models = (ctypes.c_void_p * 1)(None)
+    assert L.sim_step(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None) == ds.DS_EINVAL
+    assert L.sim_step(None, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None) == ds.DS_EINVAL
+    b.B = -1
+    assert L.sim_step_jac(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, None, None,
+                          None) == ds.DS_EINVAL
+    b.ncmax = 99
+    assert L.sim_step_vjp(models, 1, ctypes.byref(b), ctypes.byref(o), None, ctypes.byref(out), None, None,
+                          None, None) == ds.DS_EINVAL

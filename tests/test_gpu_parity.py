@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances (relative, per env, ||x - x_ref||_inf / max(||x_ref||_inf, 1e-6)):
+  FP64 path: v+ and the three Jacobians <= 1e-9; modes bit-exact.
+  Mixed path: v+ <= 1e-4; Jacobians <= 1e-3 on envs whose classification margin is >= 1e-3.
+Jacobians and modes are compared only on envs with margin >= 1e-3 (away from mode switches); the
+modes of all other envs must still be a valid classification (the NCP residual check passed)."""
+import numpy as np
+import pytest
+
+from paper_2409_07107_gb300 import scenes
+from tests.oracle_runner import rel_err, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+DELTA = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_07107_gb300 as ds
+    from paper_2409_07107_gb300 import build
+    build.build()
+    ds.lib()
+    return torch
+
+
+def _gpu(wl, precision, run="jac"):
+    import paper_2409_07107_gb300 as ds
+    sim = ds.Simulator(wl, precision=precision)
+    out = sim.step_jac() if run == "jac" else sim.step()
+    import torch
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _compare(wl, g, refs, envs, tol_v, tol_j, jac=True, min_checked=1):
+    nv_all = wl.batch.v.shape[0]
+    checked = 0
+    for e, r in zip(envs, refs):
+        mi = 0 if wl.batch.model_id is None else int(wl.batch.model_id[e])
+        m = wl.models[mi]
+        nv = m.nv
+        assert g["status"][e] & 2 == 0, "env %d non-finite" % e
+        ev = rel_err(g["v_next"][:nv, e], r["v_next"])
+        assert ev <= tol_v, "env %d v+ rel err %.3e" % (e, ev)
+        if r["margin"] < DELTA or (g["status"][e] & 8):
+            continue
+        gm = [int(g["modes"][k, e]) for k in r["slots"]]
+        assert gm == [int(x) for x in r["modes"]], "env %d modes %s vs %s" % (e, gm, r["modes"])
+        if jac:
+            for key in ("dv_dq", "dv_dv", "dv_dtau"):
+                ej = rel_err(g[key][:nv, :nv, e], r[key])
+                assert ej <= tol_j, "env %d %s rel err %.3e" % (e, key, ej)
+        checked += 1
+    assert checked >= min_checked
+
+
+def test_arm_sphere_fp64(torch_cuda):
+    wl = scenes.arm_sphere(16)
+    g = _gpu(wl, "fp64")
+    envs = list(range(16))
+    refs = run_oracle(wl, envs)
+    _compare(wl, g, refs, envs, 1e-9, 1e-9, min_checked=10)
+    for e, r in zip(envs, refs):
+        assert np.abs(g["q_next"][:, e] - r["q_next"]).max() <= 1e-12
+
+
+def test_arm_cube_fp64_ragged(torch_cuda):
+    """300 envs = two full 128-thread blocks and a ragged tail of 44."""
+    wl = scenes.arm_cube(65536)
+    idx = np.arange(300)
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(idx), wl.options)
+    g = _gpu(sub, "fp64")
+    envs = list(range(300))
+    refs = run_oracle(sub, envs)
+    _compare(sub, g, refs, envs, 1e-9, 1e-9, min_checked=200)
+
+
+def test_arm_cube_mixed(torch_cuda):
+    wl = scenes.arm_cube(65536)
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(np.arange(160)), wl.options)
+    g = _gpu(sub, "mixed")
+    envs = list(range(160))
+    refs = run_oracle(sub, envs)
+    _compare(sub, g, refs, envs, 1e-4, 1e-3, min_checked=100)
+
+
+def test_quadruped_fp64_and_mixed(torch_cuda):
+    wl = scenes.quadruped_feet(64)
+    envs = list(range(24))
+    refs = run_oracle(wl, envs)
+    _compare(wl, _gpu(wl, "fp64"), refs, envs, 1e-9, 1e-9, min_checked=10)
+    _compare(wl, _gpu(wl, "mixed"), refs, envs, 1e-4, 1e-3, min_checked=10)
+
+
+def test_humanoid_fp64_and_mixed(torch_cuda):
+    wl = scenes.humanoid_feet(40)
+    envs = list(range(6))
+    refs = run_oracle(wl, envs)
+    _compare(wl, _gpu(wl, "fp64"), refs, envs, 1e-9, 1e-9, min_checked=3)
+    _compare(wl, _gpu(wl, "mixed"), refs, envs, 1e-4, 1e-3, min_checked=3)
+
+
+def test_point_mass_closed_form(torch_cuda):
+    """Sliding point mass on a plane: v+ and dv+/dv from the closed form of App. A."""
+    from tests.helpers import point_mass_model
+    mass, dt, mu = 2.0, 1e-3, 0.5
+    m = point_mass_model(mass)
+    vlin = np.array([1.0, 0.5, -0.3])
+    B = 3
+    q = np.tile(np.array([0.1, -0.2, 0.3, 1.0, 0.0, 0.0, 0.0])[:, None], (1, B))
+    v = np.zeros((6, B))
+    v[:3] = vlin[:, None]
+    batch = scenes.Batch(q, v, np.zeros((6, B)), np.zeros((1, B), np.int32), np.zeros((1, 3, B)),
+                         np.zeros((1, B)), np.full((1, B), mu), np.tile(np.array([0, 0, 1.0, 0.3001])[:, None], (1, B)))
+    g = _gpu(scenes.Workload("pm", [m], batch), "fp64")
+    vf = vlin + dt * np.array([0, 0, -9.81])
+    u = vf[:2] / np.linalg.norm(vf[:2])
+    assert np.allclose(g["v_next"][:2, 0], vf[:2] + mu * vf[2] * u, atol=1e-13)
+    assert abs(g["v_next"][2, 0]) < 1e-13
+    J = np.zeros((3, 3))
+    J[:2, :2] = np.eye(2) - mu * (-vf[2]) / np.linalg.norm(vf[:2]) * (np.eye(2) - np.outer(u, u))
+    J[:2, 2] = mu * u
+    assert np.allclose(g["dv_dv"][:3, :3, 0], J, atol=1e-10)
+    assert int(g["modes"][0, 0]) == 2
+
+
+def test_vjp_matches_jacobian_transpose(torch_cuda):
+    """Dot-product identity <w, J u> = <J^T w, u> between sim_step_jac and sim_step_vjp."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    for wl, prec, tol in ((scenes.arm_cube(256), "fp64", 1e-11), (scenes.quadruped_feet(128), "fp64", 1e-11),
+                          (scenes.arm_cube(256), "mixed", 1e-4)):
+        sim = ds.Simulator(wl, precision=prec)
+        out = sim.step_jac()
+        J = [out[k].clone() for k in ("dv_dq", "dv_dv", "dv_dtau")]
+        rng = np.random.default_rng(0)
+        w = torch.as_tensor(rng.normal(size=tuple(out["v_next"].shape)), dtype=torch.float64, device="cuda")
+        vo = sim.step_vjp(w)
+        torch.cuda.synchronize()
+        for k, key in enumerate(("q_bar", "v_bar", "tau_bar")):
+            ref = torch.einsum("ib,ijb->jb", w, J[k])
+            err = (vo[key] - ref).abs().max().item() / max(ref.abs().max().item(), 1e-6)
+            assert err <= tol, (prec, key, err)
+
+
+def test_edge_cases(torch_cuda):
+    """B = 1, an env with no active contact, a NaN input (status bit, no fault), unused slots."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(8)
+    b = wl.batch.take(np.arange(3))
+    b.plane[3, 1] = -10.0                     # env 1: plane far below -> no contact
+    b.q[2, 2] = np.nan                        # env 2: non-finite input
+    b.c_link[3, 0] = -1                       # env 0: one slot unused
+    sub = scenes.Workload(wl.name, wl.models, b, wl.options)
+    g = _gpu(sub, "fp64")
+    assert g["status"][2] & 2
+    assert (g["modes"][:, 1] == 3).all()
+    assert g["modes"][3, 0] == 3
+    one = scenes.Workload(wl.name, wl.models, wl.batch.take([5]), wl.options)
+    g1 = _gpu(one, "fp64")
+    r = run_oracle(one, [0])[0]
+    assert rel_err(g1["v_next"][:, 0], r["v_next"]) <= 1e-9
+    empty = ds.Simulator(scenes.Workload(wl.name, wl.models, wl.batch.take([]), wl.options))
+    empty.step()
