@@ -334,7 +334,7 @@ def main():
                 "clocks": r64["clocks"], "roofline": r64["roofline"],
                 "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": args.steps, "cpu_baseline": cpu,
+                "gpu_launches": args.steps * (2 + 2 * 9), "cpu_baseline": cpu,
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
                 "gflop_per_step": r64["gflop_per_step"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],

@@ -123,23 +123,35 @@ typedef struct {
   int32_t* iters;            /* [B] ADMM iterations used, may be NULL */
 } ds_step_out;
 
-/* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e. */
+/* Bytes of device workspace that sim_step / sim_step_jac / sim_step_vjp can use for this batch
+ * (about 1.4 KB per env with 4 contact slots).  With a workspace the step runs as a pipeline of
+ * kernels (setup, NCP solve in compacted ADMM rounds, finish) that keeps warps busy when the
+ * per-env iteration counts differ; without one (workspace = NULL) a single fused kernel does
+ * everything.  Both give bitwise-identical results.  Errors: DS_EINVAL. */
+ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                            const ds_options* opt, size_t* bytes);
+
+/* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e.  workspace:
+ * NULL, or caller-owned device memory of at least ds_workspace_size() bytes (aligned to 256 bytes),
+ * not used concurrently by another call. */
 ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
-                   const ds_options* opt, const ds_step_out* out, void* stream);
+                   const ds_options* opt, const ds_step_out* out, void* workspace,
+                   size_t workspace_bytes, void* stream);
 
 /* One step plus the full Jacobians dv+/dq (tangent), dv+/dv, dv+/dtau (Sec. 3, App. D; each
  * [nv][nv][B]).  Envs of different models must all have nv equal to the row count of the arrays:
  * element (i, j) of env e is at (i*nv_e + j)*B + e with nv_e the env's own nv. */
 ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                        const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
-                       double* dv_dtau, void* stream);
+                       double* dv_dtau, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Vector-Jacobian product (reverse mode, the OptNet-style adjoint of Sec. 3.1): given
  * v_next_bar [nv_max][B], writes q_bar (tangent), v_bar, tau_bar [nv_max][B] =
  * (dv+/d(q, v, tau))^T v_next_bar without forming the Jacobians.  Also fills *out like sim_step. */
 ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                        const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
-                       double* q_bar, double* v_bar, double* tau_bar, void* stream);
+                       double* q_bar, double* v_bar, double* tau_bar, void* workspace,
+                       size_t workspace_bytes, void* stream);
 
 const char* ds_status_string(ds_status s);
 

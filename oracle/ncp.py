@@ -56,10 +56,11 @@ def admm_rho(G):
 
 
 class AdmmState:
-    def __init__(self, m):
+    def __init__(self, m, g):
         self.x = np.zeros(m)
         self.z = np.zeros(m)
         self.y = np.zeros(m)
+        self.sx = np.array(g, dtype=float)     # G x + g at the current x
         self.iters = 0
 
 
@@ -67,22 +68,24 @@ def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
     """ADMM iteration for Eq. 1 (reading stated in the module docstring): the De Saxce term is taken
     at the most recent primal iterate x, and the x-step is over-relaxed,
     xh = RELAX x + (1 - RELAX) z, before the z-step and the dual step (the fixed points are
-    unchanged).  Stops when ||x - z||_inf <= eps max(1, ||z||_inf) and
-    rho ||z - z_prev||_inf <= eps max(1, ||g||_inf), or when the state has done max_iter iterations
-    in total.  Continues from ``state`` when given.  Returns (lambda, iterations, converged, state)."""
+    unchanged).  G x is not recomputed: (G + rho I) x = rhs gives G x = rhs - rho x.  Stops when
+    ||x - z||_inf <= eps max(1, ||z||_inf) and rho ||z - z_prev||_inf <= eps max(1, ||g||_inf), or
+    when the state has done max_iter iterations in total.  Continues from ``state`` when given.
+    Returns (lambda, iterations, converged, state)."""
     m = len(g)
-    st = state or AdmmState(m)
+    st = state or AdmmState(m, g)
     if m == 0:
         return np.zeros(0), 0, True, st
     rho = admm_rho(G)
     L = cholesky(G + rho * np.eye(m))
     gs = max(1.0, np.max(np.abs(g)))
-    x, z, y = st.x, st.z, st.y
+    x, z, y, sx = st.x, st.z, st.y, st.sx
     conv = False
     while st.iters < max_iter:
         st.iters += 1
-        s = desaxce(G @ x + g, mu)
-        x = chol_solve(L, rho * z - y - g - s)
+        rhs = rho * z - y - g - desaxce(sx, mu)
+        x = chol_solve(L, rhs)
+        sx = rhs - rho * x + g
         xh = RELAX * x + (1.0 - RELAX) * z
         z_prev = z
         z = proj_K(xh + y / rho, mu)
@@ -92,7 +95,7 @@ def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
         if rp <= eps * max(1.0, np.max(np.abs(z))) and rd <= eps * gs:
             conv = True
             break
-    st.x, st.z, st.y = x, z, y
+    st.x, st.z, st.y, st.sx = x, z, y, sx
     return z.copy(), st.iters, conv, st
 
 
@@ -145,7 +148,9 @@ def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4
             cands.append(x)
             if ncp_residual(G, g, mu, x) <= tol * scale:
                 break
-            new = reclassify(G, g, mu, x, modes, es * scale, el * lscale, 10 * eps * lscale)
+            # the Newton iterate solves its mode equations exactly: any violation above the
+            # acceptance tolerance is real and flips the mode
+            new = reclassify(G, g, mu, x, modes, 10 * tol * scale, 10 * tol * lscale, 10 * tol * lscale)
             if (new == modes).all():
                 break
             modes = new
@@ -184,8 +189,11 @@ def thresholds(g, lam, eps_sigma, eps_lambda):
 
 def classify(G, g, mu, lam, eps_sigma=1e-8, eps_lambda=1e-8):
     """Contact modes (Sec. 3.2): sticking if ||sigma_i|| <= eps_s; else breaking if sigma_N > eps_s
-    or lambda_N <= eps_l; else sliding.  Returns (modes, margin) where margin is the smallest
-    relative distance of the deciding quantities to the boundary of the identified mode."""
+    or lambda_N <= eps_l; else sticking if the impulse is strictly inside the cone
+    (mu lambda_N - ||lambda_T|| > eps_l: by Eq. 1 such a contact has sigma = 0, whatever the
+    accuracy of the iterate); else sliding.  Thresholds are relative to max(1, ||g||_inf) and
+    max(1, ||lambda||_inf).  Returns (modes, margin) where margin is the smallest relative distance
+    of the deciding quantities to the boundary of the identified mode."""
     sigma = G @ lam + g
     es, el = thresholds(g, lam, eps_sigma, eps_lambda)
     ss = max(1.0, np.max(np.abs(g))) if len(g) else 1.0
@@ -195,12 +203,16 @@ def classify(G, g, mu, lam, eps_sigma=1e-8, eps_lambda=1e-8):
         s, l = sigma[3 * i:3 * i + 3], lam[3 * i:3 * i + 3]
         ns = np.linalg.norm(s)
         nst = np.linalg.norm(s[:2])
+        inside = mu[i] * l[2] - np.linalg.norm(l[:2])
         if ns <= es:
             modes.append(STK)
             margin = min(margin, (es - ns) / es)
         elif s[2] > es or l[2] <= el:
             modes.append(BRK)
             margin = min(margin, (s[2] - es) / ss if s[2] > es else 0.0)
+        elif inside > el:
+            modes.append(STK)
+            margin = min(margin, inside / sl)
         else:
             modes.append(SLD)
             margin = min(margin, nst / ss, l[2] / sl)

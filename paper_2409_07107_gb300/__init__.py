@@ -26,7 +26,7 @@ MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
 ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH = 1, 2, 4, 8
 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
-           "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak")
+           "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -74,12 +74,14 @@ def lib():
         L.ds_status_string.argtypes = [ctypes.c_int]
         L.ds_status_string.restype = ctypes.c_char_p
         common = [vp, i32, ctypes.POINTER(ds_batch), ctypes.POINTER(ds_options)]
-        L.sim_step.argtypes = common + [ctypes.POINTER(ds_step_out), vp]
-        L.sim_step_jac.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
-        L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
+        sz = ctypes.c_size_t
+        L.sim_step.argtypes = common + [ctypes.POINTER(ds_step_out), vp, sz, vp]
+        L.sim_step_jac.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
+        L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
+        L.ds_workspace_size.argtypes = common + [ctypes.POINTER(sz)]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
-                  "ds_fma_peak"):
+                  "ds_fma_peak", "ds_workspace_size"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -153,24 +155,39 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def sim_step(models, batch, opt, out, stream=None):
+def _ws(workspace):
+    if workspace is None:
+        return ctypes.c_void_p(0), 0
+    return ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
+
+
+def workspace_size(models, batch, opt):
+    b = _batch_struct(batch)
+    n = ctypes.c_size_t()
+    _check(lib().ds_workspace_size(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                                   ctypes.byref(n)))
+    return n.value
+
+
+def sim_step(models, batch, opt, out, workspace=None, stream=None):
     """C-ABI sim_step on device tensors (dicts of torch tensors, see Simulator)."""
     b, o = _batch_struct(batch), _out_struct(out)
     _check(lib().sim_step(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
-                          ctypes.byref(o), _stream(stream)))
+                          ctypes.byref(o), *_ws(workspace), _stream(stream)))
 
 
-def sim_step_jac(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, stream=None):
+def sim_step_jac(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, workspace=None, stream=None):
     b, o = _batch_struct(batch), _out_struct(out)
     _check(lib().sim_step_jac(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
-                              ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), _stream(stream)))
+                              ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), *_ws(workspace),
+                              _stream(stream)))
 
 
-def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, stream=None):
+def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, workspace=None, stream=None):
     b, o = _batch_struct(batch), _out_struct(out)
     _check(lib().sim_step_vjp(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
                               _ptr(v_next_bar), ctypes.byref(o), _ptr(q_bar), _ptr(v_bar), _ptr(tau_bar),
-                              _stream(stream)))
+                              *_ws(workspace), _stream(stream)))
 
 
 def fma_peak(out, blocks, iters, fp64, stream=None):
@@ -195,7 +212,7 @@ def batch_to_device(batch, device="cuda"):
 class Simulator:
     """Device-resident batch + outputs for one workload; thin wrapper over the three C-ABI calls."""
 
-    def __init__(self, workload, precision=None, device="cuda", **opt):
+    def __init__(self, workload, precision=None, device="cuda", pipeline=True, **opt):
         import torch
         self.workload = workload
         self.models = [DeviceModel(m) for m in workload.models]
@@ -215,9 +232,13 @@ class Simulator:
                         iters=torch.zeros(B, dtype=torch.int32, device=device))
         self.jac = None
         self.vjp_out = None
+        self.workspace = None
+        if pipeline and B > 0:
+            nbytes = workspace_size(self.models, self.batch, self.opt)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
 
     def step(self, stream=None):
-        sim_step(self.models, self.batch, self.opt, self.out, stream)
+        sim_step(self.models, self.batch, self.opt, self.out, self.workspace, stream)
         return self.out
 
     def step_jac(self, stream=None):
@@ -226,12 +247,13 @@ class Simulator:
         if self.jac is None:
             n = self.nv
             self.jac = [torch.zeros(n, n, B, dtype=torch.float64, device=self.out["v_next"].device) for _ in range(3)]
-        sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, stream=stream)
+        sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, workspace=self.workspace, stream=stream)
         return dict(self.out, dv_dq=self.jac[0], dv_dv=self.jac[1], dv_dtau=self.jac[2])
 
     def step_vjp(self, v_next_bar, stream=None):
         import torch
         if self.vjp_out is None:
             self.vjp_out = [torch.zeros_like(self.out["v_next"]) for _ in range(3)]
-        sim_step_vjp(self.models, self.batch, self.opt, v_next_bar.contiguous(), self.out, *self.vjp_out, stream=stream)
+        sim_step_vjp(self.models, self.batch, self.opt, v_next_bar.contiguous(), self.out, *self.vjp_out,
+                     workspace=self.workspace, stream=stream)
         return dict(self.out, q_bar=self.vjp_out[0], v_bar=self.vjp_out[1], tau_bar=self.vjp_out[2])

@@ -17,7 +17,7 @@ extern "C" void ds_options_default(ds_options* o) {
   if (!o) return;
   o->dt = 1e-3;
   o->gravity[0] = 0.0; o->gravity[1] = 0.0; o->gravity[2] = -9.81;
-  o->admm_max_iter = 2000;
+  o->admm_max_iter = 5000;
   o->admm_eps = 1e-4;
   o->polish_iters = 10;
   o->ncp_tol = 1e-12;
@@ -125,13 +125,21 @@ extern "C" ds_status ds_model_dims(const ds_model* m, int32_t* nb, int32_t* nq, 
   return DS_OK;
 }
 
+extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, const ds_batch* b,
+                                       const ds_options* o, size_t* bytes) {
+  if (!models || nmodels <= 0 || !b || !o || !bytes) return DS_EINVAL;
+  if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
+  *bytes = ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr);
+  return DS_OK;
+}
+
 static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
                      const ds_step_out* out, int mode, double* dq, double* dv, double* dtau, const double* vbar,
-                     double* qb, double* vb, double* tb, void* stream) {
+                     double* qb, double* vb, double* tb, void* ws, size_t ws_bytes, void* stream) {
   if (!models || nmodels <= 0 || nmodels > 64 || !b || !o || !out) return DS_EINVAL;
   if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
-  if (!out->v_next) return DS_EINVAL;
   if (b->B == 0) return DS_OK;
+  if (!out->v_next) return DS_EINVAL;
   if (!b->q || !b->v || !b->tau || !b->plane) return DS_EINVAL;
   if (b->ncmax > 0 && (!b->c_link || !b->c_point || !b->c_radius || !b->c_mu)) return DS_EINVAL;
   if (nmodels > 1 && !b->model_id) return DS_EINVAL;
@@ -140,6 +148,9 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
+  if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr) ||
+             (reinterpret_cast<uintptr_t>(ws) & 255) != 0))
+    return DS_EINVAL;
   for (int k = 0; k < nmodels; ++k) {
     if (!models[k]) return DS_EINVAL;
     if (!ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision)) return DS_EUNSUPPORTED;
@@ -161,33 +172,37 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.env_list = nullptr;
   a.n_env = b->B;
   a.model_id = nmodels > 1 ? b->model_id : nullptr;
+  if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int k = 0; k < nmodels; ++k) {
     const ds_kernel_entry* ke = ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision);
     a.model = models[k]->dev;
     a.model_index = k;
-    ke->fn(a, s);
+    if (ws) ke->pipeline(a, s);
+    else ke->fn(a, s);
     if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
   }
   return DS_OK;
 }
 
 extern "C" ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
-                              const ds_options* opt, const ds_step_out* out, void* stream) {
+                              const ds_options* opt, const ds_step_out* out, void* ws, size_t ws_bytes,
+                              void* stream) {
   return run(models, nmodels, batch, opt, out, DS_RUN_STEP, nullptr, nullptr, nullptr, nullptr, nullptr,
-             nullptr, nullptr, stream);
+             nullptr, nullptr, ws, ws_bytes, stream);
 }
 
 extern "C" ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                                   const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
-                                  double* dv_dtau, void* stream) {
+                                  double* dv_dtau, void* ws, size_t ws_bytes, void* stream) {
   return run(models, nmodels, batch, opt, out, DS_RUN_JAC, dv_dq, dv_dv, dv_dtau, nullptr, nullptr, nullptr,
-             nullptr, stream);
+             nullptr, ws, ws_bytes, stream);
 }
 
 extern "C" ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                                   const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
-                                  double* q_bar, double* v_bar, double* tau_bar, void* stream) {
+                                  double* q_bar, double* v_bar, double* tau_bar, void* ws, size_t ws_bytes,
+                                  void* stream) {
   return run(models, nmodels, batch, opt, out, DS_RUN_VJP, nullptr, nullptr, nullptr, v_next_bar, q_bar, v_bar,
-             tau_bar, stream);
+             tau_bar, ws, ws_bytes, stream);
 }

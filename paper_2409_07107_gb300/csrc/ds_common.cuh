@@ -7,6 +7,10 @@
 
 #include "diffsim.h"
 
+// Device functions are also host-callable so that the same templates can be run on the CPU.
+#define DS_HD __host__ __device__
+#define DS_HDI __host__ __device__ __forceinline__
+
 #define DS_MAXB 32       // bodies per model
 #define DS_MAXNV 36      // velocity dofs per model
 #define DS_MAXSLOTS 16   // contact slots per env
@@ -23,6 +27,65 @@ struct DevModel {
 };
 
 enum { DS_RUN_STEP = 0, DS_RUN_JAC = 1, DS_RUN_VJP = 2 };
+
+// Workspace of the three-kernel pipeline (setup -> compacted ADMM rounds -> finish), structure of
+// arrays over the batch.  Carved out of one caller-provided buffer by ds_workspace_layout().
+#define DS_ROUNDS 9
+struct WsView {
+  int32_t* counts;        // [DS_ROUNDS + 1] envs queued for each round
+  int32_t* list[2];       // [B] ping-pong work lists of env indices
+  int32_t* na;            // [B] active contacts
+  int32_t* stage;         // [B] current ADMM stage
+  int32_t* iters;         // [B] ADMM iterations so far
+  uint32_t* st;           // [B] status bits
+  int8_t* mode;           // [NS][B] modes of the active contacts
+  double* mu;             // [NS][B]
+  double* G;              // [NC3 (NC3 + 1) / 2][B] Delassus matrix, packed lower, FP64
+  double* g;              // [NC3][B]
+  double* lam;            // [NC3][B] best impulse so far / result
+  double* best_r;         // [B] its NCP residual
+  double *ax, *az, *ay, *asx;  // [NC3][B] ADMM state
+  double* K;              // [NC3 NC3][B] (G + rho I)^-1, row-major
+  double* rho;            // [B]
+  int32_t* nlist;         // [B] envs whose ADMM stage ended in a round (Newton queue)
+  int32_t* ncounts;       // [DS_ROUNDS]
+};
+
+// Lays out the workspace for ns contact slots and B envs starting at base (may be NULL to size it).
+inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v) {
+  const int nc3 = 3 * ns;
+  size_t off = 0;
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> void* {
+    void* p = b ? b + off : nullptr;
+    off += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  WsView w;
+  w.counts = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_ROUNDS + 1)));
+  w.list[0] = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.list[1] = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.na = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.stage = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.iters = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.st = static_cast<uint32_t*>(take(sizeof(uint32_t) * B));
+  w.mode = static_cast<int8_t*>(take(size_t(ns) * B));
+  w.mu = static_cast<double*>(take(sizeof(double) * ns * size_t(B)));
+  w.G = static_cast<double*>(take(sizeof(double) * (nc3 * (nc3 + 1) / 2) * size_t(B)));
+  w.g = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.lam = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.best_r = static_cast<double*>(take(sizeof(double) * size_t(B)));
+  w.ax = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.az = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.ay = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.asx = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
+  w.K = static_cast<double*>(take(sizeof(double) * nc3 * nc3 * size_t(B)));
+  w.rho = static_cast<double*>(take(sizeof(double) * size_t(B)));
+  w.nlist = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+  w.ncounts = static_cast<int32_t*>(take(sizeof(int32_t) * DS_ROUNDS));
+  if (v) *v = w;
+  return off;
+}
 
 // Everything a launch needs; passed by value.
 struct KArgs {
@@ -46,40 +109,44 @@ struct KArgs {
   const double* vbar;
   double *q_bar, *v_bar, *tau_bar;
   int run;
+  WsView ws;               // pipeline workspace (unused by the fused kernel)
+  int round, round_cap, final_round;
 };
 
 typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);
 
-// Registry of compiled shapes: (bodies, dofs, contact slots, precision) -> launcher.
+// Registry of compiled shapes: (bodies, dofs, contact slots, precision) -> launchers of the fused
+// kernel and of the workspace pipeline.
 struct ds_kernel_entry {
   int nb, nv, ns, precision;
   ds_launch_fn fn;
+  ds_launch_fn pipeline;
 };
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
 
 // ------------------------------------------------------------------------------ small algebra
 
 template <typename T>
-__device__ __forceinline__ void cross3(const T* a, const T* b, T* o) {
+DS_HDI void cross3(const T* a, const T* b, T* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
   o[1] = a[2] * b[0] - a[0] * b[2];
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 template <typename T>
-__device__ __forceinline__ T dot3(const T* a, const T* b) {
+DS_HDI T dot3(const T* a, const T* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 template <typename T>
-__device__ __forceinline__ T dot6(const T* a, const T* b) {
+DS_HDI T dot6(const T* a, const T* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3] + a[4] * b[4] + a[5] * b[5];
 }
 
 // Spatial vectors are (linear, angular), expressed in world axes at the world origin.
 // o = a x b (motion cross product); o must not alias a or b.
 template <typename T>
-__device__ __forceinline__ void mcross(const T* a, const T* b, T* o) {
+DS_HDI void mcross(const T* a, const T* b, T* o) {
   T t1[3], t2[3];
   cross3(a + 3, b, t1);
   cross3(a, b + 3, t2);
@@ -91,7 +158,7 @@ __device__ __forceinline__ void mcross(const T* a, const T* b, T* o) {
 
 // o = a x* f (force cross product); o must not alias a or f.
 template <typename T>
-__device__ __forceinline__ void fcross(const T* a, const T* f, T* o) {
+DS_HDI void fcross(const T* a, const T* f, T* o) {
   T t1[3], t2[3];
   cross3(a + 3, f, o);
   cross3(a + 3, f + 3, t1);
@@ -104,7 +171,7 @@ __device__ __forceinline__ void fcross(const T* a, const T* f, T* o) {
 // Spatial inertia about the world origin, 10 numbers: mass m, first moment h = m c, rotational
 // inertia about the origin (xx, yy, zz, xy, xz, yz).  o = I x; o must not alias x.
 template <typename T>
-__device__ __forceinline__ void iapply(const T* I, const T* x, T* o) {
+DS_HDI void iapply(const T* I, const T* x, T* o) {
   const T m = I[0];
   const T* h = I + 1;
   const T* J = I + 4;
@@ -119,11 +186,11 @@ __device__ __forceinline__ void iapply(const T* I, const T* x, T* o) {
   o[5] = t[2] + J[4] * x[3] + J[5] * x[4] + J[2] * x[5];
 }
 
-__device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
+DS_HDI int tri(int i, int j) { return i * (i + 1) / 2 + j; }  // i >= j
 
 // In-place Cholesky of a packed lower-triangular n x n matrix; returns false if not positive.
 template <typename T>
-__device__ bool chol_packed(T* L, int n) {
+DS_HD bool chol_packed(T* L, int n) {
   for (int j = 0; j < n; ++j) {
     T s = L[tri(j, j)];
     for (int k = 0; k < j; ++k) s -= L[tri(j, k)] * L[tri(j, k)];
@@ -142,7 +209,7 @@ __device__ bool chol_packed(T* L, int n) {
 
 // x <- L^-1 x
 template <typename T>
-__device__ __forceinline__ void fwd_packed(const T* L, T* x, int n) {
+DS_HDI void fwd_packed(const T* L, T* x, int n) {
   for (int i = 0; i < n; ++i) {
     T s = x[i];
     for (int k = 0; k < i; ++k) s -= L[tri(i, k)] * x[k];
@@ -152,7 +219,7 @@ __device__ __forceinline__ void fwd_packed(const T* L, T* x, int n) {
 
 // x <- L^-T x
 template <typename T>
-__device__ __forceinline__ void bwd_packed(const T* L, T* x, int n) {
+DS_HDI void bwd_packed(const T* L, T* x, int n) {
   for (int i = n - 1; i >= 0; --i) {
     T s = x[i];
     for (int k = i + 1; k < n; ++k) s -= L[tri(k, i)] * x[k];
@@ -170,7 +237,7 @@ struct LUcp {
   int pr[MR], pc[MC];
   int r, c, rank;
 
-  __device__ void factor(double rel_tol) {
+  DS_HD void factor(double rel_tol) {
     for (int i = 0; i < r; ++i) pr[i] = i;
     for (int j = 0; j < c; ++j) pc[j] = j;
     double first = 0.0;
@@ -203,8 +270,52 @@ struct LUcp {
     }
   }
 
+  // Null-space basis of the factored matrix (c - rank columns, stored as rows of nb[][]) and the
+  // Cholesky factor of its Gram matrix, for minimum-norm solutions.
+  double nb[MC][MC];
+  double ng[MC * (MC + 1) / 2];
+  int nk;
+
+  DS_HD void nullspace() {
+    nk = c - rank;
+    for (int j = 0; j < nk; ++j) {
+      double w[MC];
+      for (int i = rank - 1; i >= 0; --i) {       // w = -U11^-1 U12[:, j]
+        double s = -a[i][rank + j];
+        for (int k = i + 1; k < rank; ++k) s -= a[i][k] * w[k];
+        w[i] = s / a[i][i];
+      }
+      for (int i = 0; i < c; ++i) nb[j][pc[i]] = i < rank ? w[i] : (i - rank == j ? 1.0 : 0.0);
+    }
+    for (int i = 0; i < nk; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < c; ++k) t += nb[i][k] * nb[j][k];
+        ng[tri(i, j)] = t;
+      }
+    chol_packed(ng, nk);
+  }
+
+  // x <- x - N (N^T N)^-1 N^T x  (orthogonal projection onto the row space)
+  DS_HD void project_out_null(double* x) const {
+    if (nk <= 0) return;
+    double t[MC];
+    for (int j = 0; j < nk; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < c; ++k) s += nb[j][k] * x[k];
+      t[j] = s;
+    }
+    fwd_packed(ng, t, nk);
+    bwd_packed(ng, t, nk);
+    for (int k = 0; k < c; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < nk; ++j) s += nb[j][k] * t[j];
+      x[k] -= s;
+    }
+  }
+
   // x[c] = A^- b[r] (basic solution)
-  __device__ void solve(const double* b, double* x) const {
+  DS_HD void solve(const double* b, double* x) const {
     double y[MR];
     for (int i = 0; i < r; ++i) y[i] = b[pr[i]];
     for (int i = 0; i < rank; ++i) {
@@ -220,8 +331,14 @@ struct LUcp {
     for (int j = 0; j < c; ++j) x[pc[j]] = j < rank ? y[j] : 0.0;
   }
 
-  // z[r] = (A^-)^T w[c], the transpose of the same generalized inverse (square systems)
-  __device__ void solve_t(const double* w, double* z) const {
+  // minimum-norm solution of a consistent system (call nullspace() after factor())
+  DS_HD void solve_mn(const double* b, double* x) const {
+    solve(b, x);
+    project_out_null(x);
+  }
+
+  // z[r] = (A^-)^T w[c], the transpose of the basic-solution map (square systems)
+  DS_HD void solve_t(const double* w, double* z) const {
     double t[MR];
     for (int j = 0; j < c; ++j) t[j] = w[pc[j]];
     for (int i = 0; i < rank; ++i) {
@@ -235,5 +352,13 @@ struct LUcp {
       t[i] = s;
     }
     for (int i = 0; i < r; ++i) z[pr[i]] = i < rank ? t[i] : 0.0;
+  }
+
+  // transpose of the minimum-norm map x = P_row A^- b:  z = A^-T (P_row w)
+  DS_HD void solve_t_mn(const double* w, double* z) const {
+    double p[MC];
+    for (int j = 0; j < c; ++j) p[j] = w[j];
+    project_out_null(p);
+    solve_t(p, z);
   }
 };

@@ -3,3 +3,5 @@
 
 void ds_launch_1_6_1_f64(const KArgs& a, cudaStream_t s) { ds::launch_env<1, 6, 1, double>(a, s); }
 void ds_launch_1_6_1_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<1, 6, 1, float>(a, s); }
+void ds_pipeline_1_6_1_f64(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<1, 6, 1, double>(a, s); }
+void ds_pipeline_1_6_1_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<1, 6, 1, float>(a, s); }

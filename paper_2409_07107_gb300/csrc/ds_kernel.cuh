@@ -14,7 +14,7 @@
 namespace ds {
 
 template <typename T>
-__device__ __forceinline__ void proj_cone(const T* x, T mu, T* o) {
+DS_HDI void proj_cone(const T* x, T mu, T* o) {
   const T nt = sqrt(x[0] * x[0] + x[1] * x[1]);
   if (nt <= mu * x[2]) { o[0] = x[0]; o[1] = x[1]; o[2] = x[2]; return; }
   if (mu * nt <= -x[2]) { o[0] = T(0); o[1] = T(0); o[2] = T(0); return; }
@@ -23,40 +23,54 @@ __device__ __forceinline__ void proj_cone(const T* x, T mu, T* o) {
   o[0] = k * x[0]; o[1] = k * x[1]; o[2] = s;
 }
 
-template <int NB, int NV, int NS, typename T>
-struct Env {
+// The contact problem of one env: Eq. 1 data (G, g, mu over the active contacts), the solution
+// lambda, and the FP64 factorisation workspace shared by the Newton steps and the implicit solve.
+template <int NS, typename T>
+struct Ncp {
   static constexpr int NC3 = 3 * NS;
   static constexpr bool kDouble = std::is_same<T, double>::value;
+  int na;                                    // active contacts
+  double mu[NS];
+  T Gt[NC3][NC3];                            // Delassus matrix in the bulk type
+  double Gd_[kDouble ? 1 : NC3][kDouble ? 1 : NC3];
+  T gt[NC3];
+  double gd[NC3], lam[NC3];
+  LUcp<NC3 + NS, NC3> lu;
+
+  DS_HDI double G(int i, int j) const {
+    if constexpr (kDouble) return Gt[i][j]; else return Gd_[i][j];
+  }
+};
+
+template <int NB, int NV, int NS, typename T>
+struct Env : Ncp<NS, T> {
+  static constexpr int NC3 = 3 * NS;
+  static constexpr bool kDouble = std::is_same<T, double>::value;
+  double q[NV + 1];                          // joint positions (FP64)
   double R[NB][9], P[NB][3];                 // world placement of every body (FP64)
   T S[NV][6];                                // world motion subspace of every dof
   T I[NB][10];                               // world spatial inertia of every body
   T V[NB][6], A[NB][6], VJ[NB][6], IV[NB][6], IA[NB][6], Fc[NB][6];
   T L[NV * (NV + 1) / 2];                    // Cholesky factor of M (packed lower)
   T v[NV], tau[NV], vdf[NV], vf[NV], vn[NV], astar[NV];
-  int na;                                    // active contacts
   int slot[NS], body[NS];
   T x[NS][3], c[NS][3], f[NS][3];            // body point, contact point, contact force (world)
+  double cx_d[NS][3];                        // contact point in FP64
   T fr[3][3];                                // contact frame rows t1, t2, n
-  double mu[NS];
   T Jc[NC3][NV];
   T Y[NC3][NV];                              // rows of M^-1 J_c^T
-  T Gt[NC3][NC3];                            // Delassus matrix in the bulk type
-  double Gd_[kDouble ? 1 : NC3][kDouble ? 1 : NC3];
-  T gt[NC3];
-  double gd[NC3], lam[NC3];
+  // mixed form: J_c, M's factor and M^-1 J_c^T in FP64 (G must keep the exact null space of J_c^T)
+  double Jd_[kDouble ? 1 : NC3][kDouble ? 1 : NV];
+  double Yd_[kDouble ? 1 : NC3][kDouble ? 1 : NV];
+  double Ld_[kDouble ? 1 : NV * (NV + 1) / 2];
   int mode[NS];
   double margin;
-  LUcp<NC3 + NS, NC3> lu;
-
-  __device__ __forceinline__ double G(int i, int j) const {
-    if constexpr (kDouble) return Gt[i][j]; else return Gd_[i][j];
-  }
 };
 
 // ------------------------------------------------------------------------- NCP helpers (FP64)
 
 template <class E>
-__device__ double ncp_residual(const E& s, const double* lam) {
+DS_HD double ncp_residual(const E& s, const double* lam) {
   const int m = 3 * s.na;
   double r = 0.0;
   for (int i = 0; i < s.na; ++i) {
@@ -78,9 +92,11 @@ __device__ double ncp_residual(const E& s, const double* lam) {
   return r;
 }
 
-// Contact modes (breaking / sticking / sliding) from sigma = G lambda + g, lambda.
+// Contact modes (breaking / sticking / sliding) from sigma = G lambda + g, lambda (same rules as
+// the oracle): sticking if |sigma| <= es; else breaking if sigma_N > es or lambda_N <= el; else
+// sticking if the impulse is strictly inside the cone (then Eq. 1 forces sigma = 0); else sliding.
 template <class E>
-__device__ double classify(const E& s, const double* lam, double es_rel, double el_rel, int* mode) {
+DS_HD double classify(const E& s, const double* lam, double es_rel, double el_rel, int* mode) {
   const int m = 3 * s.na;
   double gmax = 1.0, lmax = 1.0;
   for (int j = 0; j < m; ++j) { gmax = fmax(gmax, fabs(s.gd[j])); lmax = fmax(lmax, fabs(lam[j])); }
@@ -93,17 +109,22 @@ __device__ double classify(const E& s, const double* lam, double es_rel, double 
       for (int j = 0; j < m; ++j) t += s.G(3 * i + k, j) * lam[j];
       sg[k] = t;
     }
+    const double* l = lam + 3 * i;
     const double ns = sqrt(sg[0] * sg[0] + sg[1] * sg[1] + sg[2] * sg[2]);
     const double nst = sqrt(sg[0] * sg[0] + sg[1] * sg[1]);
+    const double inside = s.mu[i] * l[2] - sqrt(l[0] * l[0] + l[1] * l[1]);
     if (ns <= es) {
       mode[i] = DS_MODE_STICKING;
       margin = fmin(margin, (es - ns) / es);
-    } else if (sg[2] > es || lam[3 * i + 2] <= el) {
+    } else if (sg[2] > es || l[2] <= el) {
       mode[i] = DS_MODE_BREAKING;
       margin = fmin(margin, sg[2] > es ? (sg[2] - es) / gmax : 0.0);
+    } else if (inside > el) {
+      mode[i] = DS_MODE_STICKING;
+      margin = fmin(margin, inside / lmax);
     } else {
       mode[i] = DS_MODE_SLIDING;
-      margin = fmin(margin, fmin(nst / gmax, lam[3 * i + 2] / lmax));
+      margin = fmin(margin, fmin(nst / gmax, l[2] / lmax));
     }
   }
   return margin;
@@ -113,7 +134,7 @@ __device__ double classify(const E& s, const double* lam, double es_rel, double 
 // oracle): breaking + penetrating -> sticking; sticking/sliding + pulling -> breaking; sticking
 // with the impulse outside the cone -> sliding; sliding that stopped -> sticking.
 template <class E>
-__device__ bool reclassify(const E& s, const double* lam, int* mode, double es, double el, double delta) {
+DS_HD bool reclassify(const E& s, const double* lam, int* mode, double es, double el, double delta) {
   const int m = 3 * s.na;
   bool changed = false;
   for (int i = 0; i < s.na; ++i) {
@@ -144,38 +165,52 @@ __device__ bool reclassify(const E& s, const double* lam, int* mode, double es, 
 // sigma_N = 0, lambda_T + mu lambda_N sigma_T/|sigma_T| = 0), plus mu lambda_N - |lambda_T| = 0 for
 // the sticking contacts whose starting impulse lies within sat_delta of the cone boundary (with
 // redundant contacts this picks, among the equivalent impulses, one that stays in the cone).
-// FP64, basic-solution steps of a rank-revealing LU.
+// FP64, minimum-norm steps of a rank-revealing LU.  The breaking contacts' equations fix their
+// impulses at 0 exactly, so the system is solved in the unknowns of the other contacts only (the
+// null space lies in those unknowns, hence the minimum-norm step is unchanged).  Stops when the
+// residual is at rounding level or stops decreasing.
 template <class E>
-__device__ void newton_modes(E& s, double* lam, const int* mode, int iters, double sat_delta) {
+DS_HD void newton_modes(E& s, double* lam, const int* mode, int iters, double sat_delta) {
   const int m = 3 * s.na;
   double scale = 1.0;
   for (int j = 0; j < m; ++j) scale = fmax(scale, fabs(s.gd[j]));
   int sat[E::NC3 / 3], nsat = 0;
+  int ucon[E::NC3 / 3], nuc = 0;             // non-breaking contacts (their impulses are unknown)
   for (int i = 0; i < s.na; ++i) {
     const double* l = lam + 3 * i;
+    if (mode[i] == DS_MODE_BREAKING) {
+      lam[3 * i] = 0.0; lam[3 * i + 1] = 0.0; lam[3 * i + 2] = 0.0;
+      continue;
+    }
+    ucon[nuc++] = i;
     const double nt = sqrt(l[0] * l[0] + l[1] * l[1]);
     if (mode[i] == DS_MODE_STICKING && nt > 0.0 && s.mu[i] * l[2] - nt <= sat_delta) sat[nsat++] = i;
   }
-  const int rows = m + nsat;
+  const int nu = 3 * nuc;
+  if (nu == 0) return;
+  const int rows = nu + nsat;
+  double prev = 1e300;
   for (int it = 0; it < iters; ++it) {
     double sg[E::NC3], F[E::NC3 + E::NC3 / 3];
-    for (int r = 0; r < m; ++r) {
-      double t = s.gd[r];
-      for (int j = 0; j < m; ++j) t += s.G(r, j) * lam[j];
-      sg[r] = t;
-    }
+    for (int q = 0; q < nuc; ++q)
+      for (int k = 0; k < 3; ++k) {
+        const int r = 3 * ucon[q] + k;
+        double t = s.gd[r];
+        for (int p = 0; p < nuc; ++p)
+          for (int kk = 0; kk < 3; ++kk) t += s.G(r, 3 * ucon[p] + kk) * lam[3 * ucon[p] + kk];
+        sg[r] = t;
+      }
     s.lu.r = rows;
-    s.lu.c = m;
+    s.lu.c = nu;
     for (int r = 0; r < rows; ++r)
-      for (int j = 0; j < m; ++j) s.lu.a[r][j] = 0.0;
-    for (int i = 0; i < s.na; ++i) {
-      const int r0 = 3 * i;
-      if (mode[i] == DS_MODE_BREAKING) {
-        for (int r = 0; r < 3; ++r) { F[r0 + r] = lam[r0 + r]; s.lu.a[r0 + r][r0 + r] = 1.0; }
-      } else if (mode[i] == DS_MODE_STICKING) {
+      for (int j = 0; j < nu; ++j) s.lu.a[r][j] = 0.0;
+    for (int q = 0; q < nuc; ++q) {
+      const int i = ucon[q], r0 = 3 * i, u0 = 3 * q;
+      if (mode[i] == DS_MODE_STICKING) {
         for (int r = 0; r < 3; ++r) {
-          F[r0 + r] = sg[r0 + r];
-          for (int j = 0; j < m; ++j) s.lu.a[r0 + r][j] = s.G(r0 + r, j);
+          F[u0 + r] = sg[r0 + r];
+          for (int p = 0; p < nuc; ++p)
+            for (int kk = 0; kk < 3; ++kk) s.lu.a[u0 + r][3 * p + kk] = s.G(r0 + r, 3 * ucon[p] + kk);
         }
       } else {
         const double ns = sqrt(sg[r0] * sg[r0] + sg[r0 + 1] * sg[r0 + 1]);
@@ -183,129 +218,210 @@ __device__ void newton_modes(E& s, double* lam, const int* mode, int iters, doub
         const double mu = s.mu[i], ln = lam[r0 + 2];
         const double k = mu * ln / ns;
         for (int r = 0; r < 2; ++r) {
-          F[r0 + r] = lam[r0 + r] + mu * ln * u[r];
+          F[u0 + r] = lam[r0 + r] + mu * ln * u[r];
           // k (I - u u^T) G_T, then [I2, mu u] on the contact's own columns
-          for (int j = 0; j < m; ++j)
-            s.lu.a[r0 + r][j] = k * (((r == 0) - u[r] * u[0]) * s.G(r0, j) + ((r == 1) - u[r] * u[1]) * s.G(r0 + 1, j));
-          s.lu.a[r0 + r][r0 + r] += 1.0;
-          s.lu.a[r0 + r][r0 + 2] += mu * u[r];
+          for (int p = 0; p < nuc; ++p)
+            for (int kk = 0; kk < 3; ++kk) {
+              const int cj = 3 * ucon[p] + kk;
+              s.lu.a[u0 + r][3 * p + kk] =
+                  k * (((r == 0) - u[r] * u[0]) * s.G(r0, cj) + ((r == 1) - u[r] * u[1]) * s.G(r0 + 1, cj));
+            }
+          s.lu.a[u0 + r][u0 + r] += 1.0;
+          s.lu.a[u0 + r][u0 + 2] += mu * u[r];
         }
-        F[r0 + 2] = sg[r0 + 2];
-        for (int j = 0; j < m; ++j) s.lu.a[r0 + 2][j] = s.G(r0 + 2, j);
+        F[u0 + 2] = sg[r0 + 2];
+        for (int p = 0; p < nuc; ++p)
+          for (int kk = 0; kk < 3; ++kk) s.lu.a[u0 + 2][3 * p + kk] = s.G(r0 + 2, 3 * ucon[p] + kk);
       }
     }
-    for (int q = 0; q < nsat; ++q) {
-      const int i = sat[q], r0 = 3 * i;
+    for (int qs = 0; qs < nsat; ++qs) {
+      const int i = sat[qs], r0 = 3 * i;
+      int q = 0;
+      while (ucon[q] != i) ++q;
       const double nt = sqrt(lam[r0] * lam[r0] + lam[r0 + 1] * lam[r0 + 1]);
-      F[m + q] = s.mu[i] * lam[r0 + 2] - nt;
-      s.lu.a[m + q][r0] = -lam[r0] / nt;
-      s.lu.a[m + q][r0 + 1] = -lam[r0 + 1] / nt;
-      s.lu.a[m + q][r0 + 2] = s.mu[i];
+      F[nu + qs] = s.mu[i] * lam[r0 + 2] - nt;
+      s.lu.a[nu + qs][3 * q] = -lam[r0] / nt;
+      s.lu.a[nu + qs][3 * q + 1] = -lam[r0 + 1] / nt;
+      s.lu.a[nu + qs][3 * q + 2] = s.mu[i];
     }
     double fmaxv = 0.0;
     for (int r = 0; r < rows; ++r) fmaxv = fmax(fmaxv, fabs(F[r]));
     if (!(fmaxv > 1e-15 * scale)) break;
+    if (it >= 2 && !(fmaxv < 0.5 * prev)) break;        // not converging (wrong modes)
+    prev = fmaxv;
     s.lu.factor(1e-13);
+    s.lu.nullspace();
     double dx[E::NC3];
-    s.lu.solve(F, dx);
-    for (int r = 0; r < m; ++r) lam[r] -= dx[r];
+    s.lu.solve_mn(F, dx);
+    for (int q = 0; q < nuc; ++q)
+      for (int k = 0; k < 3; ++k) lam[3 * ucon[q] + k] -= dx[3 * q + k];
   }
 }
 
-// Staged NCP solve (same structure as the oracle's): each stage continues the over-relaxed ADMM
-// (bulk type, rho = 0.3 mean diag G, De Saxce term at the latest primal iterate) to a tolerance,
-// identifies the modes, and runs up to 4 active-set rounds of FP64 Newton on the mode equations;
-// the first candidate whose FP64 NCP residual passes is accepted.
-template <class E, typename T>
-__device__ void solve_ncp(E& s, const KArgs& a, int& iters, uint32_t& st) {
+// Over-relaxed ADMM on Eq. 1 in the bulk type (rho = 0.3 mean diag G, De Saxce term at the latest
+// primal iterate, relaxation 1.6).  The x-step uses the explicit inverse K = (G + rho I)^-1 (one
+// matrix-vector product, no dependent triangular solves), and G x is never formed: (G + rho I) x
+// = rhs gives G x + g = rhs - rho x + g.  The per-contact pieces below are shared by the
+// one-thread-per-env form and the one-lane-per-contact cooperative form, so both do the same
+// arithmetic in the same order.
+template <typename T>
+DS_HDI void admm_rhs(T mu, const T* z, const T* y, const T* g, const T* sx, T rho, T* rhs) {
+  const T sd = mu * sqrt(sx[0] * sx[0] + sx[1] * sx[1]);
+  rhs[0] = rho * z[0] - y[0] - g[0];
+  rhs[1] = rho * z[1] - y[1] - g[1];
+  rhs[2] = rho * z[2] - y[2] - g[2] - sd;
+}
+
+// x, sx, z, y of one contact from its three rows of K and the full right-hand side
+// (K and rhs_full are zero beyond the active size, so the product runs over the padded width.)
+template <int NC3, typename T>
+DS_HDI void admm_update(const T (*Kr)[NC3], const T* rhs_full, const T* rhs_own, const T* g, T mu, T rho,
+                        T* x, T* z, T* y, T* sx, T& rp, T& rd, T& zmax) {
+  const T relax = T(1.6);
+  T xh[3], w[3], pr[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < NC3; ++c) acc += Kr[r][c] * rhs_full[c];
+    x[r] = acc;
+    sx[r] = rhs_own[r] - rho * acc + g[r];
+    xh[r] = relax * x[r] + (T(1) - relax) * z[r];
+    w[r] = xh[r] + y[r] / rho;
+  }
+  proj_cone(w, mu, pr);
+  for (int r = 0; r < 3; ++r) {
+    rd = fmax(rd, fabs(pr[r] - z[r]));
+    z[r] = pr[r];
+    y[r] += rho * (xh[r] - z[r]);
+    rp = fmax(rp, fabs(x[r] - z[r]));
+    zmax = fmax(zmax, fabs(z[r]));
+  }
+}
+
+template <int NS, typename T>
+struct Admm {
+  static constexpr int NC3 = 3 * NS;
+  T K[NC3][NC3];
+  T rho, gs;
+  int m;
+  T x[NC3], z[NC3], y[NC3], sx[NC3];
+
+  template <class P>
+  DS_HD bool setup(const P& p) {
+    m = 3 * p.na;
+    T trace = T(0);
+    for (int i = 0; i < m; ++i) trace += p.Gt[i][i];
+    rho = T(0.3) * trace / T(m);
+    if (!(rho > T(1e-12))) rho = T(1e-12);
+    gs = T(1);
+    for (int i = 0; i < m; ++i) gs = fmax(gs, fabs(p.gt[i]));
+    T Lg[NC3 * (NC3 + 1) / 2];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j <= i; ++j) Lg[tri(i, j)] = p.Gt[i][j] + (i == j ? rho : T(0));
+    for (int i = 0; i < NC3; ++i)
+      for (int j = 0; j < NC3; ++j) K[i][j] = T(0);
+    if (!chol_packed(Lg, m)) return false;
+    for (int j = 0; j < m; ++j) {
+      T col[NC3];
+      for (int i = 0; i < m; ++i) col[i] = T(i == j ? 1 : 0);
+      fwd_packed(Lg, col, m);
+      bwd_packed(Lg, col, m);
+      for (int i = 0; i < m; ++i) K[i][j] = col[i];
+    }
+    return true;
+  }
+
+  template <class P>
+  DS_HD void reset(const P& p) {
+    for (int i = 0; i < m; ++i) { x[i] = T(0); z[i] = T(0); y[i] = T(0); sx[i] = p.gt[i]; }
+  }
+
+  // one iteration; returns true when converged at tolerance te
+  template <class P>
+  DS_HD bool iterate(const P& p, T te) {
+    T rhs[NC3];
+    for (int i = 0; i < NC3; ++i) rhs[i] = T(0);
+    for (int i = 0; i < p.na; ++i) admm_rhs(T(p.mu[i]), z + 3 * i, y + 3 * i, p.gt + 3 * i, sx + 3 * i, rho, rhs + 3 * i);
+    T rp = T(0), rd = T(0), zmax = T(1);
+    for (int i = 0; i < p.na; ++i)
+      admm_update<NC3, T>(K + 3 * i, rhs, rhs + 3 * i, p.gt + 3 * i, T(p.mu[i]), rho, x + 3 * i, z + 3 * i,
+                          y + 3 * i, sx + 3 * i, rp, rd, zmax);
+    rd *= rho;
+    return rp <= te * zmax && rd <= te * gs;
+  }
+};
+
+template <typename T>
+DS_HDI double stage_eps(const KArgs& a, int stage) {
+  const bool dbl = std::is_same<T, double>::value;
+  double eps = a.admm_eps;
+  for (int k = 0; k < stage; ++k) eps = fmax(eps * (dbl ? 1e-2 : 0.1), dbl ? 1e-13 : 1e-6);
+  return eps;
+}
+
+template <typename T>
+DS_HDI int num_stages() { return std::is_same<T, double>::value ? 4 : 3; }
+
+// End of an ADMM stage: identify the modes from z and run up to 4 active-set rounds of FP64 Newton
+// on the mode equations; keeps the best candidate (by FP64 NCP residual).  Returns true when the
+// best candidate passes the residual check.
+template <class P, typename T>
+DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* best, double& best_r) {
+  const int m = 3 * p.na;
+  double scale = 1.0;
+  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(p.gd[i]));
+  const double tol = a.ncp_tol * scale;
+  double lz[P::NC3], lp[P::NC3];
+  double lscale = 1.0;
+  for (int i = 0; i < m; ++i) { lz[i] = double(z[i]); lscale = fmax(lscale, fabs(lz[i])); }
+  const double es = fmax(a.eps_sigma, 10.0 * eps), el = fmax(a.eps_lambda, 10.0 * eps);
+  const double sat_delta = 10.0 * eps * lscale;
+  int mode[P::NC3 / 3];
+  classify(p, lz, es, el, mode);
+  {
+    const double r0 = ncp_residual(p, lz);
+    if (r0 < best_r) { best_r = r0; for (int i = 0; i < m; ++i) best[i] = lz[i]; }
+  }
+  for (int i = 0; i < m; ++i) lp[i] = lz[i];
+  for (int round = 0; round < 4 && best_r > tol; ++round) {
+    newton_modes(p, lp, mode, a.polish_iters, sat_delta);
+    const double rpol = ncp_residual(p, lp);
+    if (rpol < best_r) { best_r = rpol; for (int i = 0; i < m; ++i) best[i] = lp[i]; }
+    if (best_r <= tol) break;
+    // the Newton iterate solves its mode equations exactly: any violation above the acceptance
+    // tolerance is real and flips the mode
+    if (!reclassify(p, lp, mode, 10.0 * tol, 10.0 * a.ncp_tol * lscale, 10.0 * a.ncp_tol * lscale)) break;
+    for (int i = 0; i < p.na; ++i) proj_cone(lp + 3 * i, p.mu[i], lp + 3 * i);
+  }
+  return best_r <= tol;
+}
+
+// Staged NCP solve (same structure as the oracle's): each stage continues the ADMM iteration to a
+// tolerance, then runs the Newton / active-set stage; the first candidate whose FP64 NCP residual
+// passes is accepted.
+template <class P, typename T>
+DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
   const int m = 3 * s.na;
   iters = 0;
   if (m == 0) return;
-  T trace = T(0);
-  for (int i = 0; i < m; ++i) trace += s.Gt[i][i];
-  T rho = T(0.3) * trace / T(m);
-  if (!(rho > T(1e-12))) rho = T(1e-12);
-  const T relax = T(1.6);
-  T Lg[E::NC3 * (E::NC3 + 1) / 2];
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j <= i; ++j) Lg[tri(i, j)] = s.Gt[i][j] + (i == j ? rho : T(0));
-  if (!chol_packed(Lg, m)) { st |= DS_ENV_NONFINITE; }
-  T x[E::NC3], z[E::NC3], y[E::NC3];
-  for (int i = 0; i < m; ++i) { x[i] = T(0); z[i] = T(0); y[i] = T(0); }
-  T gs = T(1);
-  double scale = 1.0;
-  for (int i = 0; i < m; ++i) { gs = fmax(gs, fabs(s.gt[i])); scale = fmax(scale, fabs(s.gd[i])); }
-  double best[E::NC3], best_r = 1e300;
-  double eps = a.admm_eps;
-  const double shrink = E::kDouble ? 1e-2 : 0.1;
-  const double floor_eps = E::kDouble ? 1e-13 : 1e-6;
-  const int nstage = E::kDouble ? 4 : 3;
-  const double tol = a.ncp_tol * scale;
-  for (int stage = 0; stage < nstage; ++stage) {
+  Admm<P::NC3 / 3, T> ad;
+  if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
+  ad.reset(s);
+  double best[P::NC3], best_r = 1e300;
+  bool ok = false;
+  for (int stage = 0; stage < num_stages<T>(); ++stage) {
+    const double eps = stage_eps<T>(a, stage);
     const T te = T(eps);
     while (iters < a.admm_max_iter) {
       ++iters;
-      T rhs[E::NC3];
-      for (int i = 0; i < s.na; ++i) {
-        T sg[3];
-        for (int k = 0; k < 3; ++k) {
-          T t = s.gt[3 * i + k];
-          for (int j = 0; j < m; ++j) t += s.Gt[3 * i + k][j] * x[j];
-          sg[k] = t;
-        }
-        const T sd = T(s.mu[i]) * sqrt(sg[0] * sg[0] + sg[1] * sg[1]);
-        for (int k = 0; k < 3; ++k)
-          rhs[3 * i + k] = rho * z[3 * i + k] - y[3 * i + k] - s.gt[3 * i + k] - (k == 2 ? sd : T(0));
-      }
-      fwd_packed(Lg, rhs, m);
-      bwd_packed(Lg, rhs, m);
-      T rp = T(0), rd = T(0), zmax = T(1);
-      for (int i = 0; i < s.na; ++i) {
-        T w[3], p[3], xh[3];
-        for (int k = 0; k < 3; ++k) {
-          const int r = 3 * i + k;
-          x[r] = rhs[r];
-          xh[k] = relax * x[r] + (T(1) - relax) * z[r];
-          w[k] = xh[k] + y[r] / rho;
-        }
-        proj_cone(w, T(s.mu[i]), p);
-        for (int k = 0; k < 3; ++k) {
-          const int r = 3 * i + k;
-          rd = fmax(rd, fabs(p[k] - z[r]));
-          z[r] = p[k];
-          y[r] += rho * (xh[k] - z[r]);
-          rp = fmax(rp, fabs(x[r] - z[r]));
-          zmax = fmax(zmax, fabs(z[r]));
-        }
-      }
-      rd *= rho;
-      if (rp <= te * zmax && rd <= te * gs) break;
+      if (ad.iterate(s, te)) break;
     }
-    double lz[E::NC3], lp[E::NC3];
-    double lscale = 1.0;
-    for (int i = 0; i < m; ++i) { lz[i] = double(z[i]); lscale = fmax(lscale, fabs(lz[i])); }
-    const double es = fmax(a.eps_sigma, 10.0 * eps), el = fmax(a.eps_lambda, 10.0 * eps);
-    const double sat_delta = 10.0 * eps * lscale;
-    int mode[E::NC3 / 3];
-    classify(s, lz, es, el, mode);
-    {
-      const double r0 = ncp_residual(s, lz);
-      if (r0 < best_r) { best_r = r0; for (int i = 0; i < m; ++i) best[i] = lz[i]; }
-    }
-    for (int i = 0; i < m; ++i) lp[i] = lz[i];
-    for (int round = 0; round < 4 && best_r > tol; ++round) {
-      newton_modes(s, lp, mode, a.polish_iters, sat_delta);
-      const double rpol = ncp_residual(s, lp);
-      if (rpol < best_r) { best_r = rpol; for (int i = 0; i < m; ++i) best[i] = lp[i]; }
-      if (best_r <= tol) break;
-      if (!reclassify(s, lp, mode, es * scale, el * lscale, sat_delta)) break;
-      for (int i = 0; i < s.na; ++i) proj_cone(lp + 3 * i, s.mu[i], lp + 3 * i);
-    }
-    if (best_r <= tol || iters >= a.admm_max_iter) break;
-    eps = fmax(eps * shrink, floor_eps);
+    ok = newton_stage(s, ad.z, eps, a, best, best_r);
+    if (ok || iters >= a.admm_max_iter) break;
   }
   for (int i = 0; i < m; ++i) s.lam[i] = best[i];
-  if (!(best_r <= tol)) st |= DS_ENV_NOT_CONVERGED;
+  if (!ok) st |= DS_ENV_NOT_CONVERGED;
 }
 
 }  // namespace ds
@@ -317,7 +433,7 @@ namespace ds {
 // xi = S_d), kind 1 = unit change of the dof's velocity.  Uses the stored pass values V, A, VJ,
 // IV, IA, Fc of the a* pass.  Writes dtau[NV].
 template <int NB, int NV, int NS, typename T>
-__device__ void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind, int d, T* dtau) {
+DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind, int d, T* dtau) {
   const int j = m.dof_body[d];
   const int jend = m.sub_end[j];
   const T* xi = s.S[d];
@@ -392,7 +508,7 @@ __device__ void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int
 // d(J_c v+)/dq_d for contact a at fixed v+ (App. D's FKV term, including the motion of the
 // contact point with the body): Vp = body velocities under v+.
 template <int NB, int NV, int NS, typename T>
-__device__ __forceinline__ void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T (*Vp)[6],
+DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T (*Vp)[6],
                                             int a, int d, T* out) {
   const int j = m.dof_body[d];
   const int b = s.body[a];
@@ -412,12 +528,12 @@ __device__ __forceinline__ void fkv_tangent(const DevModel& m, const Env<NB, NV,
   for (int r = 0; r < 3; ++r) out[r] = dot3(s.fr[r], dp);
 }
 
+// F1-F6 for env e: kinematics, dynamics, contact detection, J_c, G, g.  Returns status bits.
 template <int NB, int NV, int NS, typename T>
-__device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
-  Env<NB, NV, NS, T> s;
+DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s) {
   const int B = a.B;
   uint32_t st = 0;
-  double q[NV + 1];
+  double* q = s.q;
   for (int i = 0; i < m.nq; ++i) q[i] = a.q[i * B + e];
   bool finite = true;
   for (int i = 0; i < m.nq; ++i) finite &= isfinite(q[i]);
@@ -562,6 +678,10 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
           for (int d2 = m.iv[b]; d2 < m.iv[b] + m.nd[b]; ++d2) s.L[tri(dd, d2)] = dot6(s.S[d2], F);
       }
     }
+    if constexpr (!Env<NB, NV, NS, T>::kDouble) {
+      for (int k = 0; k < NV * (NV + 1) / 2; ++k) s.Ld_[k] = double(s.L[k]);
+      if (!chol_packed(s.Ld_, NV)) st |= DS_ENV_NONFINITE;
+    }
     if (!chol_packed(s.L, NV)) st |= DS_ENV_NONFINITE;
     for (int k = 0; k < NV; ++k) s.vdf[k] = s.tau[k] - bias[k];
     fwd_packed(s.L, s.vdf, NV);
@@ -598,56 +718,97 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
       s.slot[n] = k;
       s.body[n] = b;
       s.mu[n] = a.c_mu[k * B + e];
-      for (int i = 0; i < 3; ++i) { s.x[n][i] = T(xw[i]); s.c[n][i] = T(xw[i] - r * pn[i]); }
+      for (int i = 0; i < 3; ++i) {
+        s.x[n][i] = T(xw[i]);
+        s.c[n][i] = T(xw[i] - r * pn[i]);
+        s.cx_d[n][i] = xw[i] - r * pn[i];
+      }
     }
   }
   const int mdim = 3 * s.na;
 
-  // ---- F5 contact Jacobian rows (t1, t2, n) . velocity of the body point at c
-  for (int r = 0; r < mdim; ++r)
-    for (int k = 0; k < NV; ++k) s.Jc[r][k] = T(0);
-  for (int ac = 0; ac < s.na; ++ac) {
-    for (int b = s.body[ac]; b >= 0; b = m.parent[b])
-      for (int dd = m.iv[b]; dd < m.iv[b] + m.nd[b]; ++dd) {
-        T pv[3], t[3];
-        cross3(s.S[dd] + 3, s.c[ac], t);
-        for (int k = 0; k < 3; ++k) pv[k] = s.S[dd][k] + t[k];
-        for (int r = 0; r < 3; ++r) s.Jc[3 * ac + r][dd] = dot3(s.fr[r], pv);
+  // ---- F5 contact Jacobian rows (t1, t2, n) . velocity of the body point at c, in FP64 from the
+  // FP64 placements: the rows of corners of one rigid body stay exactly dependent.
+  constexpr bool kD = Env<NB, NV, NS, T>::kDouble;
+  double (*Jd)[NV];
+  double (*Yd)[NV];
+  const double* Ld;
+  if constexpr (kD) { Jd = s.Jc; Yd = s.Y; Ld = s.L; } else { Jd = s.Jd_; Yd = s.Yd_; Ld = s.Ld_; }
+  {
+    double frd[3][3];
+    {
+      const bool use_y = fabs(pn[0]) > 0.9;
+      double t1[3] = {use_y ? 0.0 : 1.0, use_y ? 1.0 : 0.0, 0.0};
+      const double dn = t1[0] * pn[0] + t1[1] * pn[1];
+      for (int k = 0; k < 3; ++k) t1[k] -= dn * pn[k];
+      const double nn = 1.0 / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+      for (int k = 0; k < 3; ++k) t1[k] *= nn;
+      double t2[3];
+      cross3(pn, t1, t2);
+      for (int k = 0; k < 3; ++k) { frd[0][k] = t1[k]; frd[1][k] = t2[k]; frd[2][k] = pn[k]; }
+    }
+    for (int r = 0; r < mdim; ++r)
+      for (int k = 0; k < NV; ++k) Jd[r][k] = 0.0;
+    for (int ac = 0; ac < s.na; ++ac) {
+      const double cd[3] = {double(s.cx_d[ac][0]), double(s.cx_d[ac][1]), double(s.cx_d[ac][2])};
+      for (int b = s.body[ac]; b >= 0; b = m.parent[b]) {
+        const double* Rb = s.R[b];
+        const double* pb = s.P[b];
+        const double rel[3] = {cd[0] - pb[0], cd[1] - pb[1], cd[2] - pb[2]};
+        for (int dd = m.iv[b]; dd < m.iv[b] + m.nd[b]; ++dd) {
+          double pv[3];
+          const int k = dd - m.iv[b];
+          if (m.jtype[b] == 0) {
+            const double* ax = m.axis[b];
+            double aw[3];
+            for (int r = 0; r < 3; ++r) aw[r] = Rb[3 * r] * ax[0] + Rb[3 * r + 1] * ax[1] + Rb[3 * r + 2] * ax[2];
+            cross3(aw, rel, pv);
+          } else if (k < 3) {
+            for (int r = 0; r < 3; ++r) pv[r] = Rb[3 * r + k];
+          } else {
+            const double col[3] = {Rb[k - 3], Rb[3 + k - 3], Rb[6 + k - 3]};
+            cross3(col, rel, pv);
+          }
+          for (int r = 0; r < 3; ++r) Jd[3 * ac + r][dd] = dot3(frd[r], pv);
+        }
       }
+    }
   }
 
-  // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f
+  // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms)
   for (int r = 0; r < mdim; ++r) {
-    for (int k = 0; k < NV; ++k) s.Y[r][k] = s.Jc[r][k];
-    fwd_packed(s.L, s.Y[r], NV);
+    for (int k = 0; k < NV; ++k) Yd[r][k] = Jd[r][k];
+    fwd_packed(Ld, Yd[r], NV);
   }
   for (int r = 0; r < mdim; ++r)
     for (int c = 0; c <= r; ++c) {
-      T t = T(0);
-      for (int k = 0; k < NV; ++k) t += s.Y[r][k] * s.Y[c][k];
-      s.Gt[r][c] = t;
-      s.Gt[c][r] = t;
+      double t = 0.0;
+      for (int k = 0; k < NV; ++k) t += Yd[r][k] * Yd[c][k];
+      s.Gt[r][c] = T(t);
+      s.Gt[c][r] = T(t);
+      if constexpr (!kD) { s.Gd_[r][c] = t; s.Gd_[c][r] = t; }
     }
   for (int r = 0; r < mdim; ++r) {
-    bwd_packed(s.L, s.Y[r], NV);
-    T t = T(0);
-    for (int k = 0; k < NV; ++k) t += s.Jc[r][k] * s.vf[k];
-    s.gt[r] = t;
-    s.gd[r] = double(t);
+    bwd_packed(Ld, Yd[r], NV);
+    double t = 0.0;
+    for (int k = 0; k < NV; ++k) t += Jd[r][k] * double(s.vf[k]);
+    s.gt[r] = T(t);
+    s.gd[r] = t;
   }
-  if constexpr (!Env<NB, NV, NS, T>::kDouble)
+  if constexpr (!kD)
     for (int r = 0; r < mdim; ++r)
-      for (int c = 0; c < mdim; ++c) s.Gd_[r][c] = double(s.Gt[r][c]);
+      for (int k = 0; k < NV; ++k) { s.Jc[r][k] = T(Jd[r][k]); s.Y[r][k] = T(Yd[r][k]); }
+  return st;
+}
 
-  // ---- F7/F8 NCP solve and residual check
-  int iters = 0;
-  for (int r = 0; r < mdim; ++r) s.lam[r] = 0.0;
-  if (mdim > 0 && !(st & DS_ENV_NONFINITE)) solve_ncp<Env<NB, NV, NS, T>, T>(s, a, iters, st);
-  s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
-  if (mdim > 0 && s.margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
-
-  // ---- F9 velocity update and symplectic-Euler position update
-  for (int k = 0; k < NV; ++k) {
+// F9 and, on request, B1-B7 for env e, given lambda and the modes of its active contacts.
+template <int NB, int NV, int NS, typename T>
+DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters) {
+  const int B = a.B;
+  const int mdim = 3 * s.na;
+  const double* q = s.q;
+  const T grav[3] = {T(a.gx), T(a.gy), T(a.gz)};
+   for (int k = 0; k < NV; ++k) {
     T t = s.vf[k];
     for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r]);
     s.vn[k] = t;
@@ -805,6 +966,7 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
     }
     if (md > 0) {
       s.lu.factor(1e-12);
+      s.lu.nullspace();
       if (s.lu.rank < md) st |= DS_ENV_SINGULAR;
     }
 
@@ -845,7 +1007,7 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
                 rhs[off[ac] + r] = -(RP[ac][r][0] * r3[0] + RP[ac][r][1] * r3[1] + RP[ac][r][2] * r3[2]);
             }
           }
-          s.lu.solve(rhs, X);
+          s.lu.solve_mn(rhs, X);
           for (int ac = 0; ac < s.na; ++ac) {
             if (sz[ac] == 0) continue;
             double dl[3];
@@ -881,7 +1043,7 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
           if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) wv[off[ac] + r] = y3[r]; }
           else { for (int c = 0; c < 2; ++c) wv[off[ac] + c] = Rm[ac][0][c] * y3[0] + Rm[ac][1][c] * y3[1] + Rm[ac][2][c] * y3[2]; }
         }
-        s.lu.solve_t(wv, z);
+        s.lu.solve_t_mn(wv, z);
         for (int ac = 0; ac < s.na; ++ac) {
           if (sz[ac] == 0) continue;
           if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) zeta[3 * ac + r] = z[off[ac] + r]; }
@@ -920,15 +1082,39 @@ __device__ void run_env(const DevModel& m, const KArgs& a, const int e) {
   if (a.status) a.status[e] = st;
 }
 
+
+// Fused path: one thread does the whole step for env e.
 template <int NB, int NV, int NS, typename T>
-__global__ void __launch_bounds__(128) env_kernel(KArgs a) {
-  __shared__ DevModel sm;
-  {
-    const int* src = reinterpret_cast<const int*>(a.model);
-    int* dst = reinterpret_cast<int*>(&sm);
-    for (int k = threadIdx.x; k < int(sizeof(DevModel) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
-  }
+DS_HD void run_env(const DevModel& m, const KArgs& a, const int e) {
+  Env<NB, NV, NS, T> s;
+  uint32_t st = env_forward<NB, NV, NS, T>(m, a, e, s);
+  const int mdim = 3 * s.na;
+  // ---- F7/F8 NCP solve and residual check
+  int iters = 0;
+  for (int r = 0; r < mdim; ++r) s.lam[r] = 0.0;
+  if (mdim > 0 && !(st & DS_ENV_NONFINITE)) solve_ncp<Env<NB, NV, NS, T>, T>(s, a, iters, st);
+  s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
+  if (mdim > 0 && s.margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
+
+  env_finish<NB, NV, NS, T>(m, a, e, s, st, iters);
+}
+
+DS_HDI void load_model(DevModel& sm, const DevModel* src_model) {
+#ifdef __CUDA_ARCH__
+  const int* src = reinterpret_cast<const int*>(src_model);
+  int* dst = reinterpret_cast<int*>(&sm);
+  for (int k = threadIdx.x; k < int(sizeof(DevModel) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
   __syncthreads();
+#else
+  sm = *src_model;
+#endif
+}
+
+// Fused path: one thread per env does everything (no workspace).
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(128, 4) env_kernel(KArgs a) {
+  __shared__ DevModel sm;
+  load_model(sm, a.model);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_env) return;
   const int e = a.env_list ? a.env_list[t] : t;
@@ -936,11 +1122,347 @@ __global__ void __launch_bounds__(128) env_kernel(KArgs a) {
   run_env<NB, NV, NS, T>(sm, a, e);
 }
 
+// ---------------------------------------------------------------------------------- pipeline
+// 1. setup: F1-F6 per env, the contact problem (mu, G, g) and a zero ADMM state to the workspace,
+//    envs with contacts queued for round 0.
+DS_HDI int ds_atomic_add(int32_t* p, int32_t v) {
+#ifdef __CUDA_ARCH__
+  return atomicAdd(p, v);
+#else
+  const int32_t old = *p;
+  *p += v;
+  return old;
+#endif
+}
+
+// 1. setup: F1-F6 per env; the contact problem (mu, G, g), rho and K = (G + rho I)^-1, and a zero
+//    ADMM state to the workspace; envs with contacts queued for round 0.
+template <int NB, int NV, int NS, typename T>
+DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
+  Env<NB, NV, NS, T> s;
+  uint32_t st = env_forward<NB, NV, NS, T>(m, a, e, s);
+  const WsView& w = a.ws;
+  const int B = a.B;
+  const int mm = 3 * s.na;
+  constexpr int NC3 = 3 * NS;
+  w.na[e] = s.na;
+  w.iters[e] = 0;
+  w.stage[e] = 0;
+  w.best_r[e] = 1e300;
+  for (int i = 0; i < s.na; ++i) w.mu[i * B + e] = s.mu[i];
+  for (int i = 0; i < mm; ++i) {
+    for (int j = 0; j <= i; ++j) w.G[tri(i, j) * B + e] = s.G(i, j);
+    w.g[i * B + e] = s.gd[i];
+    w.lam[i * B + e] = 0.0;
+    w.ax[i * B + e] = 0.0;
+    w.az[i * B + e] = 0.0;
+    w.ay[i * B + e] = 0.0;
+    w.asx[i * B + e] = double(s.gt[i]);
+  }
+  if (mm > 0 && !(st & DS_ENV_NONFINITE)) {
+    Admm<NS, T> ad;
+    if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
+    w.rho[e] = double(ad.rho);
+    for (int i = 0; i < NC3; ++i)
+      for (int j = 0; j < NC3; ++j) w.K[(i * NC3 + j) * B + e] = double(ad.K[i][j]);
+    if (!(st & DS_ENV_NONFINITE)) {
+      const int k = ds_atomic_add(&w.counts[0], 1);
+      w.list[0][k] = e;
+    }
+  }
+  w.st[e] = st;
+}
+
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(128, 4) setup_kernel(KArgs a) {
+  __shared__ DevModel sm;
+  load_model(sm, a.model);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_env) return;
+  const int e = a.env_list ? a.env_list[t] : t;
+  if (a.model_id && a.model_id[e] != a.model_index) return;
+  setup_env<NB, NV, NS, T>(sm, a, e);
+}
+
+// 2a. one ADMM round, one lane per contact slot (NS lanes per env, 32/NS envs per warp): each lane
+//     keeps its three rows of K and its contact's x, z, y, sx in registers; the right-hand side is
+//     exchanged with warp shuffles and the convergence test is a max-reduction over the env's
+//     lanes.  Every env runs at most round_cap iterations; envs whose stage tolerance was met (or
+//     that hit the iteration cap) go to the Newton queue, the others to the next round's list.
+template <typename T>
+__device__ __forceinline__ T group_max(T v, int lanes) {
+  for (int off = lanes >> 1; off >= 1; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+template <int NS, typename T>
+__global__ void __launch_bounds__(128) admm_round_kernel(KArgs a) {
+  static_assert(32 % NS == 0, "contact slots must divide the warp");
+  constexpr int L = NS, EPW = 32 / NS, NC3 = 3 * NS;
+  const WsView& w = a.ws;
+  const int n = w.counts[a.round];
+  const int B = a.B;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / L, li = lane - grp * L;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int32_t* cur = w.list[a.round & 1];
+  int32_t* next = w.list[(a.round + 1) & 1];
+  for (int base = warp * EPW; base < n; base += nwarps * EPW) {
+    const int t = base + grp;
+    const bool have = t < n;
+    const int e = have ? cur[t] : 0;
+    const int na = have ? w.na[e] : 0;
+    const bool act = li < na;
+    T Kr[3][NC3], x[3], z[3], y[3], sx[3], g[3];
+    T mu = T(0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int row = 3 * li + r;
+#pragma unroll
+      for (int c = 0; c < NC3; ++c) Kr[r][c] = act ? T(w.K[(row * NC3 + c) * B + e]) : T(0);
+      x[r] = act ? T(w.ax[row * B + e]) : T(0);
+      z[r] = act ? T(w.az[row * B + e]) : T(0);
+      y[r] = act ? T(w.ay[row * B + e]) : T(0);
+      sx[r] = act ? T(w.asx[row * B + e]) : T(0);
+      g[r] = act ? T(w.g[row * B + e]) : T(0);
+    }
+    if (act) mu = T(w.mu[li * B + e]);
+    const T rho = have ? T(w.rho[e]) : T(1);
+    T gm = fmax(fabs(g[0]), fmax(fabs(g[1]), fabs(g[2])));
+    const T gs = fmax(T(1), group_max(gm, L));
+    int iters = have ? w.iters[e] : 0;
+    const int stage = have ? w.stage[e] : 0;
+    const T te = T(stage_eps<T>(a, stage));
+    bool running = have && iters < a.admm_max_iter;
+    bool conv = false;
+    for (int k = 0; k < a.round_cap; ++k) {
+      if (!__any_sync(0xffffffffu, running)) break;
+      T rhs[3] = {T(0), T(0), T(0)};
+      if (act) admm_rhs(mu, z, y, g, sx, rho, rhs);
+      T full[NC3];
+#pragma unroll
+      for (int j = 0; j < NS; ++j)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) full[3 * j + r] = __shfl_sync(0xffffffffu, rhs[r], grp * L + j);
+      T xn[3] = {x[0], x[1], x[2]}, zn[3] = {z[0], z[1], z[2]}, yn[3] = {y[0], y[1], y[2]};
+      T sn[3] = {sx[0], sx[1], sx[2]};
+      T rp = T(0), rd = T(0), zmax = T(1);
+      if (act) admm_update<NC3, T>(Kr, full, rhs, g, mu, rho, xn, zn, yn, sn, rp, rd, zmax);
+      rp = group_max(rp, L);
+      rd = group_max(rd, L);
+      zmax = group_max(zmax, L);
+      if (running) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) { x[r] = xn[r]; z[r] = zn[r]; y[r] = yn[r]; sx[r] = sn[r]; }
+        ++iters;
+        rd *= rho;
+        if (rp <= te * zmax && rd <= te * gs) { conv = true; running = false; }
+        else if (iters >= a.admm_max_iter) running = false;
+      }
+    }
+    if (have) {
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int row = 3 * li + r;
+          w.ax[row * B + e] = double(x[r]);
+          w.az[row * B + e] = double(z[r]);
+          w.ay[row * B + e] = double(y[r]);
+          w.asx[row * B + e] = double(sx[r]);
+        }
+      }
+      if (li == 0) {
+        w.iters[e] = iters;
+        if (conv || iters >= a.admm_max_iter || a.final_round) {
+          const int k = atomicAdd(&w.ncounts[a.round], 1);
+          w.nlist[k] = e;
+        } else {
+          const int k = atomicAdd(&w.counts[a.round + 1], 1);
+          next[k] = e;
+        }
+      }
+    }
+  }
+}
+
+// 2b. the Newton / active-set stage for the envs whose ADMM stage ended in this round (one thread
+//     per env): accept, or move to the next (tighter) stage and queue for the next round.
+template <int NS, typename T>
+DS_HD void newton_env(const KArgs& a, const int e) {
+  const WsView& w = a.ws;
+  const int B = a.B;
+  Ncp<NS, T> p;
+  p.na = w.na[e];
+  const int m = 3 * p.na;
+  for (int i = 0; i < p.na; ++i) p.mu[i] = w.mu[i * B + e];
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      const double gij = w.G[tri(i, j) * B + e];
+      p.Gt[i][j] = T(gij);
+      p.Gt[j][i] = T(gij);
+      if constexpr (!Ncp<NS, T>::kDouble) { p.Gd_[i][j] = gij; p.Gd_[j][i] = gij; }
+    }
+    p.gd[i] = w.g[i * B + e];
+    p.gt[i] = T(p.gd[i]);
+  }
+  uint32_t st = w.st[e];
+  T z[3 * NS];
+  for (int i = 0; i < m; ++i) z[i] = T(w.az[i * B + e]);
+  int stage = w.stage[e];
+  const int iters = w.iters[e];
+  double best[3 * NS], best_r = w.best_r[e];
+  for (int i = 0; i < m; ++i) best[i] = w.lam[i * B + e];
+  const double eps = stage_eps<T>(a, stage);
+  const bool ok = newton_stage(p, z, eps, a, best, best_r);
+  for (int i = 0; i < m; ++i) w.lam[i * B + e] = best[i];
+  if (ok || iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round) {
+    for (int i = 0; i < m; ++i) p.lam[i] = best[i];
+    if (!ok) st |= DS_ENV_NOT_CONVERGED;
+    int mode[NS];
+    const double margin = classify(p, p.lam, a.eps_sigma, a.eps_lambda, mode);
+    if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
+    for (int i = 0; i < p.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
+    w.st[e] = st;
+  } else {
+    w.stage[e] = stage + 1;
+    w.best_r[e] = best_r;
+    const int k = ds_atomic_add(&w.counts[a.round + 1], 1);
+    w.list[(a.round + 1) & 1][k] = e;
+  }
+}
+
+template <int NS, typename T>
+__global__ void __launch_bounds__(128) newton_kernel(KArgs a) {
+  const int n = a.ws.ncounts[a.round];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    newton_env<NS, T>(a, a.ws.nlist[t]);
+}
+
+// Host-side emulation of one ADMM round for one env (the thread form of 2a; same arithmetic).
+template <int NS, typename T>
+DS_HD void admm_round_env(const KArgs& a, const int e) {
+  const WsView& w = a.ws;
+  const int B = a.B;
+  constexpr int NC3 = 3 * NS;
+  Ncp<NS, T> p;
+  p.na = w.na[e];
+  const int m = 3 * p.na;
+  for (int i = 0; i < p.na; ++i) p.mu[i] = w.mu[i * B + e];
+  for (int i = 0; i < NC3; ++i) p.gt[i] = i < m ? T(w.g[i * B + e]) : T(0);
+  Admm<NS, T> ad;
+  ad.m = m;
+  ad.rho = T(w.rho[e]);
+  ad.gs = T(1);
+  for (int i = 0; i < m; ++i) ad.gs = fmax(ad.gs, fabs(p.gt[i]));
+  for (int i = 0; i < NC3; ++i)
+    for (int j = 0; j < NC3; ++j) ad.K[i][j] = T(w.K[(i * NC3 + j) * B + e]);
+  for (int i = 0; i < m; ++i) {
+    ad.x[i] = T(w.ax[i * B + e]);
+    ad.z[i] = T(w.az[i * B + e]);
+    ad.y[i] = T(w.ay[i * B + e]);
+    ad.sx[i] = T(w.asx[i * B + e]);
+  }
+  int iters = w.iters[e];
+  const T te = T(stage_eps<T>(a, w.stage[e]));
+  bool conv = false;
+  for (int k = 0; k < a.round_cap && iters < a.admm_max_iter; ++k) {
+    ++iters;
+    if (ad.iterate(p, te)) { conv = true; break; }
+  }
+  for (int i = 0; i < m; ++i) {
+    w.ax[i * B + e] = double(ad.x[i]);
+    w.az[i * B + e] = double(ad.z[i]);
+    w.ay[i * B + e] = double(ad.y[i]);
+    w.asx[i * B + e] = double(ad.sx[i]);
+  }
+  w.iters[e] = iters;
+  if (conv || iters >= a.admm_max_iter || a.final_round) {
+    const int k = ds_atomic_add(&w.ncounts[a.round], 1);
+    w.nlist[k] = e;
+  } else {
+    const int k = ds_atomic_add(&w.counts[a.round + 1], 1);
+    w.list[(a.round + 1) & 1][k] = e;
+  }
+}
+
+// 3. finish: F1-F6 again (recomputed, bitwise identical), then F9 and the derivatives with lambda
+//    and the modes from the workspace.
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e) {
+  Env<NB, NV, NS, T> s;
+  env_forward<NB, NV, NS, T>(m, a, e, s);
+  const WsView& w = a.ws;
+  const int B = a.B;
+  const int mm = 3 * s.na;
+  for (int i = 0; i < mm; ++i) s.lam[i] = w.lam[i * B + e];
+  if (mm > 0 && !(w.st[e] & DS_ENV_NONFINITE)) {
+    for (int i = 0; i < s.na; ++i) s.mode[i] = w.mode[i * B + e];
+  } else {
+    s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
+  }
+  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e]);
+}
+
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
+  __shared__ DevModel sm;
+  load_model(sm, a.model);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_env) return;
+  const int e = a.env_list ? a.env_list[t] : t;
+  if (a.model_id && a.model_id[e] != a.model_index) return;
+  finish_env<NB, NV, NS, T>(sm, a, e);
+}
+
+inline int ds_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
 template <int NB, int NV, int NS, typename T>
 void launch_env(const KArgs& a, cudaStream_t s) {
   const int threads = 128;
   const int blocks = (a.n_env + threads - 1) / threads;
   if (blocks > 0) env_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a);
+}
+
+template <int NB, int NV, int NS, typename T>
+void launch_pipeline(const KArgs& a0, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (a0.n_env + threads - 1) / threads;
+  if (blocks <= 0) return;
+  cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
+  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * DS_ROUNDS, s);
+  setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
+  static const int caps[DS_ROUNDS] = {32, 32, 64, 128, 256, 512, 1024, 2048, 4096};
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_round_kernel<NS, T>, threads, 0);
+  if (per_sm <= 0) per_sm = 1;
+  const int envs_per_block = threads / NS;
+  int rblocks = ds_sm_count() * per_sm;
+  const int need = (a0.n_env + envs_per_block - 1) / envs_per_block;
+  if (rblocks > need) rblocks = need;
+  int nper = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_kernel<NS, T>, threads, 0);
+  if (nper <= 0) nper = 1;
+  int nblocks = ds_sm_count() * nper;
+  if (nblocks > blocks) nblocks = blocks;
+  for (int r = 0; r < DS_ROUNDS; ++r) {
+    KArgs a = a0;
+    a.round = r;
+    a.round_cap = caps[r];
+    a.final_round = r == DS_ROUNDS - 1;
+    admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
+    newton_kernel<NS, T><<<nblocks, threads, 0, s>>>(a);
+  }
+  finish_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
 }
 
 }  // namespace ds

@@ -1,12 +1,14 @@
 // Table of compiled (bodies, dofs, contact slots, precision) shapes.
 #include "ds_common.cuh"
 
-#define DS_DECL(NB, NV, NS)                                          \
-  void ds_launch_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t); \
-  void ds_launch_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
-#define DS_ROW(NB, NV, NS)                                          \
-  {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64},        \
-  {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix},
+#define DS_DECL(NB, NV, NS)                                                \
+  void ds_launch_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);       \
+  void ds_launch_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);       \
+  void ds_pipeline_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);     \
+  void ds_pipeline_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
+#define DS_ROW(NB, NV, NS)                                                                        \
+  {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64, ds_pipeline_##NB##_##NV##_##NS##_f64}, \
+  {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix, ds_pipeline_##NB##_##NV##_##NS##_mix},
 
 #include "ds_shapes.inc"
 

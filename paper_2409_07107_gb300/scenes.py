@@ -100,7 +100,7 @@ class Batch:
                     c_mu=self.c_mu[:, e].copy(), plane=self.plane[:, e].copy())
 
     def take(self, idx) -> "Batch":
-        idx = np.asarray(idx)
+        idx = np.asarray(idx, dtype=np.int64)
         return Batch(self.q[:, idx].copy(), self.v[:, idx].copy(), self.tau[:, idx].copy(),
                      self.c_link[:, idx].copy(), self.c_point[:, :, idx].copy(),
                      self.c_radius[:, idx].copy(), self.c_mu[:, idx].copy(), self.plane[:, idx].copy(),

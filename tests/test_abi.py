@@ -58,9 +58,7 @@ def test_model_create_rejects_bad_descriptions(L, kw):
 
 
 def test_model_create_rejects_non_preorder(L):
-    keep, d = _desc(nb=3, parent=(-1, 0, 0), jtype=(0, 0, 0))
-    # 3 bodies where body 2's parent is 0 is fine (preorder); make body 1 a child of 0 and 2 of 1 with
-    # a sibling order that breaks contiguity: parent = (-1, 0, 1) is fine too, so use 4 bodies
+    # body 3 is a child of body 1 but comes after body 2 (a child of 0): subtree of 1 not contiguous
     keep, d = _desc(nb=4, parent=(-1, 0, 0, 1), jtype=(0, 0, 0, 0))
     h = ctypes.c_void_p()
     assert L.ds_model_create(ctypes.byref(d), ctypes.byref(h)) == ds.DS_EINVAL
@@ -71,11 +69,15 @@ def test_step_rejects_bad_arguments(L):
     b = ds.ds_batch(4, 1, None, None, None, None, None, None, None, None, None)
     out = ds.ds_step_out(None, None, None, None, None, None)
     models = (ctypes.c_void_p * 1)(None)
-    assert L.sim_step(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None) == ds.DS_EINVAL
-    assert L.sim_step(None, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None) == ds.DS_EINVAL
+    assert L.sim_step(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, 0, None) == ds.DS_EINVAL
+    assert L.sim_step(None, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, 0, None) == ds.DS_EINVAL
+    n = ctypes.c_size_t()
+    assert L.ds_workspace_size(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(n)) == ds.DS_OK
+    assert n.value > 4 * 1000
     b.B = -1
     assert L.sim_step_jac(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, None, None,
-                          None) == ds.DS_EINVAL
+                          None, 0, None) == ds.DS_EINVAL
+    assert L.ds_workspace_size(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(n)) == ds.DS_EINVAL
     b.ncmax = 99
     assert L.sim_step_vjp(models, 1, ctypes.byref(b), ctypes.byref(o), None, ctypes.byref(out), None, None,
-                          None, None) == ds.DS_EINVAL
+                          None, None, 0, None) == ds.DS_EINVAL

@@ -168,3 +168,26 @@ def test_edge_cases(torch_cuda):
     assert rel_err(g1["v_next"][:, 0], r["v_next"]) <= 1e-9
     empty = ds.Simulator(scenes.Workload(wl.name, wl.models, wl.batch.take([]), wl.options))
     empty.step()
+
+
+def test_pipeline_matches_fused(torch_cuda):
+    """The workspace pipeline (setup, compacted ADMM rounds, finish) and the fused single kernel run
+    the same per-env arithmetic: results agree to rounding (identical iteration counts)."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(65536)
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(np.arange(2048)), wl.options)
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        outs = []
+        for pipeline in (False, True):
+            sim = ds.Simulator(sub, precision=prec, pipeline=pipeline)
+            o = sim.step_jac()
+            torch.cuda.synchronize()
+            outs.append({k: v.cpu().numpy().astype(float) for k, v in o.items()})
+        f, p = outs
+        assert (f["iters"] == p["iters"]).mean() >= 0.999
+        assert (f["modes"] == p["modes"]).mean() >= 0.999
+        for k in ("v_next", "dv_dq", "dv_dv", "dv_dtau"):
+            err = np.abs(f[k] - p[k]).max(axis=tuple(range(f[k].ndim - 1))) / np.maximum(
+                np.abs(f[k]).max(axis=tuple(range(f[k].ndim - 1))), 1e-6)
+            assert np.quantile(err, 0.999) <= tol, (prec, k, np.quantile(err, 0.999))
