@@ -46,7 +46,8 @@ typedef enum {
   DS_EINVAL = -1,        /* a NULL pointer, a size out of range, an unsupported model shape   */
   DS_ECUDA = -2,         /* a CUDA runtime call or kernel launch failed                         */
   DS_ENOMEM = -3,        /* ds_model_create could not allocate the model's device copy          */
-  DS_EUNSUPPORTED = -4   /* no compiled kernel for this (bodies, dofs, contact slots) shape     */
+  DS_EUNSUPPORTED = -4,  /* no compiled kernel for this (bodies, dofs, contact slots) shape     */
+  DS_ETOOLARGE = -5      /* batch too large for sim_step_jac_noalloc's fixed scratch           */
 } ds_status;
 
 typedef enum { DS_FP64 = 0, DS_MIXED = 1 } ds_precision;
@@ -154,6 +155,26 @@ ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_
                        size_t workspace_bytes, void* stream);
 
 const char* ds_status_string(ds_status s);
+
+/* Allocation-free sim_step_jac (no counterpart in the paper; a convenience of this library).
+ * Some callers cannot allocate device memory when they step the simulation: a real-time control
+ * loop that forbids allocation after start-up (allocation latency is unbounded), or a plug-in that
+ * does not own the process's CUDA memory.  This call computes exactly what sim_step_jac computes
+ * with a workspace, but takes that workspace from a fixed array of DS_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that the library holds on every device that loads it, until the process exits.  It
+ * calls no cudaMalloc / cudaFree and no allocating routine.
+ *   - Batches whose ds_workspace_size() exceeds the array are rejected with DS_ETOOLARGE
+ *     (about 6900 envs of the 7-dof arm with 4 contact slots).
+ *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress);
+ *     make that first call outside any stream capture.
+ *   - Every call shares the one array and leaves its contents behind; the counters that must
+ *     start at zero are cleared by each call.  Calls whose work overlaps on the GPU (different
+ *     streams, or host threads without ordering) race on the array: serialize them.
+ * Arguments, outputs and errors otherwise as for sim_step_jac. */
+#define DS_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                               const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
+                               double* dv_dtau, void* stream);
 
 /* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
  * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per

@@ -20,13 +20,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdiffsim.so")
 
-DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED = 0, -1, -2, -3, -4
+DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED, DS_ETOOLARGE = 0, -1, -2, -3, -4, -5
 DS_FP64, DS_MIXED = 0, 1
 MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
 ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH = 1, 2, 4, 8
 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
-           "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size")
+           "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
+           "sim_step_jac_noalloc")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -79,9 +80,10 @@ def lib():
         L.sim_step_jac.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
         L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
         L.ds_workspace_size.argtypes = common + [ctypes.POINTER(sz)]
+        L.sim_step_jac_noalloc.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
-                  "ds_fma_peak", "ds_workspace_size"):
+                  "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -181,6 +183,13 @@ def sim_step_jac(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, workspace=None,
     _check(lib().sim_step_jac(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
                               ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), *_ws(workspace),
                               _stream(stream)))
+
+
+def sim_step_jac_noalloc(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, stream=None):
+    """C-ABI sim_step_jac_noalloc: sim_step_jac with the library's fixed scratch, no allocation."""
+    b, o = _batch_struct(batch), _out_struct(out)
+    _check(lib().sim_step_jac_noalloc(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                                      ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), _stream(stream)))
 
 
 def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, workspace=None, stream=None):

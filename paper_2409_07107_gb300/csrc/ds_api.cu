@@ -34,6 +34,7 @@ extern "C" const char* ds_status_string(ds_status s) {
     case DS_ECUDA: return "CUDA error";
     case DS_ENOMEM: return "out of device memory";
     case DS_EUNSUPPORTED: return "no compiled kernel for this model shape";
+    case DS_ETOOLARGE: return "batch too large for the fixed scratch of sim_step_jac_noalloc";
   }
   return "unknown status";
 }
