@@ -36,66 +36,6 @@ def _peaks():
         return {}
 
 
-# ------------------------------------------------------------------------------------ flop model
-def step_flops(nb, nv, depth_dofs, subtree_bodies, na, m_red, iters, polish_iters_run, jac=True):
-    """Arithmetic (FMA = 2 flops) of one env-step of the kernel's algorithm, counted from its loops.
-
-    nb, nv: bodies / dofs; depth_dofs[d]: dofs on the path root..body(d) (incl. d);
-    subtree_bodies[d]: bodies in the subtree of dof d's body; na active contacts; m_red = size of
-    the reduced implicit system; iters ADMM iterations; polish_iters_run Newton steps."""
-    m = 3 * na
-    f = 0.0
-    f += nb * 340                     # placements, motion subspaces, world inertias
-    f += nb * 200                     # bias RNEA
-    f += sum(42 + 11 * dd for dd in depth_dofs) + 10 * nb    # composite inertia + M entries
-    f += nv ** 3 / 3 + 2 * nv ** 2 + 2 * nv                    # Cholesky of M and v_f
-    f += na * 27 * (sum(depth_dofs) / max(nv, 1))             # J_c rows
-    f += 2 * m * nv ** 2 + m * (m + 1) * nv + 2 * m * nv      # W, G, Y, g
-    if na:
-        f += m ** 3 / 3 + m * m                                # factor G + rho I
-        f += iters * (4 * m * m + 10 * m + 25 * na)            # ADMM iterations
-        f += polish_iters_run * (2 * m ** 3 / 3 + 6 * m * m)   # Newton steps on the mode equations
-        f += 3 * (4 * m * m + 60 * na)                         # residual / classification checks
-    f += 2 * m * nv                                            # v+
-    if not jac:
-        return f
-    f += nb * 120 + 2 * m * nv                                 # a* pass, contact forces, v+ velocities
-    f += (2.0 / 3.0) * m_red ** 3 + 4 * m_red * m_red          # reduced system and its LU
-    tq = sum(400 * s for s in subtree_bodies) + sum(11 * dd for dd in depth_dofs)
-    tv = sum(200 * s for s in subtree_bodies) + sum(11 * dd for dd in depth_dofs)
-    f += tq + tv                                               # tangent passes (2 nv directions)
-    f += 3 * nv * (2 * nv * nv)                                # M^-1 on 3 nv columns
-    f += 3 * nv * (m * 2 * nv + 2 * m_red * m_red + m * 2 * nv) + nv * na * 40   # RHS, solve, dv
-    return f
-
-
-def model_shape(model):
-    iv = model.iv
-    nd = [6 if t == scenes.FREEFLYER else 1 for t in model.jtype]
-    dof_body = [i for i in range(model.nb) for _ in range(nd[i])]
-    sub = []
-    for i in range(model.nb):
-        e = i + 1
-        while e < model.nb:
-            b = e
-            while b > i:
-                b = model.parent[b]
-            if b != i:
-                break
-            e += 1
-        sub.append(e - i)
-    depth = []
-    for d in range(model.nv):
-        b = dof_body[d]
-        n = (d - iv[b]) + 1
-        b = model.parent[b]
-        while b >= 0:
-            n += nd[b]
-            b = model.parent[b]
-        depth.append(n)
-    return depth, [sub[dof_body[d]] for d in range(model.nv)]
-
-
 # ---------------------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -184,22 +124,29 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--envs", type=int, default=WORKLOAD_B)
+    ap.add_argument("--envs", type=int, default=None)
+    ap.add_argument("--workload", default="arm7-cube", choices=["arm7-cube", "humanoid36-feet", "quadruped18-feet"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
-    B = args.envs
-    wl_name = "arm7-cube"
-    cfg = {"workload": "%s: 7-dof arm + 0.05 m cube, 4 corner contacts, %d envs per GPU, dt=1e-3" % (wl_name, B),
+    wl_name = args.workload
+    B = args.envs or {"arm7-cube": WORKLOAD_B, "humanoid36-feet": 16384, "quadruped18-feet": 32768}[wl_name]
+    desc = {"arm7-cube": "7-dof arm + 0.05 m cube, 4 corner contacts",
+            "humanoid36-feet": "36-dof humanoid (free-flyer + 30 joints), 2 box feet, 0-8 corner contacts",
+            "quadruped18-feet": "18-dof quadruped (free-flyer + 12 joints), 4 point feet"}[wl_name]
+    cfg = {"workload": "%s: %s, %d envs per GPU, dt=1e-3" % (wl_name, desc, B),
            "envs_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)"}
+    make = {"arm7-cube": lambda n, r: scenes.arm_cube(n, seed=1001 + r * 7919),
+            "humanoid36-feet": lambda n, r: scenes.humanoid_feet(n, seed=1002 + r * 7919),
+            "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=1004 + r * 7919)}[wl_name]
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        wl = scenes.arm_cube(B)
+        wl = make(B, 0)
         rate, procs, n, dt = cpu_oracle_rate(wl, seconds=max(5.0, 12.0 * args.steps / 20.0))
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / rate, "higher_is_better": True,
@@ -220,7 +167,7 @@ def main():
     build.build()
     ds.lib()
     dev = torch.cuda.current_device()
-    wl = scenes.arm_cube(B, seed=1001 + rank * 7919)
+    wl = make(B, rank)
     peaks = _peaks()
 
     # measured CUDA-core FMA peaks (the path is bound by plain FP64 / FP32 arithmetic)
@@ -245,6 +192,8 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
+        ds.profile(True)
+        ds.profile_read()
         times = []
         with ClockSampler(dev) as clk:
             for _ in range(args.steps):
@@ -255,6 +204,8 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
+        stages = ds.profile_read()
+        ds.profile(False)
         if world > 1:
             t = torch.tensor([sum(times)], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -263,33 +214,38 @@ def main():
             total_ms = sum(times)
         ms = total_ms / args.steps
         out = sim.out
-        iters = out["iters"].cpu().numpy()
+        iters = out["iters"].cpu().numpy().astype(np.int64)
         modes = out["modes"].cpu().numpy()
         status = out["status"].cpu().numpy()
-        # algorithmic flops per launch from the per-env ADMM iteration counts and contact modes
-        m = wl.models[0]
-        depth, subtree = model_shape(m)
         na = (modes != 3).sum(0)
-        nstk = (modes == 1).sum(0)
-        nsld = (modes == 2).sum(0)
-        mred = 3 * nstk + 2 * nsld
-        fl = 0.0
-        for k in np.unique(np.stack([na, mred, np.minimum(iters, 10 ** 6)]), axis=1).T:
-            sel = (na == k[0]) & (mred == k[1]) & (iters == k[2])
-            fl += sel.sum() * step_flops(m.nb, m.nv, depth, subtree, int(k[0]), int(k[1]), int(k[2]), 2)
+        m = 3 * na
+        # algorithmic flops of the ADMM rounds: per env-iteration, the x-step (K times rhs, 2 m^2)
+        # plus the right-hand side, De Saxce term, relaxation, projection and dual step (30 m)
+        admm_flops = float(np.sum(iters * (2.0 * m * m + 30.0 * m)))
+        stage_ms = {k: v[0] / args.steps for k, v in stages.items() if v[1]}
+        stage_launches = {k: v[1] // args.steps for k, v in stages.items() if v[1]}
+        t_admm = stage_ms.get("admm", float("nan"))
         peak = fma["fp64"] if prec == "fp64" else fma["fp32"]
-        achieved = fl / (ms * 1e-3) / 1e12
-        results[prec] = dict(ms=ms, value=B * world / (total_ms / args.steps * 1e-3), clocks=clk.summary(),
-                             roofline={"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                       "frac": achieved / peak, "traffic": None,
-                                       "peak_source": "measured FMA probe (%s CUDA cores) in this run" % ("FP64" if prec == "fp64" else "FP32")},
-                             admm_iters={"mean": float(iters.mean()), "p50": float(np.median(iters)),
-                                         "p99": float(np.percentile(iters, 99)), "max": int(iters.max())},
-                             modes={"breaking": int((modes == 0).sum()), "sticking": int((modes == 1).sum()),
-                                    "sliding": int((modes == 2).sum())},
-                             status={"not_converged": int((status & 1 != 0).sum()), "nonfinite": int((status & 2 != 0).sum()),
-                                     "singular": int((status & 4 != 0).sum()), "near_switch": int((status & 8 != 0).sum())},
-                             gflop_per_step=fl / 1e9)
+        achieved = admm_flops / (t_admm * 1e-3) / 1e12
+        dominant = max(stage_ms, key=stage_ms.get) if stage_ms else None
+        results[prec] = dict(
+            ms=ms, value=B * world / (ms * 1e-3), clocks=clk.summary(),
+            roofline={"bound": "alu", "kernel": "admm_round_kernel (ADMM rounds, one lane per contact)",
+                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                      "traffic": None,
+                      "peak_source": "measured FMA probe (%s CUDA cores) in this run" % ("FP64" if prec == "fp64" else "FP32"),
+                      "algorithmic_gflop_per_step": admm_flops / 1e9,
+                      "launches_per_step": stage_launches.get("admm"),
+                      "avg_launch_ms": t_admm / max(stage_launches.get("admm", 1), 1)},
+            stages={k: {"ms_per_step": v, "share": v / ms, "launches_per_step": stage_launches[k]} for k, v in stage_ms.items()},
+            dominant_stage=dominant,
+            admm_iters={"mean": float(iters.mean()), "p50": float(np.median(iters)),
+                        "p99": float(np.percentile(iters, 99)), "max": int(iters.max())},
+            modes={"breaking": int((modes == 0).sum()), "sticking": int((modes == 1).sum()),
+                   "sliding": int((modes == 2).sum())},
+            status={"not_converged": int((status & 1 != 0).sum()), "nonfinite": int((status & 2 != 0).sum()),
+                    "singular": int((status & 4 != 0).sum()), "near_switch": int((status & 8 != 0).sum())},
+            launches=sum(stage_launches.values()))
         del sim
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
@@ -334,10 +290,11 @@ def main():
                 "clocks": r64["clocks"], "roofline": r64["roofline"],
                 "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": args.steps * (2 + 2 * 9), "cpu_baseline": cpu,
+                "gpu_launches": args.steps * r64["launches"], "cpu_baseline": cpu,
+                "stages": r64["stages"], "dominant_stage": r64["dominant_stage"],
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
-                "gflop_per_step": r64["gflop_per_step"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],
+                          "stages": rmx["stages"], "dominant_stage": rmx["dominant_stage"],
                           "clocks": rmx["clocks"], "admm_iters": rmx["admm_iters"], "modes": rmx["modes"],
                           "env_status": rmx["status"]},
                 "fma_peak_tflops": fma, "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}}

@@ -176,6 +176,14 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
                                const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
                                double* dv_dtau, void* stream);
 
+/* Stage tracing (no counterpart in the paper): with ds_profile(1), every kernel the library
+ * launches is bracketed by CUDA events on its own stream, grouped in DS_NSTAGES = 5 classes:
+ * 0 setup, 1 ADMM rounds, 2 Newton / active-set, 3 finish (step update + derivatives), 4 fused
+ * single-kernel path.  ds_profile_read waits for the recorded events, writes the summed
+ * milliseconds and launch counts per class to ms[5], launches[5], and clears the record. */
+ds_status ds_profile(int32_t enable);
+ds_status ds_profile_read(double* ms, int32_t* launches);
+
 /* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
  * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per
  * thread to out[blocks*256] (device, FP64).  Used to measure the CUDA-core FMA peak that bounds

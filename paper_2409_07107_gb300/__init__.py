@@ -27,7 +27,7 @@ ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH = 1, 2, 4, 8
 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
-           "sim_step_jac_noalloc")
+           "sim_step_jac_noalloc", "ds_profile", "ds_profile_read")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -81,9 +81,11 @@ def lib():
         L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
         L.ds_workspace_size.argtypes = common + [ctypes.POINTER(sz)]
         L.sim_step_jac_noalloc.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
+        L.ds_profile.argtypes = [i32]
+        L.ds_profile_read.argtypes = [vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
-                  "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc"):
+                  "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -202,6 +204,22 @@ def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, wor
 def fma_peak(out, blocks, iters, fp64, stream=None):
     """Launch the FMA-throughput probe (2 * 8 * iters * blocks * 256 flops)."""
     _check(lib().ds_fma_peak(_ptr(out), blocks, iters, 1 if fp64 else 0, _stream(stream)))
+
+
+STAGES = ("setup", "admm", "newton", "finish", "fused")
+
+
+def profile(enable):
+    """Turn stage tracing (CUDA events around every library kernel) on or off."""
+    _check(lib().ds_profile(1 if enable else 0))
+
+
+def profile_read():
+    """{stage: (milliseconds, launches)} since the last read; waits for the recorded events."""
+    ms = (ctypes.c_double * 5)()
+    n = (ctypes.c_int32 * 5)()
+    _check(lib().ds_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p)))
+    return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
 
 
 def batch_to_device(batch, device="cuda"):

@@ -115,6 +115,11 @@ struct KArgs {
 
 typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);
 
+// Stage tracing: when enabled, the launchers bracket every kernel with events on its stream.
+enum { DS_STAGE_SETUP = 0, DS_STAGE_ADMM = 1, DS_STAGE_NEWTON = 2, DS_STAGE_FINISH = 3, DS_STAGE_FUSED = 4,
+       DS_NSTAGES = 5 };
+void ds_trace_mark(int stage, int begin, cudaStream_t s);   // no-op unless tracing is on
+
 // Registry of compiled shapes: (bodies, dofs, contact slots, precision) -> launchers of the fused
 // kernel and of the workspace pipeline.
 struct ds_kernel_entry {
