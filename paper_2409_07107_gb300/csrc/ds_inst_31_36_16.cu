@@ -1,5 +1,5 @@
 // Kernel instantiation for 31 bodies, 36 dofs, 16 contact slots (FP64 and mixed precision).
-#include "ds_kernel.cuh"
+#include "ds_launch.cuh"
 
 void ds_launch_31_36_16_f64(const KArgs& a, cudaStream_t s) { ds::launch_env<31, 36, 16, double>(a, s); }
 void ds_launch_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<31, 36, 16, float>(a, s); }

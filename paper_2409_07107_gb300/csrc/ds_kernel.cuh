@@ -1445,65 +1445,4 @@ __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
   finish_env<NB, NV, NS, T>(sm, a, e);
 }
 
-inline int ds_sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
-template <int NB, int NV, int NS, typename T>
-void launch_env(const KArgs& a, cudaStream_t s) {
-  const int threads = 128;
-  const int blocks = (a.n_env + threads - 1) / threads;
-  if (blocks <= 0) return;
-  ds_trace_mark(DS_STAGE_FUSED, 1, s);
-  env_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a);
-  ds_trace_mark(DS_STAGE_FUSED, 0, s);
-}
-
-template <int NB, int NV, int NS, typename T>
-void launch_pipeline(const KArgs& a0, cudaStream_t s) {
-  const int threads = 128;
-  const int blocks = (a0.n_env + threads - 1) / threads;
-  if (blocks <= 0) return;
-  cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
-  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * DS_ROUNDS, s);
-  ds_trace_mark(DS_STAGE_SETUP, 1, s);
-  setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
-  ds_trace_mark(DS_STAGE_SETUP, 0, s);
-  static const int caps[DS_ROUNDS] = {32, 32, 64, 128, 256, 512, 1024, 2048, 4096};
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_round_kernel<NS, T>, threads, 0);
-  if (per_sm <= 0) per_sm = 1;
-  const int envs_per_block = threads / NS;
-  int rblocks = ds_sm_count() * per_sm;
-  const int need = (a0.n_env + envs_per_block - 1) / envs_per_block;
-  if (rblocks > need) rblocks = need;
-  int nper = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_kernel<NS, T>, threads, 0);
-  if (nper <= 0) nper = 1;
-  int nblocks = ds_sm_count() * nper;
-  if (nblocks > blocks) nblocks = blocks;
-  for (int r = 0; r < DS_ROUNDS; ++r) {
-    KArgs a = a0;
-    a.round = r;
-    a.round_cap = caps[r];
-    a.final_round = r == DS_ROUNDS - 1;
-    ds_trace_mark(DS_STAGE_ADMM, 1, s);
-    admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
-    ds_trace_mark(DS_STAGE_ADMM, 0, s);
-    ds_trace_mark(DS_STAGE_NEWTON, 1, s);
-    newton_kernel<NS, T><<<nblocks, threads, 0, s>>>(a);
-    ds_trace_mark(DS_STAGE_NEWTON, 0, s);
-  }
-  ds_trace_mark(DS_STAGE_FINISH, 1, s);
-  finish_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
-  ds_trace_mark(DS_STAGE_FINISH, 0, s);
-}
-
 }  // namespace ds

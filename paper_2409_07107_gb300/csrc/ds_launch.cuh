@@ -1,0 +1,81 @@
+// Host launchers of the fused kernel and of the workspace pipeline (setup, compacted ADMM rounds
+// with their Newton stages, finish).
+#pragma once
+#include "ds_newton_coop.cuh"
+
+namespace ds {
+
+inline int ds_sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int NB, int NV, int NS, typename T>
+void launch_env(const KArgs& a, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (a.n_env + threads - 1) / threads;
+  if (blocks <= 0) return;
+  ds_trace_mark(DS_STAGE_FUSED, 1, s);
+  env_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a);
+  ds_trace_mark(DS_STAGE_FUSED, 0, s);
+}
+
+template <int NB, int NV, int NS, typename T>
+void launch_pipeline(const KArgs& a0, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (a0.n_env + threads - 1) / threads;
+  if (blocks <= 0) return;
+  cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
+  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * DS_ROUNDS, s);
+  ds_trace_mark(DS_STAGE_SETUP, 1, s);
+  setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
+  ds_trace_mark(DS_STAGE_SETUP, 0, s);
+  static const int caps[DS_ROUNDS] = {32, 32, 64, 128, 256, 512, 1024, 2048, 4096};
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_round_kernel<NS, T>, threads, 0);
+  if (per_sm <= 0) per_sm = 1;
+  const int envs_per_block = threads / NS;
+  int rblocks = ds_sm_count() * per_sm;
+  const int need = (a0.n_env + envs_per_block - 1) / envs_per_block;
+  if (rblocks > need) rblocks = need;
+  // Newton stage: the cooperative kernel (4 NS lanes per env) where 4 NS divides the warp, else
+  // one thread per env.
+  constexpr bool kCoop = 32 % (4 * NS) == 0;
+  const int nthreads = kCoop ? coop::Shape<kCoop ? NS : 1>::THREADS : threads;
+  const int envs_per_nblock = kCoop ? nthreads / (4 * NS) : nthreads;
+  int nper = 0;
+  if constexpr (kCoop)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_coop_kernel<NS, T>, nthreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_kernel<NS, T>, nthreads, 0);
+  if (nper <= 0) nper = 1;
+  int nblocks = ds_sm_count() * nper;
+  const int nneed = (a0.n_env + envs_per_nblock - 1) / envs_per_nblock;
+  if (nblocks > nneed) nblocks = nneed;
+  for (int r = 0; r < DS_ROUNDS; ++r) {
+    KArgs a = a0;
+    a.round = r;
+    a.round_cap = caps[r];
+    a.final_round = r == DS_ROUNDS - 1;
+    ds_trace_mark(DS_STAGE_ADMM, 1, s);
+    admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
+    ds_trace_mark(DS_STAGE_ADMM, 0, s);
+    ds_trace_mark(DS_STAGE_NEWTON, 1, s);
+    if constexpr (kCoop)
+      newton_coop_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
+    else
+      newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
+    ds_trace_mark(DS_STAGE_NEWTON, 0, s);
+  }
+  ds_trace_mark(DS_STAGE_FINISH, 1, s);
+  finish_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
+  ds_trace_mark(DS_STAGE_FINISH, 0, s);
+}
+
+}  // namespace ds
