@@ -4,7 +4,8 @@
 Workload (default): 65536 envs of a 7-dof fixed-base arm with a 0.05 m cube at the tip, 4 corner
 contacts on a plane, mu ~ U(0.2, 1.0), half the envs set up to stick and half to slide, dt = 1e-3.
 One "step" = one sim_step_jac call over the whole batch (forward step, NCP solve, implicit
-derivatives, all three Jacobians written).  The headline value is the plain FP64 method; the same
+derivatives, all three Jacobians written); with --workload uneven (a batch that mixes the arm, the
+quadruped and the humanoid) one sim_step_vjp call.  The headline value is the plain FP64 method; the same
 line carries the mixed-precision form (FP32 bulk, FP64 polish / residual / reduced system).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -26,6 +27,7 @@ from paper_2409_07107_gb300 import scenes  # noqa: E402
 
 WORKLOAD_B = 65536
 METRIC = "env-steps/s with full dv'/d(q,v,tau) at 1 GB300"
+METRIC_VJP = "env-steps/s with the VJP of the step at 1 GB300"
 
 
 def _peaks():
@@ -93,21 +95,25 @@ class ClockSampler:
 def _oracle_one(args):
     model, env, opt = args
     from oracle import step as S
-    S.step_jac(model, env, opt)
+    S.step_jac(model, env, opt)     # the VJP of the uneven workload is a product with this Jacobian
     return 1
 
 
 def cpu_oracle_rate(wl, n_envs=None, seconds=20.0, processes=None):
     """Oracle env-steps/s (step + full Jacobian) on the host cores, on a bounded sample."""
     import multiprocessing as mp
-    m = wl.models[0]
     procs = processes or os.cpu_count() or 1
+
+    def model_of(e):
+        return wl.models[0 if wl.batch.model_id is None else int(wl.batch.model_id[e])]
+
     if n_envs is None:
         t0 = time.perf_counter()
-        _oracle_one((m, wl.batch.env(0, m), wl.options))
-        per = max(time.perf_counter() - t0, 1e-3)
+        for e in range(len(wl.models)):
+            _oracle_one((model_of(e), wl.batch.env(e, model_of(e)), wl.options))
+        per = max((time.perf_counter() - t0) / len(wl.models), 1e-3)
         n_envs = int(max(procs, min(wl.batch.B, seconds * procs / per)))
-    args = [(m, wl.batch.env(e, m), wl.options) for e in range(n_envs)]
+    args = [(model_of(e), wl.batch.env(e, model_of(e)), wl.options) for e in range(n_envs)]
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
         pool.map(_oracle_one, args[:procs])        # warm the workers
@@ -115,6 +121,80 @@ def cpu_oracle_rate(wl, n_envs=None, seconds=20.0, processes=None):
         pool.map(_oracle_one, args, chunksize=max(1, n_envs // (4 * procs)))
         dt = time.perf_counter() - t0
     return n_envs / dt, procs, n_envs, dt
+
+
+# -------------------------------------------------------------------------------------- rollout
+def bench_rollout(args, rank, world):
+    """Gradient of a T-step rollout loss w.r.t. all joint torques (forward + reverse pass), the
+    quadruped standing on the ground; with segment recomputation every 20 steps and with every
+    step's inputs kept.  One timed step = one full rollout forward + backward."""
+    import torch
+    import paper_2409_07107_gb300 as ds
+    from paper_2409_07107_gb300 import build, rollout as R
+    build.build()
+    ds.lib()
+    B, T, every = args.envs or 4096, args.horizon, 20
+    wl = scenes.quadruped_feet(B, seed=1004 + rank * 7919)
+    rng = np.random.default_rng(21 + rank)
+    dev = dict(dtype=torch.float64, device="cuda")
+    nv = wl.batch.v.shape[0]
+    mask = torch.ones(1, nv, 1, **dev)
+    mask[:, :6] = 0.0                                    # no actuation of the floating base
+    tau0 = torch.tensor(rng.normal(size=(T, nv, B)) * 2.0, **dev) * mask
+    q0, v0 = torch.tensor(wl.batch.q, **dev), torch.tensor(wl.batch.v, **dev)
+    sc = R.StepContext(wl, precision="fp64")
+    with torch.no_grad():                                 # reachable goal: a perturbed-torque rollout
+        goal, _ = R.rollout(sc, q0, v0, list(tau0 + torch.tensor(rng.normal(size=(T, nv, B)) * 0.5, **dev) * mask), 0)
+
+    def one(ev):
+        tau = tau0.clone().requires_grad_(True)
+        qT, _ = R.rollout(sc, q0, v0, list(tau * mask), ev)
+        loss = ((qT - goal) ** 2).sum()
+        loss.backward()
+        return tau.grad
+
+    res = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for ev in (every, 0):
+        for _ in range(args.warmup):
+            one(ev)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        times = []
+        ds.profile(True)
+        ds.profile_read()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                one(ev)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+        # library kernels counted by the stage tracer, plus the two cotangent-map kernels per reverse step
+        launches = sum(n for _, n in ds.profile_read().values()) + 2 * T * args.steps
+        ds.profile(False)
+        ms = float(np.mean(times))
+        res[ev] = {"ms_per_rollout": ms, "value": B * T / (ms * 1e-3),
+                   "peak_extra_mib": (torch.cuda.max_memory_allocated() - base) / 2 ** 20, "clocks": clk.summary(),
+                   "launches": launches}
+    r = res[every]
+    line = {"metric": "rollout env-steps/s, forward + reverse pass (d loss / d tau_t) at 1 GB300", "value": r["value"],
+            "unit": "env-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms_per_rollout"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "quadruped18-rollout: 18-dof quadruped, 4 point feet, %d envs, T=%d steps, "
+                                   "loss = sum |q_T - q_goal|^2 (raw q), checkpoint every %d steps" % (B, T, every),
+                       "envs_per_gpu": B, "horizon": T, "l2": "flushed between timed rollouts (256 MiB write)"},
+            "clocks": r["clocks"], "peak_extra_mib": r["peak_extra_mib"],
+            "no_recompute": {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_rollout"],
+                             "peak_extra_mib": res[0]["peak_extra_mib"]},
+            "gpu_launches": r["launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 # ------------------------------------------------------------------------------------------ main
@@ -125,30 +205,46 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=None)
-    ap.add_argument("--workload", default="arm7-cube", choices=["arm7-cube", "humanoid36-feet", "quadruped18-feet"])
+    ap.add_argument("--workload", default="arm7-cube", choices=["arm7-cube", "humanoid36-feet", "quadruped18-feet", "uneven",
+                                                         "quadruped18-rollout"])
+    ap.add_argument("--horizon", type=int, default=200, help="rollout length (quadruped18-rollout)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if args.workload == "quadruped18-rollout":
+        if args.impl != "reference":
+            return bench_rollout(args, rank, world)
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single steps; the rollout "
+                              "workload has no CPU arm"}), flush=True)
+        return 0
     wl_name = args.workload
-    B = args.envs or {"arm7-cube": WORKLOAD_B, "humanoid36-feet": 16384, "quadruped18-feet": 32768}[wl_name]
+    B = args.envs or {"arm7-cube": WORKLOAD_B, "humanoid36-feet": 16384, "quadruped18-feet": 32768,
+                      "uneven": 32768}[wl_name]
+    vjp = wl_name == "uneven"          # the mixed-robot batch is timed with sim_step_vjp
+    metric = METRIC_VJP if vjp else METRIC
     desc = {"arm7-cube": "7-dof arm + 0.05 m cube, 4 corner contacts",
             "humanoid36-feet": "36-dof humanoid (free-flyer + 30 joints), 2 box feet, 0-8 corner contacts",
-            "quadruped18-feet": "18-dof quadruped (free-flyer + 12 joints), 4 point feet"}[wl_name]
+            "quadruped18-feet": "18-dof quadruped (free-flyer + 12 joints), 4 point feet",
+            "uneven": "mixed batch, envs interleaved: 7-dof arm + cube (8 slots), 18-dof quadruped (4 feet), "
+                      "36-dof humanoid (8 foot + 8 hand corners); 16 slots per env; step + VJP with "
+                      "v_bar ~ N(0, 1)"}[wl_name]
     cfg = {"workload": "%s: %s, %d envs per GPU, dt=1e-3" % (wl_name, desc, B),
            "envs_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)"}
     make = {"arm7-cube": lambda n, r: scenes.arm_cube(n, seed=1001 + r * 7919),
             "humanoid36-feet": lambda n, r: scenes.humanoid_feet(n, seed=1002 + r * 7919),
-            "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=1004 + r * 7919)}[wl_name]
+            "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=1004 + r * 7919),
+            "uneven": lambda n, r: scenes.uneven(n, seed=1003 + r * 7919)}[wl_name]
 
     if args.impl == "reference":
         if rank != 0:
             return 0
         wl = make(B, 0)
         rate, procs, n, dt = cpu_oracle_rate(wl, seconds=max(5.0, 12.0 * args.steps / 20.0))
-        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
+        line = {"impl": "reference", "metric": metric, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / rate, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
                 "cpu_baseline": {"value": rate, "unit": "env-steps/s", "cores": procs, "kind": "oracle",
@@ -184,11 +280,17 @@ def main():
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     results = {}
+    vbar = torch.as_tensor(np.random.default_rng(17 + rank).normal(size=wl.batch.v.shape), dtype=torch.float64,
+                           device="cuda")
+
+    def one_step(sim):
+        return sim.step_vjp(vbar) if vjp else sim.step_jac()
+
     for prec in ("fp64", "mixed"):
         sim = ds.Simulator(wl, precision=prec)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
-            sim.step_jac()
+            one_step(sim)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -200,7 +302,7 @@ def main():
                 flush.fill_(1.0)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                sim.step_jac()
+                one_step(sim)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -250,12 +352,15 @@ def main():
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
     sim = ds.Simulator(wl, precision="fp64")
-    host_in = {k: v.cpu().pin_memory() for k, v in sim.batch.items()}
+    host_in = {k: v.cpu().pin_memory() for k, v in sim.batch.items() if k != "model_slots"}
     host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
                 for k, v in [("v_next", sim.out["v_next"]), ("q_next", sim.out["q_next"]), ("status", sim.out["status"])]}
-    jac0 = sim.step_jac()
-    host_jac = [torch.empty(jac0[k].shape, dtype=torch.float64, pin_memory=True) for k in ("dv_dq", "dv_dv", "dv_dtau")]
-    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    dkeys = ("q_bar", "v_bar", "tau_bar") if vjp else ("dv_dq", "dv_dv", "dv_dtau")
+    if vjp:
+        host_in["vbar"] = vbar.cpu().pin_memory()
+    jac0 = one_step(sim)
+    host_jac = [torch.empty(jac0[k].shape, dtype=torch.float64, pin_memory=True) for k in dkeys]
+    h2d = sum(v.numel() * v.element_size() for k, v in host_in.items() if k != "model_slots")
     d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + sum(v.numel() * 8 for v in host_jac)
     stream = torch.cuda.current_stream()
     e2e_ms = []
@@ -264,11 +369,14 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k, v in host_in.items():
-            sim.batch[k].copy_(v, non_blocking=True)
-        r = sim.step_jac()
+            if k == "vbar":
+                vbar.copy_(v, non_blocking=True)
+            elif k != "model_slots":
+                sim.batch[k].copy_(v, non_blocking=True)
+        r = one_step(sim)
         for k, v in host_out.items():
             v.copy_(r[k], non_blocking=True)
-        for hj, k in zip(host_jac, ("dv_dq", "dv_dv", "dv_dtau")):
+        for hj, k in zip(host_jac, dkeys):
             hj.copy_(r[k], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -284,7 +392,7 @@ def main():
 
     if rank == 0:
         r64, rmx = results["fp64"], results["mixed"]
-        line = {"metric": METRIC, "value": r64["value"], "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric, "value": r64["value"], "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r64["ms"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
                 "clocks": r64["clocks"], "roofline": r64["roofline"],

@@ -26,7 +26,9 @@
  *     (e_y instead of e_x when |n_x| > 0.9), t2 = n x t1, normal last;
  *   - lambda [3*ncmax][B]: contact IMPULSES per slot (0 for inactive slots);
  *   - modes [ncmax][B]: DS_MODE_* per slot;
- *   - Jacobians dv_dq, dv_dv, dv_dtau [nv][nv][B]: element (row i, col j) at (i*nv + j)*B + e.
+ *   - Jacobians dv_dq, dv_dv, dv_dtau [nv][nv][B]: element (row i, col j) at (i*nv + j)*B + e;
+ *   - a batch may mix models (model_id): each env reads and writes the leading nq / nv rows of
+ *     the arrays for its own model.
  * All calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL = default
  * stream).  The return code reports argument and launch errors only; per-environment numerical
  * outcomes go to env_status.  Inputs are never modified.
@@ -61,6 +63,7 @@ enum { DS_MODE_BREAKING = 0, DS_MODE_STICKING = 1, DS_MODE_SLIDING = 2, DS_MODE_
 #define DS_ENV_NONFINITE     2u  /* NaN/Inf in the inputs or the results of this env            */
 #define DS_ENV_SINGULAR      4u  /* the reduced implicit system was rank deficient (basic solution used) */
 #define DS_ENV_NEAR_SWITCH   8u  /* mode-classification margin below margin_delta               */
+#define DS_ENV_BAD_SLOT     16u  /* a contact slot beyond the model's declared slot count is in use */
 
 /* Host description of a kinematic tree; copied by ds_model_create (the caller keeps ownership).
  * Bodies are numbered in depth-first preorder (parent[i] < i and every subtree is a contiguous
@@ -97,6 +100,12 @@ typedef struct {
   const double* c_radius;    /* [ncmax][B]  */
   const double* c_mu;        /* [ncmax][B]  */
   const double* plane;       /* [4][B]      */
+  const int32_t* model_slots; /* HOST array [nmodels] or NULL: envs of models[k] use only the
+                               * leading model_slots[k] (0..ncmax) slots, the rest hold -1.  Lets a
+                               * batch that mixes robots (ncmax set by the one with most contacts)
+                               * run every model with a kernel sized for its own contact count;
+                               * NULL = ncmax for every model.  A used slot at or beyond the
+                               * declared count is ignored and flagged DS_ENV_BAD_SLOT.          */
 } ds_batch;
 
 typedef struct {
@@ -128,11 +137,14 @@ typedef struct {
  * (about 1.4 KB per env with 4 contact slots).  With a workspace the step runs as a pipeline of
  * kernels (setup, NCP solve in compacted ADMM rounds, finish) that keeps warps busy when the
  * per-env iteration counts differ; without one (workspace = NULL) a single fused kernel does
- * everything.  Both give bitwise-identical results.  Errors: DS_EINVAL. */
+ * everything.  Both compute the same step; they differ only by rounding (the NCP solve is
+ * organised differently across kernels).  Errors: DS_EINVAL. */
 ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                             const ds_options* opt, size_t* bytes);
 
-/* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e.  workspace:
+/* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e; the kernel of a
+ * model is the compiled shape (bodies, dofs, slots S) with model_slots[k] <= S <= ncmax and the
+ * fewest slots (DS_EUNSUPPORTED if none).  Models run one after the other on the stream.  workspace:
  * NULL, or caller-owned device memory of at least ds_workspace_size() bytes (aligned to 256 bytes),
  * not used concurrently by another call. */
 ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
@@ -148,13 +160,33 @@ ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels, const ds_
 
 /* Vector-Jacobian product (reverse mode, the OptNet-style adjoint of Sec. 3.1): given
  * v_next_bar [nv_max][B], writes q_bar (tangent), v_bar, tau_bar [nv_max][B] =
- * (dv+/d(q, v, tau))^T v_next_bar without forming the Jacobians.  Also fills *out like sim_step. */
+ * (dv+/d(q, v, tau))^T v_next_bar without forming the Jacobians.  Also fills *out like sim_step.
+ * q_next_bar [nv_max][B] (may be NULL): a cotangent of q+ as well, in the tangent coordinates at
+ * q+ (the free-flyer's (linear, angular) in its own frame).  The adjoint of the position update
+ * q+ = q (+) dt v+ (symplectic Euler, Sec. 2.3) is then chained in: the step's outputs get the
+ * cotangent of (q+, v+) jointly, which is what a rollout's backward pass passes from step to step. */
 ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
-                       const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
-                       double* q_bar, double* v_bar, double* tau_bar, void* workspace,
-                       size_t workspace_bytes, void* stream);
+                       const ds_options* opt, const double* v_next_bar, const double* q_next_bar,
+                       const ds_step_out* out, double* q_bar, double* v_bar, double* tau_bar,
+                       void* workspace, size_t workspace_bytes, void* stream);
 
 const char* ds_status_string(ds_status s);
+
+/* Cotangent coordinate maps for the configuration (the derivative convention above: q (+) eta with
+ * position += R eta_lin and quaternion <- quaternion * exp(eta_ang / 2), Sec. 2.3's integrator on
+ * the configuration manifold).  Callers whose losses are written in the raw coordinates of q
+ * (nq numbers per env, quaternion included) use them at the two ends of a reverse pass:
+ *   ds_cotangent_to_tangent: q_bar_tangent [nv_max][B] = (dq_raw/deta)^T q_bar_raw [nq_max][B];
+ *   ds_cotangent_to_raw:     q_bar_raw [nq_max][B] = (deta/dq_raw)^T q_bar_tangent [nv_max][B],
+ *                            which has no component along the quaternion (normalisation).
+ * q [nq_max][B] is the configuration at which the cotangents live; model_id as in ds_batch (NULL
+ * when nmodels == 1).  Revolute rows are copied.  Asynchronous on stream; errors: DS_EINVAL, DS_ECUDA. */
+ds_status ds_cotangent_to_tangent(const ds_model* const* models, int32_t nmodels, int32_t B,
+                                  const int32_t* model_id, const double* q, const double* q_bar_raw,
+                                  double* q_bar_tangent, void* stream);
+ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t nmodels, int32_t B,
+                              const int32_t* model_id, const double* q, const double* q_bar_tangent,
+                              double* q_bar_raw, void* stream);
 
 /* Allocation-free sim_step_jac (no counterpart in the paper; a convenience of this library).
  * Some callers cannot allocate device memory when they step the simulation: a real-time control

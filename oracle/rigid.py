@@ -327,6 +327,49 @@ def integrate(model, q, dv):
     return out
 
 
+def local_difference(model, q0, q1):
+    """The tangent eta with q0 (+) eta = q1 to first order in (q1 - q0): revolute q1 - q0; free-flyer
+    R0^T (p1 - p0) and 2 vec(conj(quat0) * quat1) (the first-order quaternion logarithm, quaternions
+    normalised).  Exact for complex-step derivatives of maps into q, whose second-order terms do not
+    reach the imaginary part."""
+    iq, iv, _, _ = index_maps(model)
+    out = np.zeros(sum(nv_of(jt) for jt in model.jtype), dtype=np.result_type(q0, q1, 1.0))
+    for i, jt in enumerate(model.jtype):
+        k, j = iq[i], iv[i]
+        if jt == REVOLUTE:
+            out[j] = q1[k] - q0[k]
+        else:
+            a, b = q0[k + 3:k + 7], q1[k + 3:k + 7]
+            a = a / np.sqrt(a @ a)
+            b = b / np.sqrt(b @ b)
+            out[j:j + 3] = quat_to_rot(a).T @ (q1[k:k + 3] - q0[k:k + 3])
+            conj = np.array([a[0], -a[1], -a[2], -a[3]])
+            out[j + 3:j + 6] = 2.0 * quat_mul(conj, b)[1:]
+    return out
+
+
+def tangent_to_raw_jacobian(model, q):
+    """d q_raw / d eta at q (nq x nv): complex step of integrate(q, eta) at eta = 0."""
+    nv = sum(nv_of(jt) for jt in model.jtype)
+    J = np.zeros((len(q), nv))
+    for j in range(nv):
+        e = np.zeros(nv, dtype=complex)
+        e[j] = 1e-30j
+        J[:, j] = np.imag(integrate(model, np.asarray(q, float), e)) / 1e-30
+    return J
+
+
+def raw_to_tangent_jacobian(model, q):
+    """d eta / d q_raw at q (nv x nq): complex step of local_difference(q, q + dq_raw) at dq_raw = 0."""
+    q = np.asarray(q, float)
+    J = np.zeros((sum(nv_of(jt) for jt in model.jtype), len(q)))
+    for j in range(len(q)):
+        e = np.zeros(len(q), dtype=complex)
+        e[j] = 1e-30j
+        J[:, j] = np.imag(local_difference(model, q, q + e)) / 1e-30
+    return J
+
+
 def gravity_potential(model, q, gravity):
     """U(q) = -sum_i m_i g . x_com,i  (gravity potential energy)."""
     _, world = fk(model, q)

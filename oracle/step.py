@@ -15,6 +15,8 @@ Derivatives (Sec. 3.1-3.3, App. B, D), w.r.t. a tangent perturbation q (+) dq of
 * Route 1 (the paper's form, App. B): A = B G C + blkdiag(0, Q, ..., Q), A X = -B (J_c D + F),
   dlambda = C X, dv+/dtheta = D + M^-1 J_c^T dlambda.  A may be singular (redundant contacts) and
   is solved in the minimum-norm sense.
+* The position update's adjoint (for rollouts): Jacobians of q+ = q (+) dt v+ in tangent
+  coordinates by complex step (integrate_jacobians), chained in by vjp().
 * Route 2 (independent check): implicit function theorem applied directly to the stacked mode
   equations E(lambda; theta) = 0 with sigma = J_c(q) v+(q, v, tau, lambda); both Jacobians of E by
   complex step; no R, P, Q, A, B or C anywhere.
@@ -217,8 +219,62 @@ def jacobian_fd(model, env, opt, h=1e-6):
     return np.stack(cols, axis=1)
 
 
-def vjp(model, env, opt, v_bar, st=None):
-    """(q_bar, v_bar, tau_bar) = J^T v_bar from the route-1 Jacobian (the definition of a VJP)."""
+def integrate_jacobians(model, q, dq):
+    """Tangent Jacobians of the position update q+ = q (+) dq (the symplectic-Euler step of Sec. 2.3
+    on the configuration manifold; dq = dt v+): with q+ (+) eta = (q (+) eps) (+) (dq + d),
+    Jq = d eta / d eps and Jd = d eta / d d at eps = d = 0.  Complex step through rigid.integrate."""
+    nv = len(dq)
+    qp = rigid.integrate(model, q, dq)
+    Jq, Jd = np.zeros((nv, nv)), np.zeros((nv, nv))
+    for j in range(nv):
+        e = np.zeros(nv, dtype=complex)
+        e[j] = 1j * H_CS
+        q_eps = rigid.integrate(model, rigid.integrate(model, q, e), dq)
+        Jq[:, j] = np.imag(rigid.local_difference(model, qp, q_eps)) / H_CS
+        Jd[:, j] = np.imag(rigid.local_difference(model, qp, rigid.integrate(model, q, dq + e))) / H_CS
+    return Jq, Jd
+
+
+def vjp(model, env, opt, v_bar, st=None, q_bar_next=None):
+    """(q_bar, v_bar, tau_bar) = J^T v_bar from the route-1 Jacobian (the definition of a VJP).  With
+    q_bar_next (a cotangent of q+ in its tangent coordinates) the adjoint of q+ = q (+) dt v+ is
+    chained in: v_bar+ <- v_bar + dt Jd^T q_bar_next and q_bar <- q_bar + Jq^T q_bar_next."""
     if st is None or "dv_dq" not in st:
         st = step_jac(model, env, opt)
-    return st["dv_dq"].T @ v_bar, st["dv_dv"].T @ v_bar, st["dv_dtau"].T @ v_bar
+    vb = np.asarray(v_bar, float)
+    qb = 0.0
+    if q_bar_next is not None:
+        Jq, Jd = integrate_jacobians(model, env["q"], opt.dt * st["v_next"])
+        vb = vb + opt.dt * (Jd.T @ q_bar_next)
+        qb = Jq.T @ q_bar_next
+    return st["dv_dq"].T @ vb + qb, st["dv_dv"].T @ vb, st["dv_dtau"].T @ vb
+
+
+def rollout(model, env0, taus, opt):
+    """States (q_t, v_t), t = 0..T, of T steps from env0 with the joint torques taus[t]."""
+    env = dict(env0)
+    states = [(np.array(env["q"], float), np.array(env["v"], float))]
+    for tau in taus:
+        env = dict(env, tau=np.asarray(tau, float))
+        st = step(model, env, opt)
+        env = dict(env, q=st["q_next"], v=st["v_next"])
+        states.append((st["q_next"], st["v_next"]))
+    return states
+
+
+def rollout_grad(model, env0, taus, opt, q_bar_T_raw):
+    """Gradient w.r.t. every taus[t] of a loss whose gradient w.r.t. the final raw configuration q_T is
+    q_bar_T_raw: reverse accumulation through the steps (vjp with the position-update adjoint), the
+    final cotangent taken to tangent coordinates with d q_raw / d eta.  Also returns the margins of
+    every step's classification (derivatives are those of the identified modes)."""
+    states = rollout(model, env0, taus, opt)
+    qT = states[-1][0]
+    qb = rigid.tangent_to_raw_jacobian(model, qT).T @ np.asarray(q_bar_T_raw, float)
+    vb = np.zeros(len(states[0][1]))
+    grads, margins = [None] * len(taus), []
+    for t in range(len(taus) - 1, -1, -1):
+        env = dict(env0, q=states[t][0], v=states[t][1], tau=np.asarray(taus[t], float))
+        st = step_jac(model, env, opt)
+        margins.append(st["margin"])
+        qb, vb, grads[t] = vjp(model, env, opt, vb, st=st, q_bar_next=qb)
+    return np.array(grads), states, min(margins) if margins else np.inf

@@ -23,11 +23,12 @@ LIB_PATH = os.path.join(HERE, "libdiffsim.so")
 DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED, DS_ETOOLARGE = 0, -1, -2, -3, -4, -5
 DS_FP64, DS_MIXED = 0, 1
 MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
-ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH = 1, 2, 4, 8
+ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 1, 2, 4, 8, 16
 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
-           "sim_step_jac_noalloc", "ds_profile", "ds_profile_read")
+           "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
+           "ds_cotangent_to_raw")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -40,7 +41,7 @@ class ds_batch(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("ncmax", ctypes.c_int32), ("model_id", ctypes.c_void_p),
                 ("q", ctypes.c_void_p), ("v", ctypes.c_void_p), ("tau", ctypes.c_void_p),
                 ("c_link", ctypes.c_void_p), ("c_point", ctypes.c_void_p), ("c_radius", ctypes.c_void_p),
-                ("c_mu", ctypes.c_void_p), ("plane", ctypes.c_void_p)]
+                ("c_mu", ctypes.c_void_p), ("plane", ctypes.c_void_p), ("model_slots", ctypes.c_void_p)]
 
 
 class ds_options(ctypes.Structure):
@@ -78,14 +79,17 @@ def lib():
         sz = ctypes.c_size_t
         L.sim_step.argtypes = common + [ctypes.POINTER(ds_step_out), vp, sz, vp]
         L.sim_step_jac.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
-        L.sim_step_vjp.argtypes = common + [vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
+        L.sim_step_vjp.argtypes = common + [vp, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp]
         L.ds_workspace_size.argtypes = common + [ctypes.POINTER(sz)]
         L.sim_step_jac_noalloc.argtypes = common + [ctypes.POINTER(ds_step_out), vp, vp, vp, vp]
         L.ds_profile.argtypes = [i32]
         L.ds_profile_read.argtypes = [vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
+        for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
+            getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
-                  "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read"):
+                  "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read",
+                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -145,7 +149,12 @@ def _models_array(models):
 def _batch_struct(t):
     return ds_batch(t["q"].shape[1], t["c_link"].shape[0], _ptr(t.get("model_id")), _ptr(t["q"]), _ptr(t["v"]),
                     _ptr(t["tau"]), _ptr(t["c_link"]), _ptr(t["c_point"]), _ptr(t["c_radius"]), _ptr(t["c_mu"]),
-                    _ptr(t["plane"]))
+                    _ptr(t["plane"]), _host_ptr(t.get("model_slots")))
+
+
+def _host_ptr(a):
+    """Address of a host int32 numpy array (kept alive by the caller's dict), or NULL."""
+    return ctypes.c_void_p(0 if a is None else a.ctypes.data)
 
 
 def _out_struct(o):
@@ -194,11 +203,24 @@ def sim_step_jac_noalloc(models, batch, opt, out, dv_dq, dv_dv, dv_dtau, stream=
                                       ctypes.byref(o), _ptr(dv_dq), _ptr(dv_dv), _ptr(dv_dtau), _stream(stream)))
 
 
-def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, workspace=None, stream=None):
+def sim_step_vjp(models, batch, opt, v_next_bar, out, q_bar, v_bar, tau_bar, workspace=None, stream=None,
+                 q_next_bar=None):
     b, o = _batch_struct(batch), _out_struct(out)
     _check(lib().sim_step_vjp(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
-                              _ptr(v_next_bar), ctypes.byref(o), _ptr(q_bar), _ptr(v_bar), _ptr(tau_bar),
-                              *_ws(workspace), _stream(stream)))
+                              _ptr(v_next_bar), _ptr(q_next_bar), ctypes.byref(o), _ptr(q_bar), _ptr(v_bar),
+                              _ptr(tau_bar), *_ws(workspace), _stream(stream)))
+
+
+def cotangent_to_tangent(models, q, q_bar_raw, q_bar_tangent, model_id=None, stream=None):
+    """C-ABI ds_cotangent_to_tangent: (dq_raw/deta)^T q_bar_raw at q, all [rows][B] device tensors."""
+    _check(lib().ds_cotangent_to_tangent(_models_array(models), len(models), q.shape[1], _ptr(model_id), _ptr(q),
+                                         _ptr(q_bar_raw), _ptr(q_bar_tangent), _stream(stream)))
+
+
+def cotangent_to_raw(models, q, q_bar_tangent, q_bar_raw, model_id=None, stream=None):
+    """C-ABI ds_cotangent_to_raw: (deta/dq_raw)^T q_bar_tangent at q, all [rows][B] device tensors."""
+    _check(lib().ds_cotangent_to_raw(_models_array(models), len(models), q.shape[1], _ptr(model_id), _ptr(q),
+                                     _ptr(q_bar_tangent), _ptr(q_bar_raw), _stream(stream)))
 
 
 def fma_peak(out, blocks, iters, fp64, stream=None):
@@ -233,6 +255,8 @@ def batch_to_device(batch, device="cuda"):
              c_mu=torch.as_tensor(batch.c_mu, **f64).contiguous(), plane=torch.as_tensor(batch.plane, **f64).contiguous())
     if batch.model_id is not None:
         t["model_id"] = torch.as_tensor(batch.model_id, **i32).contiguous()
+    if batch.model_slots is not None:
+        t["model_slots"] = np.ascontiguousarray(batch.model_slots, dtype=np.int32)   # host array
     return t
 
 
@@ -277,10 +301,11 @@ class Simulator:
         sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, workspace=self.workspace, stream=stream)
         return dict(self.out, dv_dq=self.jac[0], dv_dv=self.jac[1], dv_dtau=self.jac[2])
 
-    def step_vjp(self, v_next_bar, stream=None):
+    def step_vjp(self, v_next_bar, stream=None, q_next_bar=None):
         import torch
         if self.vjp_out is None:
             self.vjp_out = [torch.zeros_like(self.out["v_next"]) for _ in range(3)]
         sim_step_vjp(self.models, self.batch, self.opt, v_next_bar.contiguous(), self.out, *self.vjp_out,
-                     workspace=self.workspace, stream=stream)
+                     workspace=self.workspace, stream=stream,
+                     q_next_bar=None if q_next_bar is None else q_next_bar.contiguous())
         return dict(self.out, q_bar=self.vjp_out[0], v_bar=self.vjp_out[1], tau_bar=self.vjp_out[2])

@@ -136,7 +136,8 @@ extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nm
 
 static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
                      const ds_step_out* out, int mode, double* dq, double* dv, double* dtau, const double* vbar,
-                     double* qb, double* vb, double* tb, void* ws, size_t ws_bytes, void* stream) {
+                     const double* qnbar, double* qb, double* vb, double* tb, void* ws, size_t ws_bytes,
+                     void* stream) {
   if (!models || nmodels <= 0 || nmodels > 64 || !b || !o || !out) return DS_EINVAL;
   if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
   if (b->B == 0) return DS_OK;
@@ -152,9 +153,13 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr) ||
              (reinterpret_cast<uintptr_t>(ws) & 255) != 0))
     return DS_EINVAL;
+  const ds_kernel_entry* kern[64];
   for (int k = 0; k < nmodels; ++k) {
     if (!models[k]) return DS_EINVAL;
-    if (!ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision)) return DS_EUNSUPPORTED;
+    const int slots = b->model_slots ? b->model_slots[k] : b->ncmax;
+    if (slots < 0 || slots > b->ncmax) return DS_EINVAL;
+    kern[k] = ds_fit_kernel(models[k]->host.nb, models[k]->host.nv, slots, b->ncmax, o->precision);
+    if (!kern[k]) return DS_EUNSUPPORTED;
   }
   KArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -168,7 +173,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.v_next = out->v_next; a.q_next = out->q_next; a.lambda = out->lambda; a.modes = out->modes;
   a.status = out->env_status; a.iters = out->iters;
   a.dv_dq = dq; a.dv_dv = dv; a.dv_dtau = dtau;
-  a.vbar = vbar; a.q_bar = qb; a.v_bar = vb; a.tau_bar = tb;
+  a.vbar = vbar; a.qnbar = qnbar; a.q_bar = qb; a.v_bar = vb; a.tau_bar = tb;
   a.run = mode;
   a.env_list = nullptr;
   a.n_env = b->B;
@@ -176,7 +181,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int k = 0; k < nmodels; ++k) {
-    const ds_kernel_entry* ke = ds_find_kernel(models[k]->host.nb, models[k]->host.nv, b->ncmax, o->precision);
+    const ds_kernel_entry* ke = kern[k];
     a.model = models[k]->dev;
     a.model_index = k;
     if (ws) ke->pipeline(a, s);
@@ -189,7 +194,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
 extern "C" ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                               const ds_options* opt, const ds_step_out* out, void* ws, size_t ws_bytes,
                               void* stream) {
-  return run(models, nmodels, batch, opt, out, DS_RUN_STEP, nullptr, nullptr, nullptr, nullptr, nullptr,
+  return run(models, nmodels, batch, opt, out, DS_RUN_STEP, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
              nullptr, nullptr, ws, ws_bytes, stream);
 }
 
@@ -197,13 +202,85 @@ extern "C" ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels
                                   const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
                                   double* dv_dtau, void* ws, size_t ws_bytes, void* stream) {
   return run(models, nmodels, batch, opt, out, DS_RUN_JAC, dv_dq, dv_dv, dv_dtau, nullptr, nullptr, nullptr,
-             nullptr, ws, ws_bytes, stream);
+             nullptr, nullptr, ws, ws_bytes, stream);
 }
 
 extern "C" ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
-                                  const ds_options* opt, const double* v_next_bar, const ds_step_out* out,
-                                  double* q_bar, double* v_bar, double* tau_bar, void* ws, size_t ws_bytes,
-                                  void* stream) {
-  return run(models, nmodels, batch, opt, out, DS_RUN_VJP, nullptr, nullptr, nullptr, v_next_bar, q_bar, v_bar,
-             tau_bar, ws, ws_bytes, stream);
+                                  const ds_options* opt, const double* v_next_bar, const double* q_next_bar,
+                                  const ds_step_out* out, double* q_bar, double* v_bar, double* tau_bar, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  return run(models, nmodels, batch, opt, out, DS_RUN_VJP, nullptr, nullptr, nullptr, v_next_bar, q_next_bar, q_bar,
+             v_bar, tau_bar, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------------ cotangent coordinate maps
+// Between a cotangent of the raw configuration vector (nq numbers per env: the free-flyer's
+// position and quaternion) and one of its tangent coordinates at q (nv numbers), for the
+// perturbation q (+) eta used by the derivatives (position += R eta_lin, quaternion <- quaternion
+// * exp(eta_ang / 2)).  With Q(quat) the matrix of left quaternion multiplication and c1, c2, c3
+// its last three columns, d q_raw / d eta = [R, 0; 0, Q(quat)[:, 1:4] / 2] and (unit quaternion)
+// d eta / d q_raw = [R^T, 0; 0, 2 Q(quat)^T[1:4, :]]; revolute rows are the identity.
+// to_tangent: out = (d q_raw / d eta)^T in; to_raw: out = (d eta / d q_raw)^T in.
+__global__ void cotangent_kernel(const DevModel* __restrict__ m, int model_index, const int32_t* model_id, int B,
+                                 const double* __restrict__ q, const double* __restrict__ in,
+                                 double* __restrict__ out, int to_raw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B) return;
+  if (model_id && model_id[e] != model_index) return;
+  const int nb = m->nb;
+  for (int i = 0; i < nb; ++i) {
+    const int k0 = m->iq[i], d0 = m->iv[i];
+    if (m->jtype[i] == 0) {
+      if (to_raw) out[k0 * B + e] = in[d0 * B + e];
+      else out[d0 * B + e] = in[k0 * B + e];
+      continue;
+    }
+    double w = q[(k0 + 3) * B + e], x = q[(k0 + 4) * B + e], y = q[(k0 + 5) * B + e], z = q[(k0 + 6) * B + e];
+    const double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                         2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    const double c[3][4] = {{-x, w, z, -y}, {-y, -z, w, x}, {-z, y, -x, w}};
+    if (to_raw) {
+      const double el[3] = {in[d0 * B + e], in[(d0 + 1) * B + e], in[(d0 + 2) * B + e]};
+      const double ea[3] = {in[(d0 + 3) * B + e], in[(d0 + 4) * B + e], in[(d0 + 5) * B + e]};
+      for (int r = 0; r < 3; ++r) out[(k0 + r) * B + e] = R[3 * r] * el[0] + R[3 * r + 1] * el[1] + R[3 * r + 2] * el[2];
+      for (int r = 0; r < 4; ++r) out[(k0 + 3 + r) * B + e] = 2.0 * (c[0][r] * ea[0] + c[1][r] * ea[1] + c[2][r] * ea[2]);
+    } else {
+      const double pb[3] = {in[k0 * B + e], in[(k0 + 1) * B + e], in[(k0 + 2) * B + e]};
+      const double qb[4] = {in[(k0 + 3) * B + e], in[(k0 + 4) * B + e], in[(k0 + 5) * B + e], in[(k0 + 6) * B + e]};
+      for (int r = 0; r < 3; ++r) out[(d0 + r) * B + e] = R[r] * pb[0] + R[3 + r] * pb[1] + R[6 + r] * pb[2];
+      for (int r = 0; r < 3; ++r)
+        out[(d0 + 3 + r) * B + e] = 0.5 * (c[r][0] * qb[0] + c[r][1] * qb[1] + c[r][2] * qb[2] + c[r][3] * qb[3]);
+    }
+  }
+}
+
+static ds_status cotangent(const ds_model* const* models, int32_t nmodels, int32_t B, const int32_t* model_id,
+                           const double* q, const double* in, double* out, int to_raw, void* stream) {
+  if (!models || nmodels <= 0 || nmodels > 64 || B < 0) return DS_EINVAL;
+  if (B == 0) return DS_OK;
+  if (!q || !in || !out || (nmodels > 1 && !model_id)) return DS_EINVAL;
+  for (int k = 0; k < nmodels; ++k)
+    if (!models[k]) return DS_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < nmodels; ++k) {
+    cotangent_kernel<<<(B + 127) / 128, 128, 0, s>>>(models[k]->dev, k, nmodels > 1 ? model_id : nullptr, B, q, in,
+                                                     out, to_raw);
+    if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
+  }
+  return DS_OK;
+}
+
+extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int32_t nmodels, int32_t B,
+                                             const int32_t* model_id, const double* q, const double* q_bar_raw,
+                                             double* q_bar_tangent, void* stream) {
+  return cotangent(models, nmodels, B, model_id, q, q_bar_raw, q_bar_tangent, 0, stream);
+}
+
+extern "C" ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t nmodels, int32_t B,
+                                         const int32_t* model_id, const double* q, const double* q_bar_tangent,
+                                         double* q_bar_raw, void* stream) {
+  return cotangent(models, nmodels, B, model_id, q, q_bar_tangent, q_bar_raw, 1, stream);
 }

@@ -107,6 +107,7 @@ struct KArgs {
   int32_t* iters;
   double *dv_dq, *dv_dv, *dv_dtau;
   const double* vbar;
+  const double* qnbar;     // [nv][B] cotangent of q+ (tangent coordinates) or NULL
   double *q_bar, *v_bar, *tau_bar;
   int run;
   WsView ws;               // pipeline workspace (unused by the fused kernel)
@@ -128,6 +129,7 @@ struct ds_kernel_entry {
   ds_launch_fn pipeline;
 };
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
+extern "C++" const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int precision);
 
 // ------------------------------------------------------------------------------ small algebra
 

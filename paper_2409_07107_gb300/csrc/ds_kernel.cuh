@@ -751,6 +751,8 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       }
     }
   }
+  for (int k = NS; k < a.ncmax; ++k)            // slots beyond this kernel's: must be unused
+    if (a.c_link[k * B + e] >= 0) st |= DS_ENV_BAD_SLOT;
   const int mdim = 3 * s.na;
 
   // ---- F5 contact Jacobian rows (t1, t2, n) . velocity of the body point at c, in FP64 from the
@@ -828,6 +830,56 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
 }
 
 // F9 and, on request, B1-B7 for env e, given lambda and the modes of its active contacts.
+// Adjoint of the position update q+ = q (+) dt v+ for the cotangent qn of q+ (in the tangent
+// coordinates at q+): vadd = dt (dq+/d delta)^T qn and qa = (dq+/dq)^T qn.  Revolute dofs: both
+// Jacobians are the identity.  Free-flyer (p+ = p + R delta_lin, R+ = R Exp(delta_ang)): with
+// E = Exp(delta_ang), dq+/dq = [[E^T, -E^T [delta_lin]x], [0, E^T]] and dq+/d delta =
+// [[E^T, 0], [0, Jr(delta_ang)]] (Jr: right Jacobian of SO(3)); E and Jr^T are applied as
+// x + c1 phi x x + c2 phi x (phi x x) with their series near phi = 0.
+DS_HDI void so3_apply(const double* phi, const double* x, double c1, double c2, double* o) {
+  double t1[3], t2[3];
+  cross3(phi, x, t1);
+  cross3(phi, t1, t2);
+  for (int k = 0; k < 3; ++k) o[k] = x[k] + c1 * t1[k] + c2 * t2[k];
+}
+
+DS_HDI void integrate_adjoint(const DevModel& m, const double* vn, double dt, const double* qn, double* vadd,
+                             double* qa) {
+  for (int i = 0; i < m.nb; ++i) {
+    const int d0 = m.iv[i];
+    if (m.jtype[i] == 0) {
+      vadd[d0] = dt * qn[d0];
+      qa[d0] = qn[d0];
+      continue;
+    }
+    const double dl[3] = {dt * vn[d0], dt * vn[d0 + 1], dt * vn[d0 + 2]};
+    const double ph[3] = {dt * vn[d0 + 3], dt * vn[d0 + 4], dt * vn[d0 + 5]};
+    const double t2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
+    double sa, ca, cb;                // sin t / t, (1 - cos t) / t^2, (t - sin t) / t^3
+    if (t2 < 1e-8) {
+      sa = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+      ca = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+      cb = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+    } else {
+      const double t = sqrt(t2);
+      sa = sin(t) / t;
+      ca = (1.0 - cos(t)) / t2;
+      cb = (t - sin(t)) / (t2 * t);
+    }
+    double el[3], ea[3], jr[3], cr[3];
+    so3_apply(ph, qn + d0, sa, ca, el);          // E qn_lin
+    so3_apply(ph, qn + d0 + 3, sa, ca, ea);      // E qn_ang
+    so3_apply(ph, qn + d0 + 3, ca, cb, jr);      // Jr^T qn_ang
+    cross3(dl, el, cr);                          // [delta_lin]x E qn_lin
+    for (int k = 0; k < 3; ++k) {
+      qa[d0 + k] = el[k];
+      qa[d0 + 3 + k] = cr[k] + ea[k];
+      vadd[d0 + k] = dt * el[k];
+      vadd[d0 + 3 + k] = dt * jr[k];
+    }
+  }
+}
+
 template <int NB, int NV, int NS, typename T>
 DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters) {
   const int B = a.B;
@@ -1052,8 +1104,18 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       // ---- B7 vector-Jacobian product (adjoint of the implicit solve, never forming D):
       // z = A^-T C^T Y^T vbar, zeta = B^T z, ubar = vbar - J_c^T zeta, w = M^-1 ubar,
       // q_bar = -dt dtau_q . w - F^T zeta, v_bar = ubar - dt dtau_v . w, tau_bar = dt w.
+      // With a cotangent of q+ as well, the position update's adjoint is chained in first (B8).
       T vb[NV], ub[NV], w2[NV];
-      for (int k = 0; k < NV; ++k) { vb[k] = T(a.vbar[k * B + e]); ub[k] = vb[k]; }
+      double qn[NV], vadd[NV], qadd[NV];
+      if (a.qnbar) {
+        double vnd[NV];
+        for (int k = 0; k < NV; ++k) { qn[k] = a.qnbar[k * B + e]; vnd[k] = double(s.vn[k]); }
+        integrate_adjoint(m, vnd, a.dt, qn, vadd, qadd);
+      }
+      for (int k = 0; k < NV; ++k) {
+        vb[k] = T(a.qnbar ? a.vbar[k * B + e] + vadd[k] : a.vbar[k * B + e]);
+        ub[k] = vb[k];
+      }
       double zeta[3 * NS];
       for (int r = 0; r < mdim; ++r) zeta[r] = 0.0;
       if (md > 0) {
@@ -1100,7 +1162,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             }
           }
           double* out = blk == 0 ? a.q_bar : a.v_bar;
-          out[d * B + e] = double(r);
+          out[d * B + e] = (blk == 0 && a.qnbar) ? double(r) + qadd[d] : double(r);
         }
       for (int k = 0; k < NV; ++k) a.tau_bar[k * B + e] = double(dt * w2[k]);
     }

@@ -23,3 +23,14 @@ const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision) {
     if (k.nb == nb && k.nv == nv && k.ns == ns && k.precision == precision) return &k;
   return nullptr;
 }
+
+// The compiled shape for a model whose envs use the leading `slots` contact slots of a batch with
+// ncmax slots: the fewest slots S with slots <= S <= ncmax (the kernel reads slots 0 .. S-1 only).
+const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int precision) {
+  const ds_kernel_entry* best = nullptr;
+  for (const ds_kernel_entry& k : kTable)
+    if (k.nb == nb && k.nv == nv && k.precision == precision && k.ns >= slots && k.ns <= ncmax &&
+        (!best || k.ns < best->ns))
+      best = &k;
+  return best;
+}

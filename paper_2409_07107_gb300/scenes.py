@@ -83,6 +83,7 @@ class Batch:
     c_mu: np.ndarray       # [ncmax][B]
     plane: np.ndarray      # [4][B]
     model_id: np.ndarray | None = None   # int32 [B] for batches that mix models
+    model_slots: np.ndarray | None = None  # int32 [nmodels]: leading slots each model's envs use
 
     @property
     def B(self) -> int:
@@ -104,7 +105,8 @@ class Batch:
         return Batch(self.q[:, idx].copy(), self.v[:, idx].copy(), self.tau[:, idx].copy(),
                      self.c_link[:, idx].copy(), self.c_point[:, :, idx].copy(),
                      self.c_radius[:, idx].copy(), self.c_mu[:, idx].copy(), self.plane[:, idx].copy(),
-                     None if self.model_id is None else self.model_id[idx].copy())
+                     None if self.model_id is None else self.model_id[idx].copy(),
+                     None if self.model_slots is None else self.model_slots.copy())
 
 
 @dataclass
@@ -485,7 +487,8 @@ def uneven(B=32768, seed=1003):
         c_mu[:nc, sel] = b.c_mu
         plane[:, sel] = b.plane
     return Workload("uneven-arm-quadruped-humanoid", models,
-                    Batch(q, v, tau, c_link, c_point, c_radius, c_mu, plane, mid), precision="mixed")
+                    Batch(q, v, tau, c_link, c_point, c_radius, c_mu, plane, mid,
+                          np.array([p.batch.ncmax for p in parts], np.int32)), precision="mixed")
 
 
 WORKLOADS = {

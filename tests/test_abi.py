@@ -80,5 +80,5 @@ def test_step_rejects_bad_arguments(L):
                           None, 0, None) == ds.DS_EINVAL
     assert L.ds_workspace_size(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(n)) == ds.DS_EINVAL
     b.ncmax = 99
-    assert L.sim_step_vjp(models, 1, ctypes.byref(b), ctypes.byref(o), None, ctypes.byref(out), None, None,
+    assert L.sim_step_vjp(models, 1, ctypes.byref(b), ctypes.byref(o), None, None, ctypes.byref(out), None, None,
                           None, None, 0, None) == ds.DS_EINVAL

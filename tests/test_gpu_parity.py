@@ -193,3 +193,51 @@ def test_pipeline_matches_fused(torch_cuda):
             err = np.abs(f[k] - p[k]).max(axis=tuple(range(f[k].ndim - 1))) / np.maximum(
                 np.abs(f[k]).max(axis=tuple(range(f[k].ndim - 1))), 1e-6)
             assert np.quantile(err, 0.99) <= tol, (prec, k, np.quantile(err, 0.99))
+
+
+def test_uneven_batch_step_and_vjp(torch_cuda):
+    """A batch that mixes the arm + cube (8 slots), the quadruped (4 slots) and the humanoid (16
+    slots), interleaved env by env; each model runs the kernel of its own slot count.  v+ and the
+    VJP (q_bar, v_bar, tau_bar = J^T v_bar+) against the oracle's step and Jacobians."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.uneven(60)
+    envs = list(range(18))                     # 6 envs of each model
+    refs = run_oracle(wl, envs)
+    rng = np.random.default_rng(7)
+    wbar = rng.normal(size=wl.batch.v.shape)
+    for prec, tol_v, tol_j in (("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)):
+        sim = ds.Simulator(wl, precision=prec)
+        out = sim.step_vjp(torch.as_tensor(wbar, dtype=torch.float64, device="cuda"))
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+        assert not (g["status"] & 16).any()
+        checked = 0
+        for e, r in zip(envs, refs):
+            nv = wl.models[int(wl.batch.model_id[e])].nv
+            assert g["status"][e] & 2 == 0
+            assert rel_err(g["v_next"][:nv, e], r["v_next"]) <= tol_v, (prec, e)
+            if r["margin"] < DELTA or (g["status"][e] & 8):
+                continue
+            for key, jk in (("q_bar", "dv_dq"), ("v_bar", "dv_dv"), ("tau_bar", "dv_dtau")):
+                ref = r[jk].T @ wbar[:nv, e]
+                assert rel_err(g[key][:nv, e], ref) <= tol_j, (prec, e, key)
+            checked += 1
+        assert checked >= 12
+
+
+def test_uneven_batch_slot_dispatch(torch_cuda):
+    """A used slot beyond a model's declared slot count is flagged (DS_ENV_BAD_SLOT), not read
+    out of range; declared counts above ncmax or with no compiled kernel are refused."""
+    import paper_2409_07107_gb300 as ds
+    wl = scenes.uneven(30)
+    b = wl.batch.take(np.arange(30))
+    b.model_slots = np.array([4, 4, 16], np.int32)     # the arm's envs use 8 slots
+    g = _gpu(scenes.Workload(wl.name, wl.models, b, wl.options), "fp64", run="step")
+    arm = b.model_id == 0
+    used_high = (b.c_link[4:] >= 0).any(axis=0)
+    assert ((g["status"] & 16) != 0).tolist() == (arm & used_high).tolist()
+    for bad in ([8, 4, 17], [8, 5, 16]):
+        b.model_slots = np.array(bad, np.int32)
+        with pytest.raises(ds.DiffsimError):
+            _gpu(scenes.Workload(wl.name, wl.models, b, wl.options), "fp64", run="step")
