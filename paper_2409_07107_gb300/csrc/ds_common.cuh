@@ -112,6 +112,7 @@ struct KArgs {
   int run;
   WsView ws;               // pipeline workspace (unused by the fused kernel)
   int round, round_cap, final_round;
+  int nchunk;              // finish kernel: threads per env (Jacobian columns split between them)
 };
 
 typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);

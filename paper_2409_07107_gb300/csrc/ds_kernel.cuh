@@ -295,11 +295,18 @@ DS_HDI void admm_rhs(T mu, const T* z, const T* y, const T* g, const T* sx, T rh
   rhs[2] = rho * z[2] - y[2] - g[2] - sd;
 }
 
+// Convergence of the ADMM iteration is tested every DS_ADMM_CHECK iterations (of the env's global
+// iteration count): the residual bookkeeping and, in the cooperative form, its reductions over the
+// env's lanes then stay off the other iterations.  FP64 instructions are this loop's bound.
+#define DS_ADMM_CHECK 4
+
 // x, sx, z, y of one contact from its three rows of K and the full right-hand side
-// (K and rhs_full are zero beyond the active size, so the product runs over the padded width.)
+// (K and rhs_full are zero beyond the active size, so the product runs over the padded width).
+// Only the tangential part of sx = G x + g is formed: the De Saxce term needs nothing else.
+// With check, also the primal / dual residual and |z| maxima for the convergence test.
 template <int NC3, typename T>
 DS_HDI void admm_update(const T (*Kr)[NC3], const T* rhs_full, const T* rhs_own, const T* g, T mu, T rho,
-                        T inv_rho, T inv1pmu2, T* x, T* z, T* y, T* sx, T& rp, T& rd, T& zmax) {
+                        T inv_rho, T inv1pmu2, T* x, T* z, T* y, T* sx, T& rp, T& rd, T& zmax, bool check) {
   const T relax = T(1.6);
   T xh[3], w[3], pr[3];
 #pragma unroll
@@ -308,17 +315,21 @@ DS_HDI void admm_update(const T (*Kr)[NC3], const T* rhs_full, const T* rhs_own,
 #pragma unroll
     for (int c = 0; c < NC3; ++c) acc += Kr[r][c] * rhs_full[c];
     x[r] = acc;
-    sx[r] = rhs_own[r] - rho * acc + g[r];
+    if (r < 2) sx[r] = rhs_own[r] - rho * acc + g[r];
     xh[r] = relax * x[r] + (T(1) - relax) * z[r];
     w[r] = xh[r] + y[r] * inv_rho;
   }
   proj_cone_fast(w, mu, inv1pmu2, pr);
+  if (check) {
+    for (int r = 0; r < 3; ++r) {
+      rd = fmax(rd, fabs(pr[r] - z[r]));
+      rp = fmax(rp, fabs(x[r] - pr[r]));
+      zmax = fmax(zmax, fabs(pr[r]));
+    }
+  }
   for (int r = 0; r < 3; ++r) {
-    rd = fmax(rd, fabs(pr[r] - z[r]));
     z[r] = pr[r];
     y[r] += rho * (xh[r] - z[r]);
-    rp = fmax(rp, fabs(x[r] - z[r]));
-    zmax = fmax(zmax, fabs(z[r]));
   }
 }
 
@@ -363,18 +374,18 @@ struct Admm {
     for (int i = 0; i < m; ++i) { x[i] = T(0); z[i] = T(0); y[i] = T(0); sx[i] = p.gt[i]; }
   }
 
-  // one iteration; returns true when converged at tolerance te
+  // one iteration; with check, returns true when converged at tolerance te
   template <class P>
-  DS_HD bool iterate(const P& p, T te) {
+  DS_HD bool iterate(const P& p, T te, bool check) {
     T rhs[NC3];
     for (int i = 0; i < NC3; ++i) rhs[i] = T(0);
     for (int i = 0; i < p.na; ++i) admm_rhs(T(p.mu[i]), z + 3 * i, y + 3 * i, p.gt + 3 * i, sx + 3 * i, rho, rhs + 3 * i);
     T rp = T(0), rd = T(0), zmax = T(1);
     for (int i = 0; i < p.na; ++i)
       admm_update<NC3, T>(K + 3 * i, rhs, rhs + 3 * i, p.gt + 3 * i, T(p.mu[i]), rho, inv_rho, inv1pmu2[i],
-                          x + 3 * i, z + 3 * i, y + 3 * i, sx + 3 * i, rp, rd, zmax);
+                          x + 3 * i, z + 3 * i, y + 3 * i, sx + 3 * i, rp, rd, zmax, check);
     rd *= rho;
-    return rp <= te * zmax && rd <= te * gs;
+    return check && rp <= te * zmax && rd <= te * gs;
   }
 };
 
@@ -441,7 +452,7 @@ DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
     const T te = T(eps);
     while (iters < a.admm_max_iter) {
       ++iters;
-      if (ad.iterate(s, te)) break;
+      if (ad.iterate(s, te, iters % DS_ADMM_CHECK == 0)) break;
     }
     ok = newton_stage(s, ad.z, eps, a, best, best_r);
     if (ok || iters >= a.admm_max_iter) break;
@@ -881,7 +892,11 @@ DS_HDI void integrate_adjoint(const DevModel& m, const double* vn, double dt, co
 }
 
 template <int NB, int NV, int NS, typename T>
-DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters) {
+DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters,
+                      int chunk = 0, int nchunk = 1) {
+  // With nchunk > 1 the Jacobian columns (or the VJP's dof passes) are split over nchunk threads of
+  // the same env; chunk 0 also writes the step's outputs.
+  const bool lead = chunk == 0;
   const int B = a.B;
   const int mdim = 3 * s.na;
   const double* q = s.q;
@@ -894,9 +909,9 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
   for (int k = 0; k < NV; ++k) {
     const double vv = double(s.vn[k]);
     if (!isfinite(vv)) st |= DS_ENV_NONFINITE;
-    a.v_next[k * B + e] = vv;
+    if (lead) a.v_next[k * B + e] = vv;
   }
-  if (a.q_next) {
+  if (a.q_next && lead) {
     for (int i = 0; i < NB; ++i) {
       const int k0 = m.iq[i], d0 = m.iv[i];
       if (m.jtype[i] == 0) {
@@ -929,17 +944,19 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       }
     }
   }
-  if (a.lambda)
-    for (int k = 0; k < 3 * a.ncmax; ++k) a.lambda[k * B + e] = 0.0;
-  if (a.modes)
-    for (int k = 0; k < a.ncmax; ++k) a.modes[k * B + e] = DS_MODE_INACTIVE;
-  for (int ac = 0; ac < s.na; ++ac) {
-    const int k = s.slot[ac];
+  if (lead) {
     if (a.lambda)
-      for (int r = 0; r < 3; ++r) a.lambda[(3 * k + r) * B + e] = s.lam[3 * ac + r];
-    if (a.modes) a.modes[k * B + e] = uint8_t(s.mode[ac]);
+      for (int k = 0; k < 3 * a.ncmax; ++k) a.lambda[k * B + e] = 0.0;
+    if (a.modes)
+      for (int k = 0; k < a.ncmax; ++k) a.modes[k * B + e] = DS_MODE_INACTIVE;
+    for (int ac = 0; ac < s.na; ++ac) {
+      const int k = s.slot[ac];
+      if (a.lambda)
+        for (int r = 0; r < 3; ++r) a.lambda[(3 * k + r) * B + e] = s.lam[3 * ac + r];
+      if (a.modes) a.modes[k * B + e] = uint8_t(s.mode[ac]);
+    }
+    if (a.iters) a.iters[e] = iters;
   }
-  if (a.iters) a.iters[e] = iters;
 
   if (a.run != DS_RUN_STEP && !(st & DS_ENV_NONFINITE)) {
     // ---- B1 pass of tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces
@@ -1052,7 +1069,8 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
     if (a.run == DS_RUN_JAC) {
       // ---- B1/B2/B5/B6 one Jacobian column at a time:
       // D = dv+/dtheta at fixed lambda, RHS = J_c D + F, X = -A^- B RHS, dv = D + Y C X
-      for (int col = 0; col < 3 * NV; ++col) {
+      const int c0 = (3 * NV * chunk) / nchunk, c1 = (3 * NV * (chunk + 1)) / nchunk;
+      for (int col = c0; col < c1; ++col) {
         const int blk = col / NV, d = col % NV;
         T Dc[NV];
         if (blk < 2) {
@@ -1145,8 +1163,10 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       for (int k = 0; k < NV; ++k) w2[k] = ub[k];
       fwd_packed(s.L, w2, NV);
       bwd_packed(s.L, w2, NV);
+      const int p0 = (2 * NV * chunk) / nchunk, p1 = (2 * NV * (chunk + 1)) / nchunk;
       for (int blk = 0; blk < 2; ++blk)
         for (int d = 0; d < NV; ++d) {
+          if (blk * NV + d < p0 || blk * NV + d >= p1) continue;
           T dtau[NV];
           rnea_tangent<NB, NV, NS, T>(m, s, blk, d, dtau);
           T r = T(0);
@@ -1164,10 +1184,11 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           double* out = blk == 0 ? a.q_bar : a.v_bar;
           out[d * B + e] = (blk == 0 && a.qnbar) ? double(r) + qadd[d] : double(r);
         }
-      for (int k = 0; k < NV; ++k) a.tau_bar[k * B + e] = double(dt * w2[k]);
+      if (lead)
+        for (int k = 0; k < NV; ++k) a.tau_bar[k * B + e] = double(dt * w2[k]);
     }
   }
-  if (a.status) a.status[e] = st;
+  if (a.status && lead) a.status[e] = st;
 }
 
 
@@ -1338,16 +1359,19 @@ __global__ void __launch_bounds__(128) admm_round_kernel(KArgs a) {
       T xn[3] = {x[0], x[1], x[2]}, zn[3] = {z[0], z[1], z[2]}, yn[3] = {y[0], y[1], y[2]};
       T sn[3] = {sx[0], sx[1], sx[2]};
       T rp = T(0), rd = T(0), zmax = T(1);
-      if (act) admm_update<NC3, T>(Kr, full, rhs, g, mu, rho, inv_rho, inv1pmu2, xn, zn, yn, sn, rp, rd, zmax);
-      rp = group_max(rp, L);
-      rd = group_max(rd, L);
-      zmax = group_max(zmax, L);
+      const bool chk = (iters + 1) % DS_ADMM_CHECK == 0;
+      if (act) admm_update<NC3, T>(Kr, full, rhs, g, mu, rho, inv_rho, inv1pmu2, xn, zn, yn, sn, rp, rd, zmax, chk);
+      if (__any_sync(0xffffffffu, running && chk)) {
+        rp = group_max(rp, L);
+        rd = group_max(rd, L);
+        zmax = group_max(zmax, L);
+      }
       if (running) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) { x[r] = xn[r]; z[r] = zn[r]; y[r] = yn[r]; sx[r] = sn[r]; }
         ++iters;
         rd *= rho;
-        if (rp <= te * zmax && rd <= te * gs) { conv = true; running = false; }
+        if (chk && rp <= te * zmax && rd <= te * gs) { conv = true; running = false; }
         else if (iters >= a.admm_max_iter) running = false;
       }
     }
@@ -1460,7 +1484,7 @@ DS_HD void admm_round_env(const KArgs& a, const int e) {
   bool conv = false;
   for (int k = 0; k < a.round_cap && iters < a.admm_max_iter; ++k) {
     ++iters;
-    if (ad.iterate(p, te)) { conv = true; break; }
+    if (ad.iterate(p, te, iters % DS_ADMM_CHECK == 0)) { conv = true; break; }
   }
   for (int i = 0; i < m; ++i) {
     w.ax[i * B + e] = double(ad.x[i]);
@@ -1481,7 +1505,7 @@ DS_HD void admm_round_env(const KArgs& a, const int e) {
 // 3. finish: F1-F6 again (recomputed, bitwise identical), then F9 and the derivatives with lambda
 //    and the modes from the workspace.
 template <int NB, int NV, int NS, typename T>
-DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e) {
+DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e, int chunk = 0, int nchunk = 1) {
   Env<NB, NV, NS, T> s;
   env_forward<NB, NV, NS, T>(m, a, e, s);
   const WsView& w = a.ws;
@@ -1493,18 +1517,20 @@ DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e) {
   } else {
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
-  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e]);
+  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk);
 }
 
 template <int NB, int NV, int NS, typename T>
 __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
   __shared__ DevModel sm;
   load_model(sm, a.model);
+  // thread t handles env t % n_env, column chunk t / n_env (consecutive threads: consecutive envs)
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_env) return;
-  const int e = a.env_list ? a.env_list[t] : t;
+  if (t >= a.n_env * a.nchunk) return;
+  const int chunk = t / a.n_env, ti = t - chunk * a.n_env;
+  const int e = a.env_list ? a.env_list[ti] : ti;
   if (a.model_id && a.model_id[e] != a.model_index) return;
-  finish_env<NB, NV, NS, T>(sm, a, e);
+  finish_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
 }
 
 }  // namespace ds

@@ -73,8 +73,20 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
       newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
   }
+  // Finish: with a small batch the Jacobian columns (VJP dof passes) of an env are split over
+  // several threads, each recomputing the env's forward pass, so that the launch still fills the
+  // GPU (about 4 CTAs of 128 threads per SM); large batches keep one thread per env.
+  KArgs af = a0;
+  af.nchunk = 1;
+  if (a0.run != DS_RUN_STEP) {
+    const int target = ds_sm_count() * 4 * threads;
+    const int maxc = a0.run == DS_RUN_JAC ? 3 * NV : 2 * NV;
+    int c = target / (a0.n_env > 0 ? a0.n_env : 1);
+    af.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);
+  }
+  const int fblocks = (a0.n_env * af.nchunk + threads - 1) / threads;
   ds_trace_mark(DS_STAGE_FINISH, 1, s);
-  finish_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
+  finish_kernel<NB, NV, NS, T><<<fblocks, threads, 0, s>>>(af);
   ds_trace_mark(DS_STAGE_FINISH, 0, s);
 }
 
