@@ -29,6 +29,7 @@ struct Shape {
   static constexpr int EPW = 32 / L;          // envs per warp
   static constexpr int PS = NC3 | 1;          // odd row stride: rows of doubles hit distinct banks
   static constexpr int THREADS = NS >= 8 ? 64 : 128;
+  static constexpr int MINB = NS >= 8 ? 1 : 4;  // blocks per SM the register budget is sized for
   static constexpr unsigned LMASK = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
 };
 
@@ -40,6 +41,7 @@ struct Smem {
   double U[Shape<NS>::NC3][Shape<NS>::PS];
   double H[Shape<NS>::NC3][Shape<NS>::PS];
   double w[Shape<NS>::NC3];
+  double rd[Shape<NS>::NC3];                 // reciprocals of the Cholesky diagonal
 };
 
 // What a lane is: its row li within the env's group, the contact ci it belongs to (row lanes:
@@ -194,82 +196,107 @@ __device__ __forceinline__ double pick(const double (&a)[N], int j) {
 // One Newton step of the reduced mode equations: the lane holds row li of the matrix (a, over the
 // env's unknown columns um) and its residual F; rowact marks the rows of the reduced system.
 // Returns dx of column li (0 for the columns that are not unknowns).
+//
+// The complete-pivot elimination swaps each pivot column into place (as the one-thread LU does), so
+// that step k touches positions k .. NC3-1 only: with the step index unrolled those ranges are
+// fixed at compile time and the FP64 work per step shrinks with k (the FP64 pipe is this kernel's
+// bound; column moves are selects).  Columns that are not unknowns hold zeros and are never
+// pivots.  mypos tracks where column li currently sits.
 template <int NS>
 __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<NS>::NC3], double F, unsigned um,
                              int nu, bool rowact, bool run) {
   constexpr int NC3 = Shape<NS>::NC3, L = Shape<NS>::L;
+  int mypos = (ln.row && ((um >> ln.li) & 1u)) ? ln.li : -1;
   bool done = !(rowact && run);     // not (or no longer) a pivot candidate
-  unsigned cm = um;                 // columns not yet pivoted
-  unsigned umask = 0u;              // columns of this lane's U row
-  int kp = -1, cp = 0;              // pivot step and pivot column of this lane
+  int kp = -1;                      // pivot step of this lane's row
+  double ipiv = 0.0;                // 1 / its pivot
   int rank = 0;
   double first = 0.0;
   bool go = run;
-#pragma unroll 1
+#pragma unroll
   for (int k = 0; k < NC3; ++k) {
-    if (!__any_sync(kFull, go)) break;
-    double bv = -1.0;
-    int bj = 0;
-    if (!done) {
+    if (go && k >= nu) go = false;
+    if (__any_sync(kFull, go)) {             // (once no env goes on, every later step is skipped)
+      // Candidates are compared by the bit patterns of |a| as integers (the same order as the
+      // values for non-negative doubles, and off the FP64 pipe); NaN entries are never candidates.
+      long long bk = -1;
+      int bj = k;
+      if (!done) {
 #pragma unroll
-      for (int j = 0; j < NC3; ++j) {
-        const double v = fabs(a[j]);
-        if (((cm >> j) & 1u) && v > bv) { bv = v; bj = j; }
+        for (int j = k; j < NC3; ++j) {
+          const long long v = __double_as_longlong(fabs(a[j]));
+          if (v <= 0x7FF0000000000000LL && v > bk) { bk = v; bj = j; }
+        }
       }
-    }
-    int key = (ln.li << 8) | bj;
+      int key = (ln.li << 8) | bj;
 #pragma unroll
-    for (int o = L / 2; o >= 1; o >>= 1) {
-      const double ov = __shfl_xor_sync(kFull, bv, o);
-      const int ok = __shfl_xor_sync(kFull, key, o);
-      if (ov > bv || (ov == bv && ok < key)) { bv = ov; key = ok; }
-    }
-    if (go) {
-      if (k == 0) first = bv;
-      if (!(bv > 1e-13 * first) || bv == 0.0) go = false;
-    }
-    const int bi = key >> 8, bjj = key & 255;
-    const int src = ln.base + (go ? bi : 0);
-    const double own_b = pick(a, bjj);
-    const double pv = __shfl_sync(kFull, own_b, src);
-    const double pf = __shfl_sync(kFull, F, src);
-    const bool elim = go && !done && ln.li != bi;
-    const double l = elim ? own_b * (1.0 / pv) : 0.0;
+      for (int o = L / 2; o >= 1; o >>= 1) {
+        const long long ov = __shfl_xor_sync(kFull, bk, o);
+        const int ok = __shfl_xor_sync(kFull, key, o);
+        if (ov > bk || (ov == bk && ok < key)) { bk = ov; key = ok; }
+      }
+      const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
+      if (go) {
+        if (k == 0) first = bv;
+        if (!(bv > 1e-13 * first) || bv == 0.0) go = false;
+      }
+      const int bi = key >> 8, bjj = key & 255;
+      if (go && bjj != k) {             // pivot column to position k, in every row of the env
+        const double t = a[k];
+        double nk = t;
 #pragma unroll
-    for (int j = 0; j < NC3; ++j) {
-      const double pj = __shfl_sync(kFull, a[j], src);
-      if (elim && ((cm >> j) & 1u) && j != bjj) a[j] -= l * pj;
-    }
-    if (elim) F -= l * pf;
-    if (go) {
-      if (ln.li == bi) { done = true; kp = k; cp = bjj; umask = cm; }
-      cm &= ~(1u << bjj);
-      ++rank;
+        for (int j = k + 1; j < NC3; ++j) {
+          const bool h = j == bjj;
+          const double aj = a[j];
+          nk = h ? aj : nk;
+          a[j] = h ? t : aj;
+        }
+        a[k] = nk;
+        if (mypos == bjj) mypos = k;
+        else if (mypos == k) mypos = bjj;
+      }
+      const int src = ln.base + (go ? bi : 0);
+      const double pv = __shfl_sync(kFull, a[k], src);
+      const double pf = __shfl_sync(kFull, F, src);
+      const bool elim = go && !done && ln.li != bi;
+      const double inv = 1.0 / pv;
+      const double l = elim ? a[k] * inv : 0.0;
+#pragma unroll
+      for (int j = k + 1; j < NC3; ++j) {
+        const double pj = __shfl_sync(kFull, a[j], src);
+        if (elim) a[j] -= l * pj;
+      }
+      if (elim) F -= l * pf;
+      if (go) {
+        if (ln.li == bi) { done = true; kp = k; ipiv = inv; }
+        ++rank;
+      }
     }
   }
   double dx = 0.0;
   const bool full = run && rank == nu;
   const bool mn = run && rank < nu;
-  const int maxrank = int(__reduce_max_sync(kFull, unsigned(run ? rank : 0)));
   // full column rank: back substitution, one pivot at a time from the last
   double s = F;
-#pragma unroll 1
-  for (int k = maxrank - 1; k >= 0; --k) {
+#pragma unroll
+  for (int k = NC3 - 1; k >= 0; --k) {
     const bool stp = full && k < rank;
-    const unsigned ob = gbits<NS>(stp && kp == k, ln);
-    const int own = ob ? __ffs(ob) - 1 : 0;
-    double xk = 0.0;
-    if (stp && kp == k) xk = s / pick(a, cp);
-    xk = __shfl_sync(kFull, xk, ln.base + own);
-    const int ck = __shfl_sync(kFull, cp, ln.base + own);
-    if (stp && kp >= 0 && kp < k) s -= pick(a, ck) * xk;
-    if (stp && ln.row && ln.li == ck) dx = xk;
+    if (__any_sync(kFull, stp)) {
+      const unsigned ob = gbits<NS>(stp && kp == k, ln);
+      const int own = ob ? __ffs(ob) - 1 : 0;
+      double xk = 0.0;
+      if (stp && kp == k) xk = s * ipiv;
+      xk = __shfl_sync(kFull, xk, ln.base + own);
+      if (stp && kp >= 0 && kp < k) s -= a[k] * xk;
+      if (stp && mypos == k) dx = xk;
+    }
   }
-  // rank deficient: x = U^T (U U^T)^-1 y
+  // rank deficient: x = U^T (U U^T)^-1 y over the positions, then back to the columns
   if (__any_sync(kFull, mn)) {
+    const int maxrank = int(__reduce_max_sync(kFull, unsigned(mn ? rank : 0)));
     if (mn && kp >= 0) {
 #pragma unroll
-      for (int j = 0; j < NC3; ++j) S.U[kp][j] = ((umask >> j) & 1u) ? a[j] : 0.0;
+      for (int j = 0; j < NC3; ++j) S.U[kp][j] = j >= kp ? a[j] : 0.0;
     }
     __syncwarp();
     if (mn && kp >= 0) {
@@ -288,13 +315,15 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
       if (stp && kp == j) {
         double d = S.H[j][j];
         for (int c = 0; c < j; ++c) d -= S.H[j][c] * S.H[j][c];
-        S.H[j][j] = sqrt(fmax(d, 1e-300));
+        const double sd = sqrt(fmax(d, 1e-300));
+        S.H[j][j] = sd;
+        S.rd[j] = 1.0 / sd;
       }
       __syncwarp();
       if (stp && kp > j) {
         double t = S.H[kp][j];
         for (int c = 0; c < j; ++c) t -= S.H[kp][c] * S.H[j][c];
-        S.H[kp][j] = t / S.H[j][j];
+        S.H[kp][j] = t * S.rd[j];
       }
       __syncwarp();
     }
@@ -306,7 +335,7 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
       const unsigned ob = gbits<NS>(stp && kp == j, ln);
       const int own = ob ? __ffs(ob) - 1 : 0;
       double wj = 0.0;
-      if (stp && kp == j) { wv = (s - acc) / S.H[j][j]; wj = wv; }
+      if (stp && kp == j) { wv = (s - acc) * S.rd[j]; wj = wv; }
       wj = __shfl_sync(kFull, wj, ln.base + own);
       if (stp && kp > j) acc += S.H[kp][j] * wj;
     }
@@ -317,15 +346,15 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
       const unsigned ob = gbits<NS>(stp && kp == j, ln);
       const int own = ob ? __ffs(ob) - 1 : 0;
       double zj = 0.0;
-      if (stp && kp == j) { zv = (wv - acc2) / S.H[j][j]; zj = zv; }
+      if (stp && kp == j) { zv = (wv - acc2) * S.rd[j]; zj = zv; }
       zj = __shfl_sync(kFull, zj, ln.base + own);
       if (stp && kp >= 0 && kp < j) acc2 += S.H[j][kp] * zj;
     }
     if (mn && kp >= 0) S.w[kp] = zv;
     __syncwarp();
-    if (mn && ln.row && ((um >> ln.li) & 1u)) {
+    if (mn && mypos >= 0) {
       double t = 0.0;
-      for (int k = 0; k < rank; ++k) t += S.U[k][ln.li] * S.w[k];
+      for (int k = 0; k < rank; ++k) t += S.U[k][mypos] * S.w[k];
       dx = t;
     }
     __syncwarp();
@@ -451,7 +480,7 @@ __device__ bool newton_stage(Smem<NS>& S, const Lane<NS>& ln, double lz, double 
 // 4 NS lanes per env.  Same bookkeeping as newton_env: accept (write lambda, modes, status), or
 // move to the next stage and queue the env for the next round.
 template <int NS, typename T>
-__global__ void __launch_bounds__(coop::Shape<NS>::THREADS) newton_coop_kernel(KArgs a) {
+__global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MINB) newton_coop_kernel(KArgs a) {
   using Sh = coop::Shape<NS>;
   constexpr int NC3 = Sh::NC3, L = Sh::L, EPW = Sh::EPW;
   static_assert(32 % L == 0, "4 NS lanes per env must divide the warp");
