@@ -308,6 +308,17 @@ def main():
                 times.append(e0.elapsed_time(e1))
         stages = ds.profile_read()
         ds.profile(False)
+        # the same step replayed from a CUDA graph (launch overhead removed)
+        replay = sim.capture("vjp", vbar) if vjp else sim.capture("jac")
+        gtimes = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gtimes.append(e0.elapsed_time(e1))
         if world > 1:
             t = torch.tensor([sum(times)], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -332,6 +343,7 @@ def main():
         dominant = max(stage_ms, key=stage_ms.get) if stage_ms else None
         results[prec] = dict(
             ms=ms, value=B * world / (ms * 1e-3), clocks=clk.summary(),
+            graph={"value": B * world / (float(np.mean(gtimes)) * 1e-3), "ms_per_step": float(np.mean(gtimes))},
             roofline={"bound": "alu", "kernel": "admm_round_kernel (ADMM rounds, one lane per contact)",
                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                       "traffic": None,
@@ -399,9 +411,10 @@ def main():
                 "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": args.steps * r64["launches"], "cpu_baseline": cpu,
-                "stages": r64["stages"], "dominant_stage": r64["dominant_stage"],
+                "stages": r64["stages"], "dominant_stage": r64["dominant_stage"], "cuda_graph_replay": r64["graph"],
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],
+                          "cuda_graph_replay": rmx["graph"],
                           "stages": rmx["stages"], "dominant_stage": rmx["dominant_stage"],
                           "clocks": rmx["clocks"], "admm_iters": rmx["admm_iters"], "modes": rmx["modes"],
                           "env_status": rmx["status"]},

@@ -144,7 +144,11 @@ ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, cons
 
 /* One step (Eq. 1, 3, 4, 6) for every env.  models[model_id[e]] describes env e; the kernel of a
  * model is the compiled shape (bodies, dofs, slots S) with model_slots[k] <= S <= ncmax and the
- * fewest slots (DS_EUNSUPPORTED if none).  Models run one after the other on the stream.  workspace:
+ * fewest slots (DS_EUNSUPPORTED if none).  With a workspace and several models, each model's
+ * pipeline runs on a helper stream of the library (forked from and joined back to `stream` with
+ * events, so the call stays ordered on `stream`); the first such call on a device creates those
+ * streams (make it outside stream capture).  Without a workspace the models run one after the
+ * other on `stream`.  workspace:
  * NULL, or caller-owned device memory of at least ds_workspace_size() bytes (aligned to 256 bytes),
  * not used concurrently by another call. */
 ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
@@ -212,7 +216,8 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * launches is bracketed by CUDA events on its own stream, grouped in DS_NSTAGES = 5 classes:
  * 0 setup, 1 ADMM rounds, 2 Newton / active-set, 3 finish (step update + derivatives), 4 fused
  * single-kernel path.  ds_profile_read waits for the recorded events, writes the summed
- * milliseconds and launch counts per class to ms[5], launches[5], and clears the record. */
+ * milliseconds and launch counts per class to ms[5], launches[5], and clears the record (kernels
+ * of different models that overlap in time are each counted in full). */
 ds_status ds_profile(int32_t enable);
 ds_status ds_profile_read(double* ms, int32_t* launches);
 

@@ -301,6 +301,22 @@ class Simulator:
         sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, workspace=self.workspace, stream=stream)
         return dict(self.out, dv_dq=self.jac[0], dv_dv=self.jac[1], dv_dtau=self.jac[2])
 
+    def capture(self, kind="jac", v_next_bar=None, q_next_bar=None):
+        """Capture one step (kind "step", "jac" or "vjp", on this Simulator's buffers) in a CUDA
+        graph and return a function that replays it on the current stream.  Inputs are read from
+        self.batch (and the given cotangent tensors) at replay time, outputs land in the same
+        tensors as the eager calls.  Run one eager call first: the library's first call on a device
+        creates its helper streams, which must not happen during capture."""
+        import torch
+        fn = {"step": lambda: self.step(), "jac": lambda: self.step_jac(),
+              "vjp": lambda: self.step_vjp(v_next_bar, q_next_bar=q_next_bar)}[kind]
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g.replay
+
     def step_vjp(self, v_next_bar, stream=None, q_next_bar=None):
         import torch
         if self.vjp_out is None:

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -130,7 +131,34 @@ extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nm
                                        const ds_options* o, size_t* bytes) {
   if (!models || nmodels <= 0 || !b || !o || !bytes) return DS_EINVAL;
   if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
-  *bytes = ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr);
+  *bytes = ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels);
+  return DS_OK;
+}
+
+// Helper streams for mixed-model batches, created on first use per device and kept until exit.
+static constexpr int kHelperStreams = 4;
+struct HelperStreams {
+  cudaStream_t s[kHelperStreams];
+  cudaEvent_t fork, join[kHelperStreams];
+};
+
+static ds_status helper_streams(HelperStreams** out) {
+  static std::mutex mu;
+  static HelperStreams* per_dev[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DS_ECUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!per_dev[dev]) {
+    HelperStreams* h = new (std::nothrow) HelperStreams;
+    if (!h) return DS_ENOMEM;
+    bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < kHelperStreams && ok; ++j)
+      ok = cudaStreamCreateWithFlags(&h->s[j], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->join[j], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) { delete h; return DS_ECUDA; }
+    per_dev[dev] = h;
+  }
+  *out = per_dev[dev];
   return DS_OK;
 }
 
@@ -150,7 +178,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
-  if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr) ||
+  if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels) ||
              (reinterpret_cast<uintptr_t>(ws) & 255) != 0))
     return DS_EINVAL;
   const ds_kernel_entry* kern[64];
@@ -178,8 +206,29 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.env_list = nullptr;
   a.n_env = b->B;
   a.model_id = nmodels > 1 ? b->model_id : nullptr;
-  if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ws && nmodels > 1) {
+    // Each model's pipeline on a helper stream of its own (fork / join with events on the caller's
+    // stream): the models' kernels are small and overlap on the GPU.
+    HelperStreams* hs = nullptr;
+    if (helper_streams(&hs) != DS_OK) return DS_ECUDA;
+    if (cudaEventRecord(hs->fork, s) != cudaSuccess) return DS_ECUDA;
+    for (int k = 0; k < nmodels; ++k) {
+      cudaStream_t sk = hs->s[k % kHelperStreams];
+      if (cudaStreamWaitEvent(sk, hs->fork, 0) != cudaSuccess) return DS_ECUDA;
+      ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k);
+      a.model = models[k]->dev;
+      a.model_index = k;
+      kern[k]->pipeline(a, sk);
+      if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
+    }
+    for (int j = 0; j < kHelperStreams && j < nmodels; ++j) {
+      if (cudaEventRecord(hs->join[j], hs->s[j]) != cudaSuccess) return DS_ECUDA;
+      if (cudaStreamWaitEvent(s, hs->join[j], 0) != cudaSuccess) return DS_ECUDA;
+    }
+    return DS_OK;
+  }
+  if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, 0);
   for (int k = 0; k < nmodels; ++k) {
     const ds_kernel_entry* ke = kern[k];
     a.model = models[k]->dev;

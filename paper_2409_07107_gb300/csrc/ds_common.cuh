@@ -49,10 +49,14 @@ struct WsView {
   double* rho;            // [B]
   int32_t* nlist;         // [B] envs whose ADMM stage ended in a round (Newton queue)
   int32_t* ncounts;       // [DS_ROUNDS]
+  int32_t* fetch;         // [DS_ROUNDS] next unclaimed entry of each round's list (follows ncounts)
 };
 
-// Lays out the workspace for ns contact slots and B envs starting at base (may be NULL to size it).
-inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v) {
+// Lays out the workspace for ns contact slots, B envs and nmodels models starting at base (may be
+// NULL to size it), and returns its size.  The per-env arrays are shared; every model has its own
+// work lists and counters (its pipeline may run concurrently with the others'), and *v gets those
+// of model `model`.
+inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmodels = 1, int model = 0) {
   const int nc3 = 3 * ns;
   size_t off = 0;
   char* b = static_cast<char*>(base);
@@ -62,9 +66,6 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v) {
     return p;
   };
   WsView w;
-  w.counts = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_ROUNDS + 1)));
-  w.list[0] = static_cast<int32_t*>(take(sizeof(int32_t) * B));
-  w.list[1] = static_cast<int32_t*>(take(sizeof(int32_t) * B));
   w.na = static_cast<int32_t*>(take(sizeof(int32_t) * B));
   w.stage = static_cast<int32_t*>(take(sizeof(int32_t) * B));
   w.iters = static_cast<int32_t*>(take(sizeof(int32_t) * B));
@@ -81,8 +82,21 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v) {
   w.asx = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
   w.K = static_cast<double*>(take(sizeof(double) * nc3 * nc3 * size_t(B)));
   w.rho = static_cast<double*>(take(sizeof(double) * size_t(B)));
-  w.nlist = static_cast<int32_t*>(take(sizeof(int32_t) * B));
-  w.ncounts = static_cast<int32_t*>(take(sizeof(int32_t) * DS_ROUNDS));
+  for (int k = 0; k < nmodels; ++k) {
+    int32_t* counts = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_ROUNDS + 1)));
+    int32_t* l0 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+    int32_t* l1 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+    int32_t* nl = static_cast<int32_t*>(take(sizeof(int32_t) * B));
+    int32_t* nc = static_cast<int32_t*>(take(sizeof(int32_t) * 2 * DS_ROUNDS));
+    if (k == model) {
+      w.counts = counts;
+      w.list[0] = l0;
+      w.list[1] = l1;
+      w.nlist = nl;
+      w.ncounts = nc;
+      w.fetch = nc + DS_ROUNDS;
+    }
+  }
   if (v) *v = w;
   return off;
 }

@@ -32,7 +32,7 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   const int blocks = (a0.n_env + threads - 1) / threads;
   if (blocks <= 0) return;
   cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
-  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * DS_ROUNDS, s);
+  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * 2 * DS_ROUNDS, s);   // ncounts and fetch
   ds_trace_mark(DS_STAGE_SETUP, 1, s);
   setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
   ds_trace_mark(DS_STAGE_SETUP, 0, s);

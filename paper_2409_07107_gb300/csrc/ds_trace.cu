@@ -13,7 +13,12 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<Mark> g_marks;      // bracketed launches since the last read
 std::vector<cudaEvent_t> g_pool;
-cudaEvent_t g_open[DS_NSTAGES];
+struct Open {
+  int stage;
+  cudaStream_t stream;
+  cudaEvent_t begin;
+};
+std::vector<Open> g_open;         // begun, not yet ended (per stage and stream: models may overlap)
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -34,11 +39,16 @@ void ds_trace_mark(int stage, int begin, cudaStream_t s) {
   if (!e) return;
   cudaEventRecord(e, s);
   if (begin) {
-    g_open[stage] = e;
-  } else if (g_open[stage]) {
-    g_marks.push_back({stage, g_open[stage], e});
-    g_open[stage] = nullptr;
+    g_open.push_back({stage, s, e});
+    return;
   }
+  for (size_t i = 0; i < g_open.size(); ++i)
+    if (g_open[i].stage == stage && g_open[i].stream == s) {
+      g_marks.push_back({stage, g_open[i].begin, e});
+      g_open.erase(g_open.begin() + i);
+      return;
+    }
+  g_pool.push_back(e);
 }
 
 extern "C" ds_status ds_profile(int32_t enable) {

@@ -241,3 +241,23 @@ def test_uneven_batch_slot_dispatch(torch_cuda):
         b.model_slots = np.array(bad, np.int32)
         with pytest.raises(ds.DiffsimError):
             _gpu(scenes.Workload(wl.name, wl.models, b, wl.options), "fp64", run="step")
+
+
+def test_uneven_batch_cuda_graph(torch_cuda):
+    """The mixed-robot step + VJP (three models, helper streams forked and joined with events)
+    captured in a CUDA graph and replayed gives the eager call's results exactly."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.uneven(96)
+    sim = ds.Simulator(wl, precision="mixed")
+    vb = torch.as_tensor(np.random.default_rng(3).normal(size=wl.batch.v.shape), dtype=torch.float64,
+                         device="cuda")
+    eager = {k: v.clone() for k, v in sim.step_vjp(vb).items()}
+    replay = sim.capture("vjp", vb)
+    for t in (sim.out["v_next"], sim.out["status"], *sim.vjp_out):
+        t.zero_()
+    replay()
+    torch.cuda.synchronize()
+    got = dict(sim.out, q_bar=sim.vjp_out[0], v_bar=sim.vjp_out[1], tau_bar=sim.vjp_out[2])
+    for key in ("v_next", "q_bar", "v_bar", "tau_bar", "status", "modes"):
+        assert torch.equal(got[key], eager[key]), key
