@@ -289,6 +289,8 @@ def main():
     for prec in ("fp64", "mixed"):
         sim = ds.Simulator(wl, precision=prec)
         stream = torch.cuda.current_stream()
+        # pick the pipeline schedule for this batch (ds_autotune; untimed, part of the set-up)
+        schedule = sim.autotune("vjp", vbar) if vjp else sim.autotune("jac")
         for _ in range(args.warmup):
             one_step(sim)
         torch.cuda.synchronize()
@@ -342,7 +344,7 @@ def main():
         achieved = admm_flops / (t_admm * 1e-3) / 1e12
         dominant = max(stage_ms, key=stage_ms.get) if stage_ms else None
         results[prec] = dict(
-            ms=ms, value=B * world / (ms * 1e-3), clocks=clk.summary(),
+            ms=ms, value=B * world / (ms * 1e-3), clocks=clk.summary(), schedule=schedule,
             graph={"value": B * world / (float(np.mean(gtimes)) * 1e-3), "ms_per_step": float(np.mean(gtimes))},
             roofline={"bound": "alu", "kernel": "admm_round_kernel (ADMM rounds, one lane per contact)",
                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -412,9 +414,10 @@ def main():
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": args.steps * r64["launches"], "cpu_baseline": cpu,
                 "stages": r64["stages"], "dominant_stage": r64["dominant_stage"], "cuda_graph_replay": r64["graph"],
+                "schedule": r64["schedule"],
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],
-                          "cuda_graph_replay": rmx["graph"],
+                          "cuda_graph_replay": rmx["graph"], "schedule": rmx["schedule"],
                           "stages": rmx["stages"], "dominant_stage": rmx["dominant_stage"],
                           "clocks": rmx["clocks"], "admm_iters": rmx["admm_iters"], "modes": rmx["modes"],
                           "env_status": rmx["status"]},

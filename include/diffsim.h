@@ -212,6 +212,30 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
                                const ds_options* opt, const ds_step_out* out, double* dv_dq, double* dv_dv,
                                double* dv_dtau, void* stream);
 
+/* Schedule autotuning (no counterpart in the paper).  How the workspace pipeline divides its work
+ * is a schedule: the table of ADMM round caps (how many iterations an env may run before the
+ * lists are compacted: default {32, 32, 64, ..., 4096}, halved, or doubled; the last round always
+ * runs to the iteration limit), the first round handled by the row-per-lane ADMM kernel (3, 5 or
+ * never), how many threads share an env's Jacobian columns in the finish kernel (a target of 0, 4
+ * or 8 CTAs per SM), and the Newton kernel's form (cooperative or one thread per env).
+ * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
+ * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing two
+ * runs of each schedule with CUDA events on `stream` after an untimed one, in a coordinate search
+ * from the default (each knob over its options with the others at the best so far: 8 schedules
+ * besides the default).  It keeps the fastest for the batch's signature (first model's bodies and
+ * dofs, number of models, ncmax, precision, mode, B rounded up to a power of two) and finally runs
+ * the call once more with it, so that *out and o0..o2 hold its results.  Later calls with the
+ * same signature use that schedule; other batches keep the default.  A schedule never changes what
+ * an env computes, except that the two Newton forms round differently (results agree to the solver
+ * tolerance).  Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be
+ * NULL) gets c + 3 (w + 3 (f + 3 n)): round caps c (0 default, 1 halved, 2 doubled), first
+ * row-per-lane round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2),
+ * Newton n (0 cooperative, 1 one thread per env).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
+ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                      const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
+                      double* o0, double* o1, double* o2, void* workspace, size_t workspace_bytes,
+                      void* stream, int32_t* chosen);
+
 /* Stage tracing (no counterpart in the paper): with ds_profile(1), every kernel the library
  * launches is bracketed by CUDA events on its own stream, grouped in DS_NSTAGES = 5 classes:
  * 0 setup, 1 ADMM rounds, 2 Newton / active-set, 3 finish (step update + derivatives), 4 fused

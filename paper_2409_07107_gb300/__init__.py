@@ -28,7 +28,7 @@ ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
-           "ds_cotangent_to_raw")
+           "ds_cotangent_to_raw", "ds_autotune")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -87,9 +87,10 @@ def lib():
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
         for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
+        L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
                   "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read",
-                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
+                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -223,6 +224,32 @@ def cotangent_to_raw(models, q, q_bar_tangent, q_bar_raw, model_id=None, stream=
                                      _ptr(q_bar_tangent), _ptr(q_bar_raw), _stream(stream)))
 
 
+SCHEDULE_CAPS = ("default", "halved", "doubled")
+SCHEDULE_WIDE = (3, 5, None)
+SCHEDULE_FINISH = (0, 4, 8)
+
+
+def describe_schedule(index):
+    """The schedule ds_autotune chose, from its index c + 3 (w + 3 (f + 3 n))."""
+    i = int(index)
+    c, i = i % 3, i // 3
+    wi, i = i % 3, i // 3
+    f, n = i % 3, i // 3
+    return {"round_caps": SCHEDULE_CAPS[c], "row_per_lane_admm_from_round": SCHEDULE_WIDE[wi],
+            "finish_ctas_per_sm": SCHEDULE_FINISH[f], "newton": "one thread per env" if n else "cooperative"}
+
+
+def autotune(models, batch, opt, mode, out, o0=None, o1=None, o2=None, v_next_bar=None, workspace=None,
+             stream=None):
+    """C-ABI ds_autotune; returns the chosen schedule index."""
+    b, o = _batch_struct(batch), _out_struct(out)
+    chosen = ctypes.c_int32(-1)
+    _check(lib().ds_autotune(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt), int(mode),
+                             _ptr(v_next_bar), ctypes.byref(o), _ptr(o0), _ptr(o1), _ptr(o2), *_ws(workspace),
+                             _stream(stream), ctypes.byref(chosen)))
+    return chosen.value
+
+
 def fma_peak(out, blocks, iters, fp64, stream=None):
     """Launch the FMA-throughput probe (2 * 8 * iters * blocks * 256 flops)."""
     _check(lib().ds_fma_peak(_ptr(out), blocks, iters, 1 if fp64 else 0, _stream(stream)))
@@ -300,6 +327,28 @@ class Simulator:
             self.jac = [torch.zeros(n, n, B, dtype=torch.float64, device=self.out["v_next"].device) for _ in range(3)]
         sim_step_jac(self.models, self.batch, self.opt, self.out, *self.jac, workspace=self.workspace, stream=stream)
         return dict(self.out, dv_dq=self.jac[0], dv_dv=self.jac[1], dv_dtau=self.jac[2])
+
+    def autotune(self, kind="jac", v_next_bar=None):
+        """Pick this batch's pipeline schedule by timing the candidates (ds_autotune); returns the
+        chosen schedule's description.  Later calls on batches of the same signature use it."""
+        import torch
+        mode = {"step": 0, "jac": 1, "vjp": 2}[kind]
+        B = self.workload.batch.B
+        dev = self.out["v_next"].device
+        if kind == "jac":
+            if self.jac is None:
+                n = self.nv
+                self.jac = [torch.zeros(n, n, B, dtype=torch.float64, device=dev) for _ in range(3)]
+            o = self.jac
+        elif kind == "vjp":
+            if self.vjp_out is None:
+                self.vjp_out = [torch.zeros_like(self.out["v_next"]) for _ in range(3)]
+            o = self.vjp_out
+        else:
+            o = [None, None, None]
+        idx = autotune(self.models, self.batch, self.opt, mode, self.out, *o, v_next_bar=v_next_bar,
+                       workspace=self.workspace)
+        return dict(describe_schedule(idx), index=idx)
 
     def capture(self, kind="jac", v_next_bar=None, q_next_bar=None):
         """Capture one step (kind "step", "jac" or "vjp", on this Simulator's buffers) in a CUDA

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -135,6 +136,9 @@ extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nm
   return DS_OK;
 }
 
+// Set only while ds_autotune times a candidate, for the calls of its own thread.
+static thread_local const ds_schedule* g_force_sched = nullptr;
+
 // Helper streams for mixed-model batches, created on first use per device and kept until exit.
 static constexpr int kHelperStreams = 4;
 struct HelperStreams {
@@ -160,6 +164,34 @@ static ds_status helper_streams(HelperStreams** out) {
   }
   *out = per_dev[dev];
   return DS_OK;
+}
+
+// Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0};
+struct SchedKey {
+  int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
+  bool operator<(const SchedKey& o) const {
+    const int x[7] = {nmodels, nb0, nv0, ncmax, precision, mode, bbucket};
+    const int y[7] = {o.nmodels, o.nb0, o.nv0, o.ncmax, o.precision, o.mode, o.bbucket};
+    for (int i = 0; i < 7; ++i)
+      if (x[i] != y[i]) return x[i] < y[i];
+    return false;
+  }
+};
+static std::mutex g_sched_mu;
+static std::map<SchedKey, ds_schedule> g_sched;
+
+static SchedKey sched_key(const ds_model* const* models, int nmodels, const ds_batch* b, const ds_options* o,
+                          int mode) {
+  int bb = 0;
+  while ((1 << bb) < b->B && bb < 30) ++bb;
+  return SchedKey{nmodels, models[0]->host.nb, models[0]->host.nv, b->ncmax, o->precision, mode, bb};
+}
+
+static ds_schedule find_schedule(const SchedKey& k) {
+  std::lock_guard<std::mutex> lock(g_sched_mu);
+  auto it = g_sched.find(k);
+  return it == g_sched.end() ? kDefaultSchedule : it->second;
 }
 
 static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
@@ -206,6 +238,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.env_list = nullptr;
   a.n_env = b->B;
   a.model_id = nmodels > 1 ? b->model_id : nullptr;
+  a.sched = g_force_sched ? *g_force_sched : find_schedule(sched_key(models, nmodels, b, o, mode));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (ws && nmodels > 1) {
     // Each model's pipeline on a helper stream of its own (fork / join with events on the caller's
@@ -332,4 +365,75 @@ extern "C" ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t 
                                          const int32_t* model_id, const double* q, const double* q_bar_tangent,
                                          double* q_bar_raw, void* stream) {
   return cotangent(models, nmodels, B, model_id, q, q_bar_tangent, q_bar_raw, 1, stream);
+}
+
+// ------------------------------------------------------------------------------ autotuning
+extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                                 const ds_options* opt, int32_t mode, const double* v_next_bar,
+                                 const ds_step_out* out, double* o0, double* o1, double* o2, void* ws,
+                                 size_t ws_bytes, void* stream, int32_t* chosen) {
+  if (!models || nmodels <= 0 || nmodels > 64 || !batch || !opt || !out || !ws) return DS_EINVAL;
+  if (mode < DS_RUN_STEP || mode > DS_RUN_VJP) return DS_EINVAL;
+  for (int k = 0; k < nmodels; ++k)
+    if (!models[k]) return DS_EINVAL;
+  if (batch->B <= 0) return DS_EINVAL;
+  static std::mutex tune_mu;
+  std::lock_guard<std::mutex> lock(tune_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto call = [&]() -> ds_status {
+    if (mode == DS_RUN_STEP) return sim_step(models, nmodels, batch, opt, out, ws, ws_bytes, stream);
+    if (mode == DS_RUN_JAC) return sim_step_jac(models, nmodels, batch, opt, out, o0, o1, o2, ws, ws_bytes, stream);
+    return sim_step_vjp(models, nmodels, batch, opt, v_next_bar, nullptr, out, o0, o1, o2, ws, ws_bytes, stream);
+  };
+  // Coordinate search from the default: each knob in turn over its options, the others held at
+  // the best found so far (round caps, first row-per-lane round, finish split target, Newton form).
+  static const int kOpts[4][3] = {{0, 1, 2}, {3, 5, DS_ROUNDS}, {0, 4, 8}, {0, 1, 0}};
+  static const int kNopt[4] = {3, 3, 3, 2};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DS_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DS_ECUDA; }
+  ds_schedule best = kDefaultSchedule;
+  ds_status st = DS_OK;
+  auto timed = [&](const ds_schedule& c, float* ms_out) -> ds_status {
+    g_force_sched = &c;
+    ds_status r = call();                                 // untimed
+    float total = 0.f;
+    for (int k = 0; k < 2 && r == DS_OK; ++k) {
+      cudaEventRecord(e0, s);
+      r = call();
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (r == DS_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        r = DS_ECUDA;
+      total += ms;
+    }
+    g_force_sched = nullptr;
+    *ms_out = total;
+    return r;
+  };
+  float best_ms = 0.f;
+  st = timed(best, &best_ms);
+  for (int d = 0; d < 4 && st == DS_OK; ++d)
+    for (int o = 0; o < kNopt[d] && st == DS_OK; ++o) {
+      ds_schedule c = best;
+      int* field = d == 0 ? &c.caps : (d == 1 ? &c.wide_from : (d == 2 ? &c.finish_ctas : &c.newton_thread));
+      if (*field == kOpts[d][o]) continue;
+      *field = kOpts[d][o];
+      float ms = 0.f;
+      st = timed(c, &ms);
+      if (st == DS_OK && ms < best_ms) { best_ms = ms; best = c; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DS_OK) return st;
+  {
+    std::lock_guard<std::mutex> l2(g_sched_mu);
+    g_sched[sched_key(models, nmodels, batch, opt, mode)] = best;
+  }
+  if (chosen) {
+    const int wi = best.wide_from == 3 ? 0 : (best.wide_from == 5 ? 1 : 2);
+    const int fi = best.finish_ctas == 0 ? 0 : (best.finish_ctas == 4 ? 1 : 2);
+    *chosen = best.caps + 3 * (wi + 3 * (fi + 3 * best.newton_thread));
+  }
+  return call();                                          // leave the outputs of the chosen schedule
 }

@@ -101,6 +101,14 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
   return off;
 }
 
+// How the pipeline divides the work (never what an env computes, except that the one-thread and
+// cooperative Newton kernels round differently): ADMM round-cap table, the first round run by the
+// row-per-lane ADMM kernel (DS_ROUNDS = never), finish-kernel target CTAs per SM for splitting
+// Jacobian columns (0 = one thread per env), Newton kernel form.
+struct ds_schedule {
+  int caps, wide_from, finish_ctas, newton_thread;
+};
+
 // Everything a launch needs; passed by value.
 struct KArgs {
   const DevModel* model;
@@ -127,6 +135,7 @@ struct KArgs {
   WsView ws;               // pipeline workspace (unused by the fused kernel)
   int round, round_cap, final_round;
   int nchunk;              // finish kernel: threads per env (Jacobian columns split between them)
+  ds_schedule sched;
 };
 
 typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);

@@ -1400,6 +1400,126 @@ __global__ void __launch_bounds__(128) admm_round_kernel(KArgs a) {
   }
 }
 
+// 2a'. the same ADMM round with one lane per row of K (3 NS rows, rounded up to a power-of-two
+//      group of lanes per env).  Each lane does a third of the 3-row form's fused multiply-adds
+//      per iteration, at fewer envs per warp.  The late rounds hold few envs, and their time is
+//      the latency of one warp's iterations: the FP64 pipe is charged per warp instruction, so a
+//      shorter instruction stream per iteration is what shortens them.  Every row's arithmetic is
+//      the 3-row form's, in the same order, so the two kernels hand envs to each other between
+//      rounds without changing any result.
+template <int NS>
+struct WideShape {
+  static constexpr int R = 3 * NS;
+  static constexpr int L = R <= 4 ? 4 : (R <= 8 ? 8 : (R <= 16 ? 16 : 32));
+  static constexpr bool kOk = R <= 32;
+};
+
+template <int NS, typename T>
+__global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
+  static_assert(WideShape<NS>::kOk, "3 NS rows must fit in a warp");
+  constexpr int L = WideShape<NS>::L, EPW = 32 / L, NC3 = 3 * NS;
+  const WsView& w = a.ws;
+  const int n = w.counts[a.round];
+  const int B = a.B;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / L, li = lane - grp * L;
+  const int gb = grp * L;
+  const int ci = li < NC3 ? li / 3 : NS - 1, kc = li < NC3 ? li - 3 * (li / 3) : 0;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int32_t* cur = w.list[a.round & 1];
+  int32_t* next = w.list[(a.round + 1) & 1];
+  for (int base = warp * EPW; base < n; base += nwarps * EPW) {
+    const int t = base + grp;
+    const bool have = t < n;
+    const int e = have ? cur[t] : 0;
+    const int na = have ? w.na[e] : 0;
+    const bool act = li < 3 * na;
+    T Kr[NC3];
+#pragma unroll
+    for (int c = 0; c < NC3; ++c) Kr[c] = act ? T(w.K[(li * NC3 + c) * B + e]) : T(0);
+    T x = act ? T(w.ax[li * B + e]) : T(0);
+    T z = act ? T(w.az[li * B + e]) : T(0);
+    T y = act ? T(w.ay[li * B + e]) : T(0);
+    T sx = act ? T(w.asx[li * B + e]) : T(0);
+    const T g = act ? T(w.g[li * B + e]) : T(0);
+    const T mu = act ? T(w.mu[ci * B + e]) : T(0);
+    const T rho = have ? T(w.rho[e]) : T(1);
+    const T inv_rho = T(1) / rho;
+    const T inv1pmu2 = T(1) / (T(1) + mu * mu);
+    const T gs = fmax(T(1), group_max(T(fabs(g)), L));
+    int iters = have ? w.iters[e] : 0;
+    const int stage = have ? w.stage[e] : 0;
+    const T te = T(stage_eps<T>(a, stage));
+    bool running = have && iters < a.admm_max_iter;
+    bool conv = false;
+    const T relax = T(1.6);
+    for (int k = 0; k < a.round_cap; ++k) {
+      if (!__any_sync(0xffffffffu, running)) break;
+      // right-hand side of this row (the De Saxce term from the contact's tangential sigma)
+      const T s0 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci);
+      const T s1 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci + 1);
+      T nt, inv;
+      norm_and_inv(s0, s1, nt, inv);
+      T rhs = rho * z - y - g;
+      if (kc == 2) rhs = rhs - mu * nt;
+      if (!act) rhs = T(0);
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NC3; ++c) acc += Kr[c] * __shfl_sync(0xffffffffu, rhs, gb + c);
+      const T xn = acc;
+      const T sxn = kc < 2 ? rhs - rho * acc + g : sx;
+      const T xh = relax * xn + (T(1) - relax) * z;
+      const T wv = xh + y * inv_rho;
+      T wc[3], pr[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) wc[r] = __shfl_sync(0xffffffffu, wv, gb + 3 * ci + r);
+      proj_cone_fast(wc, mu, inv1pmu2, pr);
+      const T zn = kc == 0 ? pr[0] : (kc == 1 ? pr[1] : pr[2]);
+      const bool chk = (iters + 1) % DS_ADMM_CHECK == 0;
+      T rp = T(0), rd = T(0), zmax = T(1);
+      if (act && chk) {
+        rd = fabs(zn - z);
+        rp = fabs(xn - zn);
+        zmax = fmax(zmax, fabs(zn));
+      }
+      if (__any_sync(0xffffffffu, running && chk)) {
+        rp = group_max(rp, L);
+        rd = group_max(rd, L);
+        zmax = group_max(zmax, L);
+      }
+      if (running) {
+        x = xn;
+        z = zn;
+        y = y + rho * (xh - zn);
+        sx = sxn;
+        ++iters;
+        rd *= rho;
+        if (chk && rp <= te * zmax && rd <= te * gs) { conv = true; running = false; }
+        else if (iters >= a.admm_max_iter) running = false;
+      }
+    }
+    if (have) {
+      if (act) {
+        w.ax[li * B + e] = double(x);
+        w.az[li * B + e] = double(z);
+        w.ay[li * B + e] = double(y);
+        w.asx[li * B + e] = double(sx);
+      }
+      if (li == 0) {
+        w.iters[e] = iters;
+        if (conv || iters >= a.admm_max_iter || a.final_round) {
+          const int k = atomicAdd(&w.ncounts[a.round], 1);
+          w.nlist[k] = e;
+        } else {
+          const int k = atomicAdd(&w.counts[a.round + 1], 1);
+          next[k] = e;
+        }
+      }
+    }
+  }
+}
+
 // 2b. the Newton / active-set stage for the envs whose ADMM stage ended in this round (one thread
 //     per env): accept, or move to the next (tighter) stage and queue for the next round.
 template <int NS, typename T>

@@ -36,7 +36,13 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   ds_trace_mark(DS_STAGE_SETUP, 1, s);
   setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
   ds_trace_mark(DS_STAGE_SETUP, 0, s);
-  static const int caps[DS_ROUNDS] = {32, 32, 64, 128, 256, 512, 1024, 2048, 4096};
+  // Round caps (ADMM iterations an env may run per round before regrouping); the last round runs
+  // up to the iteration limit, so the choice of table never changes an env's result.
+  static const int kCaps[3][DS_ROUNDS] = {{32, 32, 64, 128, 256, 512, 1024, 2048, 4096},
+                                          {16, 16, 32, 64, 128, 256, 512, 1024, 2048},
+                                          {64, 64, 128, 256, 512, 1024, 2048, 4096, 4096}};
+  const ds_schedule sc = a0.sched;
+  const int* caps = kCaps[(sc.caps >= 0 && sc.caps < 3) ? sc.caps : 0];
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_round_kernel<NS, T>, threads, 0);
   if (per_sm <= 0) per_sm = 1;
@@ -44,16 +50,30 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   int rblocks = ds_sm_count() * per_sm;
   const int need = (a0.n_env + envs_per_block - 1) / envs_per_block;
   if (rblocks > need) rblocks = need;
+  // the row-per-lane ADMM kernel for the late rounds (where the schedule says so and 3 NS <= 32)
+  constexpr bool kWideOk = WideShape<NS>::kOk;
+  int wblocks = 1;
+  if constexpr (kWideOk) {
+    int wper = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, admm_round_wide_kernel<NS, T>, threads, 0);
+    if (wper <= 0) wper = 1;
+    const int wenvs = threads / WideShape<NS>::L;
+    wblocks = ds_sm_count() * wper;
+    const int wneed = (a0.n_env + wenvs - 1) / wenvs;
+    if (wblocks > wneed) wblocks = wneed;
+  }
   // Newton stage: the cooperative kernel (4 NS lanes per env) where 4 NS divides the warp, else
   // one thread per env.
-  constexpr bool kCoop = 32 % (4 * NS) == 0;
-  const int nthreads = kCoop ? coop::Shape<kCoop ? NS : 1>::THREADS : threads;
-  const int envs_per_nblock = kCoop ? nthreads / (4 * NS) : nthreads;
+  // (the schedule may ask for the one-thread form instead).
+  constexpr bool kCoopOk = 32 % (4 * NS) == 0;
+  const bool coop = kCoopOk && !sc.newton_thread;
+  const int nthreads = coop ? coop::Shape<kCoopOk ? NS : 1>::THREADS : threads;
+  const int envs_per_nblock = coop ? nthreads / (4 * NS) : nthreads;
   int nper = 0;
-  if constexpr (kCoop)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_coop_kernel<NS, T>, nthreads, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_kernel<NS, T>, nthreads, 0);
+  if constexpr (kCoopOk) {
+    if (coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_coop_kernel<NS, T>, nthreads, 0);
+  }
+  if (!coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nper, newton_kernel<NS, T>, nthreads, 0);
   if (nper <= 0) nper = 1;
   int nblocks = ds_sm_count() * nper;
   const int nneed = (a0.n_env + envs_per_nblock - 1) / envs_per_nblock;
@@ -61,25 +81,30 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   for (int r = 0; r < DS_ROUNDS; ++r) {
     KArgs a = a0;
     a.round = r;
-    a.round_cap = caps[r];
     a.final_round = r == DS_ROUNDS - 1;
+    a.round_cap = a.final_round ? (a0.admm_max_iter > caps[r] ? a0.admm_max_iter : caps[r]) : caps[r];
     ds_trace_mark(DS_STAGE_ADMM, 1, s);
-    admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
+    bool wide = false;
+    if constexpr (kWideOk) {
+      if (r >= sc.wide_from) { admm_round_wide_kernel<NS, T><<<wblocks, threads, 0, s>>>(a); wide = true; }
+    }
+    if (!wide) admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_ADMM, 0, s);
     ds_trace_mark(DS_STAGE_NEWTON, 1, s);
-    if constexpr (kCoop)
-      newton_coop_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
-    else
-      newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
+    bool launched = false;
+    if constexpr (kCoopOk) {
+      if (coop) { newton_coop_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a); launched = true; }
+    }
+    if (!launched) newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
   }
   // Finish: with a small batch the Jacobian columns (VJP dof passes) of an env are split over
   // several threads, each recomputing the env's forward pass, so that the launch still fills the
-  // GPU (about 4 CTAs of 128 threads per SM); large batches keep one thread per env.
+  // GPU (by default about 4 CTAs of 128 threads per SM); large batches keep one thread per env.
   KArgs af = a0;
   af.nchunk = 1;
-  if (a0.run != DS_RUN_STEP) {
-    const int target = ds_sm_count() * 4 * threads;
+  if (a0.run != DS_RUN_STEP && sc.finish_ctas > 0) {
+    const int target = ds_sm_count() * sc.finish_ctas * threads;
     const int maxc = a0.run == DS_RUN_JAC ? 3 * NV : 2 * NV;
     int c = target / (a0.n_env > 0 ? a0.n_env : 1);
     af.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);

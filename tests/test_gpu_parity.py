@@ -261,3 +261,26 @@ def test_uneven_batch_cuda_graph(torch_cuda):
     got = dict(sim.out, q_bar=sim.vjp_out[0], v_bar=sim.vjp_out[1], tau_bar=sim.vjp_out[2])
     for key in ("v_next", "q_bar", "v_bar", "tau_bar", "status", "modes"):
         assert torch.equal(got[key], eager[key]), key
+
+
+def test_autotune_keeps_results(torch_cuda):
+    """ds_autotune picks a schedule by timing; the step's results under it agree with the
+    default schedule's (schedules change how work is divided, not an env's arithmetic, except the
+    Newton form's rounding)."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(3000)
+    sim = ds.Simulator(wl, precision="fp64")
+    ref = {k: v.clone() for k, v in sim.step_jac().items()}
+    desc = sim.autotune("jac")
+    assert 0 <= desc["index"] < 54
+    got = sim.step_jac()
+    torch.cuda.synchronize()
+    ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
+    assert ok.float().mean().item() > 0.8
+    scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
+    assert ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale)[ok].max().item() <= 1e-9
+    for key in ("dv_dq", "dv_dv", "dv_dtau"):
+        sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
+        assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[ok].max().item() <= 1e-8, key
+    assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
