@@ -23,7 +23,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2409_07107_gb300 import scenes  # noqa: E402
+from paper_2409_07107_gb300 import replicas, scenes  # noqa: E402
 
 WORKLOAD_B = 65536
 METRIC = "env-steps/s with full dv'/d(q,v,tau) at 1 GB300"
@@ -131,10 +131,14 @@ def bench_rollout(args, rank, world):
     import torch
     import paper_2409_07107_gb300 as ds
     from paper_2409_07107_gb300 import build, rollout as R
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
     build.build()
     ds.lib()
     B, T, every = args.envs or 4096, args.horizon, 20
-    wl = scenes.quadruped_feet(B, seed=1004 + rank * 7919)
+    wl = scenes.quadruped_feet(B, seed=replicas.rank_seed(1004, rank))
     rng = np.random.default_rng(21 + rank)
     dev = dict(dtype=torch.float64, device="cuda")
     nv = wl.batch.v.shape[0]
@@ -159,6 +163,8 @@ def bench_rollout(args, rank, world):
         for _ in range(args.warmup):
             one(ev)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.reset_peak_memory_stats()
         base = torch.cuda.memory_allocated()
         times = []
@@ -176,8 +182,8 @@ def bench_rollout(args, rank, world):
         # library kernels counted by the stage tracer, plus the two cotangent-map kernels per reverse step
         launches = sum(n for _, n in ds.profile_read().values()) + 2 * T * args.steps
         ds.profile(False)
-        ms = float(np.mean(times))
-        res[ev] = {"ms_per_rollout": ms, "value": B * T / (ms * 1e-3),
+        ms = replicas.slowest_ms(float(np.mean(times)))
+        res[ev] = {"ms_per_rollout": ms, "value": replicas.job_throughput(B * T, world, ms),
                    "peak_extra_mib": (torch.cuda.max_memory_allocated() - base) / 2 ** 20, "clocks": clk.summary(),
                    "launches": launches}
     r = res[every]
@@ -194,6 +200,8 @@ def bench_rollout(args, rank, world):
             "gpu_launches": r["launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -210,6 +218,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=200, help="rollout length (quadruped18-rollout)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default pipeline schedule")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -234,10 +243,10 @@ def main():
                       "v_bar ~ N(0, 1)"}[wl_name]
     cfg = {"workload": "%s: %s, %d envs per GPU, dt=1e-3" % (wl_name, desc, B),
            "envs_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)"}
-    make = {"arm7-cube": lambda n, r: scenes.arm_cube(n, seed=1001 + r * 7919),
-            "humanoid36-feet": lambda n, r: scenes.humanoid_feet(n, seed=1002 + r * 7919),
-            "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=1004 + r * 7919),
-            "uneven": lambda n, r: scenes.uneven(n, seed=1003 + r * 7919)}[wl_name]
+    make = {"arm7-cube": lambda n, r: scenes.arm_cube(n, seed=replicas.rank_seed(1001, r)),
+            "humanoid36-feet": lambda n, r: scenes.humanoid_feet(n, seed=replicas.rank_seed(1002, r)),
+            "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=replicas.rank_seed(1004, r)),
+            "uneven": lambda n, r: scenes.uneven(n, seed=replicas.rank_seed(1003, r))}[wl_name]
 
     if args.impl == "reference":
         if rank != 0:
@@ -290,7 +299,9 @@ def main():
         sim = ds.Simulator(wl, precision=prec)
         stream = torch.cuda.current_stream()
         # pick the pipeline schedule for this batch (ds_autotune; untimed, part of the set-up)
-        schedule = sim.autotune("vjp", vbar) if vjp else sim.autotune("jac")
+        schedule = None
+        if not args.no_autotune:
+            schedule = sim.autotune("vjp", vbar) if vjp else sim.autotune("jac")
         for _ in range(args.warmup):
             one_step(sim)
         torch.cuda.synchronize()
@@ -321,12 +332,7 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             gtimes.append(e0.elapsed_time(e1))
-        if world > 1:
-            t = torch.tensor([sum(times)], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = t.item()
-        else:
-            total_ms = sum(times)
+        total_ms = replicas.slowest_ms(sum(times))      # max over ranks (replicas; no data exchange)
         ms = total_ms / args.steps
         out = sim.out
         iters = out["iters"].cpu().numpy().astype(np.int64)
@@ -344,7 +350,7 @@ def main():
         achieved = admm_flops / (t_admm * 1e-3) / 1e12
         dominant = max(stage_ms, key=stage_ms.get) if stage_ms else None
         results[prec] = dict(
-            ms=ms, value=B * world / (ms * 1e-3), clocks=clk.summary(), schedule=schedule,
+            ms=ms, value=replicas.job_throughput(B, world, ms), clocks=clk.summary(), schedule=schedule,
             graph={"value": B * world / (float(np.mean(gtimes)) * 1e-3), "ms_per_step": float(np.mean(gtimes))},
             roofline={"bound": "alu", "kernel": "admm_round_kernel (ADMM rounds, one lane per contact)",
                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -396,7 +402,7 @@ def main():
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_value = B * world / (np.mean(e2e_ms) * 1e-3)
+    e2e_value = replicas.job_throughput(B, world, replicas.slowest_ms(float(np.mean(e2e_ms))))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1067,9 +1067,38 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
 
     const T dt = T(a.dt);
     if (a.run == DS_RUN_JAC) {
-      // ---- B1/B2/B5/B6 one Jacobian column at a time:
-      // D = dv+/dtheta at fixed lambda, RHS = J_c D + F, X = -A^- B RHS, dv = D + Y C X
+      // ---- B1/B2/B5/B6: dv = D + Y C X with X = -A^- B (J_c D + F), column by column.  When this
+      // thread has more columns than there are rows, the implicit part is applied by rows:
+      // P_k = B^T (A^-)^T C^T Y^T e_k (one transposed minimum-norm solve per output row, nv of
+      // them) gives row k of Y C A^- B, and every column then costs a dot product per row instead
+      // of a solve; otherwise each column solves for its X.
       const int c0 = (3 * NV * chunk) / nchunk, c1 = (3 * NV * (chunk + 1)) / nchunk;
+      const bool by_rows = md > 0 && NV < c1 - c0;
+      double P[NV][3 * NS];
+      if (by_rows) {
+        for (int k = 0; k < NV; ++k) {
+          double u[3 * NS], z[3 * NS];
+          for (int ac = 0; ac < s.na; ++ac) {
+            if (sz[ac] == 0) continue;
+            if (sz[ac] == 3) {
+              for (int r = 0; r < 3; ++r) u[off[ac] + r] = double(s.Y[3 * ac + r][k]);
+            } else {
+              for (int c = 0; c < 2; ++c)
+                u[off[ac] + c] = Rm[ac][0][c] * double(s.Y[3 * ac][k]) + Rm[ac][1][c] * double(s.Y[3 * ac + 1][k]) +
+                                 Rm[ac][2][c] * double(s.Y[3 * ac + 2][k]);
+            }
+          }
+          s.lu.solve_t_mn(u, z);
+          for (int ac = 0; ac < s.na; ++ac) {
+            for (int r = 0; r < 3; ++r) {
+              double p = 0.0;
+              if (sz[ac] == 3) p = z[off[ac] + r];
+              else if (sz[ac] == 2) p = RP[ac][0][r] * z[off[ac]] + RP[ac][1][r] * z[off[ac] + 1];
+              P[k][3 * ac + r] = p;
+            }
+          }
+        }
+      }
       for (int col = c0; col < c1; ++col) {
         const int blk = col / NV, d = col % NV;
         T Dc[NV];
@@ -1084,7 +1113,24 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           fwd_packed(s.L, Dc, NV);
           bwd_packed(s.L, Dc, NV);
         }
-        if (md > 0) {
+        if (by_rows) {
+          double rfull[3 * NS];
+          for (int ac = 0; ac < s.na; ++ac) {
+            T fk[3] = {T(0), T(0), T(0)};
+            if (sz[ac] != 0 && blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
+            for (int r = 0; r < 3; ++r) {
+              T t = fk[r];
+              if (sz[ac] != 0)
+                for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * Dc[k];
+              rfull[3 * ac + r] = double(t);
+            }
+          }
+          for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int j = 0; j < mdim; ++j) t += P[k][j] * rfull[j];
+            Dc[k] -= T(t);
+          }
+        } else if (md > 0) {
           double rhs[3 * NS], X[3 * NS];
           for (int ac = 0; ac < s.na; ++ac) {
             if (sz[ac] == 0) continue;

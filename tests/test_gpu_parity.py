@@ -284,3 +284,21 @@ def test_autotune_keeps_results(torch_cuda):
         sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
         assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[ok].max().item() <= 1e-8, key
     assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+def test_arm_cube_full_size_sampled(torch_cuda, precision, tol_v, tol_j):
+    """The benchmark's configuration: 65536 envs in one call (one thread per env in the finish
+    kernel, the implicit part applied by rows), with outputs sampled across the batch (first,
+    last and 46 seeded indices) against the oracle."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(65536)
+    sim = ds.Simulator(wl, precision=precision)
+    out = sim.step_jac()
+    torch.cuda.synchronize()
+    envs = sorted(set([0, 65535] + list(np.random.default_rng(5).choice(65536, 46, replace=False))))
+    g = {k: v[..., envs].cpu().numpy() for k, v in out.items()}
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
+    refs = run_oracle(sub, list(range(len(envs))))
+    _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=30)

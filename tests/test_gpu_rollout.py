@@ -109,3 +109,35 @@ def test_rollout_gradient(torch_cuda, every):
         assert rel_err(g[:, :, e], ref) <= 1e-8, e
         checked += 1
     assert checked >= 2
+
+
+def test_rollout_gradient_vs_gpu_central_differences(torch_cuda):
+    """The rollout check on the GPU path itself: per-env directional derivatives of
+    loss = |q_T - q_goal|^2 (20 steps, 8 envs, checkpoints every 5 steps) by central differences of
+    GPU rollouts (h = 1e-6, FP64) against the autograd gradient.  An env whose trajectory crosses a
+    mode or contact switch within h is not differentiable there, so 6 of the 8 must agree."""
+    from paper_2409_07107_gb300 import rollout as R
+    torch = torch_cuda
+    wl = scenes.quadruped_feet(8)
+    T, h = 20, 1e-6
+    rng = np.random.default_rng(17)
+    dev = dict(dtype=torch.float64, device="cuda")
+    nv = wl.batch.v.shape[0]
+    mask = torch.ones(1, nv, 1, **dev)
+    mask[:, :6] = 0.0
+    taus = torch.tensor(rng.normal(size=(T, nv, wl.batch.B)) * 2.0, **dev) * mask
+    sc = R.StepContext(wl, precision="fp64")
+    q0, v0 = torch.tensor(wl.batch.q, **dev), torch.tensor(wl.batch.v, **dev)
+    with torch.no_grad():
+        goal, _ = R.rollout(sc, q0, v0, list(taus + torch.tensor(rng.normal(size=taus.shape) * 0.5, **dev) * mask), 0)
+    tau_p = taus.clone().requires_grad_(True)
+    qT, _ = R.rollout(sc, q0, v0, list(tau_p), 5)
+    ((qT - goal) ** 2).sum().backward()
+    u = torch.tensor(rng.normal(size=taus.shape), **dev) * mask
+    with torch.no_grad():
+        lp = ((R.rollout(sc, q0, v0, list(taus + h * u), 0)[0] - goal) ** 2).sum(0)
+        lm = ((R.rollout(sc, q0, v0, list(taus - h * u), 0)[0] - goal) ** 2).sum(0)
+    fd = ((lp - lm) / (2 * h)).cpu().numpy()
+    an = (tau_p.grad * u).sum((0, 1)).cpu().numpy()
+    rel = np.abs(fd - an) / np.maximum(np.abs(an), 1e-8)
+    assert (rel <= 1e-4).sum() >= 6, rel
