@@ -148,7 +148,9 @@ ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, cons
  * pipeline runs on a helper stream of the library (forked from and joined back to `stream` with
  * events, so the call stays ordered on `stream`); the first such call on a device creates those
  * streams (make it outside stream capture).  Without a workspace the models run one after the
- * other on `stream`.  workspace:
+ * other on `stream`.  With a workspace the finish of the envs solved early may also run on a helper
+ * stream (the schedule's overlap, see ds_autotune), joined back to `stream` before the call's work
+ * ends there.  workspace:
  * NULL, or caller-owned device memory of at least ds_workspace_size() bytes (aligned to 256 bytes),
  * not used concurrently by another call. */
 ds_status sim_step(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
@@ -217,20 +219,23 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * lists are compacted: default {32, 32, 64, ..., 4096}, halved, or doubled; the last round always
  * runs to the iteration limit), the first round handled by the row-per-lane ADMM kernel (3, 5 or
  * never), how many threads share an env's Jacobian columns in the finish kernel (a target of 0, 4
- * or 8 CTAs per SM), and the Newton kernel's form (cooperative or one thread per env).
+ * or 8 CTAs per SM), the Newton kernel's form (cooperative or one thread per env), and the round
+ * after which the envs already solved are finished on a side stream of the library while the slow
+ * ones still iterate (2, 4 or never).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing two
  * runs of each schedule with CUDA events on `stream` after an untimed one, in a coordinate search
- * from the default (each knob over its options with the others at the best so far: 8 schedules
+ * from the default (each knob over its options with the others at the best so far: 10 schedules
  * besides the default).  It keeps the fastest for the batch's signature (first model's bodies and
  * dofs, number of models, ncmax, precision, mode, B rounded up to a power of two) and finally runs
  * the call once more with it, so that *out and o0..o2 hold its results.  Later calls with the
  * same signature use that schedule; other batches keep the default.  A schedule never changes what
  * an env computes, except that the two Newton forms round differently (results agree to the solver
  * tolerance).  Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be
- * NULL) gets c + 3 (w + 3 (f + 3 n)): round caps c (0 default, 1 halved, 2 doubled), first
- * row-per-lane round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2),
- * Newton n (0 cooperative, 1 one thread per env).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
+ * NULL) gets c + 3 (w + 3 (f + 3 (n + 2 o))): round caps c (0 default, 1 halved, 2 doubled),
+ * first row-per-lane round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1,
+ * 2), Newton n (0 cooperative, 1 one thread per env), overlapped finish o (0: after round 2, 1:
+ * after round 4, 2: never).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
                       double* o0, double* o1, double* o2, void* workspace, size_t workspace_bytes,

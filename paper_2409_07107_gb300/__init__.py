@@ -227,16 +227,19 @@ def cotangent_to_raw(models, q, q_bar_tangent, q_bar_raw, model_id=None, stream=
 SCHEDULE_CAPS = ("default", "halved", "doubled")
 SCHEDULE_WIDE = (3, 5, None)
 SCHEDULE_FINISH = (0, 4, 8)
+SCHEDULE_OVERLAP = (2, 4, None)
 
 
 def describe_schedule(index):
-    """The schedule ds_autotune chose, from its index c + 3 (w + 3 (f + 3 n))."""
+    """The schedule ds_autotune chose, from its index c + 3 (w + 3 (f + 3 (n + 2 o)))."""
     i = int(index)
     c, i = i % 3, i // 3
     wi, i = i % 3, i // 3
-    f, n = i % 3, i // 3
+    f, i = i % 3, i // 3
+    n, o = i % 2, i // 2
     return {"round_caps": SCHEDULE_CAPS[c], "row_per_lane_admm_from_round": SCHEDULE_WIDE[wi],
-            "finish_ctas_per_sm": SCHEDULE_FINISH[f], "newton": "one thread per env" if n else "cooperative"}
+            "finish_ctas_per_sm": SCHEDULE_FINISH[f], "newton": "one thread per env" if n else "cooperative",
+            "overlapped_finish_after_round": SCHEDULE_OVERLAP[o]}
 
 
 def autotune(models, batch, opt, mode, out, o0=None, o1=None, o2=None, v_next_bar=None, workspace=None,

@@ -139,12 +139,18 @@ extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nm
 // Set only while ds_autotune times a candidate, for the calls of its own thread.
 static thread_local const ds_schedule* g_force_sched = nullptr;
 
-// Helper streams for mixed-model batches, created on first use per device and kept until exit.
+// Helper streams, created on first use per device and kept until exit: streams 0-3 run the
+// pipelines of a mixed-model batch, streams 4-7 their overlapped finish (side streams).
 static constexpr int kHelperStreams = 4;
 struct HelperStreams {
-  cudaStream_t s[kHelperStreams];
+  cudaStream_t s[2 * kHelperStreams];
   cudaEvent_t fork, join[kHelperStreams];
+  cudaEvent_t side_fork[kHelperStreams], side_join[kHelperStreams];
 };
+
+// Cleared by sim_step_jac_noalloc around its call: it creates no streams or events.
+static thread_local bool g_allow_helpers = true;
+void ds_allow_helper_streams(bool on) { g_allow_helpers = on; }
 
 static ds_status helper_streams(HelperStreams** out) {
   static std::mutex mu;
@@ -156,9 +162,12 @@ static ds_status helper_streams(HelperStreams** out) {
     HelperStreams* h = new (std::nothrow) HelperStreams;
     if (!h) return DS_ENOMEM;
     bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < 2 * kHelperStreams && ok; ++j)
+      ok = cudaStreamCreateWithFlags(&h->s[j], cudaStreamNonBlocking) == cudaSuccess;
     for (int j = 0; j < kHelperStreams && ok; ++j)
-      ok = cudaStreamCreateWithFlags(&h->s[j], cudaStreamNonBlocking) == cudaSuccess &&
-           cudaEventCreateWithFlags(&h->join[j], cudaEventDisableTiming) == cudaSuccess;
+      ok = cudaEventCreateWithFlags(&h->join[j], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->side_fork[j], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&h->side_join[j], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) { delete h; return DS_ECUDA; }
     per_dev[dev] = h;
   }
@@ -167,7 +176,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 4};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -240,11 +249,12 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.model_id = nmodels > 1 ? b->model_id : nullptr;
   a.sched = g_force_sched ? *g_force_sched : find_schedule(sched_key(models, nmodels, b, o, mode));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (ws && nmodels > 1) {
+  HelperStreams* hs = nullptr;
+  if (ws && g_allow_helpers && helper_streams(&hs) != DS_OK) return DS_ECUDA;
+  a.side = nullptr;
+  if (ws && hs && nmodels > 1) {
     // Each model's pipeline on a helper stream of its own (fork / join with events on the caller's
     // stream): the models' kernels are small and overlap on the GPU.
-    HelperStreams* hs = nullptr;
-    if (helper_streams(&hs) != DS_OK) return DS_ECUDA;
     if (cudaEventRecord(hs->fork, s) != cudaSuccess) return DS_ECUDA;
     for (int k = 0; k < nmodels; ++k) {
       cudaStream_t sk = hs->s[k % kHelperStreams];
@@ -252,6 +262,9 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
       ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k);
       a.model = models[k]->dev;
       a.model_index = k;
+      a.side = hs->s[kHelperStreams + k % kHelperStreams];
+      a.ev_fork = hs->side_fork[k % kHelperStreams];
+      a.ev_join = hs->side_join[k % kHelperStreams];
       kern[k]->pipeline(a, sk);
       if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
     }
@@ -261,9 +274,14 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
     }
     return DS_OK;
   }
-  if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, 0);
+  if (hs) {
+    a.side = hs->s[kHelperStreams];
+    a.ev_fork = hs->side_fork[0];
+    a.ev_join = hs->side_join[0];
+  }
   for (int k = 0; k < nmodels; ++k) {
     const ds_kernel_entry* ke = kern[k];
+    if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k);
     a.model = models[k]->dev;
     a.model_index = k;
     if (ws) ke->pipeline(a, s);
@@ -387,8 +405,8 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
   };
   // Coordinate search from the default: each knob in turn over its options, the others held at
   // the best found so far (round caps, first row-per-lane round, finish split target, Newton form).
-  static const int kOpts[4][3] = {{0, 1, 2}, {3, 5, DS_ROUNDS}, {0, 4, 8}, {0, 1, 0}};
-  static const int kNopt[4] = {3, 3, 3, 2};
+  static const int kOpts[5][3] = {{0, 1, 2}, {3, 5, DS_ROUNDS}, {0, 4, 8}, {0, 1, 0}, {2, 4, DS_ROUNDS}};
+  static const int kNopt[5] = {3, 3, 3, 2, 3};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DS_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DS_ECUDA; }
@@ -413,10 +431,12 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
   };
   float best_ms = 0.f;
   st = timed(best, &best_ms);
-  for (int d = 0; d < 4 && st == DS_OK; ++d)
+  for (int d = 0; d < 5 && st == DS_OK; ++d)
     for (int o = 0; o < kNopt[d] && st == DS_OK; ++o) {
       ds_schedule c = best;
-      int* field = d == 0 ? &c.caps : (d == 1 ? &c.wide_from : (d == 2 ? &c.finish_ctas : &c.newton_thread));
+      int* field = d == 0 ? &c.caps
+                   : (d == 1 ? &c.wide_from
+                             : (d == 2 ? &c.finish_ctas : (d == 3 ? &c.newton_thread : &c.overlap_from)));
       if (*field == kOpts[d][o]) continue;
       *field = kOpts[d][o];
       float ms = 0.f;
@@ -433,7 +453,8 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
   if (chosen) {
     const int wi = best.wide_from == 3 ? 0 : (best.wide_from == 5 ? 1 : 2);
     const int fi = best.finish_ctas == 0 ? 0 : (best.finish_ctas == 4 ? 1 : 2);
-    *chosen = best.caps + 3 * (wi + 3 * (fi + 3 * best.newton_thread));
+    const int oi = best.overlap_from == 2 ? 0 : (best.overlap_from == 4 ? 1 : 2);
+    *chosen = best.caps + 3 * (wi + 3 * (fi + 3 * (best.newton_thread + 2 * oi)));
   }
   return call();                                          // leave the outputs of the chosen schedule
 }

@@ -50,6 +50,8 @@ struct WsView {
   int32_t* nlist;         // [B] envs whose ADMM stage ended in a round (Newton queue)
   int32_t* ncounts;       // [DS_ROUNDS]
   int32_t* fetch;         // [DS_ROUNDS] next unclaimed entry of each round's list (follows ncounts)
+  int32_t* dlist;         // [B] envs whose NCP solve is complete, in completion order
+  int32_t* dcount;        // [2] entries of dlist; a snapshot of it (follows fetch)
 };
 
 // Lays out the workspace for ns contact slots, B envs and nmodels models starting at base (may be
@@ -87,7 +89,8 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
     int32_t* l0 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     int32_t* l1 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     int32_t* nl = static_cast<int32_t*>(take(sizeof(int32_t) * B));
-    int32_t* nc = static_cast<int32_t*>(take(sizeof(int32_t) * 2 * DS_ROUNDS));
+    int32_t* nc = static_cast<int32_t*>(take(sizeof(int32_t) * (2 * DS_ROUNDS + 2)));
+    int32_t* dl = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     if (k == model) {
       w.counts = counts;
       w.list[0] = l0;
@@ -95,6 +98,8 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
       w.nlist = nl;
       w.ncounts = nc;
       w.fetch = nc + DS_ROUNDS;
+      w.dcount = nc + 2 * DS_ROUNDS;
+      w.dlist = dl;
     }
   }
   if (v) *v = w;
@@ -104,9 +109,11 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
 // How the pipeline divides the work (never what an env computes, except that the one-thread and
 // cooperative Newton kernels round differently): ADMM round-cap table, the first round run by the
 // row-per-lane ADMM kernel (DS_ROUNDS = never), finish-kernel target CTAs per SM for splitting
-// Jacobian columns (0 = one thread per env), Newton kernel form.
+// Jacobian columns (0 = one thread per env), Newton kernel form, and the round after which the
+// envs already solved are finished on a side stream while the slow ones still iterate.
 struct ds_schedule {
   int caps, wide_from, finish_ctas, newton_thread;
+  int overlap_from;   // after this round, finish the completed envs on a side stream (DS_ROUNDS = never)
 };
 
 // Everything a launch needs; passed by value.
@@ -136,6 +143,12 @@ struct KArgs {
   int round, round_cap, final_round;
   int nchunk;              // finish kernel: threads per env (Jacobian columns split between them)
   ds_schedule sched;
+  // finish kernel over a device-side range of ws.dlist: entries [*flo, *fhi) (flo NULL = from 0);
+  // fhi NULL = every env of the launch
+  const int32_t* flo;
+  const int32_t* fhi;
+  cudaStream_t side;       // pipeline: stream for the overlapped finish (NULL = no overlap)
+  cudaEvent_t ev_fork, ev_join;
 };
 
 typedef void (*ds_launch_fn)(const KArgs& a, cudaStream_t s);
@@ -154,6 +167,8 @@ struct ds_kernel_entry {
 };
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
 extern "C++" const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int precision);
+// Whether calls of this host thread may use the library's helper streams (on by default).
+extern "C++" void ds_allow_helper_streams(bool on);
 
 // ------------------------------------------------------------------------------ small algebra
 

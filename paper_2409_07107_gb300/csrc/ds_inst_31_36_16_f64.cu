@@ -1,0 +1,5 @@
+// Kernel instantiation for 31 bodies, 36 dofs, 16 contact slots, FP64.
+#include "ds_launch.cuh"
+
+void ds_launch_31_36_16_f64(const KArgs& a, cudaStream_t s) { ds::launch_env<31, 36, 16, double>(a, s); }
+void ds_pipeline_31_36_16_f64(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<31, 36, 16, double>(a, s); }

@@ -1,0 +1,5 @@
+// Kernel instantiation for 31 bodies, 36 dofs, 16 contact slots, mixed precision.
+#include "ds_launch.cuh"
+
+void ds_launch_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<31, 36, 16, float>(a, s); }
+void ds_pipeline_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<31, 36, 16, float>(a, s); }

@@ -1,0 +1,5 @@
+// Kernel instantiation for 7 bodies, 7 dofs, 4 contact slots, FP64.
+#include "ds_launch.cuh"
+
+void ds_launch_7_7_4_f64(const KArgs& a, cudaStream_t s) { ds::launch_env<7, 7, 4, double>(a, s); }
+void ds_pipeline_7_7_4_f64(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<7, 7, 4, double>(a, s); }

@@ -1323,9 +1323,13 @@ DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
     if (!(st & DS_ENV_NONFINITE)) {
       const int k = ds_atomic_add(&w.counts[0], 1);
       w.list[0][k] = e;
+      w.st[e] = st;
+      return;
     }
   }
   w.st[e] = st;
+  const int k = ds_atomic_add(&w.dcount[0], 1);   // nothing to solve: ready for the finish
+  w.dlist[k] = e;
 }
 
 template <int NB, int NV, int NS, typename T>
@@ -1604,6 +1608,8 @@ DS_HD void newton_env(const KArgs& a, const int e) {
     if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
     for (int i = 0; i < p.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
     w.st[e] = st;
+    const int k = ds_atomic_add(&w.dcount[0], 1);
+    w.dlist[k] = e;
   } else {
     w.stage[e] = stage + 1;
     w.best_r[e] = best_r;
@@ -1686,17 +1692,26 @@ DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e, int chunk 
   env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk);
 }
 
+// Copies the completed-env count to its snapshot slot (the split point of an overlapped finish).
+static __global__ void dcount_snapshot_kernel(int32_t* dcount) { dcount[1] = dcount[0]; }
+
 template <int NB, int NV, int NS, typename T>
 __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
   __shared__ DevModel sm;
   load_model(sm, a.model);
-  // thread t handles env t % n_env, column chunk t / n_env (consecutive threads: consecutive envs)
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_env * a.nchunk) return;
-  const int chunk = t / a.n_env, ti = t - chunk * a.n_env;
-  const int e = a.env_list ? a.env_list[ti] : ti;
-  if (a.model_id && a.model_id[e] != a.model_index) return;
-  finish_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
+  // work item t handles env t % n, column chunk t / n (consecutive threads: consecutive envs); the
+  // envs are the launch's, or the range [*flo, *fhi) of the completed-env list
+  const int lo = a.flo ? *a.flo : 0;
+  const int n = a.fhi ? *a.fhi - lo : a.n_env;
+  if (n <= 0) return;
+  const long long total = (long long)n * a.nchunk;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = int(t / n), ti = int(t - (long long)chunk * n);
+    const int e = a.fhi ? a.ws.dlist[lo + ti] : (a.env_list ? a.env_list[ti] : ti);
+    if (a.model_id && a.model_id[e] != a.model_index) continue;
+    finish_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
+  }
 }
 
 }  // namespace ds

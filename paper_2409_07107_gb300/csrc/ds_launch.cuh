@@ -26,13 +26,19 @@ void launch_env(const KArgs& a, cudaStream_t s) {
   ds_trace_mark(DS_STAGE_FUSED, 0, s);
 }
 
+// Blocks for n envs x nchunk work items (the finish kernel loops over the rest).
+inline int finish_blocks(int n, int nchunk, int threads) {
+  const long long b = ((long long)n * nchunk + threads - 1) / threads;
+  return int(b < (1 << 20) ? (b > 0 ? b : 1) : (1 << 20));
+}
+
 template <int NB, int NV, int NS, typename T>
 void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   const int threads = 128;
   const int blocks = (a0.n_env + threads - 1) / threads;
   if (blocks <= 0) return;
   cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
-  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * 2 * DS_ROUNDS, s);   // ncounts and fetch
+  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * (2 * DS_ROUNDS + 2), s);   // ncounts, fetch, dcount
   ds_trace_mark(DS_STAGE_SETUP, 1, s);
   setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
   ds_trace_mark(DS_STAGE_SETUP, 0, s);
@@ -78,6 +84,20 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   int nblocks = ds_sm_count() * nper;
   const int nneed = (a0.n_env + envs_per_nblock - 1) / envs_per_nblock;
   if (nblocks > nneed) nblocks = nneed;
+  // Finish: with a small batch the Jacobian columns (VJP dof passes) of an env are split over
+  // several threads, each recomputing the env's forward pass, so that the launch still fills the
+  // GPU (by default about 4 CTAs of 128 threads per SM); large batches keep one thread per env.
+  KArgs af = a0;
+  af.nchunk = 1;
+  const int maxc = a0.run == DS_RUN_JAC ? 3 * NV : 2 * NV;
+  if (a0.run != DS_RUN_STEP && sc.finish_ctas > 0) {
+    const int target = ds_sm_count() * sc.finish_ctas * threads;
+    int c = target / (a0.n_env > 0 ? a0.n_env : 1);
+    af.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);
+  }
+  // With a side stream and an overlap round, the envs solved by then are finished on the side
+  // stream while the late ADMM rounds (few, slow envs) run; the rest are finished at the end.
+  const bool overlap = a0.side && sc.overlap_from < DS_ROUNDS - 1;
   for (int r = 0; r < DS_ROUNDS; ++r) {
     KArgs a = a0;
     a.round = r;
@@ -97,19 +117,34 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     }
     if (!launched) newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
+    if (overlap && r == sc.overlap_from) {
+      dcount_snapshot_kernel<<<1, 1, 0, s>>>(a0.ws.dcount);
+      cudaEventRecord(a0.ev_fork, s);
+      cudaStreamWaitEvent(a0.side, a0.ev_fork, 0);
+      KArgs fa = af;
+      fa.flo = nullptr;
+      fa.fhi = a0.ws.dcount + 1;
+      const int fb = finish_blocks(a0.n_env, fa.nchunk, threads);
+      ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
+      finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
+      ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);
+      cudaEventRecord(a0.ev_join, a0.side);
+    }
   }
-  // Finish: with a small batch the Jacobian columns (VJP dof passes) of an env are split over
-  // several threads, each recomputing the env's forward pass, so that the launch still fills the
-  // GPU (by default about 4 CTAs of 128 threads per SM); large batches keep one thread per env.
-  KArgs af = a0;
-  af.nchunk = 1;
-  if (a0.run != DS_RUN_STEP && sc.finish_ctas > 0) {
-    const int target = ds_sm_count() * sc.finish_ctas * threads;
-    const int maxc = a0.run == DS_RUN_JAC ? 3 * NV : 2 * NV;
-    int c = target / (a0.n_env > 0 ? a0.n_env : 1);
-    af.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);
+  if (overlap) {
+    // the envs completed after the split: few, so every column gets its own thread
+    KArgs fb_args = af;
+    fb_args.nchunk = a0.run == DS_RUN_STEP ? 1 : maxc;
+    fb_args.flo = a0.ws.dcount + 1;
+    fb_args.fhi = a0.ws.dcount;
+    const int fb = finish_blocks(a0.n_env, fb_args.nchunk, threads);
+    ds_trace_mark(DS_STAGE_FINISH, 1, s);
+    finish_kernel<NB, NV, NS, T><<<fb, threads, 0, s>>>(fb_args);
+    ds_trace_mark(DS_STAGE_FINISH, 0, s);
+    cudaStreamWaitEvent(s, a0.ev_join, 0);
+    return;
   }
-  const int fblocks = (a0.n_env * af.nchunk + threads - 1) / threads;
+  const int fblocks = finish_blocks(a0.n_env, af.nchunk, threads);
   ds_trace_mark(DS_STAGE_FINISH, 1, s);
   finish_kernel<NB, NV, NS, T><<<fblocks, threads, 0, s>>>(af);
   ds_trace_mark(DS_STAGE_FINISH, 0, s);

@@ -535,6 +535,8 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
         if (!ok) st |= DS_ENV_NOT_CONVERGED;
         if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
         w.st[e] = st;
+        const int k = atomicAdd(&w.dcount[0], 1);
+        w.dlist[k] = e;
       }
     } else if (have && ln.li == 0) {
       w.stage[e] = stage + 1;

@@ -36,6 +36,8 @@ extern "C" ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t
   void* ws = nullptr;
   s = scratch_for_current_device(&ws);
   if (s != DS_OK) return s;
-  return sim_step_jac(models, nmodels, batch, opt, out, dv_dq, dv_dv, dv_dtau, ws, DS_NOALLOC_SCRATCH_BYTES,
-                      stream);
+  ds_allow_helper_streams(false);   // no stream or event creation on this path
+  s = sim_step_jac(models, nmodels, batch, opt, out, dv_dq, dv_dv, dv_dtau, ws, DS_NOALLOC_SCRATCH_BYTES, stream);
+  ds_allow_helper_streams(true);
+  return s;
 }

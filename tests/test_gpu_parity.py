@@ -273,7 +273,7 @@ def test_autotune_keeps_results(torch_cuda):
     sim = ds.Simulator(wl, precision="fp64")
     ref = {k: v.clone() for k, v in sim.step_jac().items()}
     desc = sim.autotune("jac")
-    assert 0 <= desc["index"] < 54
+    assert 0 <= desc["index"] < 162
     got = sim.step_jac()
     torch.cuda.synchronize()
     ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
