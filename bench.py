@@ -307,8 +307,6 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        ds.profile(True)
-        ds.profile_read()
         times = []
         with ClockSampler(dev) as clk:
             for _ in range(args.steps):
@@ -319,6 +317,15 @@ def main():
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
+        # a separate traced pass (CUDA events around every library kernel) for the stage split and
+        # the ADMM kernels' time; tracing itself costs time, so it stays out of the timed loop
+        traced = max(1, min(args.steps, 5))
+        ds.profile(True)
+        ds.profile_read()
+        for _ in range(traced):
+            flush.fill_(1.0)
+            one_step(sim)
+        torch.cuda.synchronize()
         stages = ds.profile_read()
         ds.profile(False)
         # the same step replayed from a CUDA graph (launch overhead removed)
@@ -343,8 +350,8 @@ def main():
         # algorithmic flops of the ADMM rounds: per env-iteration, the x-step (K times rhs, 2 m^2)
         # plus the right-hand side, De Saxce term, relaxation, projection and dual step (30 m)
         admm_flops = float(np.sum(iters * (2.0 * m * m + 30.0 * m)))
-        stage_ms = {k: v[0] / args.steps for k, v in stages.items() if v[1]}
-        stage_launches = {k: v[1] // args.steps for k, v in stages.items() if v[1]}
+        stage_ms = {k: v[0] / traced for k, v in stages.items() if v[1]}
+        stage_launches = {k: v[1] // traced for k, v in stages.items() if v[1]}
         t_admm = stage_ms.get("admm", float("nan"))
         peak = fma["fp64"] if prec == "fp64" else fma["fp32"]
         achieved = admm_flops / (t_admm * 1e-3) / 1e12
@@ -420,6 +427,9 @@ def main():
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": args.steps * r64["launches"], "cpu_baseline": cpu,
                 "stages": r64["stages"], "dominant_stage": r64["dominant_stage"], "cuda_graph_replay": r64["graph"],
+                "stages_note": "kernel time per stage from a separate traced pass (CUDA events around every "
+                               "library kernel, kept out of the timed loop); the finish of early-solved envs "
+                               "overlaps the late ADMM rounds on a second stream, so stages can sum past the step",
                 "schedule": r64["schedule"],
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],

@@ -53,8 +53,11 @@ typedef enum {
 } ds_status;
 
 typedef enum { DS_FP64 = 0, DS_MIXED = 1 } ds_precision;
-/* DS_MIXED: kinematics, contact detection, the NCP polish, the residual check and the reduced
- * implicit system in FP64; dynamics, Delassus matrix, ADMM iterations and derivative passes in FP32. */
+/* DS_MIXED: kinematics, contact detection, J_c, G and g, the residuals of the NCP polish, the NCP
+ * residual check and the reduced implicit system in FP64; dynamics, ADMM iterations, derivative
+ * passes and, before an env's last solver stage, the factorisations of the polish's Newton steps
+ * in FP32 (the FP64 residuals make the polish an iterative refinement that still reaches the FP64
+ * acceptance tolerance; an env's last stage factors in FP64). */
 
 enum { DS_MODE_BREAKING = 0, DS_MODE_STICKING = 1, DS_MODE_SLIDING = 2, DS_MODE_INACTIVE = 3 };
 

@@ -118,7 +118,9 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     if (!launched) newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
     if (overlap && r == sc.overlap_from) {
+      ds_trace_mark(DS_STAGE_FINISH, 1, s);
       dcount_snapshot_kernel<<<1, 1, 0, s>>>(a0.ws.dcount);
+      ds_trace_mark(DS_STAGE_FINISH, 0, s);
       cudaEventRecord(a0.ev_fork, s);
       cudaStreamWaitEvent(a0.side, a0.ev_fork, 0);
       KArgs fa = af;

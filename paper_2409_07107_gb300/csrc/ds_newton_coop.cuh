@@ -33,15 +33,43 @@ struct Shape {
   static constexpr unsigned LMASK = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
 };
 
-// Per-env shared memory: the Delassus matrix, the pivot rows U (in pivot order) and U U^T with its
-// Cholesky factor, and a vector.
-template <int NS>
+// Work space of the minimum-norm step in the LU's type LT: the pivot rows U (in pivot order),
+// U U^T with its Cholesky factor, and a vector.
+template <int NS, typename LT>
+struct LUWork {
+  LT U[Shape<NS>::NC3][Shape<NS>::PS];
+  LT H[Shape<NS>::NC3][Shape<NS>::PS];
+  LT w[Shape<NS>::NC3];
+  LT rd[Shape<NS>::NC3];                     // reciprocals of the Cholesky diagonal
+};
+
+// Per-env shared memory: the Delassus matrix (FP64) and the step work spaces: FP64 always, FP32 as
+// well in the mixed form (whose Newton steps factor in FP32 except in the last stage).
+template <int NS, typename T>
 struct Smem {
   double G[Shape<NS>::NC3][Shape<NS>::PS];
-  double U[Shape<NS>::NC3][Shape<NS>::PS];
-  double H[Shape<NS>::NC3][Shape<NS>::PS];
-  double w[Shape<NS>::NC3];
-  double rd[Shape<NS>::NC3];                 // reciprocals of the Cholesky diagonal
+  LUWork<NS, double> d;
+  typename std::conditional<std::is_same<T, float>::value, LUWork<NS, float>, char>::type f;
+};
+
+// Integer views of |x| for pivot comparisons (same order as the values for non-negative x).
+template <typename LT>
+struct LUBits;
+template <>
+struct LUBits<double> {
+  using I = long long;
+  static __device__ __forceinline__ I bits(double x) { return __double_as_longlong(fabs(x)); }
+  static __device__ __forceinline__ double value(I b) { return __longlong_as_double(b); }
+  static constexpr I kInf = 0x7FF0000000000000LL;
+  static constexpr double kRankTol = 1e-13;
+};
+template <>
+struct LUBits<float> {
+  using I = int;
+  static __device__ __forceinline__ I bits(float x) { return __float_as_int(fabsf(x)); }
+  static __device__ __forceinline__ float value(I b) { return __int_as_float(b); }
+  static constexpr I kInf = 0x7F800000;
+  static constexpr float kRankTol = 1e-5f;
 };
 
 // What a lane is: its row li within the env's group, the contact ci it belongs to (row lanes:
@@ -80,8 +108,8 @@ __device__ __forceinline__ bool gany(bool p, const Lane<NS>& ln) { return gbits<
 
 // sigma_li = g_li + sum_j G[li][j] lambda_j (row lanes; the sum runs over the padded width, where
 // G and lambda are zero, in the same order as the one-thread form).
-template <int NS>
-__device__ __forceinline__ double sigma_row(const Smem<NS>& S, const Lane<NS>& ln, double lam) {
+template <int NS, class SM>
+__device__ __forceinline__ double sigma_row(const SM& S, const Lane<NS>& ln, double lam) {
   constexpr int NC3 = Shape<NS>::NC3;
   const int r = ln.row ? ln.li : 0;
   double t = ln.g;
@@ -101,8 +129,8 @@ __device__ __forceinline__ void contact3(double v, const Lane<NS>& ln, double* o
 }
 
 // FP64 NCP residual of lambda (the max over contacts of the one-thread ncp_residual terms).
-template <int NS>
-__device__ double residual(const Smem<NS>& S, const Lane<NS>& ln, double lam) {
+template <int NS, class SM>
+__device__ double residual(const SM& S, const Lane<NS>& ln, double lam) {
   const double sg = sigma_row<NS>(S, ln, lam);
   double s[3], l[3];
   contact3<NS>(sg, ln, s);
@@ -122,8 +150,8 @@ __device__ double residual(const Smem<NS>& S, const Lane<NS>& ln, double lam) {
 
 // Modes (same rules as the one-thread classify); every lane gets the mode of its contact.
 // Returns the classification margin (group-uniform).
-template <int NS>
-__device__ double classify(const Smem<NS>& S, const Lane<NS>& ln, double lam, double es_rel, double el_rel,
+template <int NS, class SM>
+__device__ double classify(const SM& S, const Lane<NS>& ln, double lam, double es_rel, double el_rel,
                            int& mode) {
   constexpr int L = Shape<NS>::L;
   const bool in = ln.row && ln.ci < ln.na;
@@ -159,8 +187,8 @@ __device__ double classify(const Smem<NS>& S, const Lane<NS>& ln, double lam, do
 
 // Active-set update (same rules as the one-thread reclassify); applied only where act.  Returns
 // whether any mode of the env changed.
-template <int NS>
-__device__ bool reclassify(const Smem<NS>& S, const Lane<NS>& ln, double lam, int& mode, double es, double el,
+template <int NS, class SM>
+__device__ bool reclassify(const SM& S, const Lane<NS>& ln, double lam, int& mode, double es, double el,
                            double delta, bool act) {
   const double sg = sigma_row<NS>(S, ln, lam);
   double s[3], l[3];
@@ -202,16 +230,17 @@ __device__ __forceinline__ double pick(const double (&a)[N], int j) {
 // fixed at compile time and the FP64 work per step shrinks with k (the FP64 pipe is this kernel's
 // bound; column moves are selects).  Columns that are not unknowns hold zeros and are never
 // pivots.  mypos tracks where column li currently sits.
-template <int NS>
-__device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<NS>::NC3], double F, unsigned um,
+template <int NS, typename LT>
+__device__ double solve_step(LUWork<NS, LT>& S, const Lane<NS>& ln, LT (&a)[Shape<NS>::NC3], LT F, unsigned um,
                              int nu, bool rowact, bool run) {
+  using Bits = LUBits<LT>;
   constexpr int NC3 = Shape<NS>::NC3, L = Shape<NS>::L;
   int mypos = (ln.row && ((um >> ln.li) & 1u)) ? ln.li : -1;
   bool done = !(rowact && run);     // not (or no longer) a pivot candidate
   int kp = -1;                      // pivot step of this lane's row
-  double ipiv = 0.0;                // 1 / its pivot
+  LT ipiv = LT(0);                  // 1 / its pivot
   int rank = 0;
-  double first = 0.0;
+  LT first = LT(0);
   bool go = run;
 #pragma unroll
   for (int k = 0; k < NC3; ++k) {
@@ -219,35 +248,35 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
     if (__any_sync(kFull, go)) {             // (once no env goes on, every later step is skipped)
       // Candidates are compared by the bit patterns of |a| as integers (the same order as the
       // values for non-negative doubles, and off the FP64 pipe); NaN entries are never candidates.
-      long long bk = -1;
+      typename Bits::I bk = -1;
       int bj = k;
       if (!done) {
 #pragma unroll
         for (int j = k; j < NC3; ++j) {
-          const long long v = __double_as_longlong(fabs(a[j]));
-          if (v <= 0x7FF0000000000000LL && v > bk) { bk = v; bj = j; }
+          const typename Bits::I v = Bits::bits(a[j]);
+          if (v <= Bits::kInf && v > bk) { bk = v; bj = j; }
         }
       }
       int key = (ln.li << 8) | bj;
 #pragma unroll
       for (int o = L / 2; o >= 1; o >>= 1) {
-        const long long ov = __shfl_xor_sync(kFull, bk, o);
+        const typename Bits::I ov = __shfl_xor_sync(kFull, bk, o);
         const int ok = __shfl_xor_sync(kFull, key, o);
         if (ov > bk || (ov == bk && ok < key)) { bk = ov; key = ok; }
       }
-      const double bv = bk < 0 ? -1.0 : __longlong_as_double(bk);
+      const LT bv = bk < 0 ? LT(-1) : Bits::value(bk);
       if (go) {
         if (k == 0) first = bv;
-        if (!(bv > 1e-13 * first) || bv == 0.0) go = false;
+        if (!(bv > Bits::kRankTol * first) || bv == LT(0)) go = false;
       }
       const int bi = key >> 8, bjj = key & 255;
       if (go && bjj != k) {             // pivot column to position k, in every row of the env
-        const double t = a[k];
-        double nk = t;
+        const LT t = a[k];
+        LT nk = t;
 #pragma unroll
         for (int j = k + 1; j < NC3; ++j) {
           const bool h = j == bjj;
-          const double aj = a[j];
+          const LT aj = a[j];
           nk = h ? aj : nk;
           a[j] = h ? t : aj;
         }
@@ -256,14 +285,14 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
         else if (mypos == k) mypos = bjj;
       }
       const int src = ln.base + (go ? bi : 0);
-      const double pv = __shfl_sync(kFull, a[k], src);
-      const double pf = __shfl_sync(kFull, F, src);
+      const LT pv = __shfl_sync(kFull, a[k], src);
+      const LT pf = __shfl_sync(kFull, F, src);
       const bool elim = go && !done && ln.li != bi;
-      const double inv = 1.0 / pv;
-      const double l = elim ? a[k] * inv : 0.0;
+      const LT inv = LT(1) / pv;
+      const LT l = elim ? a[k] * inv : LT(0);
 #pragma unroll
       for (int j = k + 1; j < NC3; ++j) {
-        const double pj = __shfl_sync(kFull, a[j], src);
+        const LT pj = __shfl_sync(kFull, a[j], src);
         if (elim) a[j] -= l * pj;
       }
       if (elim) F -= l * pf;
@@ -277,18 +306,18 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
   const bool full = run && rank == nu;
   const bool mn = run && rank < nu;
   // full column rank: back substitution, one pivot at a time from the last
-  double s = F;
+  LT s = F;
 #pragma unroll
   for (int k = NC3 - 1; k >= 0; --k) {
     const bool stp = full && k < rank;
     if (__any_sync(kFull, stp)) {
       const unsigned ob = gbits<NS>(stp && kp == k, ln);
       const int own = ob ? __ffs(ob) - 1 : 0;
-      double xk = 0.0;
+      LT xk = LT(0);
       if (stp && kp == k) xk = s * ipiv;
       xk = __shfl_sync(kFull, xk, ln.base + own);
       if (stp && kp >= 0 && kp < k) s -= a[k] * xk;
-      if (stp && mypos == k) dx = xk;
+      if (stp && mypos == k) dx = double(xk);
     }
   }
   // rank deficient: x = U^T (U U^T)^-1 y over the positions, then back to the columns
@@ -296,12 +325,12 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
     const int maxrank = int(__reduce_max_sync(kFull, unsigned(mn ? rank : 0)));
     if (mn && kp >= 0) {
 #pragma unroll
-      for (int j = 0; j < NC3; ++j) S.U[kp][j] = j >= kp ? a[j] : 0.0;
+      for (int j = 0; j < NC3; ++j) S.U[kp][j] = j >= kp ? a[j] : LT(0);
     }
     __syncwarp();
     if (mn && kp >= 0) {
       for (int k2 = 0; k2 <= kp; ++k2) {
-        double t = 0.0;
+        LT t = LT(0);
 #pragma unroll
         for (int j = 0; j < NC3; ++j) t += S.U[kp][j] * S.U[k2][j];
         S.H[kp][k2] = t;
@@ -313,39 +342,39 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
     for (int j = 0; j < maxrank; ++j) {
       const bool stp = mn && j < rank;
       if (stp && kp == j) {
-        double d = S.H[j][j];
+        LT d = S.H[j][j];
         for (int c = 0; c < j; ++c) d -= S.H[j][c] * S.H[j][c];
-        const double sd = sqrt(fmax(d, 1e-300));
+        const LT sd = sqrt(fmax(d, LT(1e-30)));
         S.H[j][j] = sd;
-        S.rd[j] = 1.0 / sd;
+        S.rd[j] = LT(1) / sd;
       }
       __syncwarp();
       if (stp && kp > j) {
-        double t = S.H[kp][j];
+        LT t = S.H[kp][j];
         for (int c = 0; c < j; ++c) t -= S.H[kp][c] * S.H[j][c];
         S.H[kp][j] = t * S.rd[j];
       }
       __syncwarp();
     }
     // forward (L w = y) and backward (L^T z = w) substitution, column sweeps
-    double acc = 0.0, wv = 0.0;
+    LT acc = LT(0), wv = LT(0);
 #pragma unroll 1
     for (int j = 0; j < maxrank; ++j) {
       const bool stp = mn && j < rank;
       const unsigned ob = gbits<NS>(stp && kp == j, ln);
       const int own = ob ? __ffs(ob) - 1 : 0;
-      double wj = 0.0;
+      LT wj = LT(0);
       if (stp && kp == j) { wv = (s - acc) * S.rd[j]; wj = wv; }
       wj = __shfl_sync(kFull, wj, ln.base + own);
       if (stp && kp > j) acc += S.H[kp][j] * wj;
     }
-    double acc2 = 0.0, zv = 0.0;
+    LT acc2 = LT(0), zv = LT(0);
 #pragma unroll 1
     for (int j = maxrank - 1; j >= 0; --j) {
       const bool stp = mn && j < rank;
       const unsigned ob = gbits<NS>(stp && kp == j, ln);
       const int own = ob ? __ffs(ob) - 1 : 0;
-      double zj = 0.0;
+      LT zj = LT(0);
       if (stp && kp == j) { zv = (wv - acc2) * S.rd[j]; zj = zv; }
       zj = __shfl_sync(kFull, zj, ln.base + own);
       if (stp && kp >= 0 && kp < j) acc2 += S.H[j][kp] * zj;
@@ -353,9 +382,9 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
     if (mn && kp >= 0) S.w[kp] = zv;
     __syncwarp();
     if (mn && mypos >= 0) {
-      double t = 0.0;
+      LT t = LT(0);
       for (int k = 0; k < rank; ++k) t += S.U[k][mypos] * S.w[k];
-      dx = t;
+      dx = double(t);
     }
     __syncwarp();
   }
@@ -364,9 +393,9 @@ __device__ double solve_step(Smem<NS>& S, const Lane<NS>& ln, double (&a)[Shape<
 
 // Newton on the mode equations of the env (the one-thread newton_modes, one lane per row).
 // lp is the lane's component of lambda (row lanes); act marks the envs that take part.
-template <int NS>
-__device__ double newton_modes(Smem<NS>& S, const Lane<NS>& ln, double lp, int mode, int iters, double sat_delta,
-                               bool act) {
+template <int NS, typename LT, class SM>
+__device__ double newton_modes(const SM& S, LUWork<NS, LT>& W, const Lane<NS>& ln, double lp, int mode, int iters,
+                               double sat_delta, bool act) {
   constexpr int NC3 = Shape<NS>::NC3, L = Shape<NS>::L;
   const bool inc = ln.ci < ln.na;
   const double scale = fmax(1.0, gmax<L>((ln.row && inc) ? fabs(ln.g) : 0.0));
@@ -430,7 +459,10 @@ __device__ double newton_modes(Smem<NS>& S, const Lane<NS>& ln, double lp, int m
       else prev = fmaxv;
     }
     if (!__any_sync(kFull, run)) break;
-    const double dx = solve_step<NS>(S, ln, a, F, um, nu, rowact, run);
+    LT al[NC3];
+#pragma unroll
+    for (int j = 0; j < NC3; ++j) al[j] = LT(a[j]);
+    const double dx = solve_step<NS, LT>(W, ln, al, LT(F), um, nu, rowact, run);
     if (run && ucol) lp -= dx;
   }
   return lp;
@@ -439,8 +471,8 @@ __device__ double newton_modes(Smem<NS>& S, const Lane<NS>& ln, double lp, int m
 // End of an ADMM stage (the one-thread newton_stage): classify z, up to four active-set rounds of
 // Newton, keep the best candidate by FP64 NCP residual.  lz and best_l are the lane's components.
 template <int NS, typename T>
-__device__ bool newton_stage(Smem<NS>& S, const Lane<NS>& ln, double lz, double eps, const KArgs& a, double& best_l,
-                             double& best_r, bool act) {
+__device__ bool newton_stage(Smem<NS, T>& S, const Lane<NS>& ln, double lz, double eps, const KArgs& a, double& best_l,
+                             double& best_r, bool act, bool last) {
   constexpr int L = Shape<NS>::L;
   const bool in = ln.row && ln.ci < ln.na;
   const double scale = fmax(1.0, gmax<L>(in ? fabs(ln.g) : 0.0));
@@ -457,7 +489,11 @@ __device__ bool newton_stage(Smem<NS>& S, const Lane<NS>& ln, double lz, double 
 #pragma unroll 1
   for (int round = 0; round < 4; ++round) {
     if (!__any_sync(kFull, go)) break;
-    lp = newton_modes<NS>(S, ln, lp, mode, a.polish_iters, sat_delta, go);
+    // mixed form: FP32 factorisations (FP64 residuals) except in an env's last chance
+    if constexpr (std::is_same<T, float>::value)
+      lp = newton_modes<NS, float>(S, S.f, ln, lp, mode, a.polish_iters, sat_delta, go && !last);
+    lp = newton_modes<NS, double>(S, S.d, ln, lp, mode, a.polish_iters, sat_delta,
+                                  go && (last || !std::is_same<T, float>::value));
     const double rpol = residual<NS>(S, ln, lp);
     if (go && rpol < best_r) { best_r = rpol; best_l = lp; }
     if (go && best_r <= tol) go = false;
@@ -484,13 +520,13 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
   using Sh = coop::Shape<NS>;
   constexpr int NC3 = Sh::NC3, L = Sh::L, EPW = Sh::EPW;
   static_assert(32 % L == 0, "4 NS lanes per env must divide the warp");
-  __shared__ coop::Smem<NS> smem[(Sh::THREADS / 32) * EPW];
+  __shared__ coop::Smem<NS, T> smem[(Sh::THREADS / 32) * EPW];
   const WsView& w = a.ws;
   const int n = w.ncounts[a.round];
   const int B = a.B;
   const int lane = threadIdx.x & 31;
   const int grp = lane / L;
-  coop::Smem<NS>& S = smem[(threadIdx.x >> 5) * EPW + grp];
+  coop::Smem<NS, T>& S = smem[(threadIdx.x >> 5) * EPW + grp];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t0 = warp * EPW; t0 < n; t0 += nwarps * EPW) {
@@ -524,7 +560,8 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
     const int iters = have ? w.iters[e] : 0;
     uint32_t st = have ? w.st[e] : 0u;
     const double eps = stage_eps<T>(a, stage);
-    const bool ok = coop::newton_stage<NS, T>(S, ln, lz, eps, a, best_l, best_r, have && m > 0);
+    const bool last = iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round;
+    const bool ok = coop::newton_stage<NS, T>(S, ln, lz, eps, a, best_l, best_r, have && m > 0, last);
     if (mine) w.lam[ln.li * B + e] = best_l;
     const bool fin = ok || iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round;
     int mode;
