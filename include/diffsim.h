@@ -226,10 +226,10 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * after which the envs already solved are finished on a side stream of the library while the slow
  * ones still iterate (2, 4 or never).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
- * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing two
- * runs of each schedule with CUDA events on `stream` after an untimed one, in a coordinate search
- * from the default (each knob over its options with the others at the best so far: 10 schedules
- * besides the default).  It keeps the fastest for the batch's signature (first model's bodies and
+ * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
+ * schedule by the fastest of three runs (CUDA events on `stream`, after an untimed run), in a
+ * coordinate search from the default (each knob over its options with the others at the best so
+ * far: 10 schedules besides the default; a schedule replaces the best only if 2 % faster).  It keeps the fastest for the batch's signature (first model's bodies and
  * dofs, number of models, ncmax, precision, mode, B rounded up to a power of two) and finally runs
  * the call once more with it, so that *out and o0..o2 hold its results.  Later calls with the
  * same signature use that schedule; other batches keep the default.  A schedule never changes what

@@ -567,7 +567,8 @@ DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T 
 
 // F1-F6 for env e: kinematics, dynamics, contact detection, J_c, G, g.  Returns status bits.
 template <int NB, int NV, int NS, typename T>
-DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s) {
+DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s,
+                           bool lite = false) {
   const int B = a.B;
   uint32_t st = 0;
   double* q = s.q;
@@ -814,7 +815,20 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     }
   }
 
-  // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms)
+  // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms).
+  // lite: g only (a caller that reads G from the workspace and applies M^-1 by solves)
+  if (lite) {
+    for (int r = 0; r < mdim; ++r) {
+      double t = 0.0;
+      for (int k = 0; k < NV; ++k) t += Jd[r][k] * double(s.vf[k]);
+      s.gt[r] = T(t);
+      s.gd[r] = t;
+    }
+    if constexpr (!kD)
+      for (int r = 0; r < mdim; ++r)
+        for (int k = 0; k < NV; ++k) s.Jc[r][k] = T(Jd[r][k]);
+    return st;
+  }
   for (int r = 0; r < mdim; ++r) {
     for (int k = 0; k < NV; ++k) Yd[r][k] = Jd[r][k];
     fwd_packed(Ld, Yd[r], NV);
@@ -893,7 +907,9 @@ DS_HDI void integrate_adjoint(const DevModel& m, const double* vn, double dt, co
 
 template <int NB, int NV, int NS, typename T>
 DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters,
-                      int chunk = 0, int nchunk = 1) {
+                      int chunk = 0, int nchunk = 1, bool lite = false) {
+  // lite: the forward part skipped Y = M^-1 J_c^T (and G, which the caller loaded); products with Y
+  // are done as solves with M's factor instead.
   // With nchunk > 1 the Jacobian columns (or the VJP's dof passes) are split over nchunk threads of
   // the same env; chunk 0 also writes the step's outputs.
   const bool lead = chunk == 0;
@@ -901,10 +917,22 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
   const int mdim = 3 * s.na;
   const double* q = s.q;
   const T grav[3] = {T(a.gx), T(a.gy), T(a.gz)};
-   for (int k = 0; k < NV; ++k) {
-    T t = s.vf[k];
-    for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r]);
-    s.vn[k] = t;
+  T ylam[NV];                                  // M^-1 J_c^T lambda
+  if (lite) {
+    for (int k = 0; k < NV; ++k) {
+      T t = T(0);
+      for (int r = 0; r < mdim; ++r) t += s.Jc[r][k] * T(s.lam[r]);
+      ylam[k] = t;
+    }
+    fwd_packed(s.L, ylam, NV);
+    bwd_packed(s.L, ylam, NV);
+    for (int k = 0; k < NV; ++k) s.vn[k] = s.vf[k] + ylam[k];
+  } else {
+    for (int k = 0; k < NV; ++k) {
+      T t = s.vf[k];
+      for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r]);
+      s.vn[k] = t;
+    }
   }
   for (int k = 0; k < NV; ++k) {
     const double vv = double(s.vn[k]);
@@ -962,7 +990,9 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
     // ---- B1 pass of tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces
     for (int k = 0; k < NV; ++k) {
       T t = s.vdf[k];
-      for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
+      if (lite) t += ylam[k] / T(a.dt);
+      else
+        for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
       s.astar[k] = t;
     }
     for (int ac = 0; ac < s.na; ++ac)
@@ -1073,7 +1103,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       // them) gives row k of Y C A^- B, and every column then costs a dot product per row instead
       // of a solve; otherwise each column solves for its X.
       const int c0 = (3 * NV * chunk) / nchunk, c1 = (3 * NV * (chunk + 1)) / nchunk;
-      const bool by_rows = md > 0 && NV < c1 - c0;
+      const bool by_rows = !lite && md > 0 && NV < c1 - c0;
       double P[NV][3 * NS];
       if (by_rows) {
         for (int k = 0; k < NV; ++k) {
@@ -1150,6 +1180,8 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             }
           }
           s.lu.solve_mn(rhs, X);
+          T wv[NV];
+          for (int k = 0; k < NV; ++k) wv[k] = T(0);
           for (int ac = 0; ac < s.na; ++ac) {
             if (sz[ac] == 0) continue;
             double dl[3];
@@ -1157,8 +1189,16 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             else { for (int r = 0; r < 3; ++r) dl[r] = Rm[ac][r][0] * X[off[ac]] + Rm[ac][r][1] * X[off[ac] + 1]; }
             for (int r = 0; r < 3; ++r) {
               const T dlr = T(dl[r]);
-              for (int k = 0; k < NV; ++k) Dc[k] += s.Y[3 * ac + r][k] * dlr;
+              if (lite)
+                for (int k = 0; k < NV; ++k) wv[k] += s.Jc[3 * ac + r][k] * dlr;
+              else
+                for (int k = 0; k < NV; ++k) Dc[k] += s.Y[3 * ac + r][k] * dlr;
             }
+          }
+          if (lite) {
+            fwd_packed(s.L, wv, NV);
+            bwd_packed(s.L, wv, NV);
+            for (int k = 0; k < NV; ++k) Dc[k] += wv[k];
           }
         }
         double* out = blk == 0 ? a.dv_dq : (blk == 1 ? a.dv_dv : a.dv_dtau);
@@ -1184,12 +1224,21 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       for (int r = 0; r < mdim; ++r) zeta[r] = 0.0;
       if (md > 0) {
         double wv[3 * NS], z[3 * NS];
+        T mvb[NV];                               // M^-1 vbar (lite: Y^T vbar = J_c M^-1 vbar)
+        if (lite) {
+          for (int k = 0; k < NV; ++k) mvb[k] = vb[k];
+          fwd_packed(s.L, mvb, NV);
+          bwd_packed(s.L, mvb, NV);
+        }
         for (int ac = 0; ac < s.na; ++ac) {
           if (sz[ac] == 0) continue;
           double y3[3];
           for (int r = 0; r < 3; ++r) {
             T t = T(0);
-            for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
+            if (lite)
+              for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * mvb[k];
+            else
+              for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
             y3[r] = double(t);
           }
           if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) wv[off[ac] + r] = y3[r]; }
@@ -1678,18 +1727,29 @@ DS_HD void admm_round_env(const KArgs& a, const int e) {
 //    and the modes from the workspace.
 template <int NB, int NV, int NS, typename T>
 DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e, int chunk = 0, int nchunk = 1) {
+  // With the columns split over several threads, each recomputes the forward part; it then skips
+  // M^-1 J_c^T and G (read from the workspace, where the setup left it) to keep that redundancy low.
+  const bool lite = nchunk > 1;
   Env<NB, NV, NS, T> s;
-  env_forward<NB, NV, NS, T>(m, a, e, s);
+  env_forward<NB, NV, NS, T>(m, a, e, s, lite);
   const WsView& w = a.ws;
   const int B = a.B;
   const int mm = 3 * s.na;
+  if (lite)
+    for (int i = 0; i < mm; ++i)
+      for (int j = 0; j <= i; ++j) {
+        const double gij = w.G[tri(i, j) * B + e];
+        s.Gt[i][j] = T(gij);
+        s.Gt[j][i] = T(gij);
+        if constexpr (!Env<NB, NV, NS, T>::kDouble) { s.Gd_[i][j] = gij; s.Gd_[j][i] = gij; }
+      }
   for (int i = 0; i < mm; ++i) s.lam[i] = w.lam[i * B + e];
   if (mm > 0 && !(w.st[e] & DS_ENV_NONFINITE)) {
     for (int i = 0; i < s.na; ++i) s.mode[i] = w.mode[i * B + e];
   } else {
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
-  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk);
+  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk, lite);
 }
 
 // Copies the completed-env count to its snapshot slot (the split point of an overlapped finish).
