@@ -179,6 +179,19 @@ ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_
                        const ds_step_out* out, double* q_bar, double* v_bar, double* tau_bar,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* sim_step_vjp from a tape: the same VJP, for the solution a preceding sim_step (or sim_step_jac /
+ * sim_step_vjp) on the same inputs and options returned, without solving the NCP again.  tape:
+ * that call's outputs lambda [3*ncmax][B], modes [ncmax][B] and env_status [B] (required; other
+ * fields ignored).  Only the finish kernel runs (kinematics, dynamics and contact Jacobians are
+ * recomputed from the inputs; lambda and the modes come from the tape), so a rollout's reverse pass
+ * differentiates exactly the trajectory its forward pass produced.  No workspace.  *out is filled
+ * like sim_step's (v_next required).  Errors: DS_EINVAL (missing tape arrays, as sim_step_vjp),
+ * DS_EUNSUPPORTED, DS_ECUDA. */
+ds_status sim_step_vjp_tape(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                            const ds_options* opt, const double* v_next_bar, const double* q_next_bar,
+                            const ds_step_out* tape, const ds_step_out* out, double* q_bar, double* v_bar,
+                            double* tau_bar, void* stream);
+
 const char* ds_status_string(ds_status s);
 
 /* Cotangent coordinate maps for the configuration (the derivative convention above: q (+) eta with

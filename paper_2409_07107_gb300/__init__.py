@@ -28,7 +28,7 @@ ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
-           "ds_cotangent_to_raw", "ds_autotune")
+           "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -88,9 +88,11 @@ def lib():
         for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
+        L.sim_step_vjp_tape.argtypes = common + [vp, vp, ctypes.POINTER(ds_step_out), ctypes.POINTER(ds_step_out),
+                                                 vp, vp, vp, vp]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
                   "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read",
-                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune"):
+                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -251,6 +253,15 @@ def autotune(models, batch, opt, mode, out, o0=None, o1=None, o2=None, v_next_ba
                              _ptr(v_next_bar), ctypes.byref(o), _ptr(o0), _ptr(o1), _ptr(o2), *_ws(workspace),
                              _stream(stream), ctypes.byref(chosen)))
     return chosen.value
+
+
+def sim_step_vjp_tape(models, batch, opt, v_next_bar, tape, out, q_bar, v_bar, tau_bar, q_next_bar=None, stream=None):
+    """C-ABI sim_step_vjp_tape: the VJP of the solution recorded in `tape` (a dict with "lambda",
+    "modes", "status" from a preceding step on the same inputs); only the finish kernel runs."""
+    b, o, t = _batch_struct(batch), _out_struct(out), _out_struct(dict(tape, v_next=None))
+    _check(lib().sim_step_vjp_tape(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt),
+                                   _ptr(v_next_bar), _ptr(q_next_bar), ctypes.byref(t), ctypes.byref(o), _ptr(q_bar),
+                                   _ptr(v_bar), _ptr(tau_bar), _stream(stream)))
 
 
 def fma_peak(out, blocks, iters, fp64, stream=None):

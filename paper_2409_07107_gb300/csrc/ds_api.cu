@@ -206,7 +206,7 @@ static ds_schedule find_schedule(const SchedKey& k) {
 static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
                      const ds_step_out* out, int mode, double* dq, double* dv, double* dtau, const double* vbar,
                      const double* qnbar, double* qb, double* vb, double* tb, void* ws, size_t ws_bytes,
-                     void* stream) {
+                     void* stream, const ds_step_out* tape = nullptr) {
   if (!models || nmodels <= 0 || nmodels > 64 || !b || !o || !out) return DS_EINVAL;
   if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
   if (b->B == 0) return DS_OK;
@@ -247,6 +247,20 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.env_list = nullptr;
   a.n_env = b->B;
   a.model_id = nmodels > 1 ? b->model_id : nullptr;
+  if (tape) {
+    if ((b->ncmax > 0 && (!tape->lambda || !tape->modes)) || !tape->env_status) return DS_EINVAL;
+    a.tlam = tape->lambda;
+    a.tmodes = tape->modes;
+    a.tstat = tape->env_status;
+    cudaStream_t ts = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < nmodels; ++k) {
+      a.model = models[k]->dev;
+      a.model_index = k;
+      kern[k]->tape(a, ts);
+      if (cudaGetLastError() != cudaSuccess) return DS_ECUDA;
+    }
+    return DS_OK;
+  }
   a.sched = g_force_sched ? *g_force_sched : find_schedule(sched_key(models, nmodels, b, o, mode));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   HelperStreams* hs = nullptr;
@@ -303,6 +317,15 @@ extern "C" ds_status sim_step_jac(const ds_model* const* models, int32_t nmodels
                                   double* dv_dtau, void* ws, size_t ws_bytes, void* stream) {
   return run(models, nmodels, batch, opt, out, DS_RUN_JAC, dv_dq, dv_dv, dv_dtau, nullptr, nullptr, nullptr,
              nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+extern "C" ds_status sim_step_vjp_tape(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                                       const ds_options* opt, const double* v_next_bar, const double* q_next_bar,
+                                       const ds_step_out* tape, const ds_step_out* out, double* q_bar, double* v_bar,
+                                       double* tau_bar, void* stream) {
+  if (!tape) return DS_EINVAL;
+  return run(models, nmodels, batch, opt, out, DS_RUN_VJP, nullptr, nullptr, nullptr, v_next_bar, q_next_bar, q_bar,
+             v_bar, tau_bar, nullptr, 0, stream, tape);
 }
 
 extern "C" ds_status sim_step_vjp(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,

@@ -136,6 +136,11 @@ struct KArgs {
   int32_t* iters;
   double *dv_dq, *dv_dv, *dv_dtau;
   const double* vbar;
+  // tape of a preceding sim_step on the same inputs (per slot impulses and modes, status): the
+  // finish reads the NCP solution from it instead of solving (NULL = no tape)
+  const double* tlam;
+  const uint8_t* tmodes;
+  const uint32_t* tstat;
   const double* qnbar;     // [nv][B] cotangent of q+ (tangent coordinates) or NULL
   double *q_bar, *v_bar, *tau_bar;
   int run;
@@ -164,6 +169,7 @@ struct ds_kernel_entry {
   int nb, nv, ns, precision;
   ds_launch_fn fn;
   ds_launch_fn pipeline;
+  ds_launch_fn tape;       // finish only, from a tape (KArgs.tlam / tmodes / tstat)
 };
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
 extern "C++" const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int precision);

@@ -1752,6 +1752,38 @@ DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e, int chunk 
   env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk, lite);
 }
 
+// Finish from a tape: F1-F6, then lambda, the modes and the status of env e from the tape of a
+// preceding sim_step on the same inputs, then F9 and the derivatives (the VJP of exactly the
+// solution the forward call returned, without solving the NCP again).
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_tape_env(const DevModel& m, const KArgs& a, const int e, int chunk, int nchunk) {
+  Env<NB, NV, NS, T> s;
+  const uint32_t fst = env_forward<NB, NV, NS, T>(m, a, e, s);
+  const int B = a.B;
+  const uint32_t st = a.tstat[e] | (fst & DS_ENV_NONFINITE);
+  for (int ac = 0; ac < s.na; ++ac)
+    for (int r = 0; r < 3; ++r) s.lam[3 * ac + r] = a.tlam[(3 * s.slot[ac] + r) * B + e];
+  if (s.na > 0 && !(st & DS_ENV_NONFINITE)) {
+    for (int ac = 0; ac < s.na; ++ac) s.mode[ac] = a.tmodes[s.slot[ac] * B + e];
+  } else {
+    s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
+  }
+  env_finish<NB, NV, NS, T>(m, a, e, s, st, 0, chunk, nchunk, false);
+}
+
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(128, 4) finish_tape_kernel(KArgs a) {
+  __shared__ DevModel sm;
+  load_model(sm, a.model);
+  const long long total = (long long)a.n_env * a.nchunk;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int chunk = int(t / a.n_env), e = int(t - (long long)chunk * a.n_env);
+    if (a.model_id && a.model_id[e] != a.model_index) continue;
+    finish_tape_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
+  }
+}
+
 // Copies the completed-env count to its snapshot slot (the split point of an overlapped finish).
 static __global__ void dcount_snapshot_kernel(int32_t* dcount) { dcount[1] = dcount[0]; }
 

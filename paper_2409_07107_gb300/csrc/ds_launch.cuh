@@ -152,4 +152,21 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   ds_trace_mark(DS_STAGE_FINISH, 0, s);
 }
 
+// Finish only, from a tape (KArgs.tlam / tmodes / tstat); columns split as in the pipeline.
+template <int NB, int NV, int NS, typename T>
+void launch_tape(const KArgs& a0, cudaStream_t s) {
+  const int threads = 128;
+  if (a0.n_env <= 0) return;
+  KArgs a = a0;
+  a.nchunk = 1;
+  if (a0.run != DS_RUN_STEP) {
+    const int maxc = a0.run == DS_RUN_JAC ? 3 * NV : 2 * NV;
+    const int c = ds_sm_count() * 4 * threads / a0.n_env;
+    a.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);
+  }
+  ds_trace_mark(DS_STAGE_FINISH, 1, s);
+  finish_tape_kernel<NB, NV, NS, T><<<finish_blocks(a0.n_env, a.nchunk, threads), threads, 0, s>>>(a);
+  ds_trace_mark(DS_STAGE_FINISH, 0, s);
+}
+
 }  // namespace ds

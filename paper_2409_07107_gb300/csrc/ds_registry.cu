@@ -5,10 +5,14 @@
   void ds_launch_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);       \
   void ds_launch_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);       \
   void ds_pipeline_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);     \
-  void ds_pipeline_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
-#define DS_ROW(NB, NV, NS)                                                                        \
-  {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64, ds_pipeline_##NB##_##NV##_##NS##_f64}, \
-  {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix, ds_pipeline_##NB##_##NV##_##NS##_mix},
+  void ds_pipeline_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);   \
+  void ds_tape_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);         \
+  void ds_tape_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
+#define DS_ROW(NB, NV, NS)                                                                          \
+  {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64, ds_pipeline_##NB##_##NV##_##NS##_f64,     \
+   ds_tape_##NB##_##NV##_##NS##_f64},                                                                 \
+  {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix, ds_pipeline_##NB##_##NV##_##NS##_mix,    \
+   ds_tape_##NB##_##NV##_##NS##_mix},
 
 #include "ds_shapes.inc"
 

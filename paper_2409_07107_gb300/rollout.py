@@ -7,7 +7,8 @@ and its tangent coordinates are library kernels too).  This module only marshals
 * ``StepContext`` holds what does not change along a rollout: device models, contact descriptors,
   options and the pipeline workspace;
 * ``SimStep.apply(q, v, tau, ctx)`` -> (q+, v+), differentiable w.r.t. q (raw coordinates, the
-  free-flyer quaternion included), v and tau;
+  free-flyer quaternion included), v and tau; its forward keeps the step's tape (impulses, modes,
+  status) and its backward differentiates that solution (sim_step_vjp_tape: no second NCP solve);
 * ``rollout(ctx, q0, v0, taus, checkpoint_every)`` runs len(taus) steps; with checkpoint_every = k
   the reverse pass recomputes each k-step segment from its first state instead of keeping every
   step's inputs (torch.utils.checkpoint), trading one extra forward step per step for memory.
@@ -16,7 +17,7 @@ import torch
 import torch.utils.checkpoint
 
 from . import (DeviceModel, batch_to_device, cotangent_to_raw, cotangent_to_tangent, make_options, sim_step,
-               sim_step_vjp, workspace_size)
+               sim_step_vjp, sim_step_vjp_tape, workspace_size)
 
 
 class StepContext:
@@ -46,21 +47,29 @@ class StepContext:
         return d
 
     def step(self, q, v, tau):
-        """(q+, v+) as new tensors."""
-        out = dict(self.scratch, v_next=torch.empty(self.nv, self.B, dtype=torch.float64, device=self.device),
+        """(q+, v+) as new tensors, and the step's tape (impulses, modes, status) for its VJP."""
+        tape = {"lambda": torch.empty(3 * self.nc, self.B, dtype=torch.float64, device=self.device),
+                "modes": torch.empty(self.nc, self.B, dtype=torch.uint8, device=self.device),
+                "status": torch.empty(self.B, dtype=torch.int32, device=self.device)}
+        out = dict(self.scratch, **tape, v_next=torch.empty(self.nv, self.B, dtype=torch.float64, device=self.device),
                    q_next=torch.empty(self.nq, self.B, dtype=torch.float64, device=self.device))
         sim_step(self.models, self._batch(q, v, tau), self.opt, out, self.workspace)
-        return out["q_next"], out["v_next"]
+        return out["q_next"], out["v_next"], tape
 
-    def vjp(self, q, v, tau, q_next, q_next_bar_raw, v_next_bar):
-        """Cotangents of (q raw, v, tau) from those of (q+ raw, v+)."""
+    def vjp(self, q, v, tau, q_next, q_next_bar_raw, v_next_bar, tape=None):
+        """Cotangents of (q raw, v, tau) from those of (q+ raw, v+); with the forward step's tape,
+        the VJP of that very solution (only the finish kernel runs)."""
         e = lambda rows: torch.empty(rows, self.B, dtype=torch.float64, device=self.device)  # noqa: E731
         qn_t = e(self.nv)
         cotangent_to_tangent(self.models, q_next, q_next_bar_raw, qn_t, self.model_id)
         out = dict(self.scratch, v_next=e(self.nv), q_next=None)
         q_bar_t, v_bar, tau_bar = e(self.nv), e(self.nv), e(self.nv)
-        sim_step_vjp(self.models, self._batch(q, v, tau), self.opt, v_next_bar, out, q_bar_t, v_bar, tau_bar,
-                     workspace=self.workspace, q_next_bar=qn_t)
+        if tape is not None:
+            sim_step_vjp_tape(self.models, self._batch(q, v, tau), self.opt, v_next_bar, tape, out, q_bar_t, v_bar,
+                              tau_bar, q_next_bar=qn_t)
+        else:
+            sim_step_vjp(self.models, self._batch(q, v, tau), self.opt, v_next_bar, out, q_bar_t, v_bar, tau_bar,
+                         workspace=self.workspace, q_next_bar=qn_t)
         q_bar = torch.zeros(self.nq, self.B, dtype=torch.float64, device=self.device)
         cotangent_to_raw(self.models, q, q_bar_t, q_bar, self.model_id)
         return q_bar, v_bar, tau_bar
@@ -72,17 +81,18 @@ class SimStep(torch.autograd.Function):
     @staticmethod
     def forward(ctx, q, v, tau, sc):
         q, v, tau = q.detach().contiguous(), v.detach().contiguous(), tau.detach().contiguous()
-        qn, vn = sc.step(q, v, tau)
+        qn, vn, tape = sc.step(q, v, tau)
         ctx.sc = sc
-        ctx.save_for_backward(q, v, tau, qn)
+        ctx.save_for_backward(q, v, tau, qn, tape["lambda"], tape["modes"], tape["status"])
         return qn, vn
 
     @staticmethod
     def backward(ctx, gq, gv):
-        q, v, tau, qn = ctx.saved_tensors
+        q, v, tau, qn, lam, modes, status = ctx.saved_tensors
         gq = torch.zeros_like(qn) if gq is None else gq.contiguous()
         gv = torch.zeros_like(v) if gv is None else gv.contiguous()
-        qb, vb, tb = ctx.sc.vjp(q, v, tau, qn, gq, gv)
+        tape = {"lambda": lam, "modes": modes, "status": status}
+        qb, vb, tb = ctx.sc.vjp(q, v, tau, qn, gq, gv, tape)
         return qb, vb, tb, None
 
 

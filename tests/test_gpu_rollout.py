@@ -141,3 +141,30 @@ def test_rollout_gradient_vs_gpu_central_differences(torch_cuda):
     an = (tau_p.grad * u).sum((0, 1)).cpu().numpy()
     rel = np.abs(fd - an) / np.maximum(np.abs(an), 1e-8)
     assert (rel <= 1e-4).sum() >= 6, rel
+
+
+@pytest.mark.parametrize("which,precision", [("quadruped", "fp64"), ("uneven", "mixed")])
+def test_vjp_from_tape_matches_vjp(torch_cuda, which, precision):
+    """sim_step_vjp_tape (finish only, impulses and modes from a preceding sim_step's outputs) gives
+    the same cotangents as sim_step_vjp, which solves the NCP again."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.quadruped_feet(96) if which == "quadruped" else scenes.uneven(96)
+    sim = ds.Simulator(wl, precision=precision)
+    out = sim.step()
+    tape = {"lambda": out["lambda"].clone(), "modes": out["modes"].clone(), "status": out["status"].clone()}
+    rng = np.random.default_rng(19)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda").contiguous()  # noqa: E731
+    vb, qb = t(rng.normal(size=wl.batch.v.shape)), t(rng.normal(size=wl.batch.v.shape))
+    ref = {k: v.clone() for k, v in sim.step_vjp(vb, q_next_bar=qb).items()}
+    got = [torch.zeros_like(vb) for _ in range(3)]
+    out2 = {"v_next": torch.zeros_like(vb)}
+    ds.sim_step_vjp_tape(sim.models, sim.batch, sim.opt, vb, tape, out2, *got, q_next_bar=qb)
+    torch.cuda.synchronize()
+    # the two finish paths order their products differently (solves with M's factor in place of
+    # M^-1 J_c^T when columns are split): rounding-level differences only
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    for g, key in zip(got, ("q_bar", "v_bar", "tau_bar")):
+        err = ((g - ref[key]).abs().amax(0) / ref[key].abs().amax(0).clamp_min(1e-6)).max().item()
+        assert err <= tol, (key, err)
+    assert ((out2["v_next"] - ref["v_next"]).abs().max() / ref["v_next"].abs().max()).item() <= tol
