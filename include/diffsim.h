@@ -237,25 +237,39 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * never), how many threads share an env's Jacobian columns in the finish kernel (a target of 0, 4
  * or 8 CTAs per SM), the Newton kernel's form (cooperative or one thread per env), and the round
  * after which the envs already solved are finished on a side stream of the library while the slow
- * ones still iterate (2, 4 or never).
+ * ones still iterate (2, 4, 5 or never), the first round handled by the two-warp ADMM kernel
+ * (FP64 with at most 10 contact slots: one warp runs the x-step and projection, the other the De
+ * Saxce term and convergence test; 3, 5 or never), and which SMs that overlapped finish leaves to
+ * the slow envs (none, every 8th or every 4th: the FP64 pipe of an SM sub-partition is shared by
+ * its warps, so the late rounds run faster on SMs the finish does not occupy).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
  * schedule by the fastest of three runs (CUDA events on `stream`, after an untimed run), in a
  * coordinate search from the default (each knob over its options with the others at the best so
- * far: 10 schedules besides the default; a schedule replaces the best only if 2 % faster).  It keeps the fastest for the batch's signature (first model's bodies and
- * dofs, number of models, ncmax, precision, mode, B rounded up to a power of two) and finally runs
- * the call once more with it, so that *out and o0..o2 hold its results.  Later calls with the
- * same signature use that schedule; other batches keep the default.  A schedule never changes what
- * an env computes, except that the two Newton forms round differently (results agree to the solver
- * tolerance).  Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be
- * NULL) gets c + 3 (w + 3 (f + 3 (n + 2 o))): round caps c (0 default, 1 halved, 2 doubled),
- * first row-per-lane round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1,
- * 2), Newton n (0 cooperative, 1 one thread per env), overlapped finish o (0: after round 2, 1:
- * after round 4, 2: never).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
+ * far, two passes over the knobs; a schedule replaces the best only if 2 % faster).  It keeps the
+ * fastest for the batch's signature (first model's bodies and dofs, number of models, ncmax,
+ * precision, mode, B rounded up to a power of two) and finally runs the call once more with it,
+ * so that *out and o0..o2 hold its results.  Later calls with the same signature use that
+ * schedule; other batches keep the default.  A schedule never changes what an env computes,
+ * except that the two Newton forms round differently (results agree to the solver tolerance).
+ * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
+ * the schedule's index (0 .. 1943), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 4 (p +
+ * 3 r))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane round w (0: 3, 1: 5,
+ * 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0 cooperative, 1 one
+ * thread per env), overlapped finish o (0: after round 2, 1: after round 4, 2: after round 5, 3:
+ * never), two-warp ADMM p (0: from round 3, 1: from round 5, 2: never), SMs kept free r (0: none,
+ * 1: every 8th, 2: every 4th).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
                       double* o0, double* o1, double* o2, void* workspace, size_t workspace_bytes,
                       void* stream, int32_t* chosen);
+
+/* Sets the schedule (index as ds_autotune's *chosen) that later calls of `mode` use for batches
+ * with this batch's signature, as if ds_autotune had chosen it; index -1 returns the signature to
+ * the default schedule (no counterpart in the paper).  For reusing a tuned schedule without timing
+ * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 1943). */
+ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                          const ds_options* opt, int32_t mode, int32_t index);
 
 /* Stage tracing (no counterpart in the paper): with ds_profile(1), every kernel the library
  * launches is bracketed by CUDA events on its own stream, grouped in DS_NSTAGES = 5 classes:

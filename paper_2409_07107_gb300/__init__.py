@@ -28,7 +28,7 @@ ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
-           "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape")
+           "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape", "ds_set_schedule")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -90,9 +90,11 @@ def lib():
         L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
         L.sim_step_vjp_tape.argtypes = common + [vp, vp, ctypes.POINTER(ds_step_out), ctypes.POINTER(ds_step_out),
                                                  vp, vp, vp, vp]
+        L.ds_set_schedule.argtypes = common + [i32, i32]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
                   "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read",
-                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape"):
+                  "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape",
+                  "ds_set_schedule"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -226,22 +228,38 @@ def cotangent_to_raw(models, q, q_bar_tangent, q_bar_raw, model_id=None, stream=
                                      _ptr(q_bar_tangent), _ptr(q_bar_raw), _stream(stream)))
 
 
-SCHEDULE_CAPS = ("default", "halved", "doubled")
-SCHEDULE_WIDE = (3, 5, None)
-SCHEDULE_FINISH = (0, 4, 8)
-SCHEDULE_OVERLAP = (2, 4, None)
+# Schedule knobs and their options, as the library encodes them: the schedule index is the
+# mixed-radix number of the option positions, the first knob the lowest digit.
+SCHEDULE_KNOBS = (
+    ("round_caps", ("default", "halved", "doubled")),
+    ("row_per_lane_admm_from_round", (3, 5, None)),
+    ("finish_ctas_per_sm", (0, 4, 8)),
+    ("newton", ("cooperative", "one thread per env")),
+    ("overlapped_finish_after_round", (2, 4, 5, None)),
+    ("two_warp_admm_from_round", (3, 5, None)),
+    ("overlapped_finish_keeps_free_every_nth_sm", (None, 8, 4)),
+)
+NUM_SCHEDULES = 1944
 
 
 def describe_schedule(index):
-    """The schedule ds_autotune chose, from its index c + 3 (w + 3 (f + 3 (n + 2 o)))."""
-    i = int(index)
-    c, i = i % 3, i // 3
-    wi, i = i % 3, i // 3
-    f, i = i % 3, i // 3
-    n, o = i % 2, i // 2
-    return {"round_caps": SCHEDULE_CAPS[c], "row_per_lane_admm_from_round": SCHEDULE_WIDE[wi],
-            "finish_ctas_per_sm": SCHEDULE_FINISH[f], "newton": "one thread per env" if n else "cooperative",
-            "overlapped_finish_after_round": SCHEDULE_OVERLAP[o]}
+    """The schedule with this index (as ds_autotune returns it), knob by knob."""
+    i, d = int(index), {}
+    for name, opts in SCHEDULE_KNOBS:
+        d[name] = opts[i % len(opts)]
+        i //= len(opts)
+    return d
+
+
+def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1):
+    """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
+    defaults give the library's default schedule."""
+    idx, mul = 0, 1
+    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve), SCHEDULE_KNOBS):
+        assert 0 <= pos < len(opts)
+        idx += pos * mul
+        mul *= len(opts)
+    return idx
 
 
 def autotune(models, batch, opt, mode, out, o0=None, o1=None, o2=None, v_next_bar=None, workspace=None,
@@ -253,6 +271,14 @@ def autotune(models, batch, opt, mode, out, o0=None, o1=None, o2=None, v_next_ba
                              _ptr(v_next_bar), ctypes.byref(o), _ptr(o0), _ptr(o1), _ptr(o2), *_ws(workspace),
                              _stream(stream), ctypes.byref(chosen)))
     return chosen.value
+
+
+def set_schedule(models, batch, opt, mode, index):
+    """C-ABI ds_set_schedule: later calls of `mode` on batches of this signature use schedule
+    `index` (as returned by autotune); -1 restores the default."""
+    b = _batch_struct(batch)
+    _check(lib().ds_set_schedule(_models_array(models), len(models), ctypes.byref(b), ctypes.byref(opt), int(mode),
+                                 int(index)))
 
 
 def sim_step_vjp_tape(models, batch, opt, v_next_bar, tape, out, q_bar, v_bar, tau_bar, q_next_bar=None, stream=None):
@@ -363,6 +389,11 @@ class Simulator:
         idx = autotune(self.models, self.batch, self.opt, mode, self.out, *o, v_next_bar=v_next_bar,
                        workspace=self.workspace)
         return dict(describe_schedule(idx), index=idx)
+
+    def set_schedule(self, index, kind="jac"):
+        """Use schedule `index` for this batch's `kind` calls (-1: the default); returns its description."""
+        set_schedule(self.models, self.batch, self.opt, {"step": 0, "jac": 1, "vjp": 2}[kind], index)
+        return None if index < 0 else dict(describe_schedule(index), index=index)
 
     def capture(self, kind="jac", v_next_bar=None, q_next_bar=None):
         """Capture one step (kind "step", "jac" or "vjp", on this Simulator's buffers) in a CUDA

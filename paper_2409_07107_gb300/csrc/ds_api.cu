@@ -176,7 +176,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 4};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -402,6 +402,61 @@ extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int3
   return cotangent(models, nmodels, B, model_id, q, q_bar_raw, q_bar_tangent, 0, stream);
 }
 
+// Schedule knobs and their options.  The index of ds_autotune / ds_set_schedule is the mixed-radix
+// number of the chosen option positions, knob 0 the lowest digit.
+static const int kKnobs = 7, kNumSchedules = 3 * 3 * 3 * 2 * 4 * 3 * 3;
+static const int kNopt[kKnobs] = {3, 3, 3, 2, 4, 3, 3};
+static const int kOpt[kKnobs][4] = {{0, 1, 2, 0},          // round-cap table
+                                    {3, 5, DS_ROUNDS, 0},  // first row-per-lane ADMM round
+                                    {0, 4, 8, 0},          // finish: target CTAs per SM
+                                    {0, 1, 0, 0},          // Newton: cooperative / one thread per env
+                                    {2, 4, 5, DS_ROUNDS},  // overlapped finish after this round
+                                    {3, 5, DS_ROUNDS, 0},  // first two-warp ADMM round
+                                    {0, 8, 4, 0}};         // overlapped finish: SM stride kept free
+static int* knob(ds_schedule& c, int d) {
+  switch (d) {
+    case 0: return &c.caps;
+    case 1: return &c.wide_from;
+    case 2: return &c.finish_ctas;
+    case 3: return &c.newton_thread;
+    case 4: return &c.overlap_from;
+    case 5: return &c.pair_from;
+    default: return &c.reserve;
+  }
+}
+static int schedule_index(ds_schedule c) {
+  int idx = 0, mul = 1;
+  for (int d = 0; d < kKnobs; ++d) {
+    int pos = 0;
+    for (int o = 0; o < kNopt[d]; ++o)
+      if (kOpt[d][o] == *knob(c, d)) { pos = o; break; }
+    idx += pos * mul;
+    mul *= kNopt[d];
+  }
+  return idx;
+}
+static ds_schedule schedule_from_index(int i) {
+  ds_schedule c;
+  for (int d = 0; d < kKnobs; ++d) {
+    *knob(c, d) = kOpt[d][i % kNopt[d]];
+    i /= kNopt[d];
+  }
+  return c;
+}
+
+extern "C" ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
+                                     const ds_options* opt, int32_t mode, int32_t index) {
+  if (!models || nmodels <= 0 || nmodels > 64 || !batch || !opt || batch->B <= 0) return DS_EINVAL;
+  if (mode < DS_RUN_STEP || mode > DS_RUN_VJP || index < -1 || index >= kNumSchedules) return DS_EINVAL;
+  for (int k = 0; k < nmodels; ++k)
+    if (!models[k]) return DS_EINVAL;
+  const SchedKey key = sched_key(models, nmodels, batch, opt, mode);
+  std::lock_guard<std::mutex> lock(g_sched_mu);
+  if (index < 0) g_sched.erase(key);
+  else g_sched[key] = schedule_from_index(index);
+  return DS_OK;
+}
+
 extern "C" ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t nmodels, int32_t B,
                                          const int32_t* model_id, const double* q, const double* q_bar_tangent,
                                          double* q_bar_raw, void* stream) {
@@ -427,9 +482,8 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
     return sim_step_vjp(models, nmodels, batch, opt, v_next_bar, nullptr, out, o0, o1, o2, ws, ws_bytes, stream);
   };
   // Coordinate search from the default: each knob in turn over its options, the others held at
-  // the best found so far (round caps, first row-per-lane round, finish split target, Newton form).
-  static const int kOpts[5][3] = {{0, 1, 2}, {3, 5, DS_ROUNDS}, {0, 4, 8}, {0, 1, 0}, {2, 4, DS_ROUNDS}};
-  static const int kNopt[5] = {3, 3, 3, 2, 3};
+  // the best found so far; two passes, since some knobs pay only together (the two-warp ADMM
+  // rounds and the SMs kept free of the overlapped finish).
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return DS_ECUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return DS_ECUDA; }
@@ -454,18 +508,17 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
   };
   float best_ms = 0.f;
   st = timed(best, &best_ms);
-  for (int d = 0; d < 5 && st == DS_OK; ++d)
-    for (int o = 0; o < kNopt[d] && st == DS_OK; ++o) {
-      ds_schedule c = best;
-      int* field = d == 0 ? &c.caps
-                   : (d == 1 ? &c.wide_from
-                             : (d == 2 ? &c.finish_ctas : (d == 3 ? &c.newton_thread : &c.overlap_from)));
-      if (*field == kOpts[d][o]) continue;
-      *field = kOpts[d][o];
-      float ms = 0.f;
-      st = timed(c, &ms);
-      if (st == DS_OK && ms < 0.98f * best_ms) { best_ms = ms; best = c; }   // 2 % to switch: noise
-    }
+  for (int pass = 0; pass < 2 && st == DS_OK; ++pass)
+    for (int d = 0; d < kKnobs && st == DS_OK; ++d)
+      for (int o = 0; o < kNopt[d] && st == DS_OK; ++o) {
+        ds_schedule c = best;
+        int* field = knob(c, d);
+        if (*field == kOpt[d][o]) continue;
+        *field = kOpt[d][o];
+        float ms = 0.f;
+        st = timed(c, &ms);
+        if (st == DS_OK && ms < 0.98f * best_ms) { best_ms = ms; best = c; }   // 2 % to switch: noise
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != DS_OK) return st;
@@ -473,11 +526,6 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
     std::lock_guard<std::mutex> l2(g_sched_mu);
     g_sched[sched_key(models, nmodels, batch, opt, mode)] = best;
   }
-  if (chosen) {
-    const int wi = best.wide_from == 3 ? 0 : (best.wide_from == 5 ? 1 : 2);
-    const int fi = best.finish_ctas == 0 ? 0 : (best.finish_ctas == 4 ? 1 : 2);
-    const int oi = best.overlap_from == 2 ? 0 : (best.overlap_from == 4 ? 1 : 2);
-    *chosen = best.caps + 3 * (wi + 3 * (fi + 3 * (best.newton_thread + 2 * oi)));
-  }
+  if (chosen) *chosen = schedule_index(best);
   return call();                                          // leave the outputs of the chosen schedule
 }

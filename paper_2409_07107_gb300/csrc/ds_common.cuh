@@ -1,6 +1,7 @@
 // Shared device-side definitions of the batched contact-step kernels (sm_103a).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -52,6 +53,7 @@ struct WsView {
   int32_t* fetch;         // [DS_ROUNDS] next unclaimed entry of each round's list (follows ncounts)
   int32_t* dlist;         // [B] envs whose NCP solve is complete, in completion order
   int32_t* dcount;        // [2] entries of dlist; a snapshot of it (follows fetch)
+  int32_t* claim;         // [1] next unclaimed work item of the overlapped finish (follows dcount)
 };
 
 // Lays out the workspace for ns contact slots, B envs and nmodels models starting at base (may be
@@ -89,7 +91,7 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
     int32_t* l0 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     int32_t* l1 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     int32_t* nl = static_cast<int32_t*>(take(sizeof(int32_t) * B));
-    int32_t* nc = static_cast<int32_t*>(take(sizeof(int32_t) * (2 * DS_ROUNDS + 2)));
+    int32_t* nc = static_cast<int32_t*>(take(sizeof(int32_t) * (2 * DS_ROUNDS + 3)));
     int32_t* dl = static_cast<int32_t*>(take(sizeof(int32_t) * B));
     if (k == model) {
       w.counts = counts;
@@ -99,6 +101,7 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
       w.ncounts = nc;
       w.fetch = nc + DS_ROUNDS;
       w.dcount = nc + 2 * DS_ROUNDS;
+      w.claim = nc + 2 * DS_ROUNDS + 2;
       w.dlist = dl;
     }
   }
@@ -114,6 +117,8 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
 struct ds_schedule {
   int caps, wide_from, finish_ctas, newton_thread;
   int overlap_from;   // after this round, finish the completed envs on a side stream (DS_ROUNDS = never)
+  int pair_from;      // first round of the two-warp ADMM kernel (FP64, 3 NS <= 32; DS_ROUNDS = never)
+  int reserve;        // overlapped finish: keep off the SMs with smid % reserve == 0 (0 = use all)
 };
 
 // Everything a launch needs; passed by value.
@@ -147,6 +152,9 @@ struct KArgs {
   WsView ws;               // pipeline workspace (unused by the fused kernel)
   int round, round_cap, final_round;
   int nchunk;              // finish kernel: threads per env (Jacobian columns split between them)
+  int fin_reserve;         // finish kernel: CTAs on SMs with smid % fin_reserve == 0 return at once
+  int32_t* claim;          // finish kernel: work items claimed a warp at a time from *claim (NULL:
+                           // a static grid-stride split)
   ds_schedule sched;
   // finish kernel over a device-side range of ws.dlist: entries [*flo, *fhi) (flo NULL = from 0);
   // fhi NULL = every env of the launch

@@ -42,6 +42,32 @@ struct Ncp {
   }
 };
 
+// Maximum of two values that are >= 0 (or NaN), taken on their bit patterns: for non-negative IEEE
+// numbers the order of the patterns as signed integers is the numeric order.  Unlike fmax, which
+// drops a NaN operand, a (positive) NaN compares above every number, so an ADMM convergence test
+// on a NaN residual fails, as the oracle's does.
+DS_HDI double nonneg_max(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(a) > __double_as_longlong(b) ? a : b;
+#else
+  long long ia, ib;
+  memcpy(&ia, &a, sizeof ia);
+  memcpy(&ib, &b, sizeof ib);
+  return ia > ib ? a : b;
+#endif
+}
+
+DS_HDI float nonneg_max(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __float_as_int(a) > __float_as_int(b) ? a : b;
+#else
+  int ia, ib;
+  memcpy(&ia, &a, sizeof ia);
+  memcpy(&ib, &b, sizeof ib);
+  return ia > ib ? a : b;
+#endif
+}
+
 // Pieces of the ADMM iteration with the divisions and square roots of the plain projection
 // replaced by one reciprocal square root and precomputed reciprocals (1/rho, 1/(1 + mu^2)): the
 // same mathematics with a shorter dependent chain (FP64 division and sqrt are long sequences).
@@ -322,9 +348,9 @@ DS_HDI void admm_update(const T (*Kr)[NC3], const T* rhs_full, const T* rhs_own,
   proj_cone_fast(w, mu, inv1pmu2, pr);
   if (check) {
     for (int r = 0; r < 3; ++r) {
-      rd = fmax(rd, fabs(pr[r] - z[r]));
-      rp = fmax(rp, fabs(x[r] - pr[r]));
-      zmax = fmax(zmax, fabs(pr[r]));
+      rd = nonneg_max(rd, T(fabs(pr[r] - z[r])));
+      rp = nonneg_max(rp, T(fabs(x[r] - pr[r])));
+      zmax = nonneg_max(zmax, T(fabs(pr[r])));
     }
   }
   for (int r = 0; r < 3; ++r) {
@@ -1399,7 +1425,7 @@ __global__ void __launch_bounds__(128, 4) setup_kernel(KArgs a) {
 //     that hit the iteration cap) go to the Newton queue, the others to the next round's list.
 template <typename T>
 __device__ __forceinline__ T group_max(T v, int lanes) {
-  for (int off = lanes >> 1; off >= 1; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  for (int off = lanes >> 1; off >= 1; off >>= 1) v = nonneg_max(v, __shfl_xor_sync(0xffffffffu, v, off));
   return v;
 }
 
@@ -1580,7 +1606,7 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
       if (act && chk) {
         rd = fabs(zn - z);
         rp = fabs(xn - zn);
-        zmax = fmax(zmax, fabs(zn));
+        zmax = nonneg_max(zmax, T(fabs(zn)));
       }
       if (__any_sync(0xffffffffu, running && chk)) {
         rp = group_max(rp, L);
@@ -1604,6 +1630,181 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
         w.az[li * B + e] = double(z);
         w.ay[li * B + e] = double(y);
         w.asx[li * B + e] = double(sx);
+      }
+      if (li == 0) {
+        w.iters[e] = iters;
+        if (conv || iters >= a.admm_max_iter || a.final_round) {
+          const int k = atomicAdd(&w.ncounts[a.round], 1);
+          w.nlist[k] = e;
+        } else {
+          const int k = atomicAdd(&w.counts[a.round + 1], 1);
+          next[k] = e;
+        }
+      }
+    }
+  }
+}
+
+// 2a''. the row-per-lane round split over the two warps of a 64-thread CTA, for the late rounds:
+//       they hold few envs, each round lasts as long as its slowest env's chain of iterations, and
+//       an SM sub-partition's FP64 pipe takes one warp instruction at a time.  Warp 0 keeps K, x,
+//       z, y and runs the x-step, the projection and the multiplier update; warp 1 (another
+//       sub-partition) keeps sx and forms the next iteration's De Saxce norm and the convergence
+//       test from what warp 0 leaves in shared memory, so those leave warp 0's instruction stream.
+//       The lane layout is the row-per-lane kernel's, and so is every row's arithmetic.  Named
+//       barriers order the hand-offs (warp-uniform; 64 threads each):
+//         kDs  warp 1 arrives, warp 0 waits: the De Saxce norms of the coming iteration and the
+//              outcome of the previous iteration's convergence test are in place;
+//         kRhs warp 0 arrives, warp 1 waits: this iteration's right-hand side, x-step and flags
+//              are in place (or the env loop ends: stop flag);
+//         kZ   warp 0 arrives, warp 1 waits, on test iterations only: the projected z is in place.
+//       A test's outcome reaches warp 0 at the top of the next iteration, before it decides to go
+//       on, so an env stops on the same iteration as in the other forms.
+__device__ __forceinline__ void named_bar_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int threads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+template <int NS, typename T>
+__global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
+  static_assert(WideShape<NS>::kOk, "3 NS rows must fit in a warp");
+  constexpr int L = WideShape<NS>::L, EPW = 32 / L, NC3 = 3 * NS;
+  constexpr int kDs = 1, kRhs = 2, kZ = 3;
+  __shared__ T s_rhs[32], s_x[32], s_z[32], s_zold[32], s_nt[32];
+  __shared__ int s_run[EPW], s_chk[EPW], s_conv[EPW], s_stop;
+  const WsView& w = a.ws;
+  const int n = w.counts[a.round];
+  const int B = a.B;
+  const int role = threadIdx.x >> 5;          // 0: x-step / projection, 1: De Saxce term and test
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / L, li = lane - grp * L;
+  const int gb = grp * L;
+  const int ci = li < NC3 ? li / 3 : NS - 1, kc = li < NC3 ? li - 3 * (li / 3) : 0;
+  const int32_t* cur = w.list[a.round & 1];
+  int32_t* next = w.list[(a.round + 1) & 1];
+  for (int base = blockIdx.x * EPW; base < n; base += gridDim.x * EPW) {
+    const int t = base + grp;
+    const bool have = t < n;
+    const int e = have ? cur[t] : 0;
+    const int na = have ? w.na[e] : 0;
+    const bool act = li < 3 * na;
+    const T g = act ? T(w.g[li * B + e]) : T(0);
+    const T rho = have ? T(w.rho[e]) : T(1);
+    const T gs = fmax(T(1), group_max(T(fabs(g)), L));
+    const int stage = have ? w.stage[e] : 0;
+    const T te = T(stage_eps<T>(a, stage));
+    if (role == 1) {
+      T sx = act ? T(w.asx[li * B + e]) : T(0);
+      {
+        const T s0 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci);
+        const T s1 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci + 1);
+        T nt, inv;
+        norm_and_inv(s0, s1, nt, inv);
+        s_nt[lane] = nt;
+        if (li == 0) s_conv[grp] = 0;
+      }
+      named_bar_arrive(kDs, 64);
+      for (;;) {
+        named_bar_sync(kRhs, 64);
+        if (s_stop) break;
+        const bool run = s_run[grp] != 0, chk = s_chk[grp] != 0;
+        bool anychk = false;
+#pragma unroll
+        for (int q = 0; q < EPW; ++q) anychk = anychk || (s_run[q] != 0 && s_chk[q] != 0);
+        const T rhs = s_rhs[lane], xn = s_x[lane];
+        if (run && kc < 2) sx = rhs - rho * xn + g;
+        const T s0 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci);
+        const T s1 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci + 1);
+        T nt, inv;
+        norm_and_inv(s0, s1, nt, inv);
+        bool conv = false;
+        if (anychk) {
+          named_bar_sync(kZ, 64);
+          T rp = T(0), rd = T(0), zmax = T(1);
+          if (act && run && chk) {
+            const T zn = s_z[lane];
+            rd = fabs(zn - s_zold[lane]);
+            rp = fabs(xn - zn);
+            zmax = nonneg_max(zmax, T(fabs(zn)));
+          }
+          rp = group_max(rp, L);
+          rd = group_max(rd, L);
+          zmax = group_max(zmax, L);
+          rd *= rho;
+          conv = run && chk && rp <= te * zmax && rd <= te * gs;
+        }
+        s_nt[lane] = nt;
+        if (li == 0) s_conv[grp] = conv ? 1 : 0;
+        named_bar_arrive(kDs, 64);
+      }
+      if (have && act) w.asx[li * B + e] = double(sx);
+      continue;
+    }
+    T Kr[NC3];
+#pragma unroll
+    for (int c = 0; c < NC3; ++c) Kr[c] = act ? T(w.K[(li * NC3 + c) * B + e]) : T(0);
+    T x = act ? T(w.ax[li * B + e]) : T(0);
+    T z = act ? T(w.az[li * B + e]) : T(0);
+    T y = act ? T(w.ay[li * B + e]) : T(0);
+    const T mu = act ? T(w.mu[ci * B + e]) : T(0);
+    const T inv_rho = T(1) / rho;
+    const T inv1pmu2 = T(1) / (T(1) + mu * mu);
+    int iters = have ? w.iters[e] : 0;
+    bool running = have && iters < a.admm_max_iter;
+    bool conv = false, pend = false;
+    const T relax = T(1.6);
+    for (int k = 0;; ++k) {
+      named_bar_sync(kDs, 64);
+      if (pend && s_conv[grp]) { conv = true; running = false; }
+      pend = false;
+      if (!(k < a.round_cap && __any_sync(0xffffffffu, running))) {
+        if (lane == 0) s_stop = 1;
+        named_bar_arrive(kRhs, 64);
+        break;
+      }
+      const bool chk = (iters + 1) % DS_ADMM_CHECK == 0;
+      const T nt = s_nt[lane];
+      T rhs = rho * z - y - g;
+      if (kc == 2) rhs = rhs - mu * nt;
+      if (!act) rhs = T(0);
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < NC3; ++c) acc += Kr[c] * __shfl_sync(0xffffffffu, rhs, gb + c);
+      const T xn = acc;
+      s_rhs[lane] = rhs;
+      s_x[lane] = xn;
+      s_zold[lane] = z;
+      if (li == 0) { s_run[grp] = running ? 1 : 0; s_chk[grp] = chk ? 1 : 0; }
+      if (lane == 0) s_stop = 0;
+      const bool anychk = __any_sync(0xffffffffu, running && chk);
+      named_bar_arrive(kRhs, 64);
+      const T xh = relax * xn + (T(1) - relax) * z;
+      const T wv = xh + y * inv_rho;
+      T wc[3], pr[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) wc[r] = __shfl_sync(0xffffffffu, wv, gb + 3 * ci + r);
+      proj_cone_fast(wc, mu, inv1pmu2, pr);
+      const T zn = kc == 0 ? pr[0] : (kc == 1 ? pr[1] : pr[2]);
+      if (anychk) {
+        s_z[lane] = zn;
+        named_bar_arrive(kZ, 64);
+      }
+      if (running) {
+        x = xn;
+        z = zn;
+        y = y + rho * (xh - zn);
+        ++iters;
+        pend = chk;
+        if (iters >= a.admm_max_iter) running = false;
+      }
+    }
+    if (have) {
+      if (act) {
+        w.ax[li * B + e] = double(x);
+        w.az[li * B + e] = double(z);
+        w.ay[li * B + e] = double(y);
       }
       if (li == 0) {
         w.iters[e] = iters;
@@ -1789,6 +1990,14 @@ static __global__ void dcount_snapshot_kernel(int32_t* dcount) { dcount[1] = dco
 
 template <int NB, int NV, int NS, typename T>
 __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
+  // The overlapped finish can keep off some SMs, so that the few slow envs of the late ADMM rounds
+  // (launched meanwhile on the other stream) find whole SMs free and do not share an SM
+  // sub-partition's FP64 pipe with the finish's warps.  The test is uniform over the CTA.
+  if (a.fin_reserve > 0) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    if (smid % unsigned(a.fin_reserve) == 0) return;
+  }
   __shared__ DevModel sm;
   load_model(sm, a.model);
   // work item t handles env t % n, column chunk t / n (consecutive threads: consecutive envs); the
@@ -1797,13 +2006,28 @@ __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
   const int n = a.fhi ? *a.fhi - lo : a.n_env;
   if (n <= 0) return;
   const long long total = (long long)n * a.nchunk;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  auto item = [&](long long t) {
     const int chunk = int(t / n), ti = int(t - (long long)chunk * n);
     const int e = a.fhi ? a.ws.dlist[lo + ti] : (a.env_list ? a.env_list[ti] : ti);
-    if (a.model_id && a.model_id[e] != a.model_index) continue;
+    if (a.model_id && a.model_id[e] != a.model_index) return;
     finish_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
+  };
+  if (a.claim) {
+    // dynamic split (CTAs that returned above leave their share to the others): a warp claims 32
+    // consecutive items at a time
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(a.claim, 32);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if ((long long)base >= total) break;
+      if ((long long)base + lane < total) item((long long)base + lane);
+    }
+    return;
   }
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    item(t);
 }
 
 }  // namespace ds

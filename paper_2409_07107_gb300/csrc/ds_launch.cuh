@@ -38,7 +38,7 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   const int blocks = (a0.n_env + threads - 1) / threads;
   if (blocks <= 0) return;
   cudaMemsetAsync(a0.ws.counts, 0, sizeof(int32_t) * (DS_ROUNDS + 1), s);
-  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * (2 * DS_ROUNDS + 2), s);   // ncounts, fetch, dcount
+  cudaMemsetAsync(a0.ws.ncounts, 0, sizeof(int32_t) * (2 * DS_ROUNDS + 3), s);   // ncounts, fetch, dcount, claim
   ds_trace_mark(DS_STAGE_SETUP, 1, s);
   setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
   ds_trace_mark(DS_STAGE_SETUP, 0, s);
@@ -67,6 +67,18 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     wblocks = ds_sm_count() * wper;
     const int wneed = (a0.n_env + wenvs - 1) / wenvs;
     if (wblocks > wneed) wblocks = wneed;
+  }
+  // the two-warp ADMM kernel (FP64; 64-thread CTAs, 32 / L envs each) from the schedule's round
+  constexpr bool kPairOk = kWideOk && std::is_same<T, double>::value;
+  int pblocks = 1;
+  if constexpr (kPairOk) {
+    int pper = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, admm_round_pair_kernel<NS, T>, 64, 0);
+    if (pper <= 0) pper = 1;
+    const int penvs = 32 / WideShape<NS>::L;
+    pblocks = ds_sm_count() * pper;
+    const int pneed = (a0.n_env + penvs - 1) / penvs;
+    if (pblocks > pneed) pblocks = pneed;
   }
   // Newton stage: the cooperative kernel (4 NS lanes per env) where 4 NS divides the warp, else
   // one thread per env.
@@ -105,8 +117,14 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     a.round_cap = a.final_round ? (a0.admm_max_iter > caps[r] ? a0.admm_max_iter : caps[r]) : caps[r];
     ds_trace_mark(DS_STAGE_ADMM, 1, s);
     bool wide = false;
+    if constexpr (kPairOk) {
+      if (r >= sc.pair_from) { admm_round_pair_kernel<NS, T><<<pblocks, 64, 0, s>>>(a); wide = true; }
+    }
     if constexpr (kWideOk) {
-      if (r >= sc.wide_from) { admm_round_wide_kernel<NS, T><<<wblocks, threads, 0, s>>>(a); wide = true; }
+      if (!wide && r >= sc.wide_from) {
+        admm_round_wide_kernel<NS, T><<<wblocks, threads, 0, s>>>(a);
+        wide = true;
+      }
     }
     if (!wide) admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_ADMM, 0, s);
@@ -126,7 +144,16 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
       KArgs fa = af;
       fa.flo = nullptr;
       fa.fhi = a0.ws.dcount + 1;
-      const int fb = finish_blocks(a0.n_env, fa.nchunk, threads);
+      int fb = finish_blocks(a0.n_env, fa.nchunk, threads);
+      if (sc.reserve > 0) {
+        // one CTA per resident slot of every SM (those on reserved SMs return at once), items
+        // claimed dynamically, so the other SMs stay full until the work runs out
+        int fper = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, finish_kernel<NB, NV, NS, T>, threads, 0);
+        fb = ds_sm_count() * (fper > 0 ? fper : 1);
+        fa.fin_reserve = sc.reserve;
+        fa.claim = a0.ws.claim;
+      }
       ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
       finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
       ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);

@@ -273,7 +273,7 @@ def test_autotune_keeps_results(torch_cuda):
     sim = ds.Simulator(wl, precision="fp64")
     ref = {k: v.clone() for k, v in sim.step_jac().items()}
     desc = sim.autotune("jac")
-    assert 0 <= desc["index"] < 162
+    assert 0 <= desc["index"] < ds.NUM_SCHEDULES
     got = sim.step_jac()
     torch.cuda.synchronize()
     ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
@@ -302,3 +302,55 @@ def test_arm_cube_full_size_sampled(torch_cuda, precision, tol_v, tol_j):
     sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
     refs = run_oracle(sub, list(range(len(envs))))
     _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=30)
+
+
+@pytest.mark.parametrize("pair", [0, 1])
+def test_two_warp_admm_rounds(torch_cuda, pair):
+    """The two-warp ADMM kernel (x-step and projection on one warp, De Saxce term and convergence
+    test on the other) does each row's arithmetic of the row-per-lane kernel: with it from round 3
+    (or 5) and halved round caps, so that many envs pass through it, v+, the iteration counts and
+    the Jacobians agree with the default schedule's."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(3000)
+    sim = ds.Simulator(wl, precision="fp64")
+    sim.set_schedule(ds.schedule_index(pair=2))          # row-per-lane rounds only
+    ref = {k: v.clone() for k, v in sim.step_jac().items()}
+    desc = sim.set_schedule(ds.schedule_index(round_caps=1, pair=pair))
+    assert desc["two_warp_admm_from_round"] == (3, 5)[pair]
+    try:
+        got = sim.step_jac()
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
+    assert (got["iters"] == ref["iters"]).float().mean().item() >= 0.99
+    ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
+    scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
+    assert ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale)[ok].max().item() <= 1e-9
+    for key in ("dv_dq", "dv_dv", "dv_dtau"):
+        sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
+        assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[ok].max().item() <= 1e-8, key
+    assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
+
+
+@pytest.mark.parametrize("overlap,reserve", [(1, 1), (2, 2)])
+def test_overlapped_finish_on_reserved_sms(torch_cuda, overlap, reserve):
+    """The overlapped finish that keeps every 8th (4th) SM free claims its work items dynamically;
+    each env's finish is the same code on the same inputs, so every output is bitwise that of the
+    finish on every SM (the ADMM kernels are the same in both)."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(20000)
+    sim = ds.Simulator(wl, precision="fp64")
+    sim.set_schedule(ds.schedule_index(overlap=1, reserve=0))    # overlapped finish on every SM
+    ref = {k: v.clone() for k, v in sim.step_jac().items()}
+    desc = sim.set_schedule(ds.schedule_index(overlap=overlap, reserve=reserve))
+    assert desc["overlapped_finish_keeps_free_every_nth_sm"] == (None, 8, 4)[reserve]
+    try:
+        got = sim.step_jac()
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
+    for k in ("v_next", "q_next", "lambda", "modes", "status", "iters", "dv_dq", "dv_dv", "dv_dtau"):
+        if k in ref:
+            assert torch.equal(got[k], ref[k]), k
