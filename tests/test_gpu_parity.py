@@ -333,18 +333,20 @@ def test_two_warp_admm_rounds(torch_cuda, pair):
     assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
 
 
-@pytest.mark.parametrize("overlap,reserve", [(1, 1), (2, 2)])
-def test_overlapped_finish_on_reserved_sms(torch_cuda, overlap, reserve):
-    """The overlapped finish that keeps every 8th (4th) SM free claims its work items dynamically;
-    each env's finish is the same code on the same inputs, so every output is bitwise that of the
-    finish on every SM (the ADMM kernels are the same in both)."""
+@pytest.mark.parametrize("overlap,reserve,B,caps", [(1, 1, 20000, 0), (2, 2, 20000, 0), (1, 1, 600, 1)])
+def test_overlapped_finish_on_reserved_sms(torch_cuda, overlap, reserve, B, caps):
+    """The overlapped finish that keeps every 8th (4th) SM free claims its work items dynamically
+    (the small batch: a launch of a few items per SM).  Each env's finish is the same code on the
+    same inputs, so every output is bitwise that of the finish on every SM (the ADMM kernels are
+    the same in both)."""
     import paper_2409_07107_gb300 as ds
     torch = torch_cuda
-    wl = scenes.arm_cube(20000)
+    wl = scenes.arm_cube(B)
     sim = ds.Simulator(wl, precision="fp64")
-    sim.set_schedule(ds.schedule_index(overlap=1, reserve=0))    # overlapped finish on every SM
+    sim.set_schedule(ds.schedule_index(round_caps=caps, overlap=1, reserve=0))    # finish on every SM
     ref = {k: v.clone() for k, v in sim.step_jac().items()}
-    desc = sim.set_schedule(ds.schedule_index(overlap=overlap, reserve=reserve))
+    assert (ref["iters"] > 256).sum().item() >= 1          # some envs reach the late rounds
+    desc = sim.set_schedule(ds.schedule_index(round_caps=caps, overlap=overlap, reserve=reserve))
     assert desc["overlapped_finish_keeps_free_every_nth_sm"] == (None, 8, 4)[reserve]
     try:
         got = sim.step_jac()
