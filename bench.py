@@ -147,6 +147,7 @@ def bench_rollout(args, rank, world):
     tau0 = torch.tensor(rng.normal(size=(T, nv, B)) * 2.0, **dev) * mask
     q0, v0 = torch.tensor(wl.batch.q, **dev), torch.tensor(wl.batch.v, **dev)
     sc = R.StepContext(wl, precision="fp64")
+    schedule = None if args.no_autotune else sc.autotune(q0, v0, tau0[0].contiguous())
     with torch.no_grad():                                 # reachable goal: a perturbed-torque rollout
         goal, _ = R.rollout(sc, q0, v0, list(tau0 + torch.tensor(rng.normal(size=(T, nv, B)) * 0.5, **dev) * mask), 0)
 
@@ -197,7 +198,7 @@ def bench_rollout(args, rank, world):
             "clocks": r["clocks"], "peak_extra_mib": r["peak_extra_mib"],
             "no_recompute": {"value": res[0]["value"], "ms_per_step": res[0]["ms_per_rollout"],
                              "peak_extra_mib": res[0]["peak_extra_mib"]},
-            "gpu_launches": r["launches"]}
+            "gpu_launches": r["launches"], "schedule": schedule}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -16,8 +16,8 @@ and its tangent coordinates are library kernels too).  This module only marshals
 import torch
 import torch.utils.checkpoint
 
-from . import (DeviceModel, batch_to_device, cotangent_to_raw, cotangent_to_tangent, make_options, sim_step,
-               sim_step_vjp, sim_step_vjp_tape, workspace_size)
+from . import (DeviceModel, autotune, batch_to_device, cotangent_to_raw, cotangent_to_tangent, describe_schedule,
+               make_options, sim_step, sim_step_vjp, sim_step_vjp_tape, workspace_size)
 
 
 class StepContext:
@@ -55,6 +55,14 @@ class StepContext:
                    q_next=torch.empty(self.nq, self.B, dtype=torch.float64, device=self.device))
         sim_step(self.models, self._batch(q, v, tau), self.opt, out, self.workspace)
         return out["q_next"], out["v_next"], tape
+
+    def autotune(self, q, v, tau):
+        """Pick the pipeline schedule of this batch's forward step by timing (ds_autotune on
+        sim_step at the state (q, v, tau)); returns the chosen schedule's description."""
+        out = dict(self.scratch, v_next=torch.empty(self.nv, self.B, dtype=torch.float64, device=self.device),
+                   q_next=torch.empty(self.nq, self.B, dtype=torch.float64, device=self.device))
+        idx = autotune(self.models, self._batch(q, v, tau), self.opt, 0, out, workspace=self.workspace)
+        return dict(describe_schedule(idx), index=idx)
 
     def vjp(self, q, v, tau, q_next, q_next_bar_raw, v_next_bar, tape=None):
         """Cotangents of (q raw, v, tau) from those of (q+ raw, v+); with the forward step's tape,
