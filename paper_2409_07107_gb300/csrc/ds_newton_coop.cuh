@@ -29,7 +29,7 @@ struct Shape {
   static constexpr int EPW = 32 / L;          // envs per warp
   static constexpr int PS = NC3 | 1;          // odd row stride: rows of doubles hit distinct banks
   static constexpr int THREADS = NS >= 8 ? 64 : 128;
-  static constexpr int MINB = NS >= 8 ? 1 : 4;  // blocks per SM the register budget is sized for
+  static constexpr int MINB = NS >= 8 ? 1 : 5;  // blocks per SM the register budget is sized for
   static constexpr unsigned LMASK = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
 };
 
