@@ -251,7 +251,9 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * precision, mode, B rounded up to a power of two) and finally runs the call once more with it,
  * so that *out and o0..o2 hold its results.  Later calls with the same signature use that
  * schedule; other batches keep the default.  A schedule never changes what an env computes,
- * except that the two Newton forms round differently (results agree to the solver tolerance).
+ * except that the two Newton forms round differently, and so does the two-warp ADMM kernel's
+ * x-step (summed in two halves) for models of 2 or 4 contact slots (results agree to the solver
+ * tolerance).
  * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
  * the schedule's index (0 .. 1943), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 4 (p +
  * 3 r))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane round w (0: 3, 1: 5,

@@ -1651,7 +1651,11 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
 //       z, y and runs the x-step, the projection and the multiplier update; warp 1 (another
 //       sub-partition) keeps sx and forms the next iteration's De Saxce norm and the convergence
 //       test from what warp 0 leaves in shared memory, so those leave warp 0's instruction stream.
-//       The lane layout is the row-per-lane kernel's, and so is every row's arithmetic.  Named
+//       Where two lanes per row fit in the warp (up to 16 lanes per env, an even number of
+//       rows), warp 0 splits the x-step K * rhs: each of a row's two lanes sums half the columns
+//       and the row's value is low half + high half (the other per-row work is mirrored on both
+//       lanes), which shortens warp 0's FP64 stream by a third of the product; the x-step then
+//       rounds differently from the other forms (results agree to the solver tolerance).  Named
 //       barriers order the hand-offs (warp-uniform; 64 threads each):
 //         kDs  warp 1 arrives, warp 0 waits: the De Saxce norms of the coming iteration and the
 //              outcome of the previous iteration's convergence test are in place;
@@ -1659,7 +1663,7 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
 //              are in place (or the env loop ends: stop flag);
 //         kZ   warp 0 arrives, warp 1 waits, on test iterations only: the projected z is in place.
 //       A test's outcome reaches warp 0 at the top of the next iteration, before it decides to go
-//       on, so an env stops on the same iteration as in the other forms.
+//       on, so the stopping rule is the other forms'.
 __device__ __forceinline__ void named_bar_sync(int id, int threads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -1667,10 +1671,21 @@ __device__ __forceinline__ void named_bar_arrive(int id, int threads) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
+template <int NS>
+struct PairShape {
+  static constexpr int L = WideShape<NS>::L;                        // lanes per half-group
+  static constexpr int NC3 = 3 * NS;
+  static constexpr int H = (2 * L <= 32 && NC3 % 2 == 0) ? 2 : 1;   // halves of the x-step
+  static constexpr int LG = H * L;                                  // lanes per env
+  static constexpr int EPW = 32 / LG;                               // envs per warp
+  static constexpr int NH = NC3 / H;                                // columns of K per lane
+};
+
 template <int NS, typename T>
 __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
   static_assert(WideShape<NS>::kOk, "3 NS rows must fit in a warp");
-  constexpr int L = WideShape<NS>::L, EPW = 32 / L, NC3 = 3 * NS;
+  using PS = PairShape<NS>;
+  constexpr int L = PS::L, H = PS::H, LG = PS::LG, EPW = PS::EPW, NH = PS::NH, NC3 = 3 * NS;
   constexpr int kDs = 1, kRhs = 2, kZ = 3;
   __shared__ T s_rhs[32], s_x[32], s_z[32], s_zold[32], s_nt[32];
   __shared__ int s_run[EPW], s_chk[EPW], s_conv[EPW], s_stop;
@@ -1679,8 +1694,11 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
   const int B = a.B;
   const int role = threadIdx.x >> 5;          // 0: x-step / projection, 1: De Saxce term and test
   const int lane = threadIdx.x & 31;
-  const int grp = lane / L, li = lane - grp * L;
-  const int gb = grp * L;
+  // lane = env group grp, half h (H = 2: the x-step's columns split in two halves, each summed by
+  // its own lane of the row and the two partial sums added low + high; the other per-row work is
+  // mirrored on both halves), row li
+  const int grp = lane / LG, qi = lane - grp * LG, h = qi / L, li = qi - h * L;
+  const int gb = grp * LG, hb = gb + h * L;
   const int ci = li < NC3 ? li / 3 : NS - 1, kc = li < NC3 ? li - 3 * (li / 3) : 0;
   const int32_t* cur = w.list[a.round & 1];
   int32_t* next = w.list[(a.round + 1) & 1];
@@ -1698,12 +1716,12 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
     if (role == 1) {
       T sx = act ? T(w.asx[li * B + e]) : T(0);
       {
-        const T s0 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci);
-        const T s1 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci + 1);
+        const T s0 = __shfl_sync(0xffffffffu, sx, hb + 3 * ci);
+        const T s1 = __shfl_sync(0xffffffffu, sx, hb + 3 * ci + 1);
         T nt, inv;
         norm_and_inv(s0, s1, nt, inv);
         s_nt[lane] = nt;
-        if (li == 0) s_conv[grp] = 0;
+        if (qi == 0) s_conv[grp] = 0;
       }
       named_bar_arrive(kDs, 64);
       for (;;) {
@@ -1715,8 +1733,8 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
         for (int q = 0; q < EPW; ++q) anychk = anychk || (s_run[q] != 0 && s_chk[q] != 0);
         const T rhs = s_rhs[lane], xn = s_x[lane];
         if (run && kc < 2) sx = rhs - rho * xn + g;
-        const T s0 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci);
-        const T s1 = __shfl_sync(0xffffffffu, sx, gb + 3 * ci + 1);
+        const T s0 = __shfl_sync(0xffffffffu, sx, hb + 3 * ci);
+        const T s1 = __shfl_sync(0xffffffffu, sx, hb + 3 * ci + 1);
         T nt, inv;
         norm_and_inv(s0, s1, nt, inv);
         bool conv = false;
@@ -1736,15 +1754,15 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
           conv = run && chk && rp <= te * zmax && rd <= te * gs;
         }
         s_nt[lane] = nt;
-        if (li == 0) s_conv[grp] = conv ? 1 : 0;
+        if (qi == 0) s_conv[grp] = conv ? 1 : 0;
         named_bar_arrive(kDs, 64);
       }
-      if (have && act) w.asx[li * B + e] = double(sx);
+      if (have && act && h == 0) w.asx[li * B + e] = double(sx);
       continue;
     }
-    T Kr[NC3];
+    T Kr[NH];
 #pragma unroll
-    for (int c = 0; c < NC3; ++c) Kr[c] = act ? T(w.K[(li * NC3 + c) * B + e]) : T(0);
+    for (int j = 0; j < NH; ++j) Kr[j] = act ? T(w.K[(li * NC3 + h * NH + j) * B + e]) : T(0);
     T x = act ? T(w.ax[li * B + e]) : T(0);
     T z = act ? T(w.az[li * B + e]) : T(0);
     T y = act ? T(w.ay[li * B + e]) : T(0);
@@ -1771,12 +1789,16 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
       if (!act) rhs = T(0);
       T acc = T(0);
 #pragma unroll
-      for (int c = 0; c < NC3; ++c) acc += Kr[c] * __shfl_sync(0xffffffffu, rhs, gb + c);
-      const T xn = acc;
+      for (int j = 0; j < NH; ++j) acc += Kr[j] * __shfl_sync(0xffffffffu, rhs, gb + h * NH + j);
+      T xn = acc;
+      if constexpr (H == 2) {
+        const T other = __shfl_xor_sync(0xffffffffu, acc, L);
+        xn = h == 0 ? acc + other : other + acc;
+      }
       s_rhs[lane] = rhs;
       s_x[lane] = xn;
       s_zold[lane] = z;
-      if (li == 0) { s_run[grp] = running ? 1 : 0; s_chk[grp] = chk ? 1 : 0; }
+      if (qi == 0) { s_run[grp] = running ? 1 : 0; s_chk[grp] = chk ? 1 : 0; }
       if (lane == 0) s_stop = 0;
       const bool anychk = __any_sync(0xffffffffu, running && chk);
       named_bar_arrive(kRhs, 64);
@@ -1784,7 +1806,7 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
       const T wv = xh + y * inv_rho;
       T wc[3], pr[3];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) wc[r] = __shfl_sync(0xffffffffu, wv, gb + 3 * ci + r);
+      for (int r = 0; r < 3; ++r) wc[r] = __shfl_sync(0xffffffffu, wv, hb + 3 * ci + r);
       proj_cone_fast(wc, mu, inv1pmu2, pr);
       const T zn = kc == 0 ? pr[0] : (kc == 1 ? pr[1] : pr[2]);
       if (anychk) {
@@ -1801,12 +1823,12 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
       }
     }
     if (have) {
-      if (act) {
+      if (act && h == 0) {
         w.ax[li * B + e] = double(x);
         w.az[li * B + e] = double(z);
         w.ay[li * B + e] = double(y);
       }
-      if (li == 0) {
+      if (qi == 0) {
         w.iters[e] = iters;
         if (conv || iters >= a.admm_max_iter || a.final_round) {
           const int k = atomicAdd(&w.ncounts[a.round], 1);

@@ -75,7 +75,7 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     int pper = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, admm_round_pair_kernel<NS, T>, 64, 0);
     if (pper <= 0) pper = 1;
-    const int penvs = 32 / WideShape<NS>::L;
+    const int penvs = PairShape<NS>::EPW;
     pblocks = ds_sm_count() * pper;
     const int pneed = (a0.n_env + penvs - 1) / penvs;
     if (pblocks > pneed) pblocks = pneed;

@@ -307,9 +307,10 @@ def test_arm_cube_full_size_sampled(torch_cuda, precision, tol_v, tol_j):
 @pytest.mark.parametrize("pair", [0, 1])
 def test_two_warp_admm_rounds(torch_cuda, pair):
     """The two-warp ADMM kernel (x-step and projection on one warp, De Saxce term and convergence
-    test on the other) does each row's arithmetic of the row-per-lane kernel: with it from round 3
-    (or 5) and halved round caps, so that many envs pass through it, v+, the iteration counts and
-    the Jacobians agree with the default schedule's."""
+    test on the other; for the 4-slot arm the x-step summed in two halves, one lane each) runs the
+    row-per-lane kernel's iteration up to the rounding of that sum: with it from round 3 (or 5)
+    and halved round caps, so that many envs pass through it, v+, the iteration counts and the
+    Jacobians agree with those of the row-per-lane rounds."""
     import paper_2409_07107_gb300 as ds
     torch = torch_cuda
     wl = scenes.arm_cube(3000)
