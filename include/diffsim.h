@@ -244,7 +244,8 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * its warps, so the late rounds run faster on SMs the finish does not occupy).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
- * schedule by the median of five runs (CUDA events on `stream`, after an untimed run; before each
+ * schedule by the second slowest of five runs (so that a schedule whose step time varies from
+ * run to run is judged by its slow runs; CUDA events on `stream`, after an untimed run; before each
  * run the call writes a 256 MB scratch buffer of its own, allocated and freed by the call, so that
  * every run starts with a cold L2 as a step of a real loop does), in a
  * coordinate search from the default (each knob over its options with the others at the best so
