@@ -1897,55 +1897,6 @@ __global__ void __launch_bounds__(128) newton_kernel(KArgs a) {
     newton_env<NS, T>(a, a.ws.nlist[t]);
 }
 
-// Host-side emulation of one ADMM round for one env (the thread form of 2a; same arithmetic).
-template <int NS, typename T>
-DS_HD void admm_round_env(const KArgs& a, const int e) {
-  const WsView& w = a.ws;
-  const int B = a.B;
-  constexpr int NC3 = 3 * NS;
-  Ncp<NS, T> p;
-  p.na = w.na[e];
-  const int m = 3 * p.na;
-  for (int i = 0; i < p.na; ++i) p.mu[i] = w.mu[i * B + e];
-  for (int i = 0; i < NC3; ++i) p.gt[i] = i < m ? T(w.g[i * B + e]) : T(0);
-  Admm<NS, T> ad;
-  ad.m = m;
-  ad.rho = T(w.rho[e]);
-  ad.inv_rho = T(1) / ad.rho;
-  for (int i = 0; i < p.na; ++i) ad.inv1pmu2[i] = T(1) / (T(1) + T(p.mu[i]) * T(p.mu[i]));
-  ad.gs = T(1);
-  for (int i = 0; i < m; ++i) ad.gs = fmax(ad.gs, fabs(p.gt[i]));
-  for (int i = 0; i < NC3; ++i)
-    for (int j = 0; j < NC3; ++j) ad.K[i][j] = T(w.K[(i * NC3 + j) * B + e]);
-  for (int i = 0; i < m; ++i) {
-    ad.x[i] = T(w.ax[i * B + e]);
-    ad.z[i] = T(w.az[i * B + e]);
-    ad.y[i] = T(w.ay[i * B + e]);
-    ad.sx[i] = T(w.asx[i * B + e]);
-  }
-  int iters = w.iters[e];
-  const T te = T(stage_eps<T>(a, w.stage[e]));
-  bool conv = false;
-  for (int k = 0; k < a.round_cap && iters < a.admm_max_iter; ++k) {
-    ++iters;
-    if (ad.iterate(p, te, iters % DS_ADMM_CHECK == 0)) { conv = true; break; }
-  }
-  for (int i = 0; i < m; ++i) {
-    w.ax[i * B + e] = double(ad.x[i]);
-    w.az[i * B + e] = double(ad.z[i]);
-    w.ay[i * B + e] = double(ad.y[i]);
-    w.asx[i * B + e] = double(ad.sx[i]);
-  }
-  w.iters[e] = iters;
-  if (conv || iters >= a.admm_max_iter || a.final_round) {
-    const int k = ds_atomic_add(&w.ncounts[a.round], 1);
-    w.nlist[k] = e;
-  } else {
-    const int k = ds_atomic_add(&w.counts[a.round + 1], 1);
-    w.list[(a.round + 1) & 1][k] = e;
-  }
-}
-
 // 3. finish: F1-F6 again (recomputed, bitwise identical), then F9 and the derivatives with lambda
 //    and the modes from the workspace.
 template <int NB, int NV, int NS, typename T>
