@@ -52,6 +52,12 @@ def contact_points(model, q, env, slots):
     return pts
 
 
+def signed_distances(model, q, env, slots):
+    """phi_k = n . x_k - d - r_k of the given slots (= n . c_k - d with the contact point c_k)."""
+    n, d = env["plane"][:3], env["plane"][3]
+    return np.array([n @ c - d for c in contact_points(model, q, env, slots)])
+
+
 def contact_jacobian(model, q, env, slots):
     """J_c (3 nc x nv): rows (t1, t2, n) . (velocity of body point at c_k)."""
     _, world = fk(model, q)

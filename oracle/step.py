@@ -6,6 +6,11 @@ v+ = v + dt UFD(q, v, tau, lambda*) (ABA with the contact impulses as external f
 symplectic-Euler position update q+ = q (+) dt v+.  lambda is an impulse, so UFD's contact term is
 M^-1 J_c^T lambda / dt and G, g are exactly those of Eq. 4.
 
+Baumgarte stabilisation (App. D): with gains K_p, K_d (options baumgarte_kp, baumgarte_kd; the
+defaults K_p = 1, K_d = 0 leave g = J_c v_f for every active contact) the normal entry of g gains
+phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N, phi the contact's signed distance; sigma = G lambda + g is
+then J_c v+ plus that term, and its derivatives enter the right-hand side of the implicit solve.
+
 Derivatives (Sec. 3.1-3.3, App. B, D), w.r.t. a tangent perturbation q (+) dq of q and w.r.t. v, tau:
 
 * D = dv+/dtheta at fixed lambda* (the second term of Eq. 7, with the collision-detection term of
@@ -24,7 +29,7 @@ Derivatives (Sec. 3.1-3.3, App. B, D), w.r.t. a tangent perturbation q (+) dq of
 import numpy as np
 
 from . import rigid
-from .contact import active_slots, contact_jacobian, contact_wrenches
+from .contact import active_slots, contact_jacobian, contact_wrenches, signed_distances
 from .ncp import (BRK, SLD, STK, admm, classify, cs_jacobian, mode_residual, ncp_residual, solve_ncp)
 
 H_CS = 1e-30
@@ -41,6 +46,22 @@ def ufd_velocity(model, env, opt, slots, q, v, tau, lam):
     return v + dt * rigid.aba(model, q, v, tau, grav, fext)
 
 
+def baumgarte(model, env, opt, slots, q, v):
+    """The Baumgarte term of g (App. D): zero on the tangent rows, and on the normal row of each
+    active slot phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N with [x]_- = min(x, 0) (decided on the real
+    part, so that complex-step derivatives pass through)."""
+    kp, kd, dt = _opt(opt, "baumgarte_kp", 1.0), _opt(opt, "baumgarte_kd", 0.0), opt.dt
+    nc = len(slots)
+    if nc == 0:
+        return np.zeros(0)
+    phi = signed_distances(model, q, env, slots) / dt
+    neg = np.where(np.real(phi) < 0.0, phi, 0.0 * phi)
+    jv = contact_jacobian(model, q, env, slots) @ v
+    b = np.zeros(3 * nc, dtype=np.result_type(phi, jv))
+    b[2::3] = phi - kp * neg - kd * jv[2::3]
+    return b
+
+
 def step(model, env, opt, do_polish=True):
     """One step.  Returns a dict with v_next, q_next, lambda, modes, margin and internals."""
     q, v, tau = env["q"], env["v"], env["tau"]
@@ -53,7 +74,7 @@ def step(model, env, opt, do_polish=True):
     mu = np.array([env["c_mu"][k] for k in slots])
     Y = rigid.chol_solve(L, Jc.T) if len(slots) else np.zeros((len(v), 0))
     G = Jc @ Y
-    g = Jc @ v_f
+    g = Jc @ v_f + baumgarte(model, env, opt, slots, q, v)
     es, el = _opt(opt, "eps_sigma", 1e-8), _opt(opt, "eps_lambda", 1e-8)
     if do_polish:
         lam, iters, conv = solve_ncp(G, g, mu, es, el)
@@ -72,7 +93,7 @@ def partials(model, env, opt, st):
     q, v, tau = env["q"], env["v"], env["tau"]
     nv = len(v)
     slots, lam, v_next = st["slots"], st["lam"], st["v_next"]
-    Dq, Dv, Dt, F = [], [], [], []
+    Dq, Dv, Dt, F, Bq, Bv = [], [], [], [], [], []
     for j in range(nv):
         e = np.zeros(nv, dtype=complex)
         e[j] = 1j * H_CS
@@ -82,9 +103,14 @@ def partials(model, env, opt, st):
         Dt.append(np.imag(ufd_velocity(model, env, opt, slots, q, v, tau + e, lam)) / H_CS)
         if len(slots):
             F.append(np.imag(contact_jacobian(model, qj, env, slots) @ v_next) / H_CS)
+            Bq.append(np.imag(baumgarte(model, env, opt, slots, qj, v)) / H_CS)
+            Bv.append(np.imag(baumgarte(model, env, opt, slots, q, v + e)) / H_CS)
     D = np.concatenate([np.stack(Dq, 1), np.stack(Dv, 1), np.stack(Dt, 1)], axis=1)
     F = np.stack(F, 1) if len(slots) else np.zeros((0, nv))
-    return D, F
+    # d(Baumgarte term)/d(q, v, tau) (App. D): the extra right-hand side of the implicit solve
+    Bt = (np.concatenate([np.stack(Bq, 1), np.stack(Bv, 1), np.zeros((3 * len(slots), nv))], axis=1)
+          if len(slots) else np.zeros((0, 3 * nv)))
+    return D, F, Bt
 
 
 def sliding_basis(lam_i, sigma_i, mu_i):
@@ -136,15 +162,17 @@ def pinv_solve(A, Bm):
     return np.linalg.pinv(A, rcond=1e-12) @ Bm
 
 
-def jacobian_route1(model, env, opt, st, D=None, F=None):
+def jacobian_route1(model, env, opt, st, D=None, F=None, Bt=None):
     if D is None:
-        D, F = partials(model, env, opt, st)
+        D, F, Bt = partials(model, env, opt, st)
     nv = len(env["v"])
     if len(st["slots"]) == 0:
         return D, dict(D=D, F=F)
     A, Bm, C = route1_matrices(st["G"], st["g"], st["mu"], st["lam"], st["modes"])
     RHS = st["Jc"] @ D
     RHS[:, :nv] += F
+    if Bt is not None:
+        RHS = RHS + Bt
     X = -pinv_solve(A, Bm @ RHS)
     dlam = C @ X
     return D + st["Y"] @ dlam, dict(D=D, F=F, A=A, B=Bm, C=C, RHS=RHS, X=X, dlam=dlam)
@@ -155,14 +183,15 @@ def jacobian_route2(model, env, opt, st, D=None):
     q, v, tau = env["q"], env["v"], env["tau"]
     nv = len(v)
     if D is None:
-        D, _ = partials(model, env, opt, st)
+        D = partials(model, env, opt, st)[0]
     slots, lam, mu, modes = st["slots"], st["lam"], st["mu"], st["modes"]
     if len(slots) == 0:
         return D
 
     def E(lam_, q_, v_, tau_):
         vn = ufd_velocity(model, env, opt, slots, q_, v_, tau_, lam_)
-        return mode_residual(lam_, contact_jacobian(model, q_, env, slots) @ vn, mu, modes)
+        sigma = contact_jacobian(model, q_, env, slots) @ vn + baumgarte(model, env, opt, slots, q_, v_)
+        return mode_residual(lam_, sigma, mu, modes)
 
     E_lam = cs_jacobian(lambda x: E(x, q, v, tau), lam)
     cols = []
