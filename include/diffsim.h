@@ -122,6 +122,9 @@ typedef struct {
   double eps_lambda;         /* mode test: impulse threshold, relative                         */
   double margin_delta;       /* DS_ENV_NEAR_SWITCH below this classification margin             */
   int32_t precision;         /* ds_precision */
+  double baumgarte_kp;       /* Baumgarte stabilisation (App. D): each active contact's normal   */
+  double baumgarte_kd;       /* entry of g gains phi/dt - kp [phi/dt]_- - kd (J_c v)_N, phi its  */
+                             /* signed distance; kp = 1, kd = 0 (the defaults) add nothing     */
 } ds_options;
 
 /* Fill *opt with the defaults used by the tests and the benchmark. */

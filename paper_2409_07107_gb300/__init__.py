@@ -48,7 +48,8 @@ class ds_options(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("admm_max_iter", ctypes.c_int32),
                 ("admm_eps", ctypes.c_double), ("polish_iters", ctypes.c_int32), ("ncp_tol", ctypes.c_double),
                 ("eps_sigma", ctypes.c_double), ("eps_lambda", ctypes.c_double),
-                ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32)]
+                ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("baumgarte_kp", ctypes.c_double), ("baumgarte_kd", ctypes.c_double)]
 
 
 class ds_step_out(ctypes.Structure):

@@ -28,6 +28,8 @@ extern "C" void ds_options_default(ds_options* o) {
   o->eps_lambda = 1e-8;
   o->margin_delta = 1e-3;
   o->precision = DS_FP64;
+  o->baumgarte_kp = 1.0;
+  o->baumgarte_kd = 0.0;
 }
 
 extern "C" const char* ds_status_string(ds_status s) {
@@ -218,6 +220,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (!(o->dt > 0.0) || o->admm_max_iter < 1 || o->polish_iters < 0 || !(o->admm_eps > 0.0) || !(o->ncp_tol > 0.0))
     return DS_EINVAL;
   if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
+  if (!std::isfinite(o->baumgarte_kp) || !std::isfinite(o->baumgarte_kd)) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
   if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels) ||
@@ -237,6 +240,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.q = b->q; a.v = b->v; a.tau = b->tau;
   a.c_link = b->c_link; a.c_point = b->c_point; a.c_radius = b->c_radius; a.c_mu = b->c_mu; a.plane = b->plane;
   a.dt = o->dt; a.gx = o->gravity[0]; a.gy = o->gravity[1]; a.gz = o->gravity[2];
+  a.bkp = o->baumgarte_kp; a.bkd = o->baumgarte_kd;
   a.admm_max_iter = o->admm_max_iter; a.polish_iters = o->polish_iters;
   a.admm_eps = o->admm_eps; a.ncp_tol = o->ncp_tol;
   a.eps_sigma = o->eps_sigma; a.eps_lambda = o->eps_lambda; a.margin_delta = o->margin_delta;

@@ -133,6 +133,7 @@ struct KArgs {
   const int32_t* c_link;
   const double *c_point, *c_radius, *c_mu, *plane;
   double dt, gx, gy, gz;
+  double bkp, bkd;         // Baumgarte gains (App. D); 1, 0: no term
   int admm_max_iter, polish_iters;
   double admm_eps, ncp_tol, eps_sigma, eps_lambda, margin_delta;
   double *v_next, *q_next, *lambda;

@@ -103,6 +103,7 @@ struct Env : Ncp<NS, T> {
   int slot[NS], body[NS];
   T x[NS][3], c[NS][3], f[NS][3];            // body point, contact point, contact force (world)
   double cx_d[NS][3];                        // contact point in FP64
+  double phi[NS];                            // signed distance of the active contact (FP64)
   T fr[3][3];                                // contact frame rows t1, t2, n
   T Jc[NC3][NV];
   T Y[NC3][NV];                              // rows of M^-1 J_c^T
@@ -591,6 +592,40 @@ DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T 
   for (int r = 0; r < 3; ++r) out[r] = dot3(s.fr[r], dp);
 }
 
+// Baumgarte stabilisation (App. D): each active contact's normal entry of g gains
+// phi/dt - kp [phi/dt]_- - kd (J_c v)_N ([x]_- = min(x, 0)), in FP64; with kp = 1, kd = 0 the term
+// is identically zero and nothing is added.
+template <int NB, int NV, int NS, typename T>
+DS_HDI void baumgarte_g(const KArgs& a, const int e, const double (*Jd)[NV], Env<NB, NV, NS, T>& s) {
+  if (a.bkp == 1.0 && a.bkd == 0.0) return;
+  for (int ac = 0; ac < s.na; ++ac) {
+    const int r = 3 * ac + 2;
+    const double pr = s.phi[ac] / a.dt;
+    double jv = 0.0;
+    for (int k = 0; k < NV; ++k) jv += Jd[r][k] * a.v[k * a.B + e];
+    const double t = s.gd[r] + (pr - a.bkp * fmin(pr, 0.0) - a.bkd * jv);
+    s.gd[r] = t;
+    s.gt[r] = T(t);
+  }
+}
+
+// The Baumgarte term's derivative w.r.t. Jacobian column (blk, d) of contact ac (its normal row):
+// d/dq_d: (1 - kp)/dt dphi/dq_d - kd d(J_c v)_N/dq_d (dphi/dq_d = (J_c)_N,d for a body-fixed
+// contact point; the second term is the FKV derivative at v); d/dv_d: -kd (J_c)_N,d; d/dtau: 0.
+template <int NB, int NV, int NS, typename T>
+DS_HDI T baumgarte_d(const DevModel& m, const KArgs& a, const Env<NB, NV, NS, T>& s, int ac, int blk, int d) {
+  if ((a.bkp == 1.0 && a.bkd == 0.0) || blk == 2) return T(0);
+  const T jn = s.Jc[3 * ac + 2][d];
+  if (blk == 1) return -T(a.bkd) * jn;
+  T r = T((1.0 - a.bkp) / a.dt) * jn;
+  if (a.bkd != 0.0) {
+    T fk[3];
+    fkv_tangent<NB, NV, NS, T>(m, s, s.V, ac, d, fk);
+    r -= T(a.bkd) * fk[2];
+  }
+  return r;
+}
+
 // F1-F6 for env e: kinematics, dynamics, contact detection, J_c, G, g.  Returns status bits.
 template <int NB, int NV, int NS, typename T>
 DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s,
@@ -782,6 +817,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       s.slot[n] = k;
       s.body[n] = b;
       s.mu[n] = a.c_mu[k * B + e];
+      s.phi[n] = phi;
       for (int i = 0; i < 3; ++i) {
         s.x[n][i] = T(xw[i]);
         s.c[n][i] = T(xw[i] - r * pn[i]);
@@ -850,6 +886,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       s.gt[r] = T(t);
       s.gd[r] = t;
     }
+    baumgarte_g(a, e, Jd, s);
     if constexpr (!kD)
       for (int r = 0; r < mdim; ++r)
         for (int k = 0; k < NV; ++k) s.Jc[r][k] = T(Jd[r][k]);
@@ -874,6 +911,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     s.gt[r] = T(t);
     s.gd[r] = t;
   }
+  baumgarte_g(a, e, Jd, s);
   if constexpr (!kD)
     for (int r = 0; r < mdim; ++r)
       for (int k = 0; k < NV; ++k) { s.Jc[r][k] = T(Jd[r][k]); s.Y[r][k] = T(Yd[r][k]); }
@@ -1174,6 +1212,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           for (int ac = 0; ac < s.na; ++ac) {
             T fk[3] = {T(0), T(0), T(0)};
             if (sz[ac] != 0 && blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
+            if (sz[ac] != 0) fk[2] += baumgarte_d(m, a, s, ac, blk, d);
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
               if (sz[ac] != 0)
@@ -1193,6 +1232,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             double r3[3];
             T fk[3] = {T(0), T(0), T(0)};
             if (blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
+            fk[2] += baumgarte_d(m, a, s, ac, blk, d);
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
               for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * Dc[k];
@@ -1294,13 +1334,13 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           for (int k = 0; k < NV; ++k) r += dtau[k] * w2[k];
           r = -dt * r;
           if (blk == 1) r += ub[d];
-          if (blk == 0) {
-            for (int ac = 0; ac < s.na; ++ac) {
-              if (sz[ac] == 0) continue;
-              T fk[3];
-              fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
-              for (int rr = 0; rr < 3; ++rr) r -= fk[rr] * T(zeta[3 * ac + rr]);
-            }
+          const bool stab = !(a.bkp == 1.0 && a.bkd == 0.0);
+          for (int ac = 0; ac < s.na && (blk == 0 || stab); ++ac) {
+            if (sz[ac] == 0) continue;
+            T fk[3] = {T(0), T(0), T(0)};
+            if (blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
+            fk[2] += baumgarte_d(m, a, s, ac, blk, d);
+            for (int rr = 0; rr < 3; ++rr) r -= fk[rr] * T(zeta[3 * ac + rr]);
           }
           double* out = blk == 0 ? a.q_bar : a.v_bar;
           out[d * B + e] = (blk == 0 && a.qnbar) ? double(r) + qadd[d] : double(r);

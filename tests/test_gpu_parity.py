@@ -357,3 +357,44 @@ def test_overlapped_finish_on_reserved_sms(torch_cuda, overlap, reserve, B, caps
     for k in ("v_next", "q_next", "lambda", "modes", "status", "iters", "dv_dq", "dv_dv", "dv_dtau"):
         if k in ref:
             assert torch.equal(got[k], ref[k]), k
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+def test_baumgarte_stabilised_step(torch_cuda, precision, tol_v, tol_j):
+    """Baumgarte stabilisation (App. D) with gains K_p = 0.4, K_d = 0.2: v+, modes and the three
+    Jacobians against the oracle's stabilised step (its closed-form and finite-difference pins are
+    in test_oracle_baumgarte.py), and the VJP against the transposed Jacobian."""
+    import types
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(512)
+    o = wl.options
+    opt = types.SimpleNamespace(dt=o.dt, gravity=o.gravity, admm_max_iter=o.admm_max_iter, admm_eps=o.admm_eps,
+                                polish_iters=o.polish_iters, eps_sigma=o.eps_sigma, eps_lambda=o.eps_lambda,
+                                baumgarte_kp=0.4, baumgarte_kd=0.2)
+    sim = ds.Simulator(wl, precision=precision)
+    sim.opt.baumgarte_kp, sim.opt.baumgarte_kd = 0.4, 0.2
+    out = sim.step_jac()
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    envs = list(range(0, 512, 16))
+    refs = run_oracle(wl, envs, opt=opt)
+    _compare(wl, g, refs, envs, tol_v, tol_j, min_checked=8)
+    if precision == "fp64":
+        vbar = torch.randn(sim.nv, wl.batch.B, dtype=torch.float64, device="cuda")
+        r = sim.step_vjp(vbar)
+        torch.cuda.synchronize()
+        qb, vb, tb = r["q_bar"], r["v_bar"], r["tau_bar"]
+        ok = (out["status"] & 8) == 0
+        for J, got in ((out["dv_dq"], qb), (out["dv_dv"], vb), (out["dv_dtau"], tb)):
+            ref = torch.einsum("kjb,kb->jb", J, vbar)
+            err = ((got - ref).abs().amax(0) / ref.abs().amax(0).clamp_min(1e-6))[ok].max().item()
+            assert err <= 1e-9, err
+    # unit gains: the unstabilised step, bitwise
+    sim.opt.baumgarte_kp, sim.opt.baumgarte_kd = 1.0, 0.0
+    a1 = {k: v.clone() for k, v in sim.step_jac().items()}
+    sim2 = ds.Simulator(wl, precision=precision)
+    a2 = sim2.step_jac()
+    torch.cuda.synchronize()
+    for k in ("v_next", "dv_dq", "dv_dv", "dv_dtau"):
+        assert torch.equal(a1[k], a2[k]), k
