@@ -220,6 +220,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pipeline schedule")
+    ap.add_argument("--baumgarte", default=None, metavar="KP,KD",
+                    help="Baumgarte stabilisation gains (App. D); default: none (1,0)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -244,6 +246,11 @@ def main():
                       "v_bar ~ N(0, 1)"}[wl_name]
     cfg = {"workload": "%s: %s, %d envs per GPU, dt=1e-3" % (wl_name, desc, B),
            "envs_per_gpu": B, "l2": "flushed between timed steps (256 MiB write)"}
+    gains = {}
+    if args.baumgarte:
+        kp, kd = (float(x) for x in args.baumgarte.split(","))
+        gains = dict(baumgarte_kp=kp, baumgarte_kd=kd)
+        cfg["baumgarte"] = {"kp": kp, "kd": kd}
     make = {"arm7-cube": lambda n, r: scenes.arm_cube(n, seed=replicas.rank_seed(1001, r)),
             "humanoid36-feet": lambda n, r: scenes.humanoid_feet(n, seed=replicas.rank_seed(1002, r)),
             "quadruped18-feet": lambda n, r: scenes.quadruped_feet(n, seed=replicas.rank_seed(1004, r)),
@@ -297,7 +304,7 @@ def main():
         return sim.step_vjp(vbar) if vjp else sim.step_jac()
 
     for prec in ("fp64", "mixed"):
-        sim = ds.Simulator(wl, precision=prec)
+        sim = ds.Simulator(wl, precision=prec, **gains)
         stream = torch.cuda.current_stream()
         # pick the pipeline schedule for this batch (ds_autotune; untimed, part of the set-up)
         schedule = None
@@ -379,7 +386,7 @@ def main():
         del sim
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
-    sim = ds.Simulator(wl, precision="fp64")
+    sim = ds.Simulator(wl, precision="fp64", **gains)
     host_in = {k: v.cpu().pin_memory() for k, v in sim.batch.items() if k != "model_slots"}
     host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
                 for k, v in [("v_next", sim.out["v_next"]), ("q_next", sim.out["q_next"]), ("status", sim.out["status"])]}
