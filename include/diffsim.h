@@ -124,10 +124,13 @@ typedef struct {
   int32_t precision;         /* ds_precision */
   double baumgarte_kp;       /* Baumgarte stabilisation (App. D): each active contact's normal   */
   double baumgarte_kd;       /* entry of g gains phi/dt - kp [phi/dt]_- - kd (J_c v)_N, phi its  */
-                             /* signed distance; kp = 1, kd = 0 (the defaults) add nothing     */
+                             /* signed distance ([x]_- = min(x, 0)); the Jacobians and the VJP */
+                             /* include the term's derivatives.  kp = 1, kd = 0 (the defaults) */
+                             /* add nothing; non-finite gains: DS_EINVAL                       */
 } ds_options;
 
-/* Fill *opt with the defaults used by the tests and the benchmark. */
+/* Fill *opt with the defaults used by the tests and the benchmark (start from these and set the
+ * fields to change, so that fields added later keep their defaults). */
 void ds_options_default(ds_options* opt);
 
 typedef struct {
