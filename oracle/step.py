@@ -49,11 +49,11 @@ def ufd_velocity(model, env, opt, slots, q, v, tau, lam):
 def baumgarte(model, env, opt, slots, q, v):
     """The Baumgarte term of g (App. D): zero on the tangent rows, and on the normal row of each
     active slot phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N with [x]_- = min(x, 0) (decided on the real
-    part, so that complex-step derivatives pass through)."""
+    part, so that complex-step derivatives pass through).  Identically zero for K_p = 1, K_d = 0."""
     kp, kd, dt = _opt(opt, "baumgarte_kp", 1.0), _opt(opt, "baumgarte_kd", 0.0), opt.dt
     nc = len(slots)
-    if nc == 0:
-        return np.zeros(0)
+    if nc == 0 or (kp == 1.0 and kd == 0.0):
+        return np.zeros(3 * nc)
     phi = signed_distances(model, q, env, slots) / dt
     neg = np.where(np.real(phi) < 0.0, phi, 0.0 * phi)
     jv = contact_jacobian(model, q, env, slots) @ v
@@ -94,6 +94,7 @@ def partials(model, env, opt, st):
     nv = len(v)
     slots, lam, v_next = st["slots"], st["lam"], st["v_next"]
     Dq, Dv, Dt, F, Bq, Bv = [], [], [], [], [], []
+    stab = not (_opt(opt, "baumgarte_kp", 1.0) == 1.0 and _opt(opt, "baumgarte_kd", 0.0) == 0.0)
     for j in range(nv):
         e = np.zeros(nv, dtype=complex)
         e[j] = 1j * H_CS
@@ -103,13 +104,15 @@ def partials(model, env, opt, st):
         Dt.append(np.imag(ufd_velocity(model, env, opt, slots, q, v, tau + e, lam)) / H_CS)
         if len(slots):
             F.append(np.imag(contact_jacobian(model, qj, env, slots) @ v_next) / H_CS)
+        if len(slots) and stab:
             Bq.append(np.imag(baumgarte(model, env, opt, slots, qj, v)) / H_CS)
             Bv.append(np.imag(baumgarte(model, env, opt, slots, q, v + e)) / H_CS)
     D = np.concatenate([np.stack(Dq, 1), np.stack(Dv, 1), np.stack(Dt, 1)], axis=1)
     F = np.stack(F, 1) if len(slots) else np.zeros((0, nv))
     # d(Baumgarte term)/d(q, v, tau) (App. D): the extra right-hand side of the implicit solve
+    # (None with the unit gains, where the term is identically zero)
     Bt = (np.concatenate([np.stack(Bq, 1), np.stack(Bv, 1), np.zeros((3 * len(slots), nv))], axis=1)
-          if len(slots) else np.zeros((0, 3 * nv)))
+          if len(slots) and stab else None)
     return D, F, Bt
 
 
