@@ -103,6 +103,35 @@ def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
     return z.copy(), st.iters, conv, st
 
 
+def pgs(G, g, mu, eps=1e-12, max_iter=20000, lam0=None):
+    """Projected Gauss-Seidel on Eq. 1, the solver family the paper cites next to ADMM (Sec. 2.2):
+    sweeps over the contacts in order; contact i takes the fixed-point step of Eq. 1 restricted to
+    its own block, lambda_i <- Proj_K(lambda_i - (sigma_i + Gamma_i(sigma_i)) / r_i), with sigma
+    = G lambda + g at the current (partly updated) lambda and r_i the largest eigenvalue of the 3x3
+    diagonal block G_ii (the step that makes the local map non-expansive).  Its fixed points are
+    Eq. 1 by Moreau's decomposition, as for the ADMM iteration.  Stops when a sweep moves lambda by
+    at most eps max(1, ||lambda||_inf), or after max_iter sweeps.  Returns (lambda, sweeps,
+    converged)."""
+    m = len(g)
+    nc = len(mu)
+    lam = np.zeros(m) if lam0 is None else np.array(lam0, dtype=float)
+    if m == 0:
+        return lam, 0, True
+    r = [max(np.linalg.eigvalsh(G[3 * i:3 * i + 3, 3 * i:3 * i + 3]).max(), 1e-300) for i in range(nc)]
+    for it in range(1, max_iter + 1):
+        delta = 0.0
+        for i in range(nc):
+            b = slice(3 * i, 3 * i + 3)
+            si = G[b] @ lam + g[b]
+            wi = si + np.array([0.0, 0.0, mu[i] * np.sqrt(si[:2] @ si[:2])])
+            new = proj_cone(lam[b] - wi / r[i], mu[i])
+            delta = max(delta, np.max(np.abs(new - lam[b])))
+            lam[b] = new
+        if delta <= eps * max(1.0, np.max(np.abs(lam))):
+            return lam, it, True
+    return lam, max_iter, False
+
+
 def reclassify(G, g, mu, lam, modes, es, el, delta):
     """Active-set update after a Newton polish that did not give an NCP solution: a breaking
     contact that penetrates becomes sticking; a sticking or sliding contact that pulls
