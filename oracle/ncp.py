@@ -11,7 +11,8 @@ here is the standard one for this problem: an x-step that minimises
 z, a z-step that projects onto K_mu, and a dual ascent step on y.  At a fixed point x = z = lambda
 and y = -(sigma + Gamma(sigma)), and lambda = Proj_K(lambda - (sigma + Gamma)/rho), which by Moreau's
 decomposition is exactly Eq. 1.  It is followed by Newton steps on the equations of the identified
-contact modes (Sec. 3.2, App. A).
+contact modes (Sec. 3.2, App. A).  A projected Gauss-Seidel solve (pgs), the other solver family
+the paper cites, has the same fixed points and serves as the reference for a PGS variant.
 """
 import numpy as np
 
