@@ -260,6 +260,8 @@ def main():
         if rank != 0:
             return 0
         wl = make(B, 0)
+        for k, val in gains.items():                  # the oracle reads the same gains
+            setattr(wl.options, k, val)
         rate, procs, n, dt = cpu_oracle_rate(wl, seconds=max(5.0, 12.0 * args.steps / 20.0))
         line = {"impl": "reference", "metric": metric, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / rate, "higher_is_better": True,
@@ -281,6 +283,8 @@ def main():
     ds.lib()
     dev = torch.cuda.current_device()
     wl = make(B, rank)
+    for k, val in gains.items():                      # the oracle (cpu_baseline) reads the same gains
+        setattr(wl.options, k, val)
     peaks = _peaks()
 
     # measured CUDA-core FMA peaks (the path is bound by plain FP64 / FP32 arithmetic)
