@@ -329,7 +329,9 @@ def batch_to_device(batch, device="cuda"):
 
 
 class Simulator:
-    """Device-resident batch + outputs for one workload; thin wrapper over the three C-ABI calls."""
+    """Device-resident batch + outputs for one workload; thin wrapper over the three C-ABI calls.
+    Keyword options are ds_options fields (e.g. admm_max_iter, baumgarte_kp, baumgarte_kd); the
+    rest keep ds_options_default's values, dt and gravity come from the workload."""
 
     def __init__(self, workload, precision=None, device="cuda", pipeline=True, **opt):
         import torch
