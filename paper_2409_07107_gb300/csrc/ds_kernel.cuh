@@ -1694,7 +1694,7 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
 //       Where two lanes per row fit in the warp (up to 16 lanes per env, an even number of
 //       rows), warp 0 splits the x-step K * rhs: each of a row's two lanes sums half the columns
 //       and the row's value is low half + high half (the other per-row work is mirrored on both
-//       lanes), which shortens warp 0's FP64 stream by a third of the product; the x-step then
+//       lanes): 6 fused multiply-adds and one add instead of 12 for 4 slots; the x-step then
 //       rounds differently from the other forms (results agree to the solver tolerance).  Named
 //       barriers order the hand-offs (warp-uniform; 64 threads each):
 //         kDs  warp 1 arrives, warp 0 waits: the De Saxce norms of the coming iteration and the
