@@ -12,7 +12,14 @@ z, a z-step that projects onto K_mu, and a dual ascent step on y.  At a fixed po
 and y = -(sigma + Gamma(sigma)), and lambda = Proj_K(lambda - (sigma + Gamma)/rho), which by Moreau's
 decomposition is exactly Eq. 1.  It is followed by Newton steps on the equations of the identified
 contact modes (Sec. 3.2, App. A).  A projected Gauss-Seidel solve (pgs), the other solver family
-the paper cites, has the same fixed points and serves as the reference for a PGS variant.
+the paper cites, has the same fixed points; solve_ncp can take either one as its iteration, which
+gives the tests two independent routes to a solution of Eq. 1.
+
+The iteration's parameters are the plain textbook choices (penalty rho = the mean diagonal of G,
+no over-relaxation, stopping test on every iteration).  Eq. 1 can have several solutions (redundant
+contacts; and Coulomb friction's non-monotone De Saxce form); where the free motion already
+separates every active contact (g_N >= 0 for all of them) lambda = 0 is one of them, and it is the
+one taken: no impulse acts when nothing pushes into the plane.
 """
 import numpy as np
 
@@ -46,13 +53,13 @@ def proj_K(x, mu):
     return np.concatenate([proj_cone(x[3 * i:3 * i + 3], mu[i]) for i in range(len(mu))]) if len(mu) else x.copy()
 
 
-RHO_SCALE = 0.3      # rho = RHO_SCALE * mean diagonal of G
-RELAX = 1.6          # over-relaxation of the x-step
-CHECK_EVERY = 4      # the stopping test runs on every 4th iteration
+RHO_SCALE = 1.0      # rho = RHO_SCALE * mean diagonal of G
+RELAX = 1.0          # relaxation of the x-step (1: none)
+CHECK_EVERY = 1      # the stopping test runs on every CHECK_EVERY-th iteration
 
 
 def admm_rho(G):
-    """Penalty parameter: 0.3 x the mean diagonal of G (the scale of the Delassus operator)."""
+    """Penalty parameter: RHO_SCALE x the mean diagonal of G (the scale of the Delassus operator)."""
     m = G.shape[0]
     return max(RHO_SCALE * np.trace(G) / m, 1e-12)
 
@@ -68,13 +75,13 @@ class AdmmState:
 
 def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
     """ADMM iteration for Eq. 1 (reading stated in the module docstring): the De Saxce term is taken
-    at the most recent primal iterate x, and the x-step is over-relaxed,
+    at the most recent primal iterate x; with RELAX != 1 the x-step is relaxed,
     xh = RELAX x + (1 - RELAX) z, before the z-step and the dual step (the fixed points are
     unchanged).  G x is not recomputed: (G + rho I) x = rhs gives G x = rhs - rho x.  Stops when
     ||x - z||_inf <= eps max(1, ||z||_inf) and rho ||z - z_prev||_inf <= eps max(1, ||g||_inf), or
     when the state has done max_iter iterations in total; the test is evaluated when the cumulative
-    iteration count is a multiple of CHECK_EVERY (part of the reading of the unspecified stopping
-    rule).  Continues from ``state`` when given.  Returns (lambda, iterations, converged, state)."""
+    iteration count is a multiple of CHECK_EVERY.  Continues from ``state`` when given.
+    Returns (lambda, iterations, converged, state)."""
     m = len(g)
     st = state or AdmmState(m, g)
     if m == 0:
@@ -158,20 +165,37 @@ def reclassify(G, g, mu, lam, modes, es, el, delta):
     return new
 
 
+def separating(g):
+    """True when the free motion separates every active contact (g_N >= 0 for all): lambda = 0 then
+    satisfies Eq. 1 (sigma = g, and g + Gamma(g) = (g_T, g_N + mu ||g_T||) lies in the dual cone
+    exactly when g_N >= 0)."""
+    return len(g) > 0 and bool(np.all(np.asarray(g)[2::3] >= 0.0))
+
+
 def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4, 1e-6, 1e-9, 1e-12),
-              rounds=4, max_iter=50000):
-    """Staged solve of Eq. 1.  Each stage continues the ADMM iteration to a tolerance, identifies
-    the contact modes, and runs up to ``rounds`` active-set rounds of Newton on the mode equations
-    (reclassify + retry from the cone projection of the last iterate).  The first candidate whose
-    NCP residual is <= tol max(1, ||g||_inf) is accepted.  Returns (lambda, admm_iterations, converged)."""
+              rounds=4, max_iter=50000, route="admm"):
+    """Staged solve of Eq. 1.  When the free motion separates every contact the solution with no
+    impulse is returned (module docstring).  Otherwise each stage continues the iteration of the
+    route ("admm", or "pgs": projected Gauss-Seidel sweeps) to a tolerance, identifies the contact
+    modes, and runs up to ``rounds`` active-set rounds of Newton on the mode equations (reclassify +
+    retry from the cone projection of the last iterate).  The first candidate whose NCP residual is
+    <= tol max(1, ||g||_inf) is accepted.  Returns (lambda, iterations, converged)."""
     m = len(g)
     if m == 0:
         return np.zeros(0), 0, True
+    if separating(g):
+        return np.zeros(m), 0, True
     scale = max(1.0, np.max(np.abs(g)))
     best, best_r = None, np.inf
-    state = None
+    state, lam, iters = None, None, 0
     for eps in stages:
-        lam, it, _, state = admm(G, g, mu, eps=eps, max_iter=max_iter, state=state)
+        if route == "admm":
+            lam, iters, _, state = admm(G, g, mu, eps=eps, max_iter=max_iter, state=state)
+        elif route == "pgs":
+            lam, sweeps, _ = pgs(G, g, mu, eps=eps, max_iter=max(1, max_iter - iters), lam0=lam)
+            iters += sweeps
+        else:
+            raise ValueError(route)
         lscale = max(1.0, np.max(np.abs(lam)))
         es, el = max(eps_sigma, 10 * eps), max(eps_lambda, 10 * eps)
         modes, _ = classify(G, g, mu, lam, es, el)
@@ -194,10 +218,10 @@ def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4
             if r < best_r:
                 best, best_r = c, r
         if best_r <= tol * scale:
-            return best, state.iters, True
-        if state.iters >= max_iter:
+            return best, iters, True
+        if iters >= max_iter:
             break
-    return best, state.iters, False
+    return best, iters, False
 
 
 def ncp_residual(G, g, mu, lam):

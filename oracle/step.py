@@ -63,7 +63,8 @@ def baumgarte(model, env, opt, slots, q, v):
 
 
 def step(model, env, opt, do_polish=True):
-    """One step.  Returns a dict with v_next, q_next, lambda, modes, margin and internals."""
+    """One step.  Returns a dict with v_next, q_next, lambda, modes, margin and internals.  The NCP
+    iteration is ADMM, or projected Gauss-Seidel when the option ``ncp_route`` is "pgs"."""
     q, v, tau = env["q"], env["v"], env["tau"]
     dt, grav = opt.dt, np.asarray(opt.gravity, float)
     M = rigid.crba(model, q)
@@ -77,7 +78,7 @@ def step(model, env, opt, do_polish=True):
     g = Jc @ v_f + baumgarte(model, env, opt, slots, q, v)
     es, el = _opt(opt, "eps_sigma", 1e-8), _opt(opt, "eps_lambda", 1e-8)
     if do_polish:
-        lam, iters, conv = solve_ncp(G, g, mu, es, el)
+        lam, iters, conv = solve_ncp(G, g, mu, es, el, route=_opt(opt, "ncp_route", "admm"))
     else:
         lam, iters, conv, _ = admm(G, g, mu, eps=1e-12, max_iter=50000)
     modes, margin = classify(G, g, mu, lam, es, el)
