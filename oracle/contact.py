@@ -25,8 +25,9 @@ def tangent_basis(n):
     return t1, t2
 
 
-def active_slots(model, q, env):
-    """Indices of the active contact slots (phi <= 0), decided on the real part."""
+def active_slots(model, q, env, margin=0.0):
+    """Indices of the active contact slots, decided on the real part: phi <= margin (the activation
+    distance; 0 unless a margin is set, see step.py)."""
     _, world = fk(model, np.real(q))
     n, d = env["plane"][:3], env["plane"][3]
     out = []
@@ -36,7 +37,7 @@ def active_slots(model, q, env):
         R, p = world[b]
         x = p + R @ env["c_point"][k]
         phi = n @ x - d - env["c_radius"][k]
-        if phi <= 0.0:
+        if phi <= margin:
             out.append(k)
     return out
 

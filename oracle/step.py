@@ -7,9 +7,13 @@ symplectic-Euler position update q+ = q (+) dt v+.  lambda is an impulse, so UFD
 M^-1 J_c^T lambda / dt and G, g are exactly those of Eq. 4.
 
 Baumgarte stabilisation (App. D): with gains K_p, K_d (options baumgarte_kp, baumgarte_kd; the
-defaults K_p = 1, K_d = 0 leave g = J_c v_f for every active contact) the normal entry of g gains
-phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N, phi the contact's signed distance; sigma = G lambda + g is
-then J_c v+ plus that term, and its derivatives enter the right-hand side of the implicit solve.
+defaults K_p = 1, K_d = 0 leave g = J_c v_f for every contact with phi <= 0) the normal entry of g
+gains phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N, phi the contact's signed distance; sigma = G lambda +
+g is then J_c v+ plus that term, and its derivatives enter the right-hand side of the implicit
+solve.  Activation margin (option contact_margin, default 0): a slot is active when phi <= margin.
+App. D's term with [phi/dt]_- implies that a contact can be active at phi > 0; such a contact gains
+phi/dt - K_d (J_c v)_N (the proportional part acts on penetration only), so that sigma_N >= 0 lets
+it approach the plane by at most phi within the step.
 
 Derivatives (Sec. 3.1-3.3, App. B, D), w.r.t. a tangent perturbation q (+) dq of q and w.r.t. v, tau:
 
@@ -46,13 +50,20 @@ def ufd_velocity(model, env, opt, slots, q, v, tau, lam):
     return v + dt * rigid.aba(model, q, v, tau, grav, fext)
 
 
+def gap_term(opt):
+    """Whether g carries the signed-distance term: gains other than (1, 0), or an activation margin."""
+    return not (_opt(opt, "baumgarte_kp", 1.0) == 1.0 and _opt(opt, "baumgarte_kd", 0.0) == 0.0
+                and _opt(opt, "contact_margin", 0.0) == 0.0)
+
+
 def baumgarte(model, env, opt, slots, q, v):
     """The Baumgarte term of g (App. D): zero on the tangent rows, and on the normal row of each
     active slot phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N with [x]_- = min(x, 0) (decided on the real
-    part, so that complex-step derivatives pass through).  Identically zero for K_p = 1, K_d = 0."""
+    part, so that complex-step derivatives pass through).  Identically zero for K_p = 1, K_d = 0
+    when no margin is set (every active contact then has phi <= 0)."""
     kp, kd, dt = _opt(opt, "baumgarte_kp", 1.0), _opt(opt, "baumgarte_kd", 0.0), opt.dt
     nc = len(slots)
-    if nc == 0 or (kp == 1.0 and kd == 0.0):
+    if nc == 0 or not gap_term(opt):
         return np.zeros(3 * nc)
     phi = signed_distances(model, q, env, slots) / dt
     neg = np.where(np.real(phi) < 0.0, phi, 0.0 * phi)
@@ -70,7 +81,7 @@ def step(model, env, opt, do_polish=True):
     M = rigid.crba(model, q)
     L = rigid.cholesky(M)
     v_f = v + dt * rigid.aba(model, q, v, tau, grav)
-    slots = active_slots(model, q, env)
+    slots = active_slots(model, q, env, _opt(opt, "contact_margin", 0.0))
     Jc = contact_jacobian(model, q, env, slots)
     mu = np.array([env["c_mu"][k] for k in slots])
     Y = rigid.chol_solve(L, Jc.T) if len(slots) else np.zeros((len(v), 0))
@@ -95,7 +106,7 @@ def partials(model, env, opt, st):
     nv = len(v)
     slots, lam, v_next = st["slots"], st["lam"], st["v_next"]
     Dq, Dv, Dt, F, Bq, Bv = [], [], [], [], [], []
-    stab = not (_opt(opt, "baumgarte_kp", 1.0) == 1.0 and _opt(opt, "baumgarte_kd", 0.0) == 0.0)
+    stab = gap_term(opt)
     for j in range(nv):
         e = np.zeros(nv, dtype=complex)
         e[j] = 1j * H_CS
