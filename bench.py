@@ -91,36 +91,195 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------- algorithmic work model
+# Floating-point operations the method has to perform per env-step (an FMA counts 2), by stage, as
+# functions of the model's shape and of the env's contact state; the derivation and the per-item
+# counts are in the design notes.  It counts what the algorithm requires once (no recomputation,
+# no explicit inverse, dense Cholesky of M, one tangent pass per derivative column), so
+# (flops / time) / peak is the fraction of the CUDA-core roofline a stage reaches.
+C_FK_BODY, C_S_DOF, C_I_BODY, C_RNEA_BODY = 100, 24, 140, 270
+C_CRBA_DOF, C_CRBA_PAIR, C_CONTACT, C_JC_DOF, C_FKV_DOF = 72, 12, 24, 25, 30
+
+
+def _dof_depths(model):
+    """Number of dofs on the path from each body to the root (its own included), and the sum over
+    dofs of the number of ancestor dofs (the nonzero lower triangle of M)."""
+    w = np.array([6 if t == scenes.FREEFLYER else 1 for t in model.jtype])
+    depth = np.zeros(model.nb, np.int64)
+    for i in range(model.nb):
+        depth[i] = w[i] + (depth[model.parent[i]] if model.parent[i] >= 0 else 0)
+    pairs = 0
+    for i in range(model.nb):
+        base = depth[model.parent[i]] if model.parent[i] >= 0 else 0
+        for k in range(w[i]):
+            pairs += base + k + 1
+    return depth, pairs
+
+
+def algorithmic_flops(model, c_link, modes, iters, kind="jac", mixed=False):
+    """Per-stage (fp32, fp64) flop totals over the envs given by c_link / modes [nc][B] (mode 3 =
+    inactive slot) and ADMM iteration counts [B].  kind "jac": full Jacobians; "vjp": the VJP."""
+    nb, nv = model.nb, model.nv
+    depth, pairs = _dof_depths(model)
+    act = modes != 3
+    na = act.sum(0).astype(float)
+    nstk = (modes == 1).sum(0).astype(float)
+    nsld = (modes == 2).sum(0).astype(float)
+    m, mu = 3.0 * na, 3.0 * (nstk + nsld)
+    mr = 3.0 * nstk + 2.0 * nsld
+    cdep = np.where(act, depth[np.clip(c_link, 0, nb - 1)], 0).sum(0).astype(float)
+    solved = (na > 0) & (iters > 0)
+    B = modes.shape[1]
+    # setup: F1-F6 (kinematics, bias, M and its factor, contacts, J_c, M^-1 J_c^T, G, g), G + rho I factor
+    kin = (C_FK_BODY + C_I_BODY) * nb + C_S_DOF * nv + C_CONTACT * na + C_JC_DOF * cdep
+    bulk = C_RNEA_BODY * nb + 10 * nb + C_CRBA_DOF * nv + C_CRBA_PAIR * pairs + 2 * nv ** 3 / 3 + 2 * nv ** 2
+    dl = 6 * na * nv ** 2 + m * (m + 1) * nv + 2 * m * nv
+    setup64 = kin + dl + bulk * (not mixed) * np.ones(B)
+    setup32 = bulk * mixed * np.ones(B)
+    admm_f = np.where(solved, 2 * m ** 3 / 3, 0.0)
+    setup32, setup64 = (setup32 + admm_f, setup64) if mixed else (setup32, setup64 + admm_f)
+    admm = iters * (2 * m ** 2 + 30 * m)
+    # Newton polish on the identified modes: one step (factor + solve) and the residual check
+    newt_fac = np.where(solved, 2 * mu ** 3 / 3 + 2 * mu ** 2, 0.0)
+    newt_res = np.where(solved, 2 * m ** 2 + 30 * na, 0.0)
+    # finish: F9, then the derivatives (B1-B6) or the adjoint (B7)
+    f9 = 2 * nv * m + nv
+    if kind == "jac":
+        tang = 2 * nv * (C_RNEA_BODY * nb + 2 * nv ** 2) + nv * 2 * nv ** 2 + nv * C_FKV_DOF * na
+        red = 20 * mr ** 2 + 2 * mr ** 3 / 3 + 3 * nv * 2 * mr ** 2 + 18 * na * nv ** 2 + 18 * mr * nv
+        asm = 12 * na * nv + 18 * na * nv ** 2
+    else:
+        tang = 2 * C_RNEA_BODY * nb + 4 * nv ** 2 + nv * C_FKV_DOF * na
+        red = 20 * mr ** 2 + 2 * mr ** 3 / 3 + 2 * mr ** 2 + 12 * mr
+        asm = 12 * na * nv
+    fin_bulk = f9 + tang + asm
+    out = {"setup": (setup32, setup64),
+           "admm": (admm, 0.0 * admm) if mixed else (0.0 * admm, admm),
+           "newton": (newt_fac, newt_res) if mixed else (0.0 * newt_fac, newt_fac + newt_res),
+           "finish": (fin_bulk, red) if mixed else (0.0 * red, fin_bulk + red)}
+    return {k: (float(np.sum(a)), float(np.sum(b))) for k, (a, b) in out.items()}
+
+
+def stage_rooflines(flops, stage_ms, step_ms, peak32, peak64):
+    """Per stage and for the whole step: achieved TFLOP/s and the fraction of the roofline time
+    (F32 / peak32 + F64 / peak64) in the measured time."""
+    res = {}
+    tot32 = tot64 = 0.0
+    for k, (f32, f64) in flops.items():
+        tot32 += f32
+        tot64 += f64
+        t = stage_ms.get(k)
+        if not t:
+            continue
+        bound = (f32 / (peak32 * 1e12) + f64 / (peak64 * 1e12)) * 1e3
+        res[k] = {"gflop": (f32 + f64) / 1e9, "fp32_share": f32 / max(f32 + f64, 1.0),
+                  "achieved_tflops": (f32 + f64) / (t * 1e-3) / 1e12, "roofline_ms": bound, "frac": bound / t}
+    bound = (tot32 / (peak32 * 1e12) + tot64 / (peak64 * 1e12)) * 1e3
+    res["step"] = {"gflop": (tot32 + tot64) / 1e9, "achieved_tflops": (tot32 + tot64) / (step_ms * 1e-3) / 1e12,
+                   "roofline_ms": bound, "frac": bound / step_ms}
+    return res
+
+
 # ------------------------------------------------------------------------------------- CPU oracle
-def _oracle_one(args):
+def _model_of(wl, e):
+    return wl.models[0 if wl.batch.model_id is None else int(wl.batch.model_id[e])]
+
+
+def _oracle_rec(args):
+    """One env through the oracle: step + full Jacobian (the VJP of the uneven workload is a product
+    with it); returns what the error statistics need."""
     model, env, opt = args
     from oracle import step as S
-    S.step_jac(model, env, opt)     # the VJP of the uneven workload is a product with this Jacobian
-    return 1
+    st = S.step_jac(model, env, opt)
+    return {k: st[k] for k in ("v_next", "modes", "margin", "slots", "dv_dq", "dv_dv", "dv_dtau")}
 
 
-def cpu_oracle_rate(wl, n_envs=None, seconds=20.0, processes=None):
-    """Oracle env-steps/s (step + full Jacobian) on the host cores, on a bounded sample."""
+def cpu_model_name():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_single_thread(wl, seconds=3.0, max_envs=64):
+    """Microseconds per env-step (step + full Jacobian) of the oracle on one core, envs in order."""
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_envs and (n < 2 or time.perf_counter() - t0 < seconds):
+        m = _model_of(wl, n)
+        _oracle_rec((m, wl.batch.env(n, m), wl.options))
+        n += 1
+    return 1e6 * (time.perf_counter() - t0) / n, n
+
+
+def oracle_sample(wl, seconds=15.0, cap=1024, processes=None):
+    """The oracle on the first n envs of the workload (n: what the host cores do in about
+    `seconds`, at most `cap`), in a spawn-started pool.  Returns (records, seconds, cores)."""
     import multiprocessing as mp
     procs = processes or os.cpu_count() or 1
-
-    def model_of(e):
-        return wl.models[0 if wl.batch.model_id is None else int(wl.batch.model_id[e])]
-
-    if n_envs is None:
+    t0 = time.perf_counter()
+    k = min(len(wl.models), wl.batch.B)
+    for e in range(k):
+        _oracle_rec((_model_of(wl, e), wl.batch.env(e, _model_of(wl, e)), wl.options))
+    per = max((time.perf_counter() - t0) / k, 1e-3)
+    n = int(max(procs, min(wl.batch.B, cap, seconds * procs / per)))
+    args = [(_model_of(wl, e), wl.batch.env(e, _model_of(wl, e)), wl.options) for e in range(n)]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_rec, args[:procs])        # warm the workers
         t0 = time.perf_counter()
-        for e in range(len(wl.models)):
-            _oracle_one((model_of(e), wl.batch.env(e, model_of(e)), wl.options))
-        per = max((time.perf_counter() - t0) / len(wl.models), 1e-3)
-        n_envs = int(max(procs, min(wl.batch.B, seconds * procs / per)))
-    args = [(model_of(e), wl.batch.env(e, model_of(e)), wl.options) for e in range(n_envs)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        pool.map(_oracle_one, args[:procs])        # warm the workers
-        t0 = time.perf_counter()
-        pool.map(_oracle_one, args, chunksize=max(1, n_envs // (4 * procs)))
+        recs = pool.map(_oracle_rec, args, chunksize=max(1, n // (4 * procs)))
         dt = time.perf_counter() - t0
-    return n_envs / dt, procs, n_envs, dt
+    return recs, dt, procs
+
+
+def _rel(x, ref, floor=1e-6):
+    x, ref = np.asarray(x, float), np.asarray(ref, float)
+    return float(np.max(np.abs(x - ref)) / max(float(np.max(np.abs(ref))) if ref.size else 0.0, floor)) if ref.size else 0.0
+
+
+def error_stats(wl, snap, recs, vbar=None, delta=1e-3):
+    """Per-env relative error (||x - x_ref||_inf / max(||x_ref||_inf, 1e-6)) of v+ and of each
+    Jacobian (or each VJP output) against the FP64 oracle, on the envs the oracle ran: max, p99
+    and median; Jacobians, VJPs and modes on envs whose oracle classification margin is >= delta;
+    counts of mode disagreements, of envs near a mode switch (oracle margin < delta) and of envs
+    whose v+ differs from the oracle's by more than 1e-6 (another solution of Eq. 1, or an error)."""
+    keys = ("q_bar", "v_bar", "tau_bar") if vbar is not None else ("dv_dq", "dv_dv", "dv_dtau")
+    err = {k: [] for k in ("v_next",) + keys}
+    mode_dis = near = far = 0
+    for e, r in enumerate(recs):
+        nv = _model_of(wl, e).nv
+        ev = _rel(snap["v_next"][:nv, e], r["v_next"])
+        err["v_next"].append(ev)
+        far += ev > 1e-6
+        if r["margin"] < delta:
+            near += 1
+            continue
+        if [int(snap["modes"][k, e]) for k in r["slots"]] != [int(x) for x in r["modes"]]:
+            mode_dis += 1
+            continue
+        for k, jk in zip(keys, ("dv_dq", "dv_dv", "dv_dtau")):
+            if vbar is None:
+                err[k].append(_rel(snap[k][:nv, :nv, e], r[jk]))
+            else:
+                err[k].append(_rel(snap[k][:nv, e], r[jk].T @ vbar[:nv, e]))
+
+    def q(v):
+        return ({"max": float(np.max(v)), "p99": float(np.percentile(v, 99)), "median": float(np.median(v)),
+                 "envs": len(v)} if len(v) else None)
+    return dict({k: q(v) for k, v in err.items()}, envs=len(recs), mode_disagreements=mode_dis,
+                near_switch=near, v_next_off_by_1e6=int(far))
 
 
 # -------------------------------------------------------------------------------------- rollout
@@ -206,6 +365,47 @@ def bench_rollout(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------------------------- reference arm
+def _oracle_count(args):
+    _oracle_rec(args)
+    return 1
+
+
+def reference_arm(args, wl, gains, metric, cfg, B):
+    """The FP64 oracle on the host cores: W + K steps, each a bounded sample of the workload (the
+    next consecutive envs, as many as the cores do in about 0.6 s), timed one by one."""
+    import multiprocessing as mp
+    for k, val in gains.items():                  # the oracle reads the same gains
+        setattr(wl.options, k, val)
+    procs = os.cpu_count() or 1
+    per, _ = oracle_single_thread(wl, seconds=1.0, max_envs=4)
+    n = int(max(procs, min(B // max(1, args.steps + args.warmup), 0.6 * procs / (per * 1e-6))))
+    times = []
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_count, [(_model_of(wl, e), wl.batch.env(e, _model_of(wl, e)), wl.options)
+                                 for e in range(procs)])
+        for i in range(args.warmup + args.steps):
+            lo = (i * n) % max(1, B - n + 1)
+            chunk = [(_model_of(wl, e), wl.batch.env(e, _model_of(wl, e)), wl.options) for e in range(lo, lo + n)]
+            t0 = time.perf_counter()
+            pool.map(_oracle_count, chunk, chunksize=max(1, n // (4 * procs)))
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t0)
+    sec = float(np.mean(times))
+    rate = n / sec
+    c = dict(cfg, reference_step="%d consecutive envs of the %d-env workload per step (the oracle's "
+                                  "bounded sample), step + full Jacobian" % (n, B))
+    line = {"impl": "reference", "metric": metric, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": c,
+            "cpu_baseline": {"value": rate, "unit": "env-steps/s", "cores": procs, "kind": "oracle",
+                             "cpu_model": cpu_model_name(),
+                             "sample": "%d steps of %d envs each, %.2f s per step" % (args.steps, n, sec)},
+            "e2e": {"value": rate, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -259,18 +459,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        wl = make(B, 0)
-        for k, val in gains.items():                  # the oracle reads the same gains
-            setattr(wl.options, k, val)
-        rate, procs, n, dt = cpu_oracle_rate(wl, seconds=max(5.0, 12.0 * args.steps / 20.0))
-        line = {"impl": "reference", "metric": metric, "value": rate, "unit": "env-steps/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / rate, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-                "cpu_baseline": {"value": rate, "unit": "env-steps/s", "cores": procs, "kind": "oracle",
-                                 "sample": "first %d envs of the workload, step + full Jacobian, %.1f s" % (n, dt)},
-                "e2e": {"value": rate, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return 0
+        return reference_arm(args, make(B, 0), gains, metric, cfg, B)
 
     import torch
     import paper_2409_07107_gb300 as ds
@@ -300,7 +489,7 @@ def main():
         fma["fp64" if fp64 else "fp32"] = 2 * 8 * iters * 152 * 16 * 256 / (e0.elapsed_time(e1) * 1e-3) / 1e12
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    results = {}
+    results, snaps = {}, {}
     vbar = torch.as_tensor(np.random.default_rng(17 + rank).normal(size=wl.batch.v.shape), dtype=torch.float64,
                            device="cuda")
 
@@ -336,7 +525,7 @@ def main():
         ds.profile_read()
         for _ in range(traced):
             flush.fill_(1.0)
-            one_step(sim)
+            one_out = one_step(sim)
         torch.cuda.synchronize()
         stages = ds.profile_read()
         ds.profile(False)
@@ -368,6 +557,23 @@ def main():
         peak = fma["fp64"] if prec == "fp64" else fma["fp32"]
         achieved = admm_flops / (t_admm * 1e-3) / 1e12
         dominant = max(stage_ms, key=stage_ms.get) if stage_ms else None
+        # algorithmic work of every stage (per model, summed) and the rooflines of stages and step
+        kind = "vjp" if vjp else "jac"
+        fl = {}
+        c_link = wl.batch.c_link
+        for mi, mdl in enumerate(wl.models):
+            sel = slice(None) if wl.batch.model_id is None else (wl.batch.model_id == mi)
+            part = algorithmic_flops(mdl, c_link[:, sel], modes[:, sel], iters[sel], kind, mixed=(prec == "mixed"))
+            for k, (a32, a64) in part.items():
+                b32, b64 = fl.get(k, (0.0, 0.0))
+                fl[k] = (a32 + b32, a64 + b64)
+        roof_stages = stage_rooflines(fl, stage_ms, ms, fma["fp32"], fma["fp64"])
+        # contact-mode pattern of every env (sorted modes of its active contacts)
+        pat = {}
+        for e in range(modes.shape[1]):
+            key = "".join("bks"[int(x)] for x in sorted(modes[:, e]) if x != 3) or "-"
+            pat[key] = pat.get(key, 0) + 1
+        snaps[prec] = {k: v[..., :1024].cpu().numpy() for k, v in one_out.items()}
         results[prec] = dict(
             ms=ms, value=replicas.job_throughput(B, world, ms), clocks=clk.summary(), schedule=schedule,
             graph={"value": B * world / (float(np.mean(gtimes)) * 1e-3), "ms_per_step": float(np.mean(gtimes))},
@@ -379,6 +585,8 @@ def main():
                       "launches_per_step": stage_launches.get("admm"),
                       "avg_launch_ms": t_admm / max(stage_launches.get("admm", 1), 1)},
             stages={k: {"ms_per_step": v, "share": v / ms, "launches_per_step": stage_launches[k]} for k, v in stage_ms.items()},
+            stage_roofline=roof_stages,
+            mode_patterns=dict(sorted(pat.items(), key=lambda kv: -kv[1])),
             dominant_stage=dominant,
             admm_iters={"mean": float(iters.mean()), "p50": float(np.median(iters)),
                         "p99": float(np.percentile(iters, 99)), "max": int(iters.max())},
@@ -423,11 +631,18 @@ def main():
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_value = replicas.job_throughput(B, world, replicas.slowest_ms(float(np.mean(e2e_ms))))
 
-    cpu = None
+    # the FP64 oracle on the host cores: the CPU baseline, and the error of both GPU forms against it
+    cpu, errors = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, procs, n, dt = cpu_oracle_rate(wl, seconds=args.cpu_seconds)
-        cpu = {"value": rate, "unit": "env-steps/s", "cores": procs, "kind": "oracle",
-               "sample": "first %d envs of the workload, step + full Jacobian (numpy oracle, spawn pool), %.1f s" % (n, dt)}
+        recs, dt, procs = oracle_sample(wl, seconds=args.cpu_seconds)
+        us1, n1 = oracle_single_thread(wl)
+        cpu = {"value": len(recs) / dt, "unit": "env-steps/s", "cores": procs, "kind": "oracle",
+               "cpu_model": cpu_model_name(),
+               "sample": "first %d envs of the workload, step + full Jacobian (numpy oracle, spawn pool), %.1f s"
+                         % (len(recs), dt),
+               "single_thread_us_per_env_step": us1, "single_thread_sample": "first %d envs, one core" % n1}
+        vb = vbar.cpu().numpy() if vjp else None
+        errors = {prec: error_stats(wl, snaps[prec], recs, vb) for prec in ("fp64", "mixed")}
 
     if rank == 0:
         r64, rmx = results["fp64"], results["mixed"]
@@ -444,11 +659,17 @@ def main():
                                "overlaps the late ADMM rounds on a second stream, so stages can sum past the step",
                 "schedule": r64["schedule"],
                 "admm_iters": r64["admm_iters"], "modes": r64["modes"], "env_status": r64["status"],
+                "mode_patterns": r64["mode_patterns"],
+                "mode_patterns_note": "envs by the sorted modes of their active contacts (b breaking, k sticking, "
+                                      "s sliding; - no contact)",
+                "stage_roofline": r64["stage_roofline"],
+                "error_vs_fp64_oracle": None if errors is None else errors["fp64"],
                 "mixed": {"value": rmx["value"], "ms_per_step": rmx["ms"], "dtype": "f32+f64", "roofline": rmx["roofline"],
                           "cuda_graph_replay": rmx["graph"], "schedule": rmx["schedule"],
                           "stages": rmx["stages"], "dominant_stage": rmx["dominant_stage"],
                           "clocks": rmx["clocks"], "admm_iters": rmx["admm_iters"], "modes": rmx["modes"],
-                          "env_status": rmx["status"]},
+                          "env_status": rmx["status"], "stage_roofline": rmx["stage_roofline"],
+                          "error_vs_fp64_oracle": None if errors is None else errors["mixed"]},
                 "fma_peak_tflops": fma, "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
         print(json.dumps(line), flush=True)
     if world > 1:

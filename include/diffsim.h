@@ -126,7 +126,12 @@ typedef struct {
   double baumgarte_kd;       /* entry of g gains phi/dt - kp [phi/dt]_- - kd (J_c v)_N, phi its  */
                              /* signed distance ([x]_- = min(x, 0)); the Jacobians and the VJP */
                              /* include the term's derivatives.  kp = 1, kd = 0 (the defaults) */
-                             /* add nothing; non-finite gains: DS_EINVAL                       */
+                             /* add nothing when contact_margin = 0; non-finite gains: DS_EINVAL */
+  double contact_margin;     /* activation distance: a slot is active when phi <= contact_margin */
+                             /* (>= 0, default 0).  A contact active at phi > 0 gains phi/dt -   */
+                             /* kd (J_c v)_N in g (the term above; the proportional part acts  */
+                             /* on penetration only), so it may approach the plane by at most   */
+                             /* phi within the step.  Negative or non-finite: DS_EINVAL         */
 } ds_options;
 
 /* Fill *opt with the defaults used by the tests and the benchmark (start from these and set the
@@ -247,7 +252,12 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * (FP64 with at most 10 contact slots: one warp runs the x-step and projection, the other the De
  * Saxce term and convergence test; 3, 5 or never), and which SMs that overlapped finish leaves to
  * the slow envs (none, every 8th or every 4th: the FP64 pipe of an SM sub-partition is shared by
- * its warps, so the late rounds run faster on SMs the finish does not occupy).
+ * its warps, so the late rounds run faster on SMs the finish does not occupy), and the round from
+ * whose end on the Newton / active-set stage also tries the iterate of every env still iterating,
+ * not only of those whose ADMM stage tolerance was met, with a fallback that enumerates the
+ * contact-mode patterns with one or two contacts in contact when the active-set rounds fail
+ * (speculative attempts from round 3, from round 5, or never; an env whose attempt fails keeps
+ * iterating in the same stage).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
  * schedule by the second slowest of five runs (so that a schedule whose step time varies from
@@ -259,17 +269,20 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * fastest for the batch's signature (first model's bodies and dofs, number of models, ncmax,
  * precision, mode, B rounded up to a power of two) and finally runs the call once more with it,
  * so that *out and o0..o2 hold its results.  Later calls with the same signature use that
- * schedule; other batches keep the default.  A schedule never changes what an env computes,
- * except that the two Newton forms round differently, and so does the two-warp ADMM kernel's
- * x-step (summed in two halves) for models of 2 or 4 contact slots (results agree to the solver
- * tolerance).
+ * schedule; other batches keep the default.  A schedule changes how the work is divided, and what
+ * an env computes only within the solver tolerance: the two Newton forms round differently, so
+ * does the two-warp ADMM kernel's x-step (summed in two halves) for models of 2 or 4 contact
+ * slots, and the round caps and speculative attempts decide at which iterates the Newton stage
+ * runs (every accepted impulse passes the same NCP residual test; where Eq. 1 has several
+ * solutions, two schedules can return different ones).
  * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
- * the schedule's index (0 .. 1943), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 4 (p +
- * 3 r))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane round w (0: 3, 1: 5,
- * 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0 cooperative, 1 one
- * thread per env), overlapped finish o (0: after round 2, 1: after round 4, 2: after round 5, 3:
- * never), two-warp ADMM p (0: from round 3, 1: from round 5, 2: never), SMs kept free r (0: none,
- * 1: every 8th, 2: every 4th).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
+ * the schedule's index (0 .. 5831), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 4 (p +
+ * 3 (r + 3 s)))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane round w (0:
+ * 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0 cooperative,
+ * 1 one thread per env), overlapped finish o (0: after round 2, 1: after round 4, 2: after round
+ * 5, 3: never), two-warp ADMM p (0: from round 3, 1: from round 5, 2: never), SMs kept free r (0:
+ * none, 1: every 8th, 2: every 4th), speculative Newton attempts s (0: from round 3, 1: from
+ * round 5, 2: never).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
                       double* o0, double* o1, double* o2, void* workspace, size_t workspace_bytes,
@@ -278,7 +291,7 @@ ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_b
 /* Sets the schedule (index as ds_autotune's *chosen) that later calls of `mode` use for batches
  * with this batch's signature, as if ds_autotune had chosen it; index -1 returns the signature to
  * the default schedule (no counterpart in the paper).  For reusing a tuned schedule without timing
- * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 1943). */
+ * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 5831). */
 ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                           const ds_options* opt, int32_t mode, int32_t index);
 

@@ -49,7 +49,8 @@ class ds_options(ctypes.Structure):
                 ("admm_eps", ctypes.c_double), ("polish_iters", ctypes.c_int32), ("ncp_tol", ctypes.c_double),
                 ("eps_sigma", ctypes.c_double), ("eps_lambda", ctypes.c_double),
                 ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("baumgarte_kp", ctypes.c_double), ("baumgarte_kd", ctypes.c_double)]
+                ("baumgarte_kp", ctypes.c_double), ("baumgarte_kd", ctypes.c_double),
+                ("contact_margin", ctypes.c_double)]
 
 
 class ds_step_out(ctypes.Structure):
@@ -239,8 +240,9 @@ SCHEDULE_KNOBS = (
     ("overlapped_finish_after_round", (2, 4, 5, None)),
     ("two_warp_admm_from_round", (3, 5, None)),
     ("overlapped_finish_keeps_free_every_nth_sm", (None, 8, 4)),
+    ("speculative_newton_from_round", (3, 5, None)),
 )
-NUM_SCHEDULES = 1944
+NUM_SCHEDULES = 5832
 
 
 def describe_schedule(index):
@@ -252,11 +254,11 @@ def describe_schedule(index):
     return d
 
 
-def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1):
+def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1, spec=0):
     """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
     defaults give the library's default schedule."""
     idx, mul = 0, 1
-    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve), SCHEDULE_KNOBS):
+    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec), SCHEDULE_KNOBS):
         assert 0 <= pos < len(opts)
         idx += pos * mul
         mul *= len(opts)

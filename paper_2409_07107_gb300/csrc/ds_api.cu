@@ -30,6 +30,7 @@ extern "C" void ds_options_default(ds_options* o) {
   o->precision = DS_FP64;
   o->baumgarte_kp = 1.0;
   o->baumgarte_kd = 0.0;
+  o->contact_margin = 0.0;
 }
 
 extern "C" const char* ds_status_string(ds_status s) {
@@ -179,7 +180,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, 3};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -221,6 +222,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
     return DS_EINVAL;
   if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
   if (!std::isfinite(o->baumgarte_kp) || !std::isfinite(o->baumgarte_kd)) return DS_EINVAL;
+  if (!(o->contact_margin >= 0.0) || !std::isfinite(o->contact_margin)) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
   if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels) ||
@@ -240,7 +242,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.q = b->q; a.v = b->v; a.tau = b->tau;
   a.c_link = b->c_link; a.c_point = b->c_point; a.c_radius = b->c_radius; a.c_mu = b->c_mu; a.plane = b->plane;
   a.dt = o->dt; a.gx = o->gravity[0]; a.gy = o->gravity[1]; a.gz = o->gravity[2];
-  a.bkp = o->baumgarte_kp; a.bkd = o->baumgarte_kd;
+  a.bkp = o->baumgarte_kp; a.bkd = o->baumgarte_kd; a.cmargin = o->contact_margin;
   a.admm_max_iter = o->admm_max_iter; a.polish_iters = o->polish_iters;
   a.admm_eps = o->admm_eps; a.ncp_tol = o->ncp_tol;
   a.eps_sigma = o->eps_sigma; a.eps_lambda = o->eps_lambda; a.margin_delta = o->margin_delta;
@@ -409,15 +411,16 @@ extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int3
 
 // Schedule knobs and their options.  The index of ds_autotune / ds_set_schedule is the mixed-radix
 // number of the chosen option positions, knob 0 the lowest digit.
-static const int kKnobs = 7, kNumSchedules = 3 * 3 * 3 * 2 * 4 * 3 * 3;
-static const int kNopt[kKnobs] = {3, 3, 3, 2, 4, 3, 3};
+static const int kKnobs = 8, kNumSchedules = 3 * 3 * 3 * 2 * 4 * 3 * 3 * 3;
+static const int kNopt[kKnobs] = {3, 3, 3, 2, 4, 3, 3, 3};
 static const int kOpt[kKnobs][4] = {{0, 1, 2, 0},          // round-cap table
                                     {3, 5, DS_ROUNDS, 0},  // first row-per-lane ADMM round
                                     {0, 4, 8, 0},          // finish: target CTAs per SM
                                     {0, 1, 0, 0},          // Newton: cooperative / one thread per env
                                     {2, 4, 5, DS_ROUNDS},  // overlapped finish after this round
                                     {3, 5, DS_ROUNDS, 0},  // first two-warp ADMM round
-                                    {0, 8, 4, 0}};         // overlapped finish: SM stride kept free
+                                    {0, 8, 4, 0},          // overlapped finish: SM stride kept free
+                                    {3, 5, DS_ROUNDS, 0}};  // speculative Newton attempts from round
 static int* knob(ds_schedule& c, int d) {
   switch (d) {
     case 0: return &c.caps;
@@ -426,7 +429,8 @@ static int* knob(ds_schedule& c, int d) {
     case 3: return &c.newton_thread;
     case 4: return &c.overlap_from;
     case 5: return &c.pair_from;
-    default: return &c.reserve;
+    case 6: return &c.reserve;
+    default: return &c.spec_from;
   }
 }
 static int schedule_index(ds_schedule c) {

@@ -32,6 +32,33 @@ enum { DS_RUN_STEP = 0, DS_RUN_JAC = 1, DS_RUN_VJP = 2 };
 // Workspace of the three-kernel pipeline (setup -> compacted ADMM rounds -> finish), structure of
 // arrays over the batch.  Carved out of one caller-provided buffer by ds_workspace_layout().
 #define DS_ROUNDS 9
+
+// Mode of the contact of rank `rank` (0 = the largest normal impulse in the iterate) in pattern p
+// of the fallback enumeration: first the 2 na patterns with one contact in contact (sticking, then
+// sliding), then for each pair of ranks (ra < rb, in order) its four sticking / sliding
+// combinations; every other contact breaks.  2 na^2 patterns in all.
+DS_HDI int enum_mode(int p, int rank, int na) {
+  if (p < 2 * na) return rank == p / 2 ? ((p & 1) ? 2 : 1) : 0;
+  p -= 2 * na;
+  int pair = p >> 2;
+  const int combo = p & 3;
+  int ra = 0, cnt = na - 1;
+  while (cnt > 0 && pair >= cnt) { pair -= cnt; ++ra; --cnt; }
+  const int rb = ra + 1 + pair;
+  if (rank == ra) return (combo & 1) ? 2 : 1;
+  if (rank == rb) return (combo & 2) ? 2 : 1;
+  return 0;
+}
+
+// ADMM iterations an env may run in round r before the lists are regrouped (and before its iterate
+// is tried by the Newton stage, in the rounds with speculative attempts), for the three tables:
+// {32, 32, 64, ..., 4096} (0), halved (1), doubled with 4096 kept as the last cap (2).  The last
+// round runs to the iteration limit whatever its cap.
+DS_HDI int ds_round_cap(int table, int r) {
+  const int base = table == 1 ? 16 : (table == 2 ? 64 : 32);
+  const int c = r == 0 ? base : base << (r - 1);
+  return c > 4096 ? 4096 : c;
+}
 struct WsView {
   int32_t* counts;        // [DS_ROUNDS + 1] envs queued for each round
   int32_t* list[2];       // [B] ping-pong work lists of env indices
@@ -109,16 +136,24 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
   return off;
 }
 
-// How the pipeline divides the work (never what an env computes, except that the one-thread and
-// cooperative Newton kernels round differently): ADMM round-cap table, the first round run by the
+// How the pipeline divides the work: ADMM round-cap table, the first round run by the
 // row-per-lane ADMM kernel (DS_ROUNDS = never), finish-kernel target CTAs per SM for splitting
 // Jacobian columns (0 = one thread per env), Newton kernel form, and the round after which the
-// envs already solved are finished on a side stream while the slow ones still iterate.
+// envs already solved are finished on a side stream while the slow ones still iterate; whether
+// the Newton stage is also tried on unconverged ADMM iterates.  It changes how the work is divided;
+// what an env computes changes only by rounding (the two Newton forms) or, through the round caps
+// and the speculative Newton attempts, by where the ADMM iteration is stopped: the accepted
+// impulse always passes the same NCP residual test.
 struct ds_schedule {
   int caps, wide_from, finish_ctas, newton_thread;
   int overlap_from;   // after this round, finish the completed envs on a side stream (DS_ROUNDS = never)
   int pair_from;      // first round of the two-warp ADMM kernel (FP64, 3 NS <= 32; DS_ROUNDS = never)
   int reserve;        // overlapped finish: keep off the SMs with smid % reserve == 0 (0 = use all)
+  int spec_from;      // from the end of this round on, every env still iterating gets a Newton /
+                      // active-set attempt (also when its stage tolerance was not met: it keeps
+                      // its stage if the attempt fails), and a failed attempt falls back to
+                      // enumerating the contact-mode patterns with one or two contacts in
+                      // contact (DS_ROUNDS = never)
 };
 
 // Everything a launch needs; passed by value.
@@ -133,7 +168,8 @@ struct KArgs {
   const int32_t* c_link;
   const double *c_point, *c_radius, *c_mu, *plane;
   double dt, gx, gy, gz;
-  double bkp, bkd;         // Baumgarte gains (App. D); 1, 0: no term
+  double bkp, bkd;         // Baumgarte gains (App. D); 1, 0 (and no margin): no term
+  double cmargin;          // activation distance: a slot is active when phi <= cmargin
   int admm_max_iter, polish_iters;
   double admm_eps, ncp_tol, eps_sigma, eps_lambda, margin_delta;
   double *v_next, *q_next, *lambda;

@@ -140,8 +140,8 @@ DS_HD double ncp_residual(const E& s, const double* lam) {
   return r;
 }
 
-// Contact modes (breaking / sticking / sliding) from sigma = G lambda + g, lambda (same rules as
-// the oracle): sticking if |sigma| <= es; else breaking if sigma_N > es or lambda_N <= el; else
+// Contact modes (breaking / sticking / sliding) from sigma = G lambda + g and lambda (Sec. 3.2, with
+// relative thresholds): sticking if |sigma| <= es; else breaking if sigma_N > es or lambda_N <= el; else
 // sticking if the impulse is strictly inside the cone (then Eq. 1 forces sigma = 0); else sliding.
 template <class E>
 DS_HD double classify(const E& s, const double* lam, double es_rel, double el_rel, int* mode) {
@@ -178,9 +178,20 @@ DS_HD double classify(const E& s, const double* lam, double es_rel, double el_re
   return margin;
 }
 
-// Active-set update after a Newton solve that did not give an NCP solution (same rules as the
-// oracle): breaking + penetrating -> sticking; sticking/sliding + pulling -> breaking; sticking
-// with the impulse outside the cone -> sliding; sliding that stopped -> sticking.
+// Eq. 1 with lambda = 0: sigma = g, and g + Gamma(g) = (g_T, g_N + mu |g_T|) lies in the dual cone
+// exactly when g_N >= 0.  So when the free motion separates every active contact, lambda = 0 is a
+// solution; it is the one the step takes (no impulse acts when nothing pushes into the plane),
+// although the non-monotone De Saxce form can admit others.  False on NaN.
+template <class E>
+DS_HDI bool separating(const E& s) {
+  bool sep = s.na > 0;
+  for (int i = 0; i < s.na; ++i) sep = sep && s.gd[3 * i + 2] >= 0.0;
+  return sep;
+}
+
+// Active-set update after a Newton solve that did not give an NCP solution: breaking + penetrating
+// -> sticking; sticking/sliding + pulling -> breaking; sticking with the impulse outside the cone
+// -> sliding; sliding that stopped -> sticking.
 template <class E>
 DS_HD bool reclassify(const E& s, const double* lam, int* mode, double es, double el, double delta) {
   const int m = 3 * s.na;
@@ -428,10 +439,13 @@ template <typename T>
 DS_HDI int num_stages() { return std::is_same<T, double>::value ? 4 : 3; }
 
 // End of an ADMM stage: identify the modes from z and run up to 4 active-set rounds of FP64 Newton
-// on the mode equations; keeps the best candidate (by FP64 NCP residual).  Returns true when the
-// best candidate passes the residual check.
+// on the mode equations; keeps the best candidate (by FP64 NCP residual).  With `enumerate` (the
+// late rounds of a schedule with speculative attempts), a failure falls back to the patterns of
+// enum_mode: Newton on each pattern's mode equations from z, in order, until one passes.  Returns
+// true when the best candidate passes the residual check.
 template <class P, typename T>
-DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* best, double& best_r) {
+DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* best, double& best_r,
+                        bool enumerate = false) {
   const int m = 3 * p.na;
   double scale = 1.0;
   for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(p.gd[i]));
@@ -458,31 +472,65 @@ DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* be
     if (!reclassify(p, lp, mode, 10.0 * tol, 10.0 * a.ncp_tol * lscale, 10.0 * a.ncp_tol * lscale)) break;
     for (int i = 0; i < p.na; ++i) proj_cone(lp + 3 * i, p.mu[i], lp + 3 * i);
   }
+  if (enumerate && best_r > tol) {
+    int rank[P::NC3 / 3];
+    for (int i = 0; i < p.na; ++i) {
+      rank[i] = 0;
+      for (int j = 0; j < p.na; ++j)
+        rank[i] += (lz[3 * j + 2] > lz[3 * i + 2]) || (lz[3 * j + 2] == lz[3 * i + 2] && j < i);
+    }
+    const int npat = 2 * p.na * p.na;
+    for (int pat = 0; pat < npat && best_r > tol; ++pat) {
+      for (int i = 0; i < p.na; ++i) mode[i] = enum_mode(pat, rank[i], p.na);
+      for (int i = 0; i < m; ++i) lp[i] = lz[i];
+      newton_modes(p, lp, mode, a.polish_iters, sat_delta);
+      const double rpol = ncp_residual(p, lp);
+      if (rpol < best_r) { best_r = rpol; for (int i = 0; i < m; ++i) best[i] = lp[i]; }
+    }
+  }
   return best_r <= tol;
 }
 
-// Staged NCP solve (same structure as the oracle's): each stage continues the ADMM iteration to a
-// tolerance, then runs the Newton / active-set stage; the first candidate whose FP64 NCP residual
-// passes is accepted.
+// Staged NCP solve in one thread, in the rounds of the pipeline's schedule: each round continues
+// the ADMM iteration for at most the round's cap (the last round: to the iteration limit) or until
+// the stage tolerance is met, then runs the Newton / active-set stage on the iterate; the first
+// candidate whose FP64 NCP residual passes is accepted.  A stage that ended without acceptance
+// moves to the next (tighter) stage; from the schedule's speculative round on, an unconverged
+// round's iterate is tried too (with the enumeration fallback) and the stage is kept.  So the fused
+// kernel reaches the same impulse as the pipeline under the same schedule.  When the free motion separates every contact, lambda stays 0
+// (see separating()).
 template <class P, typename T>
 DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
   const int m = 3 * s.na;
   iters = 0;
-  if (m == 0) return;
+  if (m == 0 || separating(s)) return;
   Admm<P::NC3 / 3, T> ad;
   if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
   ad.reset(s);
   double best[P::NC3], best_r = 1e300;
   bool ok = false;
-  for (int stage = 0; stage < num_stages<T>(); ++stage) {
+  const int table = (a.sched.caps >= 0 && a.sched.caps < 3) ? a.sched.caps : 0;
+  int stage = 0;
+  for (int r = 0; r < DS_ROUNDS; ++r) {
+    const bool final_round = r == DS_ROUNDS - 1;
+    const int cap = ds_round_cap(table, r);
+    const int lim = final_round ? (a.admm_max_iter > cap ? a.admm_max_iter : cap) : cap;
     const double eps = stage_eps<T>(a, stage);
     const T te = T(eps);
-    while (iters < a.admm_max_iter) {
+    bool conv = false;
+    for (int k = 0; k < lim && iters < a.admm_max_iter; ++k) {
       ++iters;
-      if (ad.iterate(s, te, iters % DS_ADMM_CHECK == 0)) break;
+      if (ad.iterate(s, te, iters % DS_ADMM_CHECK == 0)) { conv = true; break; }
     }
-    ok = newton_stage(s, ad.z, eps, a, best, best_r);
-    if (ok || iters >= a.admm_max_iter) break;
+    const bool ended = conv || iters >= a.admm_max_iter || final_round;
+    const bool late = r >= a.sched.spec_from;
+    if (!ended && !late) continue;
+    ok = newton_stage(s, ad.z, eps, a, best, best_r, late);
+    if (ok) break;
+    if (ended) {
+      if (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || final_round) break;
+      ++stage;
+    }
   }
   for (int i = 0; i < m; ++i) s.lam[i] = best[i];
   if (!ok) st |= DS_ENV_NOT_CONVERGED;
@@ -592,12 +640,17 @@ DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T 
   for (int r = 0; r < 3; ++r) out[r] = dot3(s.fr[r], dp);
 }
 
+// Whether g carries the signed-distance term of App. D: gains other than (1, 0), or an activation
+// margin (a contact active at phi > 0 then gains phi/dt).
+DS_HDI bool gap_term(const KArgs& a) { return !(a.bkp == 1.0 && a.bkd == 0.0 && a.cmargin == 0.0); }
+
 // Baumgarte stabilisation (App. D): each active contact's normal entry of g gains
-// phi/dt - kp [phi/dt]_- - kd (J_c v)_N ([x]_- = min(x, 0)), in FP64; with kp = 1, kd = 0 the term
-// is identically zero and nothing is added.
+// phi/dt - kp [phi/dt]_- - kd (J_c v)_N ([x]_- = min(x, 0)), in FP64; with kp = 1, kd = 0 and no
+// activation margin (so phi <= 0 on every active contact) the term is identically zero and
+// nothing is added.
 template <int NB, int NV, int NS, typename T>
 DS_HDI void baumgarte_g(const KArgs& a, const int e, const double (*Jd)[NV], Env<NB, NV, NS, T>& s) {
-  if (a.bkp == 1.0 && a.bkd == 0.0) return;
+  if (!gap_term(a)) return;
   for (int ac = 0; ac < s.na; ++ac) {
     const int r = 3 * ac + 2;
     const double pr = s.phi[ac] / a.dt;
@@ -610,14 +663,15 @@ DS_HDI void baumgarte_g(const KArgs& a, const int e, const double (*Jd)[NV], Env
 }
 
 // The Baumgarte term's derivative w.r.t. Jacobian column (blk, d) of contact ac (its normal row):
-// d/dq_d: (1 - kp)/dt dphi/dq_d - kd d(J_c v)_N/dq_d (dphi/dq_d = (J_c)_N,d for a body-fixed
-// contact point; the second term is the FKV derivative at v); d/dv_d: -kd (J_c)_N,d; d/dtau: 0.
+// d/dq_d: (1 - kp)/dt dphi/dq_d (1/dt where phi >= 0: [x]_- is flat there) - kd d(J_c v)_N/dq_d
+// (dphi/dq_d = (J_c)_N,d for a body-fixed contact point; the second term is the FKV derivative at
+// v); d/dv_d: -kd (J_c)_N,d; d/dtau: 0.
 template <int NB, int NV, int NS, typename T>
 DS_HDI T baumgarte_d(const DevModel& m, const KArgs& a, const Env<NB, NV, NS, T>& s, int ac, int blk, int d) {
-  if ((a.bkp == 1.0 && a.bkd == 0.0) || blk == 2) return T(0);
+  if (!gap_term(a) || blk == 2) return T(0);
   const T jn = s.Jc[3 * ac + 2][d];
   if (blk == 1) return -T(a.bkd) * jn;
-  T r = T((1.0 - a.bkp) / a.dt) * jn;
+  T r = T((s.phi[ac] < 0.0 ? 1.0 - a.bkp : 1.0) / a.dt) * jn;
   if (a.bkd != 0.0) {
     T fk[3];
     fkv_tangent<NB, NV, NS, T>(m, s, s.V, ac, d, fk);
@@ -812,7 +866,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     double xw[3];
     for (int i = 0; i < 3; ++i) xw[i] = s.P[b][i] + s.R[b][3 * i] * pl[0] + s.R[b][3 * i + 1] * pl[1] + s.R[b][3 * i + 2] * pl[2];
     const double phi = pn[0] * xw[0] + pn[1] * xw[1] + pn[2] * xw[2] - pd - r;
-    if (phi <= 0.0) {
+    if (phi <= a.cmargin) {
       const int n = s.na++;
       s.slot[n] = k;
       s.body[n] = b;
@@ -1334,7 +1388,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           for (int k = 0; k < NV; ++k) r += dtau[k] * w2[k];
           r = -dt * r;
           if (blk == 1) r += ub[d];
-          const bool stab = !(a.bkp == 1.0 && a.bkd == 0.0);
+          const bool stab = gap_term(a);
           for (int ac = 0; ac < s.na && (blk == 0 || stab); ++ac) {
             if (sz[ac] == 0) continue;
             T fk[3] = {T(0), T(0), T(0)};
@@ -1429,7 +1483,14 @@ DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
     w.ay[i * B + e] = 0.0;
     w.asx[i * B + e] = double(s.gt[i]);
   }
-  if (mm > 0 && !(st & DS_ENV_NONFINITE)) {
+  if (mm > 0 && !(st & DS_ENV_NONFINITE) && separating(s)) {
+    // lambda = 0 solves Eq. 1 (separating()): no ADMM; the modes of that solution go to the finish
+    for (int i = 0; i < mm; ++i) s.lam[i] = 0.0;
+    int mode[NS];
+    const double margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, mode);
+    if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
+    for (int i = 0; i < s.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
+  } else if (mm > 0 && !(st & DS_ENV_NONFINITE)) {
     Admm<NS, T> ad;
     if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
     w.rho[e] = double(ad.rho);
@@ -1456,6 +1517,24 @@ __global__ void __launch_bounds__(128, 4) setup_kernel(KArgs a) {
   const int e = a.env_list ? a.env_list[t] : t;
   if (a.model_id && a.model_id[e] != a.model_index) return;
   setup_env<NB, NV, NS, T>(sm, a, e);
+}
+
+// End of an env's ADMM round: to the Newton queue when its stage ended (tolerance met, iteration
+// limit, or the last round), else to the next round's list -- or, from the schedule's speculative
+// round on, to the Newton queue as ~e (the Newton stage tries the unconverged iterate and, if that
+// fails, returns the env to the next round in the same stage).
+__device__ __forceinline__ void route_after_round(const KArgs& a, int e, bool conv, int iters, int32_t* next) {
+  const WsView& w = a.ws;
+  if (conv || iters >= a.admm_max_iter || a.final_round) {
+    const int k = atomicAdd(&w.ncounts[a.round], 1);
+    w.nlist[k] = e;
+  } else if (a.round >= a.sched.spec_from) {
+    const int k = atomicAdd(&w.ncounts[a.round], 1);
+    w.nlist[k] = ~e;
+  } else {
+    const int k = atomicAdd(&w.counts[a.round + 1], 1);
+    next[k] = e;
+  }
 }
 
 // 2a. one ADMM round, one lane per contact slot (NS lanes per env, 32/NS envs per warp): each lane
@@ -1553,13 +1632,7 @@ __global__ void __launch_bounds__(128) admm_round_kernel(KArgs a) {
       }
       if (li == 0) {
         w.iters[e] = iters;
-        if (conv || iters >= a.admm_max_iter || a.final_round) {
-          const int k = atomicAdd(&w.ncounts[a.round], 1);
-          w.nlist[k] = e;
-        } else {
-          const int k = atomicAdd(&w.counts[a.round + 1], 1);
-          next[k] = e;
-        }
+        route_after_round(a, e, conv, iters, next);
       }
     }
   }
@@ -1673,13 +1746,7 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
       }
       if (li == 0) {
         w.iters[e] = iters;
-        if (conv || iters >= a.admm_max_iter || a.final_round) {
-          const int k = atomicAdd(&w.ncounts[a.round], 1);
-          w.nlist[k] = e;
-        } else {
-          const int k = atomicAdd(&w.counts[a.round + 1], 1);
-          next[k] = e;
-        }
+        route_after_round(a, e, conv, iters, next);
       }
     }
   }
@@ -1870,13 +1937,7 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
       }
       if (qi == 0) {
         w.iters[e] = iters;
-        if (conv || iters >= a.admm_max_iter || a.final_round) {
-          const int k = atomicAdd(&w.ncounts[a.round], 1);
-          w.nlist[k] = e;
-        } else {
-          const int k = atomicAdd(&w.counts[a.round + 1], 1);
-          next[k] = e;
-        }
+        route_after_round(a, e, conv, iters, next);
       }
     }
   }
@@ -1885,7 +1946,10 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
 // 2b. the Newton / active-set stage for the envs whose ADMM stage ended in this round (one thread
 //     per env): accept, or move to the next (tighter) stage and queue for the next round.
 template <int NS, typename T>
-DS_HD void newton_env(const KArgs& a, const int e) {
+DS_HD void newton_env(const KArgs& a, const int entry) {
+  // entry = e: the env's ADMM stage ended; ~e: a speculative attempt on an unconverged iterate
+  const bool spec = entry < 0;
+  const int e = spec ? ~entry : entry;
   const WsView& w = a.ws;
   const int B = a.B;
   Ncp<NS, T> p;
@@ -1910,9 +1974,9 @@ DS_HD void newton_env(const KArgs& a, const int e) {
   double best[3 * NS], best_r = w.best_r[e];
   for (int i = 0; i < m; ++i) best[i] = w.lam[i * B + e];
   const double eps = stage_eps<T>(a, stage);
-  const bool ok = newton_stage(p, z, eps, a, best, best_r);
+  const bool ok = newton_stage(p, z, eps, a, best, best_r, a.round >= a.sched.spec_from);
   for (int i = 0; i < m; ++i) w.lam[i * B + e] = best[i];
-  if (ok || iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round) {
+  if (ok || (!spec && (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round))) {
     for (int i = 0; i < m; ++i) p.lam[i] = best[i];
     if (!ok) st |= DS_ENV_NOT_CONVERGED;
     int mode[NS];
@@ -1923,7 +1987,7 @@ DS_HD void newton_env(const KArgs& a, const int e) {
     const int k = ds_atomic_add(&w.dcount[0], 1);
     w.dlist[k] = e;
   } else {
-    w.stage[e] = stage + 1;
+    if (!spec) w.stage[e] = stage + 1;
     w.best_r[e] = best_r;
     const int k = ds_atomic_add(&w.counts[a.round + 1], 1);
     w.list[(a.round + 1) & 1][k] = e;

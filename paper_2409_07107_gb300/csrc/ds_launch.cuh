@@ -42,13 +42,10 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   ds_trace_mark(DS_STAGE_SETUP, 1, s);
   setup_kernel<NB, NV, NS, T><<<blocks, threads, 0, s>>>(a0);
   ds_trace_mark(DS_STAGE_SETUP, 0, s);
-  // Round caps (ADMM iterations an env may run per round before regrouping); the last round runs
-  // up to the iteration limit, so the choice of table never changes an env's result.
-  static const int kCaps[3][DS_ROUNDS] = {{32, 32, 64, 128, 256, 512, 1024, 2048, 4096},
-                                          {16, 16, 32, 64, 128, 256, 512, 1024, 2048},
-                                          {64, 64, 128, 256, 512, 1024, 2048, 4096, 4096}};
+  // Round caps (ADMM iterations an env may run per round before regrouping and, with speculative
+  // attempts, before the Newton stage tries its iterate); the last round runs to the iteration limit.
   const ds_schedule sc = a0.sched;
-  const int* caps = kCaps[(sc.caps >= 0 && sc.caps < 3) ? sc.caps : 0];
+  const int table = (sc.caps >= 0 && sc.caps < 3) ? sc.caps : 0;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, admm_round_kernel<NS, T>, threads, 0);
   if (per_sm <= 0) per_sm = 1;
@@ -114,7 +111,8 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     KArgs a = a0;
     a.round = r;
     a.final_round = r == DS_ROUNDS - 1;
-    a.round_cap = a.final_round ? (a0.admm_max_iter > caps[r] ? a0.admm_max_iter : caps[r]) : caps[r];
+    const int cap = ds_round_cap(table, r);
+    a.round_cap = a.final_round ? (a0.admm_max_iter > cap ? a0.admm_max_iter : cap) : cap;
     ds_trace_mark(DS_STAGE_ADMM, 1, s);
     bool wide = false;
     if constexpr (kPairOk) {

@@ -469,10 +469,12 @@ __device__ double newton_modes(const SM& S, LUWork<NS, LT>& W, const Lane<NS>& l
 }
 
 // End of an ADMM stage (the one-thread newton_stage): classify z, up to four active-set rounds of
-// Newton, keep the best candidate by FP64 NCP residual.  lz and best_l are the lane's components.
+// Newton, keep the best candidate by FP64 NCP residual; with `enumerate`, a failure falls back to
+// the contact-mode patterns of enum_mode (FP64 Newton from z on each, in order, until one passes).
+// lz and best_l are the lane's components.
 template <int NS, typename T>
 __device__ bool newton_stage(Smem<NS, T>& S, const Lane<NS>& ln, double lz, double eps, const KArgs& a, double& best_l,
-                             double& best_r, bool act, bool last) {
+                             double& best_r, bool act, bool last, bool enumerate) {
   constexpr int L = Shape<NS>::L;
   const bool in = ln.row && ln.ci < ln.na;
   const double scale = fmax(1.0, gmax<L>(in ? fabs(ln.g) : 0.0));
@@ -507,14 +509,36 @@ __device__ bool newton_stage(Smem<NS, T>& S, const Lane<NS>& ln, double lz, doub
       lp = p[ln.kc];
     }
   }
+  // fallback: the enumerated contact-mode patterns, ranked by the normal impulses of z
+  bool eg = enumerate && act && best_r > tol;
+  if (__any_sync(kFull, eg)) {
+    int rank = 0;
+#pragma unroll
+    for (int c = 0; c < NS; ++c) {
+      const double lnc = __shfl_sync(kFull, lz, ln.base + 3 * c + 2);
+      const double own = __shfl_sync(kFull, lz, ln.base + 3 * (ln.ci < NS ? ln.ci : 0) + 2);
+      if (c < ln.na && (lnc > own || (lnc == own && c < ln.ci))) ++rank;
+    }
+    const int npat = 2 * ln.na * ln.na;
+#pragma unroll 1
+    for (int pat = 0; __any_sync(kFull, eg); ++pat) {
+      if (pat >= npat) eg = false;
+      const int pm = (ln.ci < ln.na && pat < npat) ? enum_mode(pat, rank, ln.na) : DS_MODE_BREAKING;
+      const double lq = newton_modes<NS, double>(S, S.d, ln, lz, pm, a.polish_iters, sat_delta, eg);
+      const double rq = residual<NS>(S, ln, lq);
+      if (eg && rq < best_r) { best_r = rq; best_l = lq; }
+      if (eg && best_r <= tol) eg = false;
+    }
+  }
   return act && best_r <= tol;
 }
 
 }  // namespace coop
 
-// 2b, cooperative: the Newton / active-set stage for the envs whose ADMM stage ended in this round,
-// 4 NS lanes per env.  Same bookkeeping as newton_env: accept (write lambda, modes, status), or
-// move to the next stage and queue the env for the next round.
+// 2b, cooperative: the Newton / active-set stage for the envs whose ADMM stage ended in this round
+// (and the speculative attempts), 4 NS lanes per env.  Same bookkeeping as newton_env: accept
+// (write lambda, modes, status), or queue the env for the next round (in the next stage unless the
+// attempt was speculative).
 template <int NS, typename T>
 __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MINB) newton_coop_kernel(KArgs a) {
   using Sh = coop::Shape<NS>;
@@ -532,7 +556,10 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
   for (int t0 = warp * EPW; t0 < n; t0 += nwarps * EPW) {
     const int t = t0 + grp;
     const bool have = t < n;
-    const int e = have ? w.nlist[t] : 0;
+    // entry e: the env's ADMM stage ended; ~e: a speculative attempt on an unconverged iterate
+    const int entry = have ? w.nlist[t] : 0;
+    const bool spec = entry < 0;
+    const int e = spec ? ~entry : entry;
     coop::Lane<NS> ln;
     ln.li = lane - grp * L;
     ln.base = grp * L;
@@ -560,10 +587,11 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
     const int iters = have ? w.iters[e] : 0;
     uint32_t st = have ? w.st[e] : 0u;
     const double eps = stage_eps<T>(a, stage);
-    const bool last = iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round;
-    const bool ok = coop::newton_stage<NS, T>(S, ln, lz, eps, a, best_l, best_r, have && m > 0, last);
+    const bool last = !spec && (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round);
+    const bool ok = coop::newton_stage<NS, T>(S, ln, lz, eps, a, best_l, best_r, have && m > 0, last,
+                                              a.round >= a.sched.spec_from);
     if (mine) w.lam[ln.li * B + e] = best_l;
-    const bool fin = ok || iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round;
+    const bool fin = ok || last;
     int mode;
     const double margin = coop::classify<NS>(S, ln, best_l, a.eps_sigma, a.eps_lambda, mode);
     if (have && fin) {
@@ -576,7 +604,7 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
         w.dlist[k] = e;
       }
     } else if (have && ln.li == 0) {
-      w.stage[e] = stage + 1;
+      if (!spec) w.stage[e] = stage + 1;
       w.best_r[e] = best_r;
       const int k = atomicAdd(&w.counts[a.round + 1], 1);
       w.list[(a.round + 1) & 1][k] = e;

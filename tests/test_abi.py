@@ -41,6 +41,10 @@ def test_status_strings_and_defaults(L):
     assert o.dt == 1e-3 and o.precision == ds.DS_FP64 and o.admm_max_iter > 0
     # the last fields of ds_options sit where the binding expects them (the C default fills them)
     assert o.margin_delta == 1e-3 and o.baumgarte_kp == 1.0 and o.baumgarte_kd == 0.0
+    raw = ds.ds_options()
+    raw.contact_margin = 7.0                 # the C default must overwrite the binding's last field
+    L.ds_options_default(ctypes.byref(raw))
+    assert raw.contact_margin == 0.0
 
 
 def _desc(nb=2, parent=(-1, 0), jtype=(0, 0), axis=None):

@@ -2,14 +2,21 @@
 
 Tolerances (relative, per env, ||x - x_ref||_inf / max(||x_ref||_inf, 1e-6)):
   FP64 path: v+ and the three Jacobians <= 1e-9; modes bit-exact.
-  Mixed path: v+ <= 1e-4; Jacobians <= 1e-3 on envs whose classification margin is >= 1e-3.
-Jacobians and modes are compared only on envs with margin >= 1e-3 (away from mode switches); the
-modes of all other envs must still be a valid classification (the NCP residual check passed)."""
+  Mixed path: v+ <= 1e-4; Jacobians <= 1e-3.
+
+Eq. 1 can have more than one solution, so the oracle solves every env by two independent routes
+(ADMM and projected Gauss-Seidel, each with the Newton polish; neither shares a parameter with the
+kernels).  The GPU's v+ must equal that of one of the oracle's solutions; an env where it equals
+none is accepted only if the GPU impulse satisfies Eq. 1 for the oracle's G, g and mu, and such envs
+must stay rare.  Modes and Jacobians are then compared with the matched oracle solution on envs
+whose oracle classification margin is >= 1e-3 (away from mode switches; the decision is the
+oracle's, not the kernel's), and Jacobians only where the oracle's routes agree on them (where they
+do not, the derivative depends on which member of a family of solutions a solver reaches)."""
 import numpy as np
 import pytest
 
 from paper_2409_07107_gb300 import scenes
-from tests.oracle_runner import rel_err, run_oracle
+from tests.oracle_runner import candidates, jac_of, rel_err, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -37,26 +44,64 @@ def _gpu(wl, precision, run="jac"):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def _compare(wl, g, refs, envs, tol_v, tol_j, jac=True, min_checked=1):
-    nv_all = wl.batch.v.shape[0]
-    checked = 0
+def _gpu_lambda(g, e, slots):
+    return np.concatenate([g["lambda"][3 * k:3 * k + 3, e] for k in slots]) if len(slots) else np.zeros(0)
+
+
+def _match(g, e, r, nv, tol_v):
+    """The oracle solution whose v+ the GPU reached, or None after checking that the GPU impulse
+    solves Eq. 1 for the oracle's problem data (another member of its solution set)."""
+    from oracle.ncp import ncp_residual
+    for c in candidates(r):
+        if rel_err(g["v_next"][:nv, e], c["v_next"]) <= tol_v:
+            return c
+    lam = _gpu_lambda(g, e, r["slots"])
+    scale = max(1.0, float(np.max(np.abs(r["g"])))) if len(r["g"]) else 1.0
+    res = ncp_residual(r["G"], r["g"], r["mu"], lam)
+    assert res <= tol_v * scale, "env %d: v+ matches no oracle solution and the impulse violates Eq. 1 (%.3e)" % (e, res)
+    return None
+
+
+def _jac_defined(r, c, tol=1e-8):
+    """False when the oracle's routes reach the matched v+ and modes but differ in the Jacobian."""
+    for o in candidates(r):
+        if o is c or list(o["modes"]) != list(c["modes"]) or rel_err(o["v_next"], c["v_next"]) > 1e-9:
+            continue
+        if rel_err(jac_of(o), jac_of(c)) > tol:
+            return False
+    return True
+
+
+def _compare(wl, g, refs, envs, tol_v, tol_j, jac=True, min_checked=1, vjp=None, max_other=0.05):
+    """Checks every env as the module docstring states.  With ``vjp`` = v_bar [nv][B] the GPU's
+    q_bar, v_bar, tau_bar are compared with J^T v_bar of the matched oracle Jacobians."""
+    checked = other = 0
     for e, r in zip(envs, refs):
         mi = 0 if wl.batch.model_id is None else int(wl.batch.model_id[e])
-        m = wl.models[mi]
-        nv = m.nv
+        nv = wl.models[mi].nv
         assert g["status"][e] & 2 == 0, "env %d non-finite" % e
-        ev = rel_err(g["v_next"][:nv, e], r["v_next"])
-        assert ev <= tol_v, "env %d v+ rel err %.3e" % (e, ev)
-        if r["margin"] < DELTA or (g["status"][e] & 8):
+        c = _match(g, e, r, nv, tol_v)
+        if c is None:
+            other += 1
             continue
-        gm = [int(g["modes"][k, e]) for k in r["slots"]]
-        assert gm == [int(x) for x in r["modes"]], "env %d modes %s vs %s" % (e, gm, r["modes"])
+        if c["margin"] < DELTA:
+            continue
+        gm = [int(g["modes"][k, e]) for k in c["slots"]]
+        assert gm == [int(x) for x in c["modes"]], "env %d modes %s vs %s" % (e, gm, c["modes"])
+        if (jac or vjp is not None) and not _jac_defined(r, c):
+            continue
         if jac:
             for key in ("dv_dq", "dv_dv", "dv_dtau"):
-                ej = rel_err(g[key][:nv, :nv, e], r[key])
+                ej = rel_err(g[key][:nv, :nv, e], c[key])
+                assert ej <= tol_j, "env %d %s rel err %.3e" % (e, key, ej)
+        if vjp is not None:
+            for key, jk in (("q_bar", "dv_dq"), ("v_bar", "dv_dv"), ("tau_bar", "dv_dtau")):
+                ej = rel_err(g[key][:nv, e], c[jk].T @ vjp[:nv, e])
                 assert ej <= tol_j, "env %d %s rel err %.3e" % (e, key, ej)
         checked += 1
-    assert checked >= min_checked
+    assert checked >= min_checked, (checked, min_checked)
+    assert other <= max(1, int(max_other * len(envs))), "%d envs reached no oracle solution" % other
+    return checked
 
 
 def test_arm_sphere_fp64(torch_cuda):
@@ -165,7 +210,7 @@ def test_edge_cases(torch_cuda):
     one = scenes.Workload(wl.name, wl.models, wl.batch.take([5]), wl.options)
     g1 = _gpu(one, "fp64")
     r = run_oracle(one, [0])[0]
-    assert rel_err(g1["v_next"][:, 0], r["v_next"]) <= 1e-9
+    _match(g1, 0, r, wl.models[0].nv, 1e-9)      # an oracle solution's v+, or a solution of Eq. 1
     empty = ds.Simulator(scenes.Workload(wl.name, wl.models, wl.batch.take([]), wl.options))
     empty.step()
 
@@ -212,18 +257,7 @@ def test_uneven_batch_step_and_vjp(torch_cuda):
         torch.cuda.synchronize()
         g = {k: v.cpu().numpy() for k, v in out.items()}
         assert not (g["status"] & 16).any()
-        checked = 0
-        for e, r in zip(envs, refs):
-            nv = wl.models[int(wl.batch.model_id[e])].nv
-            assert g["status"][e] & 2 == 0
-            assert rel_err(g["v_next"][:nv, e], r["v_next"]) <= tol_v, (prec, e)
-            if r["margin"] < DELTA or (g["status"][e] & 8):
-                continue
-            for key, jk in (("q_bar", "dv_dq"), ("v_bar", "dv_dv"), ("tau_bar", "dv_dtau")):
-                ref = r[jk].T @ wbar[:nv, e]
-                assert rel_err(g[key][:nv, e], ref) <= tol_j, (prec, e, key)
-            checked += 1
-        assert checked >= 12
+        _compare(wl, g, refs, envs, tol_v, tol_j, jac=False, vjp=wbar, min_checked=12)
 
 
 def test_uneven_batch_slot_dispatch(torch_cuda):
@@ -263,10 +297,26 @@ def test_uneven_batch_cuda_graph(torch_cuda):
         assert torch.equal(got[key], eager[key]), key
 
 
+def _same_solutions(ref, got, frac=0.995):
+    """Two GPU runs of one batch under different schedules: away from mode switches, v+, the modes
+    and the Jacobians agree (v+ 1e-9, Jacobians 1e-8) on all but a few envs, those where Eq. 1 has
+    several solutions and the runs stopped their iterations at different iterates."""
+    ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
+    assert ok.float().mean().item() > 0.8
+    scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
+    same = ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale) <= 1e-9
+    assert same[ok].float().mean().item() >= frac
+    both = ok & same
+    for key in ("dv_dq", "dv_dv", "dv_dtau"):
+        sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
+        assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[both].max().item() <= 1e-8, key
+    assert (got["modes"] == ref["modes"])[:, both].float().mean().item() >= 0.995
+
+
 def test_autotune_keeps_results(torch_cuda):
     """ds_autotune picks a schedule by timing; the step's results under it agree with the
-    default schedule's (schedules change how work is divided, not an env's arithmetic, except the
-    Newton form's rounding)."""
+    default schedule's (schedules change how work is divided; an env's result changes by rounding,
+    or, where Eq. 1 has several solutions, can be another one)."""
     import paper_2409_07107_gb300 as ds
     torch = torch_cuda
     wl = scenes.arm_cube(3000)
@@ -276,14 +326,7 @@ def test_autotune_keeps_results(torch_cuda):
     assert 0 <= desc["index"] < ds.NUM_SCHEDULES
     got = sim.step_jac()
     torch.cuda.synchronize()
-    ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
-    assert ok.float().mean().item() > 0.8
-    scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
-    assert ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale)[ok].max().item() <= 1e-9
-    for key in ("dv_dq", "dv_dv", "dv_dtau"):
-        sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
-        assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[ok].max().item() <= 1e-8, key
-    assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
+    _same_solutions(ref, got)
 
 
 @pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
@@ -315,7 +358,7 @@ def test_two_warp_admm_rounds(torch_cuda, pair):
     torch = torch_cuda
     wl = scenes.arm_cube(3000)
     sim = ds.Simulator(wl, precision="fp64")
-    sim.set_schedule(ds.schedule_index(pair=2))          # row-per-lane rounds only
+    sim.set_schedule(ds.schedule_index(round_caps=1, pair=2))     # row-per-lane rounds only
     ref = {k: v.clone() for k, v in sim.step_jac().items()}
     desc = sim.set_schedule(ds.schedule_index(round_caps=1, pair=pair))
     assert desc["two_warp_admm_from_round"] == (3, 5)[pair]
@@ -325,13 +368,7 @@ def test_two_warp_admm_rounds(torch_cuda, pair):
     finally:
         sim.set_schedule(-1)
     assert (got["iters"] == ref["iters"]).float().mean().item() >= 0.99
-    ok = ((ref["status"] & 8) == 0) & ((got["status"] & 8) == 0)
-    scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
-    assert ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale)[ok].max().item() <= 1e-9
-    for key in ("dv_dq", "dv_dv", "dv_dtau"):
-        sj = ref[key].abs().amax((0, 1)).clamp_min(1e-6)
-        assert ((got[key] - ref[key]).abs().amax((0, 1)) / sj)[ok].max().item() <= 1e-8, key
-    assert (got["modes"] == ref["modes"])[:, ok].float().mean().item() >= 0.995
+    _same_solutions(ref, got)
 
 
 @pytest.mark.parametrize("overlap,reserve,B,caps", [(1, 1, 20000, 0), (2, 2, 20000, 0), (1, 1, 600, 1)])
@@ -398,3 +435,92 @@ def test_baumgarte_stabilised_step(torch_cuda, precision, tol_v, tol_j):
     torch.cuda.synchronize()
     for k in ("v_next", "dv_dq", "dv_dv", "dv_dtau"):
         assert torch.equal(a1[k], a2[k]), k
+
+
+def _sampled(B, n, seed):
+    return sorted(set([0, B - 1] + [int(x) for x in np.random.default_rng(seed).choice(B, n, replace=False)]))
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+def test_humanoid_full_size_sampled(torch_cuda, precision, tol_v, tol_j):
+    """The 36-dof humanoid at its benchmark size (16384 envs in one call: the finish kernel's launch
+    shape for that size), outputs sampled across the batch against the oracle.  Envs without an
+    active contact are cheap to check and are included; at least 30 envs must be fully compared."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    B = 16384
+    wl = scenes.humanoid_feet(B)
+    sim = ds.Simulator(wl, precision=precision)
+    out = sim.step_jac()
+    torch.cuda.synchronize()
+    envs = _sampled(B, 62, 11)
+    g = {k: v[..., envs].cpu().numpy() for k, v in out.items()}
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
+    refs = run_oracle(sub, list(range(len(envs))))
+    assert sum(len(r["slots"]) > 0 for r in refs) >= 20
+    _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=30)
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+def test_quadruped_full_size_sampled(torch_cuda, precision, tol_v, tol_j):
+    """The 18-dof quadruped at 32768 envs in one call, sampled against the oracle."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    B = 32768
+    wl = scenes.quadruped_feet(B)
+    sim = ds.Simulator(wl, precision=precision)
+    out = sim.step_jac()
+    torch.cuda.synchronize()
+    envs = _sampled(B, 46, 12)
+    g = {k: v[..., envs].cpu().numpy() for k, v in out.items()}
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
+    refs = run_oracle(sub, list(range(len(envs))))
+    _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=30)
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+def test_uneven_full_size_sampled_vjp(torch_cuda, precision, tol_v, tol_j):
+    """The mixed-robot batch at 32768 envs (arm + cube, quadruped, humanoid interleaved), step and
+    VJP with N(0,1) cotangents in one call, sampled (a third of the samples from each model)
+    against the oracle's J^T v_bar."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    B = 32768
+    wl = scenes.uneven(B)
+    sim = ds.Simulator(wl, precision=precision)
+    wbar = np.random.default_rng(13).normal(size=wl.batch.v.shape)
+    out = sim.step_vjp(torch.as_tensor(wbar, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(14)
+    envs = sorted(set([0, 1, 2, B - 3, B - 2, B - 1] + [int(3 * k + r) for r in range(3)
+                                                          for k in rng.choice(B // 3, 16, replace=False)]))
+    g = {k: v[..., envs].cpu().numpy() for k, v in out.items()}
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
+    refs = run_oracle(sub, list(range(len(envs))))
+    assert not (g["status"] & 16).any()
+    _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, jac=False, vjp=wbar[:, envs], min_checked=30)
+
+
+def test_speculative_newton_attempts(torch_cuda):
+    """From round 3 on (the default schedule) every env still iterating gets a Newton / active-set
+    attempt on its iterate, with the contact-mode enumeration as fallback: the slow envs stop far
+    earlier than with attempts only where a stage's tolerance is met, and they reach the same
+    solutions (up to the documented non-unique ones)."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(8000)
+    sim = ds.Simulator(wl, precision="fp64")
+    sim.set_schedule(ds.schedule_index(spec=2))
+    try:
+        ref = {k: v.clone() for k, v in sim.step_jac().items()}
+        sim.set_schedule(ds.schedule_index(spec=0))
+        got = {k: v.clone() for k, v in sim.step_jac().items()}
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
+    _same_solutions(ref, got)
+    it_ref, it_got = ref["iters"].double(), got["iters"].double()
+    assert it_got.mean().item() <= it_ref.mean().item()
+    assert torch.quantile(it_got, 0.999).item() < torch.quantile(it_ref, 0.999).item(), (
+        torch.quantile(it_got, 0.999).item(), torch.quantile(it_ref, 0.999).item())
+    assert ((got["status"] & 1) != 0).sum().item() <= ((ref["status"] & 1) != 0).sum().item()
