@@ -53,6 +53,11 @@ typedef enum {
 } ds_status;
 
 typedef enum { DS_FP64 = 0, DS_MIXED = 1 } ds_precision;
+/* The iteration of the NCP solve (Eq. 1; Sec. 2.2 names both families): DS_ADMM, the relaxed
+ * ADMM with the De Saxce term; DS_PGS, projected Gauss-Seidel sweeps over the contacts (contact i
+ * takes the fixed-point step of Eq. 1 on its own 3x3 block of G with step 1 / lambda_max(G_ii)).
+ * Either iteration is staged with the same Newton polish and FP64 residual acceptance. */
+typedef enum { DS_ADMM = 0, DS_PGS = 1 } ds_solver;
 /* DS_MIXED: kinematics, contact detection, J_c, G and g, the residuals of the NCP polish, the NCP
  * residual check and the reduced implicit system in FP64; dynamics, ADMM iterations, derivative
  * passes and, before an env's last solver stage, the factorisations of the polish's Newton steps
@@ -132,6 +137,7 @@ typedef struct {
                              /* kd (J_c v)_N in g (the term above; the proportional part acts  */
                              /* on penetration only), so it may approach the plane by at most   */
                              /* phi within the step.  Negative or non-finite: DS_EINVAL         */
+  int32_t ncp_solver;        /* ds_solver (default DS_ADMM); other values: DS_EINVAL             */
 } ds_options;
 
 /* Fill *opt with the defaults used by the tests and the benchmark (start from these and set the

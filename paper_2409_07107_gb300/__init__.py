@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libdiffsim.so")
 
 DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED, DS_ETOOLARGE = 0, -1, -2, -3, -4, -5
 DS_FP64, DS_MIXED = 0, 1
+DS_ADMM, DS_PGS = 0, 1
 MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
 ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 1, 2, 4, 8, 16
 
@@ -50,7 +51,7 @@ class ds_options(ctypes.Structure):
                 ("eps_sigma", ctypes.c_double), ("eps_lambda", ctypes.c_double),
                 ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("baumgarte_kp", ctypes.c_double), ("baumgarte_kd", ctypes.c_double),
-                ("contact_margin", ctypes.c_double)]
+                ("contact_margin", ctypes.c_double), ("ncp_solver", ctypes.c_int32)]
 
 
 class ds_step_out(ctypes.Structure):
@@ -254,7 +255,7 @@ def describe_schedule(index):
     return d
 
 
-def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1, spec=0):
+def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1, spec=2):
     """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
     defaults give the library's default schedule."""
     idx, mul = 0, 1

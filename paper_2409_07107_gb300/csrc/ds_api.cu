@@ -31,6 +31,7 @@ extern "C" void ds_options_default(ds_options* o) {
   o->baumgarte_kp = 1.0;
   o->baumgarte_kd = 0.0;
   o->contact_margin = 0.0;
+  o->ncp_solver = DS_ADMM;
 }
 
 extern "C" const char* ds_status_string(ds_status s) {
@@ -180,7 +181,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, 3};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -223,6 +224,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (o->precision != DS_FP64 && o->precision != DS_MIXED) return DS_EINVAL;
   if (!std::isfinite(o->baumgarte_kp) || !std::isfinite(o->baumgarte_kd)) return DS_EINVAL;
   if (!(o->contact_margin >= 0.0) || !std::isfinite(o->contact_margin)) return DS_EINVAL;
+  if (o->ncp_solver != DS_ADMM && o->ncp_solver != DS_PGS) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
   if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels) ||
@@ -243,6 +245,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.c_link = b->c_link; a.c_point = b->c_point; a.c_radius = b->c_radius; a.c_mu = b->c_mu; a.plane = b->plane;
   a.dt = o->dt; a.gx = o->gravity[0]; a.gy = o->gravity[1]; a.gz = o->gravity[2];
   a.bkp = o->baumgarte_kp; a.bkd = o->baumgarte_kd; a.cmargin = o->contact_margin;
+  a.solver = o->ncp_solver;
   a.admm_max_iter = o->admm_max_iter; a.polish_iters = o->polish_iters;
   a.admm_eps = o->admm_eps; a.ncp_tol = o->ncp_tol;
   a.eps_sigma = o->eps_sigma; a.eps_lambda = o->eps_lambda; a.margin_delta = o->margin_delta;

@@ -33,6 +33,10 @@ enum { DS_RUN_STEP = 0, DS_RUN_JAC = 1, DS_RUN_VJP = 2 };
 // arrays over the batch.  Carved out of one caller-provided buffer by ds_workspace_layout().
 #define DS_ROUNDS 9
 
+// Newton steps per pattern of the fallback enumeration (a pattern that is the solution converges
+// quadratically from a nearby iterate; the others are dropped early).
+#define DS_ENUM_NEWTON_ITERS 5
+
 // Mode of the contact of rank `rank` (0 = the largest normal impulse in the iterate) in pattern p
 // of the fallback enumeration: first the 2 na patterns with one contact in contact (sticking, then
 // sliding), then for each pair of ranks (ra < rb, in order) its four sticking / sliding
@@ -151,8 +155,8 @@ struct ds_schedule {
   int reserve;        // overlapped finish: keep off the SMs with smid % reserve == 0 (0 = use all)
   int spec_from;      // from the end of this round on, every env still iterating gets a Newton /
                       // active-set attempt (also when its stage tolerance was not met: it keeps
-                      // its stage if the attempt fails), and a failed attempt falls back to
-                      // enumerating the contact-mode patterns with one or two contacts in
+                      // its stage if the attempt fails); in this round a failed attempt falls
+                      // back to enumerating the contact-mode patterns with one or two contacts in
                       // contact (DS_ROUNDS = never)
 };
 
@@ -170,6 +174,7 @@ struct KArgs {
   double dt, gx, gy, gz;
   double bkp, bkd;         // Baumgarte gains (App. D); 1, 0 (and no margin): no term
   double cmargin;          // activation distance: a slot is active when phi <= cmargin
+  int solver;              // ds_solver: the NCP iteration (ADMM or projected Gauss-Seidel)
   int admm_max_iter, polish_iters;
   double admm_eps, ncp_tol, eps_sigma, eps_lambda, margin_delta;
   double *v_next, *q_next, *lambda;

@@ -371,9 +371,88 @@ DS_HDI void admm_update(const T (*Kr)[NC3], const T* rhs_full, const T* rhs_own,
   }
 }
 
+// Largest eigenvalue of a symmetric 3x3 matrix (row-major), from the trigonometric solution of its
+// characteristic cubic (O. K. Smith, "Eigenvalues of a symmetric 3x3 matrix", Commun. ACM 4(4),
+// 1961): with q = tr/3 and p the scaled deviation, the eigenvalues are q + 2 p cos(phi + 2 pi k/3),
+// phi = acos(det((a - q I)/p)/2)/3, and k = 0 gives the largest.
+template <typename T>
+DS_HDI T sym3_max_eig(const T* a) {
+  const T p1 = a[1] * a[1] + a[2] * a[2] + a[5] * a[5];
+  const T q = (a[0] + a[4] + a[8]) / T(3);
+  const T d0 = a[0] - q, d1 = a[4] - q, d2 = a[8] - q;
+  const T p2 = d0 * d0 + d1 * d1 + d2 * d2 + T(2) * p1;
+  if (!(p2 > T(0))) return q;
+  const T pp = sqrt(p2 / T(6));
+  const T ip = T(1) / pp;
+  const T b00 = d0 * ip, b11 = d1 * ip, b22 = d2 * ip, b01 = a[1] * ip, b02 = a[2] * ip, b12 = a[5] * ip;
+  T r = (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02)) / T(2);
+  r = fmin(T(1), fmax(T(-1), r));
+  return q + T(2) * pp * cos(acos(r) / T(3));
+}
+
+// Projected Gauss-Seidel on Eq. 1 (the solver family named beside ADMM in Sec. 2.2): a sweep
+// visits the active contacts in order; contact i takes the fixed-point step of Eq. 1 restricted
+// to its own block, lambda_i <- Proj_K(lambda_i - (sigma_i + Gamma_i(sigma_i)) / r_i), sigma =
+// G lambda + g at the current (partly updated) lambda, r_i = lambda_max(G_ii) (the step that makes
+// the local map non-expansive).  Its fixed points are those of Eq. 1 (Moreau).  A sweep counts as
+// one iteration; it has converged when it moved lambda by at most te max(1, |lambda|_inf).  z is
+// the iterate, as for the ADMM (the Newton stage reads it).
+template <int NS, typename T>
+struct Pgs {
+  static constexpr int NC3 = 3 * NS;
+  static constexpr int kCheck = 1;             // the stopping test runs after every sweep
+  T z[NC3];
+  T ir[NS];
+
+  template <class P>
+  DS_HD bool setup(const P& p) {
+    bool ok = true;
+    for (int i = 0; i < p.na; ++i) {
+      T blk[9];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) blk[3 * r + c] = p.Gt[3 * i + r][3 * i + c];
+      const T lm = sym3_max_eig(blk);
+      ok = ok && lm > T(0);
+      ir[i] = lm > T(0) ? T(1) / lm : T(0);
+    }
+    return ok;
+  }
+
+  template <class P>
+  DS_HD void reset(const P& p) {
+    for (int i = 0; i < NC3; ++i) z[i] = T(0);
+  }
+
+  template <class P>
+  DS_HD bool iterate(const P& p, T te, bool check) {
+    const int m = 3 * p.na;
+    T dmax = T(0), lmax = T(1);
+    for (int i = 0; i < p.na; ++i) {
+      T sg[3];
+      for (int k = 0; k < 3; ++k) {
+        T t = p.gt[3 * i + k];
+        for (int j = 0; j < m; ++j) t += p.Gt[3 * i + k][j] * z[j];
+        sg[k] = t;
+      }
+      const T mu = T(p.mu[i]);
+      const T nt = sqrt(sg[0] * sg[0] + sg[1] * sg[1]);
+      const T x[3] = {z[3 * i] - sg[0] * ir[i], z[3 * i + 1] - sg[1] * ir[i], z[3 * i + 2] - (sg[2] + mu * nt) * ir[i]};
+      T o[3];
+      proj_cone(x, mu, o);
+      for (int k = 0; k < 3; ++k) {
+        dmax = fmax(dmax, fabs(o[k] - z[3 * i + k]));
+        z[3 * i + k] = o[k];
+        lmax = fmax(lmax, fabs(o[k]));
+      }
+    }
+    return check && dmax <= te * lmax;
+  }
+};
+
 template <int NS, typename T>
 struct Admm {
   static constexpr int NC3 = 3 * NS;
+  static constexpr int kCheck = DS_ADMM_CHECK;   // the stopping test runs on every 4th iteration
   T K[NC3][NC3];
   T rho, gs, inv_rho;
   T inv1pmu2[NS];
@@ -440,8 +519,9 @@ DS_HDI int num_stages() { return std::is_same<T, double>::value ? 4 : 3; }
 
 // End of an ADMM stage: identify the modes from z and run up to 4 active-set rounds of FP64 Newton
 // on the mode equations; keeps the best candidate (by FP64 NCP residual).  With `enumerate` (the
-// late rounds of a schedule with speculative attempts), a failure falls back to the patterns of
-// enum_mode: Newton on each pattern's mode equations from z, in order, until one passes.  Returns
+// first round of speculative attempts), a failure falls back to the patterns of enum_mode: at most
+// DS_ENUM_NEWTON_ITERS Newton steps on each pattern's mode equations from z, in order, until one
+// passes.  Returns
 // true when the best candidate passes the residual check.
 template <class P, typename T>
 DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* best, double& best_r,
@@ -483,7 +563,7 @@ DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* be
     for (int pat = 0; pat < npat && best_r > tol; ++pat) {
       for (int i = 0; i < p.na; ++i) mode[i] = enum_mode(pat, rank[i], p.na);
       for (int i = 0; i < m; ++i) lp[i] = lz[i];
-      newton_modes(p, lp, mode, a.polish_iters, sat_delta);
+      newton_modes(p, lp, mode, DS_ENUM_NEWTON_ITERS, sat_delta);
       const double rpol = ncp_residual(p, lp);
       if (rpol < best_r) { best_r = rpol; for (int i = 0; i < m; ++i) best[i] = lp[i]; }
     }
@@ -492,19 +572,17 @@ DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* be
 }
 
 // Staged NCP solve in one thread, in the rounds of the pipeline's schedule: each round continues
-// the ADMM iteration for at most the round's cap (the last round: to the iteration limit) or until
-// the stage tolerance is met, then runs the Newton / active-set stage on the iterate; the first
-// candidate whose FP64 NCP residual passes is accepted.  A stage that ended without acceptance
-// moves to the next (tighter) stage; from the schedule's speculative round on, an unconverged
-// round's iterate is tried too (with the enumeration fallback) and the stage is kept.  So the fused
-// kernel reaches the same impulse as the pipeline under the same schedule.  When the free motion separates every contact, lambda stays 0
-// (see separating()).
-template <class P, typename T>
-DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
+// the iteration It (ADMM or PGS) for at most the round's cap (the last round: to the iteration
+// limit) or until the stage tolerance is met, then runs the Newton / active-set stage on the
+// iterate; the first candidate whose FP64 NCP residual passes is accepted.  A stage that ended
+// without acceptance moves to the next (tighter) stage; from the schedule's speculative round on,
+// an unconverged round's iterate is tried too and the stage is kept.  So the fused kernel reaches
+// the same impulse as the pipeline under the same schedule.  When the free motion separates every
+// contact, lambda stays 0 (see separating()).
+template <class It, class P, typename T>
+DS_HD void solve_ncp_with(P& s, const KArgs& a, int& iters, uint32_t& st) {
   const int m = 3 * s.na;
-  iters = 0;
-  if (m == 0 || separating(s)) return;
-  Admm<P::NC3 / 3, T> ad;
+  It ad;
   if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
   ad.reset(s);
   double best[P::NC3], best_r = 1e300;
@@ -520,12 +598,12 @@ DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
     bool conv = false;
     for (int k = 0; k < lim && iters < a.admm_max_iter; ++k) {
       ++iters;
-      if (ad.iterate(s, te, iters % DS_ADMM_CHECK == 0)) { conv = true; break; }
+      if (ad.iterate(s, te, iters % It::kCheck == 0)) { conv = true; break; }
     }
     const bool ended = conv || iters >= a.admm_max_iter || final_round;
     const bool late = r >= a.sched.spec_from;
     if (!ended && !late) continue;
-    ok = newton_stage(s, ad.z, eps, a, best, best_r, late);
+    ok = newton_stage(s, ad.z, eps, a, best, best_r, r == a.sched.spec_from);
     if (ok) break;
     if (ended) {
       if (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || final_round) break;
@@ -534,6 +612,14 @@ DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
   }
   for (int i = 0; i < m; ++i) s.lam[i] = best[i];
   if (!ok) st |= DS_ENV_NOT_CONVERGED;
+}
+
+template <class P, typename T>
+DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
+  iters = 0;
+  if (s.na == 0 || separating(s)) return;
+  if (a.solver == DS_PGS) solve_ncp_with<Pgs<P::NC3 / 3, T>, P, T>(s, a, iters, st);
+  else solve_ncp_with<Admm<P::NC3 / 3, T>, P, T>(s, a, iters, st);
 }
 
 }  // namespace ds
@@ -1491,11 +1577,13 @@ DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
     if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
     for (int i = 0; i < s.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
   } else if (mm > 0 && !(st & DS_ENV_NONFINITE)) {
-    Admm<NS, T> ad;
-    if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
-    w.rho[e] = double(ad.rho);
-    for (int i = 0; i < NC3; ++i)
-      for (int j = 0; j < NC3; ++j) w.K[(i * NC3 + j) * B + e] = double(ad.K[i][j]);
+    if (a.solver == DS_ADMM) {
+      Admm<NS, T> ad;
+      if (!ad.setup(s)) st |= DS_ENV_NONFINITE;
+      w.rho[e] = double(ad.rho);
+      for (int i = 0; i < NC3; ++i)
+        for (int j = 0; j < NC3; ++j) w.K[(i * NC3 + j) * B + e] = double(ad.K[i][j]);
+    }
     if (!(st & DS_ENV_NONFINITE)) {
       const int k = ds_atomic_add(&w.counts[0], 1);
       w.list[0][k] = e;
@@ -1945,6 +2033,55 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
 
 // 2b. the Newton / active-set stage for the envs whose ADMM stage ended in this round (one thread
 //     per env): accept, or move to the next (tighter) stage and queue for the next round.
+// 2a''. one round of projected Gauss-Seidel (the ds_options ncp_solver = DS_PGS form of the NCP
+//       iteration), one thread per env: loads the env's contact problem and iterate, runs at most
+//       round_cap sweeps (or to the stage tolerance), stores the iterate and routes the env like
+//       the ADMM rounds.
+template <int NS, typename T>
+struct PgsData {
+  static constexpr int NC3 = 3 * NS;
+  int na;
+  double mu[NS];
+  T Gt[NC3][NC3], gt[NC3];
+};
+
+template <int NS, typename T>
+__global__ void __launch_bounds__(128) pgs_round_kernel(KArgs a) {
+  const WsView& w = a.ws;
+  const int n = w.counts[a.round];
+  const int B = a.B;
+  const int32_t* cur = w.list[a.round & 1];
+  int32_t* next = w.list[(a.round + 1) & 1];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int e = cur[t];
+    PgsData<NS, T> d;
+    d.na = w.na[e];
+    const int m = 3 * d.na;
+    for (int i = 0; i < d.na; ++i) d.mu[i] = w.mu[i * B + e];
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j <= i; ++j) {
+        const T gij = T(w.G[tri(i, j) * B + e]);
+        d.Gt[i][j] = gij;
+        d.Gt[j][i] = gij;
+      }
+      d.gt[i] = T(w.g[i * B + e]);
+    }
+    Pgs<NS, T> it;
+    it.setup(d);
+    for (int i = 0; i < m; ++i) it.z[i] = T(w.az[i * B + e]);
+    int iters = w.iters[e];
+    const T te = T(stage_eps<T>(a, w.stage[e]));
+    bool conv = false;
+    for (int k = 0; k < a.round_cap && iters < a.admm_max_iter; ++k) {
+      ++iters;
+      if (it.iterate(d, te, true)) { conv = true; break; }
+    }
+    for (int i = 0; i < m; ++i) w.az[i * B + e] = double(it.z[i]);
+    w.iters[e] = iters;
+    route_after_round(a, e, conv, iters, next);
+  }
+}
+
 template <int NS, typename T>
 DS_HD void newton_env(const KArgs& a, const int entry) {
   // entry = e: the env's ADMM stage ended; ~e: a speculative attempt on an unconverged iterate
@@ -1974,7 +2111,7 @@ DS_HD void newton_env(const KArgs& a, const int entry) {
   double best[3 * NS], best_r = w.best_r[e];
   for (int i = 0; i < m; ++i) best[i] = w.lam[i * B + e];
   const double eps = stage_eps<T>(a, stage);
-  const bool ok = newton_stage(p, z, eps, a, best, best_r, a.round >= a.sched.spec_from);
+  const bool ok = newton_stage(p, z, eps, a, best, best_r, a.round == a.sched.spec_from);
   for (int i = 0; i < m; ++i) w.lam[i * B + e] = best[i];
   if (ok || (!spec && (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round))) {
     for (int i = 0; i < m; ++i) p.lam[i] = best[i];

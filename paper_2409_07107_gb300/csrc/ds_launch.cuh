@@ -53,6 +53,12 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   int rblocks = ds_sm_count() * per_sm;
   const int need = (a0.n_env + envs_per_block - 1) / envs_per_block;
   if (rblocks > need) rblocks = need;
+  // the PGS round kernel (ncp_solver = DS_PGS): one thread per env
+  int gper = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, pgs_round_kernel<NS, T>, threads, 0);
+  if (gper <= 0) gper = 1;
+  int gblocks = ds_sm_count() * gper;
+  if (gblocks > blocks) gblocks = blocks;
   // the row-per-lane ADMM kernel for the late rounds (where the schedule says so and 3 NS <= 32)
   constexpr bool kWideOk = WideShape<NS>::kOk;
   int wblocks = 1;
@@ -114,17 +120,18 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     const int cap = ds_round_cap(table, r);
     a.round_cap = a.final_round ? (a0.admm_max_iter > cap ? a0.admm_max_iter : cap) : cap;
     ds_trace_mark(DS_STAGE_ADMM, 1, s);
-    bool wide = false;
+    bool done = a0.solver == DS_PGS;
+    if (done) pgs_round_kernel<NS, T><<<gblocks, threads, 0, s>>>(a);
     if constexpr (kPairOk) {
-      if (r >= sc.pair_from) { admm_round_pair_kernel<NS, T><<<pblocks, 64, 0, s>>>(a); wide = true; }
+      if (!done && r >= sc.pair_from) { admm_round_pair_kernel<NS, T><<<pblocks, 64, 0, s>>>(a); done = true; }
     }
     if constexpr (kWideOk) {
-      if (!wide && r >= sc.wide_from) {
+      if (!done && r >= sc.wide_from) {
         admm_round_wide_kernel<NS, T><<<wblocks, threads, 0, s>>>(a);
-        wide = true;
+        done = true;
       }
     }
-    if (!wide) admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
+    if (!done) admm_round_kernel<NS, T><<<rblocks, threads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_ADMM, 0, s);
     ds_trace_mark(DS_STAGE_NEWTON, 1, s);
     bool launched = false;

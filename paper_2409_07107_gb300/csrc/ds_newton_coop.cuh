@@ -524,7 +524,7 @@ __device__ bool newton_stage(Smem<NS, T>& S, const Lane<NS>& ln, double lz, doub
     for (int pat = 0; __any_sync(kFull, eg); ++pat) {
       if (pat >= npat) eg = false;
       const int pm = (ln.ci < ln.na && pat < npat) ? enum_mode(pat, rank, ln.na) : DS_MODE_BREAKING;
-      const double lq = newton_modes<NS, double>(S, S.d, ln, lz, pm, a.polish_iters, sat_delta, eg);
+      const double lq = newton_modes<NS, double>(S, S.d, ln, lz, pm, DS_ENUM_NEWTON_ITERS, sat_delta, eg);
       const double rq = residual<NS>(S, ln, lq);
       if (eg && rq < best_r) { best_r = rq; best_l = lq; }
       if (eg && best_r <= tol) eg = false;
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
     const double eps = stage_eps<T>(a, stage);
     const bool last = !spec && (iters >= a.admm_max_iter || stage + 1 >= num_stages<T>() || a.final_round);
     const bool ok = coop::newton_stage<NS, T>(S, ln, lz, eps, a, best_l, best_r, have && m > 0, last,
-                                              a.round >= a.sched.spec_from);
+                                              a.round == a.sched.spec_from);
     if (mine) w.lam[ln.li * B + e] = best_l;
     const bool fin = ok || last;
     int mode;

@@ -524,3 +524,25 @@ def test_speculative_newton_attempts(torch_cuda):
     assert torch.quantile(it_got, 0.999).item() < torch.quantile(it_ref, 0.999).item(), (
         torch.quantile(it_got, 0.999).item(), torch.quantile(it_ref, 0.999).item())
     assert ((got["status"] & 1) != 0).sum().item() <= ((ref["status"] & 1) != 0).sum().item()
+
+
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+@pytest.mark.parametrize("pipeline", [True, False])
+def test_pgs_solver(torch_cuda, precision, tol_v, tol_j, pipeline):
+    """The projected Gauss-Seidel form of the NCP iteration (ncp_solver = DS_PGS), with the same
+    Newton polish and FP64 residual acceptance: v+, modes and the Jacobians against the oracle
+    (whose second route is PGS), in the pipeline (ragged batch of 300) and in the fused kernel."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(65536)
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(np.arange(300)), wl.options)
+    sim = ds.Simulator(sub, precision=precision, pipeline=pipeline, ncp_solver=ds.DS_PGS)
+    out = sim.step_jac()
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    assert (g["iters"] > 0).sum() > 200
+    envs = list(range(0, 300, 3))
+    refs = run_oracle(sub, envs)
+    _compare(sub, g, refs, envs, tol_v, tol_j, min_checked=60)
+    if precision == "fp64":
+        assert not (g["status"] & 1).any()
