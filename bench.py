@@ -26,6 +26,22 @@ sys.path.insert(0, ROOT)
 from paper_2409_07107_gb300 import replicas, scenes  # noqa: E402
 
 WORKLOAD_B = 65536
+
+# DRAM bytes (read + write) per env and launch of the FP64 ADMM round kernels on the arm + cube
+# workload, from one ncu capture of a default-schedule step at 16384 envs (nine launches, 117.2 MB);
+# the workspace traffic grows with the envs.  Valid only for the kernel sources it was taken on.
+ADMM_TRAFFIC = {"bytes_per_env_launch": 117.2e6 / 9 / 16384,
+                "sources_sha256_16": {"ds_kernel.cuh": "2b4374f85ab650f4", "ds_common.cuh": "c6a81f42512c998f"}}
+
+
+def _admm_traffic_valid():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2409_07107_gb300", "csrc")
+    for f, h in ADMM_TRAFFIC["sources_sha256_16"].items():
+        with open(os.path.join(csrc, f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
+                return False
+    return True
 METRIC = "env-steps/s with full dv'/d(q,v,tau) at 1 GB300"
 METRIC_VJP = "env-steps/s with the VJP of the step at 1 GB300"
 
@@ -574,12 +590,18 @@ def main():
             key = "".join("bks"[int(x)] for x in sorted(modes[:, e]) if x != 3) or "-"
             pat[key] = pat.get(key, 0) + 1
         snaps[prec] = {k: v[..., :1024].cpu().numpy() for k, v in one_out.items()}
+        traffic = None
+        if prec == "fp64" and wl_name == "arm7-cube" and _admm_traffic_valid():
+            traffic = ADMM_TRAFFIC["bytes_per_env_launch"] * B
         results[prec] = dict(
             ms=ms, value=replicas.job_throughput(B, world, ms), clocks=clk.summary(), schedule=schedule,
             graph={"value": B * world / (float(np.mean(gtimes)) * 1e-3), "ms_per_step": float(np.mean(gtimes))},
             roofline={"bound": "alu", "kernel": "admm_round_kernel (ADMM rounds, one lane per contact)",
                       "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                      "traffic": None,
+                      "traffic": traffic,
+                      "traffic_note": "DRAM read + write bytes per ADMM launch, from an ncu capture at "
+                                      "16384 envs scaled to this batch (null unless the kernels are "
+                                      "the captured ones)",
                       "peak_source": "measured FMA probe (%s CUDA cores) in this run" % ("FP64" if prec == "fp64" else "FP32"),
                       "algorithmic_gflop_per_step": admm_flops / 1e9,
                       "launches_per_step": stage_launches.get("admm"),
