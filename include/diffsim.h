@@ -154,11 +154,15 @@ typedef struct {
 } ds_step_out;
 
 /* Bytes of device workspace that sim_step / sim_step_jac / sim_step_vjp can use for this batch
- * (about 1.4 KB per env with 4 contact slots).  With a workspace the step runs as a pipeline of
+ * (about 6.3 KB per env for the 7-dof arm with 4 contact slots, 2.4 KB of it the contact
+ * problem and the solver state, the rest the forward quantities the setup keeps for the finish;
+ * about 30 KB for the 36-dof humanoid with 8).  With a workspace the step runs as a pipeline of
  * kernels (setup, NCP solve in compacted ADMM rounds, finish) that keeps warps busy when the
  * per-env iteration counts differ; without one (workspace = NULL) a single fused kernel does
  * everything.  Both compute the same step; they differ only by rounding (the NCP solve is
- * organised differently across kernels).  Errors: DS_EINVAL. */
+ * organised differently across kernels).  The size depends on the models (their forward state)
+ * and the batch.  Errors: DS_EINVAL (a NULL model among them, or a model with no compiled kernel for
+ * its contact slots). */
 ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                             const ds_options* opt, size_t* bytes);
 
@@ -235,7 +239,7 @@ ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t nmodels, in
  * (16 MiB) that the library holds on every device that loads it, until the process exits.  It
  * calls no cudaMalloc / cudaFree and no allocating routine.
  *   - Batches whose ds_workspace_size() exceeds the array are rejected with DS_ETOOLARGE
- *     (about 6900 envs of the 7-dof arm with 4 contact slots).
+ *     (about 2650 envs of the 7-dof arm with 4 contact slots).
  *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress);
  *     make that first call outside any stream capture.
  *   - Every call shares the one array and leaves its contents behind; the counters that must

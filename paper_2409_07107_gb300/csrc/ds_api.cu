@@ -133,11 +133,29 @@ extern "C" ds_status ds_model_dims(const ds_model* m, int32_t* nb, int32_t* nq, 
   return DS_OK;
 }
 
+// Rows of forward state per env in the workspace: the most any model of the batch needs (each env
+// uses its own model's rows).  -1 when a model is missing or has no kernel for its slots.
+static int forward_rows(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o) {
+  int rows = 0;
+  for (int k = 0; k < nmodels; ++k) {
+    if (!models[k]) return -1;
+    const int slots = b->model_slots ? b->model_slots[k] : b->ncmax;
+    if (slots < 0 || slots > b->ncmax) return -1;
+    const ds_kernel_entry* ke = ds_fit_kernel(models[k]->host.nb, models[k]->host.nv, slots, b->ncmax, o->precision);
+    if (!ke) return -1;
+    const int r = ds_forward_rows(ke->nb, ke->nv, ke->ns);
+    if (r > rows) rows = r;
+  }
+  return rows;
+}
+
 extern "C" ds_status ds_workspace_size(const ds_model* const* models, int32_t nmodels, const ds_batch* b,
                                        const ds_options* o, size_t* bytes) {
   if (!models || nmodels <= 0 || !b || !o || !bytes) return DS_EINVAL;
   if (b->B < 0 || b->ncmax < 0 || b->ncmax > DS_MAXSLOTS) return DS_EINVAL;
-  *bytes = ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels);
+  const int fw = forward_rows(models, nmodels, b, o);
+  if (fw < 0) return DS_EINVAL;
+  *bytes = ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels, 0, fw);
   return DS_OK;
 }
 
@@ -227,17 +245,20 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (o->ncp_solver != DS_ADMM && o->ncp_solver != DS_PGS) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
-  if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels) ||
-             (reinterpret_cast<uintptr_t>(ws) & 255) != 0))
-    return DS_EINVAL;
   const ds_kernel_entry* kern[64];
+  int fw_rows = 0;
   for (int k = 0; k < nmodels; ++k) {
     if (!models[k]) return DS_EINVAL;
     const int slots = b->model_slots ? b->model_slots[k] : b->ncmax;
     if (slots < 0 || slots > b->ncmax) return DS_EINVAL;
     kern[k] = ds_fit_kernel(models[k]->host.nb, models[k]->host.nv, slots, b->ncmax, o->precision);
     if (!kern[k]) return DS_EUNSUPPORTED;
+    const int r = ds_forward_rows(kern[k]->nb, kern[k]->nv, kern[k]->ns);
+    if (r > fw_rows) fw_rows = r;
   }
+  if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels, 0, fw_rows) ||
+             (reinterpret_cast<uintptr_t>(ws) & 255) != 0))
+    return DS_EINVAL;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.B = b->B; a.ncmax = b->ncmax;
@@ -283,7 +304,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
     for (int k = 0; k < nmodels; ++k) {
       cudaStream_t sk = hs->s[k % kHelperStreams];
       if (cudaStreamWaitEvent(sk, hs->fork, 0) != cudaSuccess) return DS_ECUDA;
-      ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k);
+      ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k, fw_rows);
       a.model = models[k]->dev;
       a.model_index = k;
       a.side = hs->s[kHelperStreams + k % kHelperStreams];
@@ -305,7 +326,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   }
   for (int k = 0; k < nmodels; ++k) {
     const ds_kernel_entry* ke = kern[k];
-    if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k);
+    if (ws) ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, k, fw_rows);
     a.model = models[k]->dev;
     a.model_index = k;
     if (ws) ke->pipeline(a, s);

@@ -63,6 +63,12 @@ DS_HDI int ds_round_cap(int table, int r) {
   const int c = r == 0 ? base : base << (r - 1);
   return c > 4096 ? 4096 : c;
 }
+// Rows (of B doubles) of the forward state that a pipeline step keeps per env from its setup for
+// its finish, for a model of nb bodies, nv dofs and ns contact slots (order: FwLayout).
+DS_HDI int ds_forward_rows(int nb, int nv, int ns) {
+  return 8 * nv + 28 * nb + nv * (nv + 1) / 2 + 6 * ns * nv + 9 * ns;
+}
+
 struct WsView {
   int32_t* counts;        // [DS_ROUNDS + 1] envs queued for each round
   int32_t* list[2];       // [B] ping-pong work lists of env indices
@@ -79,6 +85,7 @@ struct WsView {
   double *ax, *az, *ay, *asx;  // [NC3][B] ADMM state
   double* K;              // [NC3 NC3][B] (G + rho I)^-1, row-major
   double* rho;            // [B]
+  double* fw;             // [forward rows][B] the setup's forward state, read by the finish
   int32_t* nlist;         // [B] envs whose ADMM stage ended in a round (Newton queue)
   int32_t* ncounts;       // [DS_ROUNDS]
   int32_t* fetch;         // [DS_ROUNDS] next unclaimed entry of each round's list (follows ncounts)
@@ -87,11 +94,12 @@ struct WsView {
   int32_t* claim;         // [1] next unclaimed work item of the overlapped finish (follows dcount)
 };
 
-// Lays out the workspace for ns contact slots, B envs and nmodels models starting at base (may be
-// NULL to size it), and returns its size.  The per-env arrays are shared; every model has its own
+// Lays out the workspace for ns contact slots, B envs, nmodels models and fw_rows rows of forward
+// state per env starting at base (may be NULL to size it), and returns its size.  The per-env arrays are shared; every model has its own
 // work lists and counters (its pipeline may run concurrently with the others'), and *v gets those
 // of model `model`.
-inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmodels = 1, int model = 0) {
+inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmodels = 1, int model = 0,
+                                  int fw_rows = 0) {
   const int nc3 = 3 * ns;
   size_t off = 0;
   char* b = static_cast<char*>(base);
@@ -117,6 +125,7 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
   w.asx = static_cast<double*>(take(sizeof(double) * nc3 * size_t(B)));
   w.K = static_cast<double*>(take(sizeof(double) * nc3 * nc3 * size_t(B)));
   w.rho = static_cast<double*>(take(sizeof(double) * size_t(B)));
+  w.fw = static_cast<double*>(take(sizeof(double) * size_t(fw_rows) * size_t(B)));
   for (int k = 0; k < nmodels; ++k) {
     int32_t* counts = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_ROUNDS + 1)));
     int32_t* l0 = static_cast<int32_t*>(take(sizeof(int32_t) * B));

@@ -768,8 +768,7 @@ DS_HDI T baumgarte_d(const DevModel& m, const KArgs& a, const Env<NB, NV, NS, T>
 
 // F1-F6 for env e: kinematics, dynamics, contact detection, J_c, G, g.  Returns status bits.
 template <int NB, int NV, int NS, typename T>
-DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s,
-                           bool lite = false) {
+DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s) {
   const int B = a.B;
   uint32_t st = 0;
   double* q = s.q;
@@ -1018,20 +1017,6 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
   }
 
   // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms).
-  // lite: g only (a caller that reads G from the workspace and applies M^-1 by solves)
-  if (lite) {
-    for (int r = 0; r < mdim; ++r) {
-      double t = 0.0;
-      for (int k = 0; k < NV; ++k) t += Jd[r][k] * double(s.vf[k]);
-      s.gt[r] = T(t);
-      s.gd[r] = t;
-    }
-    baumgarte_g(a, e, Jd, s);
-    if constexpr (!kD)
-      for (int r = 0; r < mdim; ++r)
-        for (int k = 0; k < NV; ++k) s.Jc[r][k] = T(Jd[r][k]);
-    return st;
-  }
   for (int r = 0; r < mdim; ++r) {
     for (int k = 0; k < NV; ++k) Yd[r][k] = Jd[r][k];
     fwd_packed(Ld, Yd[r], NV);
@@ -1056,6 +1041,119 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     for (int r = 0; r < mdim; ++r)
       for (int k = 0; k < NV; ++k) { s.Jc[r][k] = T(Jd[r][k]); s.Y[r][k] = T(Yd[r][k]); }
   return st;
+}
+
+// The forward state a pipeline step keeps per env from its setup for its finish, as rows of the
+// workspace's fw array (row r of env e at fw[r * B + e]), in this order: vdf, v_f (NV each), the
+// world motion subspaces S (6 NV), the world spatial inertias I (10 NB), the bias pass's body
+// velocities V, joint velocities VJ and momenta I V (6 NB each), M's packed factor L, the rows of
+// J_c and of M^-1 J_c^T (NC3 x NV each, active contacts first), and per contact slot of the
+// active list its body point x (3), contact point c (3), signed distance, slot and body.  Stored
+// in FP64 whatever the bulk type (exact for FP32 values).  ds_forward_rows counts the same rows.
+template <int NB, int NV, int NS>
+struct FwLayout {
+  static constexpr int NC3 = 3 * NS, NL = NV * (NV + 1) / 2;
+  static constexpr int vdf = 0, vf = NV, S = 2 * NV, I = 8 * NV, V = I + 10 * NB, VJ = V + 6 * NB, IV = VJ + 6 * NB;
+  static constexpr int L = IV + 6 * NB, Jc = L + NL, Y = Jc + NC3 * NV, C = Y + NC3 * NV;
+  static constexpr int rows = C + 9 * NS;
+};
+
+template <int NB, int NV, int NS, typename T>
+DS_HD void store_forward(const KArgs& a, const int e, const Env<NB, NV, NS, T>& s) {
+  using F = FwLayout<NB, NV, NS>;
+  static_assert(F::rows == 8 * NV + 28 * NB + NV * (NV + 1) / 2 + 6 * NS * NV + 9 * NS, "forward rows");
+  const int B = a.B;
+  double* fw = a.ws.fw;
+  auto put = [&](int r, double x) { fw[size_t(r) * B + e] = x; };
+  for (int k = 0; k < NV; ++k) { put(F::vdf + k, double(s.vdf[k])); put(F::vf + k, double(s.vf[k])); }
+  for (int d = 0; d < NV; ++d)
+    for (int k = 0; k < 6; ++k) put(F::S + 6 * d + k, double(s.S[d][k]));
+  for (int i = 0; i < NB; ++i) {
+    for (int k = 0; k < 10; ++k) put(F::I + 10 * i + k, double(s.I[i][k]));
+    for (int k = 0; k < 6; ++k) {
+      put(F::V + 6 * i + k, double(s.V[i][k]));
+      put(F::VJ + 6 * i + k, double(s.VJ[i][k]));
+      put(F::IV + 6 * i + k, double(s.IV[i][k]));
+    }
+  }
+  for (int k = 0; k < F::NL; ++k) put(F::L + k, double(s.L[k]));
+  const int mdim = 3 * s.na;
+  for (int r = 0; r < mdim; ++r)
+    for (int k = 0; k < NV; ++k) { put(F::Jc + r * NV + k, double(s.Jc[r][k])); put(F::Y + r * NV + k, double(s.Y[r][k])); }
+  for (int ac = 0; ac < s.na; ++ac) {
+    const int r0 = F::C + 9 * ac;
+    for (int k = 0; k < 3; ++k) { put(r0 + k, double(s.x[ac][k])); put(r0 + 3 + k, double(s.c[ac][k])); }
+    put(r0 + 6, s.phi[ac]);
+    put(r0 + 7, double(s.slot[ac]));
+    put(r0 + 8, double(s.body[ac]));
+  }
+}
+
+// The finish's Env from the inputs, the contact problem in the workspace and the forward state the
+// setup stored (instead of recomputing F1-F6): q, v, tau, the active contacts, mu, G, g, the
+// contact frame and the fields store_forward wrote.
+template <int NB, int NV, int NS, typename T>
+DS_HD void load_forward(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s) {
+  using F = FwLayout<NB, NV, NS>;
+  const int B = a.B;
+  const WsView& w = a.ws;
+  const double* fw = w.fw;
+  auto get = [&](int r) { return fw[size_t(r) * B + e]; };
+  for (int i = 0; i < m.nq; ++i) s.q[i] = a.q[i * B + e];
+  for (int k = 0; k < NV; ++k) {
+    s.v[k] = T(a.v[k * B + e]);
+    s.tau[k] = T(a.tau[k * B + e]);
+    s.vdf[k] = T(get(F::vdf + k));
+    s.vf[k] = T(get(F::vf + k));
+  }
+  for (int d = 0; d < NV; ++d)
+    for (int k = 0; k < 6; ++k) s.S[d][k] = T(get(F::S + 6 * d + k));
+  for (int i = 0; i < NB; ++i) {
+    for (int k = 0; k < 10; ++k) s.I[i][k] = T(get(F::I + 10 * i + k));
+    for (int k = 0; k < 6; ++k) {
+      s.V[i][k] = T(get(F::V + 6 * i + k));
+      s.VJ[i][k] = T(get(F::VJ + 6 * i + k));
+      s.IV[i][k] = T(get(F::IV + 6 * i + k));
+    }
+  }
+  for (int k = 0; k < F::NL; ++k) s.L[k] = T(get(F::L + k));
+  s.na = w.na[e];
+  const int mdim = 3 * s.na;
+  for (int r = 0; r < mdim; ++r)
+    for (int k = 0; k < NV; ++k) { s.Jc[r][k] = T(get(F::Jc + r * NV + k)); s.Y[r][k] = T(get(F::Y + r * NV + k)); }
+  for (int ac = 0; ac < s.na; ++ac) {
+    const int r0 = F::C + 9 * ac;
+    for (int k = 0; k < 3; ++k) {
+      s.x[ac][k] = T(get(r0 + k));
+      s.c[ac][k] = T(get(r0 + 3 + k));
+      s.cx_d[ac][k] = get(r0 + 3 + k);
+    }
+    s.phi[ac] = get(r0 + 6);
+    s.slot[ac] = int(get(r0 + 7));
+    s.body[ac] = int(get(r0 + 8));
+    s.mu[ac] = w.mu[ac * B + e];
+  }
+  // contact frame rows t1, t2, n from the plane normal (as in the forward pass)
+  const double pn[3] = {a.plane[0 * B + e], a.plane[1 * B + e], a.plane[2 * B + e]};
+  const bool use_y = fabs(pn[0]) > 0.9;
+  double t1[3] = {use_y ? 0.0 : 1.0, use_y ? 1.0 : 0.0, 0.0};
+  const double dn = t1[0] * pn[0] + t1[1] * pn[1];
+  for (int k = 0; k < 3; ++k) t1[k] -= dn * pn[k];
+  const double nn = 1.0 / sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int k = 0; k < 3; ++k) t1[k] *= nn;
+  double t2[3];
+  cross3(pn, t1, t2);
+  for (int k = 0; k < 3; ++k) { s.fr[0][k] = T(t1[k]); s.fr[1][k] = T(t2[k]); s.fr[2][k] = T(pn[k]); }
+  for (int i = 0; i < mdim; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      const double gij = w.G[tri(i, j) * B + e];
+      s.Gt[i][j] = T(gij);
+      s.Gt[j][i] = T(gij);
+      if constexpr (!Env<NB, NV, NS, T>::kDouble) { s.Gd_[i][j] = gij; s.Gd_[j][i] = gij; }
+    }
+    s.gd[i] = w.g[i * B + e];
+    s.gt[i] = T(s.gd[i]);
+  }
 }
 
 // F9 and, on request, B1-B7 for env e, given lambda and the modes of its active contacts.
@@ -1111,9 +1209,7 @@ DS_HDI void integrate_adjoint(const DevModel& m, const double* vn, double dt, co
 
 template <int NB, int NV, int NS, typename T>
 DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters,
-                      int chunk = 0, int nchunk = 1, bool lite = false) {
-  // lite: the forward part skipped Y = M^-1 J_c^T (and G, which the caller loaded); products with Y
-  // are done as solves with M's factor instead.
+                      int chunk = 0, int nchunk = 1) {
   // With nchunk > 1 the Jacobian columns (or the VJP's dof passes) are split over nchunk threads of
   // the same env; chunk 0 also writes the step's outputs.
   const bool lead = chunk == 0;
@@ -1121,22 +1217,10 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
   const int mdim = 3 * s.na;
   const double* q = s.q;
   const T grav[3] = {T(a.gx), T(a.gy), T(a.gz)};
-  T ylam[NV];                                  // M^-1 J_c^T lambda
-  if (lite) {
-    for (int k = 0; k < NV; ++k) {
-      T t = T(0);
-      for (int r = 0; r < mdim; ++r) t += s.Jc[r][k] * T(s.lam[r]);
-      ylam[k] = t;
-    }
-    fwd_packed(s.L, ylam, NV);
-    bwd_packed(s.L, ylam, NV);
-    for (int k = 0; k < NV; ++k) s.vn[k] = s.vf[k] + ylam[k];
-  } else {
-    for (int k = 0; k < NV; ++k) {
-      T t = s.vf[k];
-      for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r]);
-      s.vn[k] = t;
-    }
+  for (int k = 0; k < NV; ++k) {
+    T t = s.vf[k];
+    for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r]);
+    s.vn[k] = t;
   }
   for (int k = 0; k < NV; ++k) {
     const double vv = double(s.vn[k]);
@@ -1194,9 +1278,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
     // ---- B1 pass of tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces
     for (int k = 0; k < NV; ++k) {
       T t = s.vdf[k];
-      if (lite) t += ylam[k] / T(a.dt);
-      else
-        for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
+      for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
       s.astar[k] = t;
     }
     for (int ac = 0; ac < s.na; ++ac)
@@ -1307,7 +1389,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       // them) gives row k of Y C A^- B, and every column then costs a dot product per row instead
       // of a solve; otherwise each column solves for its X.
       const int c0 = (3 * NV * chunk) / nchunk, c1 = (3 * NV * (chunk + 1)) / nchunk;
-      const bool by_rows = !lite && md > 0 && NV < c1 - c0;
+      const bool by_rows = md > 0 && NV < c1 - c0;
       double P[NV][3 * NS];
       if (by_rows) {
         for (int k = 0; k < NV; ++k) {
@@ -1386,8 +1468,6 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             }
           }
           s.lu.solve_mn(rhs, X);
-          T wv[NV];
-          for (int k = 0; k < NV; ++k) wv[k] = T(0);
           for (int ac = 0; ac < s.na; ++ac) {
             if (sz[ac] == 0) continue;
             double dl[3];
@@ -1395,16 +1475,8 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             else { for (int r = 0; r < 3; ++r) dl[r] = Rm[ac][r][0] * X[off[ac]] + Rm[ac][r][1] * X[off[ac] + 1]; }
             for (int r = 0; r < 3; ++r) {
               const T dlr = T(dl[r]);
-              if (lite)
-                for (int k = 0; k < NV; ++k) wv[k] += s.Jc[3 * ac + r][k] * dlr;
-              else
-                for (int k = 0; k < NV; ++k) Dc[k] += s.Y[3 * ac + r][k] * dlr;
+              for (int k = 0; k < NV; ++k) Dc[k] += s.Y[3 * ac + r][k] * dlr;
             }
-          }
-          if (lite) {
-            fwd_packed(s.L, wv, NV);
-            bwd_packed(s.L, wv, NV);
-            for (int k = 0; k < NV; ++k) Dc[k] += wv[k];
           }
         }
         double* out = blk == 0 ? a.dv_dq : (blk == 1 ? a.dv_dv : a.dv_dtau);
@@ -1430,21 +1502,12 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       for (int r = 0; r < mdim; ++r) zeta[r] = 0.0;
       if (md > 0) {
         double wv[3 * NS], z[3 * NS];
-        T mvb[NV];                               // M^-1 vbar (lite: Y^T vbar = J_c M^-1 vbar)
-        if (lite) {
-          for (int k = 0; k < NV; ++k) mvb[k] = vb[k];
-          fwd_packed(s.L, mvb, NV);
-          bwd_packed(s.L, mvb, NV);
-        }
         for (int ac = 0; ac < s.na; ++ac) {
           if (sz[ac] == 0) continue;
           double y3[3];
           for (int r = 0; r < 3; ++r) {
             T t = T(0);
-            if (lite)
-              for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * mvb[k];
-            else
-              for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
+            for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
             y3[r] = double(t);
           }
           if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) wv[off[ac] + r] = y3[r]; }
@@ -1545,12 +1608,14 @@ DS_HDI int ds_atomic_add(int32_t* p, int32_t v) {
 #endif
 }
 
-// 1. setup: F1-F6 per env; the contact problem (mu, G, g), rho and K = (G + rho I)^-1, and a zero
-//    ADMM state to the workspace; envs with contacts queued for round 0.
+// 1. setup: F1-F6 per env; the forward state the finish needs, the contact problem (mu, G, g), rho
+//    and K = (G + rho I)^-1, and a zero ADMM state to the workspace; envs with contacts queued for
+//    round 0.
 template <int NB, int NV, int NS, typename T>
 DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
   Env<NB, NV, NS, T> s;
   uint32_t st = env_forward<NB, NV, NS, T>(m, a, e, s);
+  store_forward<NB, NV, NS, T>(a, e, s);
   const WsView& w = a.ws;
   const int B = a.B;
   const int mm = 3 * s.na;
@@ -2138,33 +2203,24 @@ __global__ void __launch_bounds__(128) newton_kernel(KArgs a) {
     newton_env<NS, T>(a, a.ws.nlist[t]);
 }
 
-// 3. finish: F1-F6 again (recomputed, bitwise identical), then F9 and the derivatives with lambda
-//    and the modes from the workspace.
+// 3. finish: the forward state the setup stored, then F9 and the derivatives with lambda and the
+//    modes from the workspace.
 template <int NB, int NV, int NS, typename T>
 DS_HD void finish_env(const DevModel& m, const KArgs& a, const int e, int chunk = 0, int nchunk = 1) {
-  // With the columns split over several threads, each recomputes the forward part; it then skips
-  // M^-1 J_c^T and G (read from the workspace, where the setup left it) to keep that redundancy low.
-  const bool lite = nchunk > 1;
+  // The forward quantities come from the setup (load_forward), so a finish thread, and each of the
+  // threads an env's columns are split over, does only F9 and its share of the derivatives.
   Env<NB, NV, NS, T> s;
-  env_forward<NB, NV, NS, T>(m, a, e, s, lite);
+  load_forward<NB, NV, NS, T>(m, a, e, s);
   const WsView& w = a.ws;
   const int B = a.B;
   const int mm = 3 * s.na;
-  if (lite)
-    for (int i = 0; i < mm; ++i)
-      for (int j = 0; j <= i; ++j) {
-        const double gij = w.G[tri(i, j) * B + e];
-        s.Gt[i][j] = T(gij);
-        s.Gt[j][i] = T(gij);
-        if constexpr (!Env<NB, NV, NS, T>::kDouble) { s.Gd_[i][j] = gij; s.Gd_[j][i] = gij; }
-      }
   for (int i = 0; i < mm; ++i) s.lam[i] = w.lam[i * B + e];
   if (mm > 0 && !(w.st[e] & DS_ENV_NONFINITE)) {
     for (int i = 0; i < s.na; ++i) s.mode[i] = w.mode[i * B + e];
   } else {
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
-  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk, lite);
+  env_finish<NB, NV, NS, T>(m, a, e, s, w.st[e], w.iters[e], chunk, nchunk);
 }
 
 // Finish from a tape: F1-F6, then lambda, the modes and the status of env e from the tape of a
@@ -2183,7 +2239,7 @@ DS_HD void finish_tape_env(const DevModel& m, const KArgs& a, const int e, int c
   } else {
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
-  env_finish<NB, NV, NS, T>(m, a, e, s, st, 0, chunk, nchunk, false);
+  env_finish<NB, NV, NS, T>(m, a, e, s, st, 0, chunk, nchunk);
 }
 
 template <int NB, int NV, int NS, typename T>

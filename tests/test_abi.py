@@ -79,8 +79,8 @@ def test_step_rejects_bad_arguments(L):
     assert L.sim_step(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, 0, None) == ds.DS_EINVAL
     assert L.sim_step(None, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, 0, None) == ds.DS_EINVAL
     n = ctypes.c_size_t()
-    assert L.ds_workspace_size(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(n)) == ds.DS_OK
-    assert n.value > 4 * 1000
+    # the workspace holds each model's forward state, so sizing it needs the models
+    assert L.ds_workspace_size(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(n)) == ds.DS_EINVAL
     b.B = -1
     assert L.sim_step_jac(models, 1, ctypes.byref(b), ctypes.byref(o), ctypes.byref(out), None, None, None,
                           None, 0, None) == ds.DS_EINVAL
