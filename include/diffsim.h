@@ -258,16 +258,19 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * never), how many threads share an env's Jacobian columns in the finish kernel (a target of 0, 4
  * or 8 CTAs per SM), the Newton kernel's form (cooperative or one thread per env), and the round
  * after which the envs already solved are finished on a side stream of the library while the slow
- * ones still iterate (2, 4, 5 or never), the first round handled by the two-warp ADMM kernel
- * (FP64 with at most 10 contact slots: one warp runs the x-step and projection, the other the De
- * Saxce term and convergence test; 3, 5 or never), and which SMs that overlapped finish leaves to
+ * ones still iterate (right after the setup, 2, 4, 5 or never), the first round handled by the
+ * two-warp ADMM kernel (FP64 with at most 10 contact slots: one warp runs the x-step and
+ * projection, the other the De Saxce term and convergence test; 3, 5 or never), and which SMs that overlapped finish leaves to
  * the slow envs (none, every 8th or every 4th: the FP64 pipe of an SM sub-partition is shared by
  * its warps, so the late rounds run faster on SMs the finish does not occupy), and the round from
  * whose end on the Newton / active-set stage also tries the iterate of every env still iterating,
  * not only of those whose ADMM stage tolerance was met, with a fallback that enumerates the
  * contact-mode patterns with one or two contacts in contact when the active-set rounds fail
  * (speculative attempts from round 3, from round 5, or never; an env whose attempt fails keeps
- * iterating in the same stage).
+ * iterating in the same stage), and whether the setup solves Eq. 1 exactly for the envs whose
+ * solution has a single contact in contact and every other contact breaking (the sticking
+ * impulse -G_ii^-1 g_i, else Newton on the sliding equations from its cone projection, accepted by
+ * the same FP64 NCP residual test as the Newton stage), so that those envs skip the ADMM rounds.
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
  * schedule by the second slowest of five runs (so that a schedule whose step time varies from
@@ -286,13 +289,15 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * runs (every accepted impulse passes the same NCP residual test; where Eq. 1 has several
  * solutions, two schedules can return different ones).
  * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
- * the schedule's index (0 .. 5831), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 4 (p +
- * 3 (r + 3 s)))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane round w (0:
- * 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0 cooperative,
- * 1 one thread per env), overlapped finish o (0: after round 2, 1: after round 4, 2: after round
- * 5, 3: never), two-warp ADMM p (0: from round 3, 1: from round 5, 2: never), SMs kept free r (0:
- * none, 1: every 8th, 2: every 4th), speculative Newton attempts s (0: from round 3, 1: from
- * round 5, 2: never).  Errors: DS_EINVAL, DS_ECUDA, those of the call. */
+ * the schedule's index (0 .. 14579), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 5 (p +
+ * 3 (r + 3 (s + 3 x))))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane
+ * round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0
+ * cooperative, 1 one thread per env), overlapped finish o (0: after the setup, 1: after round 2,
+ * 2: after round 4, 3: after round 5, 4: never), two-warp ADMM p (0: from round 3, 1: from round 5,
+ * 2: never), SMs kept
+ * free r (0: none, 1: every 8th, 2: every 4th), speculative Newton attempts s (0: from round 3, 1:
+ * from round 5, 2: never), single-contact presolve x (0 on, 1 off).  Errors: DS_EINVAL, DS_ECUDA,
+ * those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
                       double* o0, double* o1, double* o2, void* workspace, size_t workspace_bytes,
@@ -301,9 +306,21 @@ ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_b
 /* Sets the schedule (index as ds_autotune's *chosen) that later calls of `mode` use for batches
  * with this batch's signature, as if ds_autotune had chosen it; index -1 returns the signature to
  * the default schedule (no counterpart in the paper).  For reusing a tuned schedule without timing
- * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 5831). */
+ * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 14579). */
 ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                           const ds_options* opt, int32_t mode, int32_t index);
+
+/* Checked build (no counterpart in the paper; a debugging aid, libdiffsim_check.so, built with
+ * -DDS_CHECK).  There every tree index (bodies, parents, dofs, subtrees), every env index read
+ * from the pipeline's work lists and every shared-memory group index of the Newton kernel is
+ * checked against its range; an index out of range is counted and replaced by 0, so that it shows
+ * up as a count instead of a memory fault.  ds_check_bad_indices synchronises the device, writes
+ * the count summed over the kernels since the last call to *count and clears it.
+ * ds_check_self_test launches one check of `index` against [0, n) and writes the count it gives
+ * (1 for an index outside the range, 0 inside): the counting itself, tested.  In the normal build
+ * both return DS_EUNSUPPORTED with *count = 0.  Errors: DS_EINVAL (NULL count, n <= 0), DS_ECUDA. */
+ds_status ds_check_bad_indices(uint64_t* count);
+ds_status ds_check_self_test(int32_t index, int32_t n, uint64_t* count);
 
 /* Stage tracing (no counterpart in the paper): with ds_profile(1), every kernel the library
  * launches is bracketed by CUDA events on its own stream, grouped in DS_NSTAGES = 5 classes:

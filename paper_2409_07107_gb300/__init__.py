@@ -18,7 +18,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdiffsim.so")
+# DIFFSIM_LIB selects another build of the library (the checked build, libdiffsim_check.so)
+LIB_PATH = os.environ.get("DIFFSIM_LIB") or os.path.join(HERE, "libdiffsim.so")
 
 DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED, DS_ETOOLARGE = 0, -1, -2, -3, -4, -5
 DS_FP64, DS_MIXED = 0, 1
@@ -29,7 +30,8 @@ ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
-           "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape", "ds_set_schedule")
+           "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape", "ds_set_schedule", "ds_check_bad_indices",
+           "ds_check_self_test")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -94,10 +96,12 @@ def lib():
         L.sim_step_vjp_tape.argtypes = common + [vp, vp, ctypes.POINTER(ds_step_out), ctypes.POINTER(ds_step_out),
                                                  vp, vp, vp, vp]
         L.ds_set_schedule.argtypes = common + [i32, i32]
+        L.ds_check_bad_indices.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.ds_check_self_test.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_uint64)]
         for f in ("ds_model_create", "ds_model_destroy", "ds_model_dims", "sim_step", "sim_step_jac", "sim_step_vjp",
                   "ds_fma_peak", "ds_workspace_size", "sim_step_jac_noalloc", "ds_profile", "ds_profile_read",
                   "ds_cotangent_to_tangent", "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape",
-                  "ds_set_schedule"):
+                  "ds_set_schedule", "ds_check_bad_indices", "ds_check_self_test"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -238,12 +242,13 @@ SCHEDULE_KNOBS = (
     ("row_per_lane_admm_from_round", (3, 5, None)),
     ("finish_ctas_per_sm", (0, 4, 8)),
     ("newton", ("cooperative", "one thread per env")),
-    ("overlapped_finish_after_round", (2, 4, 5, None)),
+    ("overlapped_finish_after_round", ("setup", 2, 4, 5, None)),
     ("two_warp_admm_from_round", (3, 5, None)),
     ("overlapped_finish_keeps_free_every_nth_sm", (None, 8, 4)),
     ("speculative_newton_from_round", (3, 5, None)),
+    ("single_contact_presolve", (True, False)),
 )
-NUM_SCHEDULES = 5832
+NUM_SCHEDULES = 14580
 
 
 def describe_schedule(index):
@@ -255,11 +260,12 @@ def describe_schedule(index):
     return d
 
 
-def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=2, pair=1, reserve=1, spec=2):
+def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=3, pair=1, reserve=1, spec=2, presolve=0):
     """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
     defaults give the library's default schedule."""
     idx, mul = 0, 1
-    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec), SCHEDULE_KNOBS):
+    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec, presolve),
+                              SCHEDULE_KNOBS):
         assert 0 <= pos < len(opts)
         idx += pos * mul
         mul *= len(opts)
@@ -313,6 +319,21 @@ def profile_read():
     n = (ctypes.c_int32 * 5)()
     _check(lib().ds_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p)))
     return {k: (ms[i], n[i]) for i, k in enumerate(STAGES)}
+
+
+def check_bad_indices():
+    """Checked build: indices found out of range by the kernels since the last call (cleared).
+    Raises DiffsimError (unsupported) with the normal build."""
+    n = ctypes.c_uint64()
+    _check(lib().ds_check_bad_indices(ctypes.byref(n)))
+    return n.value
+
+
+def check_self_test(index, n):
+    """Checked build: the count one check of `index` against [0, n) gives (1 outside, 0 inside)."""
+    c = ctypes.c_uint64()
+    _check(lib().ds_check_self_test(int(index), int(n), ctypes.byref(c)))
+    return c.value
 
 
 def batch_to_device(batch, device="cuda"):

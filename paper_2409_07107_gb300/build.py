@@ -13,6 +13,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdiffsim.so")
+OBJ_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libdiffsim_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -37,17 +39,21 @@ def _stale(src, obj):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, jobs=None):
-    """Compile every .cu under csrc/ and link libdiffsim.so.  Returns the library path."""
-    os.makedirs(OBJ, exist_ok=True)
+def build(verbose=False, jobs=None, check=False):
+    """Compile every .cu under csrc/ and link libdiffsim.so (with check=True: the checked build,
+    -DDS_CHECK, as libdiffsim_check.so, objects apart).  Returns the library path."""
+    obj_dir = OBJ_CHECK if check else OBJ
+    lib = LIB_CHECK if check else LIB
+    flags = FLAGS + (["-DDS_CHECK"] if check else [])
+    os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     srcs = sources()
-    objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if _stale(s, o)]
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", s, "-o", o]
+        cmd = [nvcc] + ARCH + flags + ["-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (s, r.stdout, r.stderr))
@@ -59,13 +65,13 @@ def build(verbose=False, jobs=None):
             for s in ex.map(compile_one, todo):
                 if verbose:
                     print("compiled", os.path.basename(s), flush=True)
-    if todo or not os.path.exists(LIB):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lcudart"]
+    if todo or not os.path.exists(lib):
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":

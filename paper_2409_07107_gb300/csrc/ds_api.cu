@@ -199,7 +199,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS, 1};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -435,16 +435,17 @@ extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int3
 
 // Schedule knobs and their options.  The index of ds_autotune / ds_set_schedule is the mixed-radix
 // number of the chosen option positions, knob 0 the lowest digit.
-static const int kKnobs = 8, kNumSchedules = 3 * 3 * 3 * 2 * 4 * 3 * 3 * 3;
-static const int kNopt[kKnobs] = {3, 3, 3, 2, 4, 3, 3, 3};
-static const int kOpt[kKnobs][4] = {{0, 1, 2, 0},          // round-cap table
+static const int kKnobs = 9, kNumSchedules = 3 * 3 * 3 * 2 * 5 * 3 * 3 * 3 * 2;
+static const int kNopt[kKnobs] = {3, 3, 3, 2, 5, 3, 3, 3, 2};
+static const int kOpt[kKnobs][5] = {{0, 1, 2, 0},          // round-cap table
                                     {3, 5, DS_ROUNDS, 0},  // first row-per-lane ADMM round
                                     {0, 4, 8, 0},          // finish: target CTAs per SM
                                     {0, 1, 0, 0},          // Newton: cooperative / one thread per env
-                                    {2, 4, 5, DS_ROUNDS},  // overlapped finish after this round
+                                    {-1, 2, 4, 5, DS_ROUNDS},  // overlapped finish after this round (-1: setup)
                                     {3, 5, DS_ROUNDS, 0},  // first two-warp ADMM round
                                     {0, 8, 4, 0},          // overlapped finish: SM stride kept free
-                                    {3, 5, DS_ROUNDS, 0}};  // speculative Newton attempts from round
+                                    {3, 5, DS_ROUNDS, 0},  // speculative Newton attempts from round
+                                    {1, 0, 0, 0}};         // single-contact presolve: on / off
 static int* knob(ds_schedule& c, int d) {
   switch (d) {
     case 0: return &c.caps;
@@ -454,7 +455,8 @@ static int* knob(ds_schedule& c, int d) {
     case 4: return &c.overlap_from;
     case 5: return &c.pair_from;
     case 6: return &c.reserve;
-    default: return &c.spec_from;
+    case 7: return &c.spec_from;
+    default: return &c.presolve;
   }
 }
 static int schedule_index(ds_schedule c) {
@@ -578,4 +580,38 @@ extern "C" ds_status ds_autotune(const ds_model* const* models, int32_t nmodels,
   }
   if (chosen) *chosen = schedule_index(best);
   return call();                                          // leave the outputs of the chosen schedule
+}
+
+// ---------------------------------------------------------------------------- checked build
+#ifdef DS_CHECK
+static __global__ void ds_check_probe_kernel(int i, int n) { (void)DS_IX(i, n); }
+#endif
+
+extern "C" ds_status ds_check_bad_indices(uint64_t* count) {
+  if (!count) return DS_EINVAL;
+#ifdef DS_CHECK
+  if (cudaDeviceSynchronize() != cudaSuccess) return DS_ECUDA;
+  *count = ds_check_sum();
+  return DS_OK;
+#else
+  *count = 0;
+  return DS_EUNSUPPORTED;
+#endif
+}
+
+extern "C" ds_status ds_check_self_test(int32_t index, int32_t n, uint64_t* count) {
+  if (!count || n <= 0) return DS_EINVAL;
+#ifdef DS_CHECK
+  unsigned z = 0, v = 0;
+  if (cudaMemcpyToSymbol(ds_check_bad, &z, sizeof z) != cudaSuccess) return DS_ECUDA;
+  ds_check_probe_kernel<<<1, 1>>>(index, n);
+  if (cudaDeviceSynchronize() != cudaSuccess) return DS_ECUDA;
+  if (cudaMemcpyFromSymbol(&v, ds_check_bad, sizeof v) != cudaSuccess) return DS_ECUDA;
+  *count = v;
+  return DS_OK;
+#else
+  (void)index;
+  *count = 0;
+  return DS_EUNSUPPORTED;
+#endif
 }

@@ -12,6 +12,25 @@
 #define DS_HD __host__ __device__
 #define DS_HDI __host__ __device__ __forceinline__
 
+// Checked build (compiled with -DDS_CHECK, a debugging aid): the tree indices (bodies, parents,
+// dofs, subtrees), the env indices read from the work lists and the shared-memory group indices go
+// through DS_IX, which counts an index outside [0, n) in this translation unit's counter (read by
+// ds_check_bad_indices) and uses 0 instead, so a bad index shows up as a count, not a memory fault.
+// In the normal build DS_IX is the index itself.
+#ifdef DS_CHECK
+static __device__ unsigned int ds_check_bad;
+DS_HDI int ds_ix(int i, int n) {
+  if (static_cast<unsigned>(i) < static_cast<unsigned>(n)) return i;
+#ifdef __CUDA_ARCH__
+  atomicAdd(&ds_check_bad, 1u);
+#endif
+  return 0;
+}
+#define DS_IX(i, n) ds_ix((i), (n))
+#else
+#define DS_IX(i, n) (i)
+#endif
+
 #define DS_MAXB 32       // bodies per model
 #define DS_MAXNV 36      // velocity dofs per model
 #define DS_MAXSLOTS 16   // contact slots per env
@@ -167,6 +186,8 @@ struct ds_schedule {
                       // its stage if the attempt fails); in this round a failed attempt falls
                       // back to enumerating the contact-mode patterns with one or two contacts in
                       // contact (DS_ROUNDS = never)
+  int presolve;       // 1: the setup solves Eq. 1 exactly for the envs whose solution has a single
+                      // contact in contact (the others breaking), which then skip the ADMM rounds
 };
 
 // Everything a launch needs; passed by value.
@@ -229,7 +250,10 @@ struct ds_kernel_entry {
   ds_launch_fn fn;
   ds_launch_fn pipeline;
   ds_launch_fn tape;       // finish only, from a tape (KArgs.tlam / tmodes / tstat)
+  unsigned (*check)();     // checked build: reads and clears the shape's bad-index count (else 0)
 };
+// Sum over the compiled shapes of their bad-index counts, cleared (0 in the normal build).
+extern "C++" unsigned long long ds_check_sum();
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);
 extern "C++" const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int precision);
 // Whether calls of this host thread may use the library's helper streams (on by default).

@@ -4,3 +4,4 @@
 void ds_launch_13_18_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<13, 18, 4, float>(a, s); }
 void ds_pipeline_13_18_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<13, 18, 4, float>(a, s); }
 void ds_tape_13_18_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_tape<13, 18, 4, float>(a, s); }
+unsigned ds_check_13_18_4_mix() { return ds::check_read(); }

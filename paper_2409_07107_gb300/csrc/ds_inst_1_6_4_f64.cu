@@ -4,3 +4,4 @@
 void ds_launch_1_6_4_f64(const KArgs& a, cudaStream_t s) { ds::launch_env<1, 6, 4, double>(a, s); }
 void ds_pipeline_1_6_4_f64(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<1, 6, 4, double>(a, s); }
 void ds_tape_1_6_4_f64(const KArgs& a, cudaStream_t s) { ds::launch_tape<1, 6, 4, double>(a, s); }
+unsigned ds_check_1_6_4_f64() { return ds::check_read(); }

@@ -4,3 +4,4 @@
 void ds_launch_1_6_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<1, 6, 4, float>(a, s); }
 void ds_pipeline_1_6_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<1, 6, 4, float>(a, s); }
 void ds_tape_1_6_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_tape<1, 6, 4, float>(a, s); }
+unsigned ds_check_1_6_4_mix() { return ds::check_read(); }

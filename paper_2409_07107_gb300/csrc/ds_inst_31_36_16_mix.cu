@@ -4,3 +4,4 @@
 void ds_launch_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<31, 36, 16, float>(a, s); }
 void ds_pipeline_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<31, 36, 16, float>(a, s); }
 void ds_tape_31_36_16_mix(const KArgs& a, cudaStream_t s) { ds::launch_tape<31, 36, 16, float>(a, s); }
+unsigned ds_check_31_36_16_mix() { return ds::check_read(); }

@@ -4,3 +4,4 @@
 void ds_launch_7_7_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_env<7, 7, 4, float>(a, s); }
 void ds_pipeline_7_7_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_pipeline<7, 7, 4, float>(a, s); }
 void ds_tape_7_7_4_mix(const KArgs& a, cudaStream_t s) { ds::launch_tape<7, 7, 4, float>(a, s); }
+unsigned ds_check_7_7_4_mix() { return ds::check_read(); }

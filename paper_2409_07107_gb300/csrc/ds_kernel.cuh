@@ -571,6 +571,94 @@ DS_HD bool newton_stage(P& p, const T* z, double eps, const KArgs& a, double* be
   return best_r <= tol;
 }
 
+// Solution of the symmetric 3x3 system A x = b by the adjugate (false when A is numerically singular).
+DS_HDI bool solve3(const double* A, const double* b, double* x) {
+  const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+  const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  const double nrm = fabs(A[0]) + fabs(A[4]) + fabs(A[8]);
+  if (!(fabs(det) > 1e-14 * nrm * nrm * nrm)) return false;
+  const double id = 1.0 / det;
+  const double c11 = A[0] * A[8] - A[2] * A[6], c12 = A[1] * A[6] - A[0] * A[7];
+  const double c22 = A[0] * A[4] - A[1] * A[3];
+  const double c10 = A[2] * A[7] - A[1] * A[8], c20 = A[1] * A[5] - A[2] * A[4], c21 = A[2] * A[3] - A[0] * A[5];
+  x[0] = (c00 * b[0] + c10 * b[1] + c20 * b[2]) * id;
+  x[1] = (c01 * b[0] + c11 * b[1] + c21 * b[2]) * id;
+  x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) * id;
+  return true;
+}
+
+// ncp_residual of an impulse that is zero except on contact i (components l3): sigma from contact
+// i's three columns of G only, and a contact j != i (lambda_j = 0) contributes nothing when its
+// sigma_N >= 0 (then sigma_j + Gamma(sigma_j) lies in the dual cone and the complementarity term
+// is 0), else the same terms as ncp_residual.  Equal to ncp_residual on such an impulse.
+template <class P>
+DS_HD double single_residual(const P& p, int i, const double* l3) {
+  double r = 0.0;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < p.na; ++j) {
+    double sg[3];
+    for (int k = 0; k < 3; ++k) {
+      double t = p.gd[3 * j + k];
+      for (int c = 0; c < 3; ++c) t += p.G(3 * j + k, 3 * i + c) * l3[c];
+      sg[k] = t;
+    }
+    if (j != i && sg[2] >= 0.0) continue;
+    const double* l = j == i ? l3 : zero;
+    double w[3] = {sg[0], sg[1], sg[2] + p.mu[j] * sqrt(sg[0] * sg[0] + sg[1] * sg[1])};
+    double q[3];
+    proj_cone(l, p.mu[j], q);
+    r = fmax(r, sqrt((l[0] - q[0]) * (l[0] - q[0]) + (l[1] - q[1]) * (l[1] - q[1]) + (l[2] - q[2]) * (l[2] - q[2])));
+    proj_cone(w, 1.0 / p.mu[j], q);
+    r = fmax(r, sqrt((w[0] - q[0]) * (w[0] - q[0]) + (w[1] - q[1]) * (w[1] - q[1]) + (w[2] - q[2]) * (w[2] - q[2])));
+    r = fmax(r, fabs(l[0] * w[0] + l[1] * w[1] + l[2] * w[2]));
+  }
+  return r;
+}
+
+// Exact solve of Eq. 1 for an env whose solution has one contact in contact and every other one
+// breaking (most arm + cube envs: the cube tips onto one corner): for each active contact, in the
+// order of its free normal velocity (most approaching first), the sticking impulse
+// lambda_i = -G_ii^-1 g_i, then the sliding solution by Newton on the sliding equations (Sec. 3.2)
+// from that impulse's projection onto the cone; the first candidate that passes the FP64 NCP
+// residual test (the Newton stage's acceptance) is the solution.  FP64 in both precisions.
+// Returns false, lam unspecified, when no single-contact candidate passes; the env then goes
+// through the ADMM rounds.
+template <class P>
+DS_HD bool presolve_single(P& p, const KArgs& a, double* lam) {
+  constexpr int NSL = P::NC3 / 3;
+  const int m = 3 * p.na;
+  double scale = 1.0;
+  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(p.gd[i]));
+  const double tol = a.ncp_tol * scale;
+  int order[NSL];
+  for (int i = 0; i < p.na; ++i) {
+    int k = i;
+    while (k > 0 && p.gd[3 * order[k - 1] + 2] > p.gd[3 * i + 2]) { order[k] = order[k - 1]; --k; }
+    order[k] = i;
+  }
+  int mode[NSL];
+  for (int q = 0; q < p.na; ++q) {
+    const int i = order[q];
+    double Gb[9], rhs[3], ls[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) Gb[3 * r + c] = p.G(3 * i + r, 3 * i + c);
+      rhs[r] = -p.gd[3 * i + r];
+    }
+    if (!solve3(Gb, rhs, ls)) continue;
+    for (int j = 0; j < m; ++j) lam[j] = 0.0;
+    for (int r = 0; r < 3; ++r) lam[3 * i + r] = ls[r];
+    if (single_residual(p, i, ls) <= tol) return true;
+    double pr[3];
+    proj_cone(ls, p.mu[i], pr);
+    if (!(pr[2] > 0.0) || (pr[0] == ls[0] && pr[1] == ls[1] && pr[2] == ls[2])) continue;
+    for (int r = 0; r < 3; ++r) lam[3 * i + r] = pr[r];
+    for (int j = 0; j < p.na; ++j) mode[j] = j == i ? DS_MODE_SLIDING : DS_MODE_BREAKING;
+    newton_modes(p, lam, mode, a.polish_iters, 0.0);
+    if (single_residual(p, i, lam + 3 * i) <= tol) return true;
+  }
+  return false;
+}
+
 // Staged NCP solve in one thread, in the rounds of the pipeline's schedule: each round continues
 // the iteration It (ADMM or PGS) for at most the round's cap (the last round: to the iteration
 // limit) or until the stage tolerance is met, then runs the Newton / active-set stage on the
@@ -618,6 +706,7 @@ template <class P, typename T>
 DS_HD void solve_ncp(P& s, const KArgs& a, int& iters, uint32_t& st) {
   iters = 0;
   if (s.na == 0 || separating(s)) return;
+  if (a.sched.presolve && presolve_single(s, a, s.lam)) return;
   if (a.solver == DS_PGS) solve_ncp_with<Pgs<P::NC3 / 3, T>, P, T>(s, a, iters, st);
   else solve_ncp_with<Admm<P::NC3 / 3, T>, P, T>(s, a, iters, st);
 }
@@ -632,8 +721,8 @@ namespace ds {
 // IV, IA, Fc of the a* pass.  Writes dtau[NV].
 template <int NB, int NV, int NS, typename T>
 DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind, int d, T* dtau) {
-  const int j = m.dof_body[d];
-  const int jend = m.sub_end[j];
+  const int j = m.dof_body[DS_IX(d, NV)];
+  const int jend = m.sub_end[DS_IX(j, NB)];
   const T* xi = s.S[d];
   T dV[NB][6], dA[NB][6], dF[NB][6];
   for (int k = 0; k < NV; ++k) dtau[k] = T(0);
@@ -644,17 +733,17 @@ DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind
     if (kind == 0) {
       for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) {
         T dS[6];
-        mcross(xi, s.S[dd], dS);
-        for (int k = 0; k < 6; ++k) { dVJ[k] += dS[k] * s.v[dd]; dSa[k] += dS[k] * s.astar[dd]; }
+        mcross(xi, s.S[DS_IX(dd, NV)], dS);
+        for (int k = 0; k < 6; ++k) { dVJ[k] += dS[k] * s.v[DS_IX(dd, NV)]; dSa[k] += dS[k] * s.astar[DS_IX(dd, NV)]; }
       }
     } else if (i == j) {
       for (int k = 0; k < 6; ++k) dVJ[k] = xi[k];
     }
     T t1[6], t2[6];
-    for (int k = 0; k < 6; ++k) dV[i][k] = (inside ? dV[par][k] : T(0)) + dVJ[k];
+    for (int k = 0; k < 6; ++k) dV[i][k] = (inside ? dV[DS_IX(par, NB)][k] : T(0)) + dVJ[k];
     mcross(dV[i], s.VJ[i], t1);
     mcross(s.V[i], dVJ, t2);
-    for (int k = 0; k < 6; ++k) dA[i][k] = (inside ? dA[par][k] : T(0)) + dSa[k] + t1[k] + t2[k];
+    for (int k = 0; k < 6; ++k) dA[i][k] = (inside ? dA[DS_IX(par, NB)][k] : T(0)) + dSa[k] + t1[k] + t2[k];
     // dF = I dA + dV x* (I V) + V x* (I dV)  [+ dI A + V x* (dI V) - dFext for q tangents]
     T u[6], w[6];
     iapply(s.I[i], dA[i], u);
@@ -686,21 +775,21 @@ DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind
   }
   for (int i = jend - 1; i >= j; --i) {
     for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) {
-      T r = dot6(s.S[dd], dF[i]);
+      T r = dot6(s.S[DS_IX(dd, NV)], dF[i]);
       if (kind == 0) {
         T dS[6];
-        mcross(xi, s.S[dd], dS);
+        mcross(xi, s.S[DS_IX(dd, NV)], dS);
         r += dot6(dS, s.Fc[i]);
       }
-      dtau[dd] = r;
+      dtau[DS_IX(dd, NV)] = r;
     }
     if (i != j) {
       const int par = m.parent[i];
-      for (int k = 0; k < 6; ++k) dF[par][k] += dF[i][k];
+      for (int k = 0; k < 6; ++k) dF[DS_IX(par, NB)][k] += dF[i][k];
     }
   }
-  for (int b = m.parent[j]; b >= 0; b = m.parent[b])
-    for (int dd = m.iv[b]; dd < m.iv[b] + m.nd[b]; ++dd) dtau[dd] = dot6(s.S[dd], dF[j]);
+  for (int b = m.parent[DS_IX(j, NB)]; b >= 0; b = m.parent[DS_IX(b, NB)])
+    for (int dd = m.iv[DS_IX(b, NB)]; dd < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++dd) dtau[DS_IX(dd, NV)] = dot6(s.S[DS_IX(dd, NV)], dF[DS_IX(j, NB)]);
 }
 
 // d(J_c v+)/dq_d for contact a at fixed v+ (App. D's FKV term, including the motion of the
@@ -708,20 +797,20 @@ DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind
 template <int NB, int NV, int NS, typename T>
 DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T (*Vp)[6],
                                             int a, int d, T* out) {
-  const int j = m.dof_body[d];
+  const int j = m.dof_body[DS_IX(d, NV)];
   const int b = s.body[a];
   out[0] = out[1] = out[2] = T(0);
-  if (b < j || b >= m.sub_end[j]) return;
+  if (b < j || b >= m.sub_end[DS_IX(j, NB)]) return;
   const T* xi = s.S[d];
-  const int pj = m.parent[j];
+  const int pj = m.parent[DS_IX(j, NB)];
   T rel[6], dVb[6], t[3], dc[3], dp[3];
-  for (int k = 0; k < 6; ++k) rel[k] = Vp[b][k] - (pj >= 0 ? Vp[pj][k] : T(0));
+  for (int k = 0; k < 6; ++k) rel[k] = Vp[DS_IX(b, NB)][k] - (pj >= 0 ? Vp[DS_IX(pj, NB)][k] : T(0));
   mcross(xi, rel, dVb);
   cross3(xi + 3, s.x[a], t);
   for (int k = 0; k < 3; ++k) dc[k] = xi[k] + t[k];
   cross3(dVb + 3, s.c[a], t);
   for (int k = 0; k < 3; ++k) dp[k] = dVb[k] + t[k];
-  cross3(Vp[b] + 3, dc, t);
+  cross3(Vp[DS_IX(b, NB)] + 3, dc, t);
   for (int k = 0; k < 3; ++k) dp[k] += t[k];
   for (int r = 0; r < 3; ++r) out[r] = dot3(s.fr[r], dp);
 }
@@ -793,8 +882,8 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     } else {
       for (int r = 0; r < 3; ++r) {
         for (int c = 0; c < 3; ++c)
-          R0[3 * r + c] = s.R[par][3 * r] * m.jrot[i][c] + s.R[par][3 * r + 1] * m.jrot[i][3 + c] + s.R[par][3 * r + 2] * m.jrot[i][6 + c];
-        p0[r] = s.P[par][r] + s.R[par][3 * r] * m.jpos[i][0] + s.R[par][3 * r + 1] * m.jpos[i][1] + s.R[par][3 * r + 2] * m.jpos[i][2];
+          R0[3 * r + c] = s.R[DS_IX(par, NB)][3 * r] * m.jrot[i][c] + s.R[DS_IX(par, NB)][3 * r + 1] * m.jrot[i][3 + c] + s.R[DS_IX(par, NB)][3 * r + 2] * m.jrot[i][6 + c];
+        p0[r] = s.P[DS_IX(par, NB)][r] + s.R[DS_IX(par, NB)][3 * r] * m.jpos[i][0] + s.R[DS_IX(par, NB)][3 * r + 1] * m.jpos[i][1] + s.R[DS_IX(par, NB)][3 * r + 2] * m.jpos[i][2];
       }
     }
     double Rj[9];
@@ -877,22 +966,22 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       T* VJ = s.VJ[i];
       for (int k = 0; k < 6; ++k) VJ[k] = T(0);
       for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
-        for (int k = 0; k < 6; ++k) VJ[k] += s.S[dd][k] * s.v[dd];
+        for (int k = 0; k < 6; ++k) VJ[k] += s.S[DS_IX(dd, NV)][k] * s.v[DS_IX(dd, NV)];
       T t[6];
-      for (int k = 0; k < 6; ++k) s.V[i][k] = (par >= 0 ? s.V[par][k] : T(0)) + VJ[k];
+      for (int k = 0; k < 6; ++k) s.V[i][k] = (par >= 0 ? s.V[DS_IX(par, NB)][k] : T(0)) + VJ[k];
       mcross(s.V[i], VJ, t);
       for (int k = 0; k < 6; ++k)
-        s.A[i][k] = (par >= 0 ? s.A[par][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
+        s.A[i][k] = (par >= 0 ? s.A[DS_IX(par, NB)][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
       iapply(s.I[i], s.V[i], s.IV[i]);
       iapply(s.I[i], s.A[i], s.IA[i]);
       fcross(s.V[i], s.IV[i], t);
       for (int k = 0; k < 6; ++k) s.Fc[i][k] = s.IA[i][k] + t[k];
     }
     for (int i = NB - 1; i >= 0; --i) {
-      for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) bias[dd] = dot6(s.S[dd], s.Fc[i]);
+      for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) bias[DS_IX(dd, NV)] = dot6(s.S[DS_IX(dd, NV)], s.Fc[i]);
       const int par = m.parent[i];
       if (par >= 0)
-        for (int k = 0; k < 6; ++k) s.Fc[par][k] += s.Fc[i][k];
+        for (int k = 0; k < 6; ++k) s.Fc[DS_IX(par, NB)][k] += s.Fc[i][k];
     }
   }
 
@@ -904,16 +993,16 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     for (int i = NB - 1; i > 0; --i) {
       const int par = m.parent[i];
       if (par >= 0)
-        for (int k = 0; k < 10; ++k) IC[par][k] += IC[i][k];
+        for (int k = 0; k < 10; ++k) IC[DS_IX(par, NB)][k] += IC[i][k];
     }
     for (int k = 0; k < NV * (NV + 1) / 2; ++k) s.L[k] = T(0);
     for (int i = 0; i < NB; ++i) {
       for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) {
         T F[6];
-        iapply(IC[i], s.S[dd], F);
-        for (int d2 = m.iv[i]; d2 <= dd; ++d2) s.L[tri(dd, d2)] = dot6(s.S[d2], F);
-        for (int b = m.parent[i]; b >= 0; b = m.parent[b])
-          for (int d2 = m.iv[b]; d2 < m.iv[b] + m.nd[b]; ++d2) s.L[tri(dd, d2)] = dot6(s.S[d2], F);
+        iapply(IC[i], s.S[DS_IX(dd, NV)], F);
+        for (int d2 = m.iv[i]; d2 <= dd; ++d2) s.L[tri(dd, d2)] = dot6(s.S[DS_IX(d2, NV)], F);
+        for (int b = m.parent[i]; b >= 0; b = m.parent[DS_IX(b, NB)])
+          for (int d2 = m.iv[DS_IX(b, NB)]; d2 < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++d2) s.L[tri(dd, d2)] = dot6(s.S[DS_IX(d2, NV)], F);
       }
     }
     if constexpr (!Env<NB, NV, NS, T>::kDouble) {
@@ -949,7 +1038,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     const double pl[3] = {a.c_point[(k * 3 + 0) * B + e], a.c_point[(k * 3 + 1) * B + e], a.c_point[(k * 3 + 2) * B + e]};
     const double r = a.c_radius[k * B + e];
     double xw[3];
-    for (int i = 0; i < 3; ++i) xw[i] = s.P[b][i] + s.R[b][3 * i] * pl[0] + s.R[b][3 * i + 1] * pl[1] + s.R[b][3 * i + 2] * pl[2];
+    for (int i = 0; i < 3; ++i) xw[i] = s.P[DS_IX(b, NB)][i] + s.R[DS_IX(b, NB)][3 * i] * pl[0] + s.R[DS_IX(b, NB)][3 * i + 1] * pl[1] + s.R[DS_IX(b, NB)][3 * i + 2] * pl[2];
     const double phi = pn[0] * xw[0] + pn[1] * xw[1] + pn[2] * xw[2] - pd - r;
     if (phi <= a.cmargin) {
       const int n = s.na++;
@@ -992,15 +1081,15 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       for (int k = 0; k < NV; ++k) Jd[r][k] = 0.0;
     for (int ac = 0; ac < s.na; ++ac) {
       const double cd[3] = {double(s.cx_d[ac][0]), double(s.cx_d[ac][1]), double(s.cx_d[ac][2])};
-      for (int b = s.body[ac]; b >= 0; b = m.parent[b]) {
-        const double* Rb = s.R[b];
-        const double* pb = s.P[b];
+      for (int b = s.body[ac]; b >= 0; b = m.parent[DS_IX(b, NB)]) {
+        const double* Rb = s.R[DS_IX(b, NB)];
+        const double* pb = s.P[DS_IX(b, NB)];
         const double rel[3] = {cd[0] - pb[0], cd[1] - pb[1], cd[2] - pb[2]};
-        for (int dd = m.iv[b]; dd < m.iv[b] + m.nd[b]; ++dd) {
+        for (int dd = m.iv[DS_IX(b, NB)]; dd < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++dd) {
           double pv[3];
-          const int k = dd - m.iv[b];
-          if (m.jtype[b] == 0) {
-            const double* ax = m.axis[b];
+          const int k = dd - m.iv[DS_IX(b, NB)];
+          if (m.jtype[DS_IX(b, NB)] == 0) {
+            const double* ax = m.axis[DS_IX(b, NB)];
             double aw[3];
             for (int r = 0; r < 3; ++r) aw[r] = Rb[3 * r] * ax[0] + Rb[3 * r + 1] * ax[1] + Rb[3 * r + 2] * ax[2];
             cross3(aw, rel, pv);
@@ -1010,7 +1099,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
             const double col[3] = {Rb[k - 3], Rb[3 + k - 3], Rb[6 + k - 3]};
             cross3(col, rel, pv);
           }
-          for (int r = 0; r < 3; ++r) Jd[3 * ac + r][dd] = dot3(frd[r], pv);
+          for (int r = 0; r < 3; ++r) Jd[3 * ac + r][DS_IX(dd, NV)] = dot3(frd[r], pv);
         }
       }
     }
@@ -1289,9 +1378,9 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       const int par = m.parent[i];
       T t[6];
       mcross(s.V[i], s.VJ[i], t);
-      for (int k = 0; k < 6; ++k) s.A[i][k] = (par >= 0 ? s.A[par][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
+      for (int k = 0; k < 6; ++k) s.A[i][k] = (par >= 0 ? s.A[DS_IX(par, NB)][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
       for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
-        for (int k = 0; k < 6; ++k) s.A[i][k] += s.S[dd][k] * s.astar[dd];
+        for (int k = 0; k < 6; ++k) s.A[i][k] += s.S[DS_IX(dd, NV)][k] * s.astar[DS_IX(dd, NV)];
       iapply(s.I[i], s.A[i], s.IA[i]);
       fcross(s.V[i], s.IV[i], t);
       for (int k = 0; k < 6; ++k) s.Fc[i][k] = s.IA[i][k] + t[k];
@@ -1305,15 +1394,15 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
     for (int i = NB - 1; i > 0; --i) {
       const int par = m.parent[i];
       if (par >= 0)
-        for (int k = 0; k < 6; ++k) s.Fc[par][k] += s.Fc[i][k];
+        for (int k = 0; k < 6; ++k) s.Fc[DS_IX(par, NB)][k] += s.Fc[i][k];
     }
     // body velocities under v+ (for the FKV term)
     T Vp[NB][6];
     for (int i = 0; i < NB; ++i) {
       const int par = m.parent[i];
-      for (int k = 0; k < 6; ++k) Vp[i][k] = (par >= 0 ? Vp[par][k] : T(0));
+      for (int k = 0; k < 6; ++k) Vp[i][k] = (par >= 0 ? Vp[DS_IX(par, NB)][k] : T(0));
       for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
-        for (int k = 0; k < 6; ++k) Vp[i][k] += s.S[dd][k] * s.vn[dd];
+        for (int k = 0; k < 6; ++k) Vp[i][k] += s.S[DS_IX(dd, NV)][k] * s.vn[DS_IX(dd, NV)];
     }
 
     // ---- B3/B4 reduced implicit system A = B G C + blkdiag(0, Q) (App. B), FP64
@@ -1590,7 +1679,7 @@ __global__ void __launch_bounds__(128, 4) env_kernel(KArgs a) {
   load_model(sm, a.model);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_env) return;
-  const int e = a.env_list ? a.env_list[t] : t;
+  const int e = DS_IX(a.env_list ? a.env_list[t] : t, a.B);
   if (a.model_id && a.model_id[e] != a.model_index) return;
   run_env<NB, NV, NS, T>(sm, a, e);
 }
@@ -1641,6 +1730,13 @@ DS_HD void setup_env(const DevModel& m, const KArgs& a, const int e) {
     const double margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, mode);
     if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
     for (int i = 0; i < s.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
+  } else if (mm > 0 && !(st & DS_ENV_NONFINITE) && a.sched.presolve && presolve_single(s, a, s.lam)) {
+    // one contact in contact, the rest breaking: solved here, no ADMM
+    for (int i = 0; i < mm; ++i) w.lam[i * B + e] = s.lam[i];
+    int mode[NS];
+    const double margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, mode);
+    if (margin < a.margin_delta) st |= DS_ENV_NEAR_SWITCH;
+    for (int i = 0; i < s.na; ++i) w.mode[i * B + e] = int8_t(mode[i]);
   } else if (mm > 0 && !(st & DS_ENV_NONFINITE)) {
     if (a.solver == DS_ADMM) {
       Admm<NS, T> ad;
@@ -1667,7 +1763,7 @@ __global__ void __launch_bounds__(128, 4) setup_kernel(KArgs a) {
   load_model(sm, a.model);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n_env) return;
-  const int e = a.env_list ? a.env_list[t] : t;
+  const int e = DS_IX(a.env_list ? a.env_list[t] : t, a.B);
   if (a.model_id && a.model_id[e] != a.model_index) return;
   setup_env<NB, NV, NS, T>(sm, a, e);
 }
@@ -1717,7 +1813,7 @@ __global__ void __launch_bounds__(128) admm_round_kernel(KArgs a) {
   for (int base = warp * EPW; base < n; base += nwarps * EPW) {
     const int t = base + grp;
     const bool have = t < n;
-    const int e = have ? cur[t] : 0;
+    const int e = have ? DS_IX(cur[t], B) : 0;
     const int na = have ? w.na[e] : 0;
     const bool act = li < na;
     T Kr[3][NC3], x[3], z[3], y[3], sx[3], g[3];
@@ -1823,7 +1919,7 @@ __global__ void __launch_bounds__(128) admm_round_wide_kernel(KArgs a) {
   for (int base = warp * EPW; base < n; base += nwarps * EPW) {
     const int t = base + grp;
     const bool have = t < n;
-    const int e = have ? cur[t] : 0;
+    const int e = have ? DS_IX(cur[t], B) : 0;
     const int na = have ? w.na[e] : 0;
     const bool act = li < 3 * na;
     T Kr[NC3];
@@ -1965,7 +2061,7 @@ __global__ void __launch_bounds__(64) admm_round_pair_kernel(KArgs a) {
   for (int base = blockIdx.x * EPW; base < n; base += gridDim.x * EPW) {
     const int t = base + grp;
     const bool have = t < n;
-    const int e = have ? cur[t] : 0;
+    const int e = have ? DS_IX(cur[t], B) : 0;
     const int na = have ? w.na[e] : 0;
     const bool act = li < 3 * na;
     const T g = act ? T(w.g[li * B + e]) : T(0);
@@ -2118,7 +2214,7 @@ __global__ void __launch_bounds__(128) pgs_round_kernel(KArgs a) {
   const int32_t* cur = w.list[a.round & 1];
   int32_t* next = w.list[(a.round + 1) & 1];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int e = cur[t];
+    const int e = DS_IX(cur[t], B);
     PgsData<NS, T> d;
     d.na = w.na[e];
     const int m = 3 * d.na;
@@ -2151,7 +2247,7 @@ template <int NS, typename T>
 DS_HD void newton_env(const KArgs& a, const int entry) {
   // entry = e: the env's ADMM stage ended; ~e: a speculative attempt on an unconverged iterate
   const bool spec = entry < 0;
-  const int e = spec ? ~entry : entry;
+  const int e = DS_IX(spec ? ~entry : entry, a.B);
   const WsView& w = a.ws;
   const int B = a.B;
   Ncp<NS, T> p;
@@ -2278,7 +2374,7 @@ __global__ void __launch_bounds__(128, 4) finish_kernel(KArgs a) {
   const long long total = (long long)n * a.nchunk;
   auto item = [&](long long t) {
     const int chunk = int(t / n), ti = int(t - (long long)chunk * n);
-    const int e = a.fhi ? a.ws.dlist[lo + ti] : (a.env_list ? a.env_list[ti] : ti);
+    const int e = DS_IX(a.fhi ? a.ws.dlist[lo + ti] : (a.env_list ? a.env_list[ti] : ti), a.B);
     if (a.model_id && a.model_id[e] != a.model_index) return;
     finish_env<NB, NV, NS, T>(sm, a, e, chunk, a.nchunk);
   };

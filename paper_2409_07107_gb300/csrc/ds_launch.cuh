@@ -5,6 +5,18 @@
 
 namespace ds {
 
+// Reads and clears this translation unit's bad-index count (the checked build; 0 otherwise).
+inline unsigned check_read() {
+#ifdef DS_CHECK
+  unsigned v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, ds_check_bad, sizeof v) != cudaSuccess) return 0xffffffffu;
+  cudaMemcpyToSymbol(ds_check_bad, &z, sizeof z);
+  return v;
+#else
+  return 0;
+#endif
+}
+
 inline int ds_sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -111,8 +123,34 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     af.nchunk = c < 1 ? 1 : (c > maxc ? maxc : c);
   }
   // With a side stream and an overlap round, the envs solved by then are finished on the side
-  // stream while the late ADMM rounds (few, slow envs) run; the rest are finished at the end.
+  // stream while the later ADMM rounds run; the rest are finished at the end.  Overlap round -1:
+  // right after the setup (the envs it solved: no contact, separating, presolved).
   const bool overlap = a0.side && sc.overlap_from < DS_ROUNDS - 1;
+  auto fork_finish = [&]() {
+    ds_trace_mark(DS_STAGE_FINISH, 1, s);
+    dcount_snapshot_kernel<<<1, 1, 0, s>>>(a0.ws.dcount);
+    ds_trace_mark(DS_STAGE_FINISH, 0, s);
+    cudaEventRecord(a0.ev_fork, s);
+    cudaStreamWaitEvent(a0.side, a0.ev_fork, 0);
+    KArgs fa = af;
+    fa.flo = nullptr;
+    fa.fhi = a0.ws.dcount + 1;
+    int fb = finish_blocks(a0.n_env, fa.nchunk, threads);
+    if (sc.reserve > 0) {
+      // one CTA per resident slot of every SM (those on reserved SMs return at once), items
+      // claimed dynamically, so the other SMs stay full until the work runs out
+      int fper = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, finish_kernel<NB, NV, NS, T>, threads, 0);
+      fb = ds_sm_count() * (fper > 0 ? fper : 1);
+      fa.fin_reserve = sc.reserve;
+      fa.claim = a0.ws.claim;
+    }
+    ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
+    finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
+    ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);
+    cudaEventRecord(a0.ev_join, a0.side);
+  };
+  if (overlap && sc.overlap_from < 0) fork_finish();
   for (int r = 0; r < DS_ROUNDS; ++r) {
     KArgs a = a0;
     a.round = r;
@@ -140,30 +178,7 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     }
     if (!launched) newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
-    if (overlap && r == sc.overlap_from) {
-      ds_trace_mark(DS_STAGE_FINISH, 1, s);
-      dcount_snapshot_kernel<<<1, 1, 0, s>>>(a0.ws.dcount);
-      ds_trace_mark(DS_STAGE_FINISH, 0, s);
-      cudaEventRecord(a0.ev_fork, s);
-      cudaStreamWaitEvent(a0.side, a0.ev_fork, 0);
-      KArgs fa = af;
-      fa.flo = nullptr;
-      fa.fhi = a0.ws.dcount + 1;
-      int fb = finish_blocks(a0.n_env, fa.nchunk, threads);
-      if (sc.reserve > 0) {
-        // one CTA per resident slot of every SM (those on reserved SMs return at once), items
-        // claimed dynamically, so the other SMs stay full until the work runs out
-        int fper = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, finish_kernel<NB, NV, NS, T>, threads, 0);
-        fb = ds_sm_count() * (fper > 0 ? fper : 1);
-        fa.fin_reserve = sc.reserve;
-        fa.claim = a0.ws.claim;
-      }
-      ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
-      finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
-      ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);
-      cudaEventRecord(a0.ev_join, a0.side);
-    }
+    if (overlap && r == sc.overlap_from) fork_finish();
   }
   if (overlap) {
     // the envs completed after the split: few, so every column gets its own thread

@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
   const int B = a.B;
   const int lane = threadIdx.x & 31;
   const int grp = lane / L;
-  coop::Smem<NS, T>& S = smem[(threadIdx.x >> 5) * EPW + grp];
+  coop::Smem<NS, T>& S = smem[DS_IX((threadIdx.x >> 5) * EPW + grp, (Sh::THREADS / 32) * EPW)];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t0 = warp * EPW; t0 < n; t0 += nwarps * EPW) {
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(coop::Shape<NS>::THREADS, coop::Shape<NS>::MIN
     // entry e: the env's ADMM stage ended; ~e: a speculative attempt on an unconverged iterate
     const int entry = have ? w.nlist[t] : 0;
     const bool spec = entry < 0;
-    const int e = spec ? ~entry : entry;
+    const int e = have ? DS_IX(spec ? ~entry : entry, B) : 0;
     coop::Lane<NS> ln;
     ln.li = lane - grp * L;
     ln.base = grp * L;

@@ -7,12 +7,14 @@
   void ds_pipeline_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);     \
   void ds_pipeline_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);   \
   void ds_tape_##NB##_##NV##_##NS##_f64(const KArgs&, cudaStream_t);         \
-  void ds_tape_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);
+  void ds_tape_##NB##_##NV##_##NS##_mix(const KArgs&, cudaStream_t);         \
+  unsigned ds_check_##NB##_##NV##_##NS##_f64();                              \
+  unsigned ds_check_##NB##_##NV##_##NS##_mix();
 #define DS_ROW(NB, NV, NS)                                                                          \
   {NB, NV, NS, DS_FP64, ds_launch_##NB##_##NV##_##NS##_f64, ds_pipeline_##NB##_##NV##_##NS##_f64,     \
-   ds_tape_##NB##_##NV##_##NS##_f64},                                                                 \
+   ds_tape_##NB##_##NV##_##NS##_f64, ds_check_##NB##_##NV##_##NS##_f64},                              \
   {NB, NV, NS, DS_MIXED, ds_launch_##NB##_##NV##_##NS##_mix, ds_pipeline_##NB##_##NV##_##NS##_mix,    \
-   ds_tape_##NB##_##NV##_##NS##_mix},
+   ds_tape_##NB##_##NV##_##NS##_mix, ds_check_##NB##_##NV##_##NS##_mix},
 
 #include "ds_shapes.inc"
 
@@ -37,4 +39,10 @@ const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int p
         (!best || k.ns < best->ns))
       best = &k;
   return best;
+}
+
+unsigned long long ds_check_sum() {
+  unsigned long long n = 0;
+  for (const ds_kernel_entry& k : kTable) n += k.check();
+  return n;
 }

@@ -371,20 +371,21 @@ def test_two_warp_admm_rounds(torch_cuda, pair):
     _same_solutions(ref, got)
 
 
-@pytest.mark.parametrize("overlap,reserve,B,caps", [(1, 1, 20000, 0), (2, 2, 20000, 0), (1, 1, 600, 1)])
+@pytest.mark.parametrize("overlap,reserve,B,caps", [(2, 1, 20000, 0), (3, 2, 20000, 0), (2, 1, 600, 1), (0, 1, 20000, 0)])
 def test_overlapped_finish_on_reserved_sms(torch_cuda, overlap, reserve, B, caps):
     """The overlapped finish that keeps every 8th (4th) SM free claims its work items dynamically
-    (the small batch: a launch of a few items per SM).  Each env's finish is the same code on the
+    (the small batch: a launch of a few items per SM), also when it starts right after the setup.  Each env's finish is the same code on the
     same inputs, so every output is bitwise that of the finish on every SM (the ADMM kernels are
     the same in both)."""
     import paper_2409_07107_gb300 as ds
     torch = torch_cuda
     wl = scenes.arm_cube(B)
     sim = ds.Simulator(wl, precision="fp64")
-    sim.set_schedule(ds.schedule_index(round_caps=caps, overlap=1, reserve=0))    # finish on every SM
+    sim.set_schedule(ds.schedule_index(round_caps=caps, overlap=overlap, reserve=0))    # finish on every SM
     ref = {k: v.clone() for k, v in sim.step_jac().items()}
     assert (ref["iters"] > 256).sum().item() >= 1          # some envs reach the late rounds
     desc = sim.set_schedule(ds.schedule_index(round_caps=caps, overlap=overlap, reserve=reserve))
+    assert desc["overlapped_finish_after_round"] == ("setup", 2, 4, 5, None)[overlap]
     assert desc["overlapped_finish_keeps_free_every_nth_sm"] == (None, 8, 4)[reserve]
     try:
         got = sim.step_jac()
@@ -510,10 +511,10 @@ def test_speculative_newton_attempts(torch_cuda):
     torch = torch_cuda
     wl = scenes.arm_cube(8000)
     sim = ds.Simulator(wl, precision="fp64")
-    sim.set_schedule(ds.schedule_index(spec=2))
+    sim.set_schedule(ds.schedule_index(spec=2, presolve=1))     # every env through the ADMM rounds
     try:
         ref = {k: v.clone() for k, v in sim.step_jac().items()}
-        sim.set_schedule(ds.schedule_index(spec=0))
+        sim.set_schedule(ds.schedule_index(spec=0, presolve=1))
         got = {k: v.clone() for k, v in sim.step_jac().items()}
         torch.cuda.synchronize()
     finally:
@@ -537,8 +538,12 @@ def test_pgs_solver(torch_cuda, precision, tol_v, tol_j, pipeline):
     wl = scenes.arm_cube(65536)
     sub = scenes.Workload(wl.name, wl.models, wl.batch.take(np.arange(300)), wl.options)
     sim = ds.Simulator(sub, precision=precision, pipeline=pipeline, ncp_solver=ds.DS_PGS)
-    out = sim.step_jac()
-    torch.cuda.synchronize()
+    sim.set_schedule(ds.schedule_index(presolve=1))      # every env with contacts through the sweeps
+    try:
+        out = sim.step_jac()
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
     g = {k: v.cpu().numpy() for k, v in out.items()}
     assert (g["iters"] > 0).sum() > 200
     envs = list(range(0, 300, 3))
@@ -546,3 +551,37 @@ def test_pgs_solver(torch_cuda, precision, tol_v, tol_j, pipeline):
     _compare(sub, g, refs, envs, tol_v, tol_j, min_checked=60)
     if precision == "fp64":
         assert not (g["status"] & 1).any()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_contact_presolve(torch_cuda, precision):
+    """The setup's exact solve for single-contact solutions (default schedule) against the same
+    step with every env through the ADMM rounds: most arm + cube envs are presolved (no ADMM
+    iteration), and both reach the same solutions (up to the documented non-unique ones); the
+    presolved envs also match the oracle."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(4000)
+    sim = ds.Simulator(wl, precision=precision)
+    sim.set_schedule(ds.schedule_index(presolve=1))
+    try:
+        ref = {k: v.clone() for k, v in sim.step_jac().items()}
+        sim.set_schedule(ds.schedule_index(presolve=0))
+        got = {k: v.clone() for k, v in sim.step_jac().items()}
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
+    if precision == "fp64":
+        _same_solutions(ref, got)
+    else:
+        scale = ref["v_next"].abs().amax(0).clamp_min(1e-6)
+        same = ((got["v_next"] - ref["v_next"]).abs().amax(0) / scale) <= 1e-4
+        assert same.float().mean().item() >= 0.995
+    pre = (got["iters"] == 0) & ((got["modes"] != 3).any(0))
+    assert pre.float().mean().item() >= 0.6, pre.float().mean().item()
+    envs = [int(e) for e in torch.nonzero(pre).flatten()[:40].cpu()]
+    g = {k: v[..., envs].cpu().numpy() for k, v in got.items()}
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(envs), wl.options)
+    refs = run_oracle(sub, list(range(len(envs))))
+    tol_v, tol_j = (1e-9, 1e-9) if precision == "fp64" else (1e-4, 1e-3)
+    _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=25)
