@@ -102,7 +102,10 @@ extern "C" ds_status ds_model_create(const ds_model_desc* d, ds_model** out) {
       while (b > i) b = h.parent[b];
       if (b == i) return DS_EINVAL;                          // not depth-first preorder
     }
-    for (int dd = h.iv[i]; dd < h.iv[i] + h.nd[i]; ++dd) h.dof_body[dd] = i;
+    for (int dd = h.iv[i]; dd < h.iv[i] + h.nd[i]; ++dd) {
+      h.dof_body[dd] = i;
+      h.dof_parent[dd] = dd > h.iv[i] ? dd - 1 : (h.parent[i] >= 0 ? h.iv[h.parent[i]] + h.nd[h.parent[i]] - 1 : -1);
+    }
   }
   ds_model* m = new (std::nothrow) ds_model;
   if (!m) return DS_ENOMEM;

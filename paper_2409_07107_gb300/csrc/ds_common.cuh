@@ -42,6 +42,7 @@ struct DevModel {
   int nb, nq, nv, pad;
   int parent[DS_MAXB], jtype[DS_MAXB], iq[DS_MAXB], iv[DS_MAXB], nd[DS_MAXB], sub_end[DS_MAXB];
   int dof_body[DS_MAXNV];
+  int dof_parent[DS_MAXNV];   // the dof before each dof on its path to the root (-1 at the root)
   double axis[DS_MAXB][3], jrot[DS_MAXB][9], jpos[DS_MAXB][3];
   double mass[DS_MAXB], com[DS_MAXB][3], inertia[DS_MAXB][6];
 };
@@ -359,6 +360,49 @@ DS_HDI void bwd_packed(const T* L, T* x, int n) {
     T s = x[i];
     for (int k = i + 1; k < n; ++k) s -= L[tri(k, i)] * x[k];
     x[i] = s / L[tri(i, i)];
+  }
+}
+
+// Factorisation M = L^T L of the joint-space inertia matrix, whose nonzeros lie on pairs of dofs one
+// of which is an ancestor of the other (par[k] < k is the dof before k on its path to the root, -1
+// at the root; packed lower storage, entries of other pairs zero).  The elimination runs from the
+// leaves to the root, so the factor keeps the tree's sparsity (no fill-in): the factorisation, and
+// the solves below, touch only ancestor pairs -- the kinematic-tree sparsity of Sec. 3.3 (for a
+// chain, every pair).  Returns false if M is not positive definite.
+template <typename T>
+DS_HD bool ltl_factor(T* L, int n, const int* par) {
+  for (int k = n - 1; k >= 0; --k) {
+    const T d = L[tri(k, k)];
+    if (!(d > T(0))) return false;
+    const T s = sqrt(d);
+    L[tri(k, k)] = s;
+    const T inv = T(1) / s;
+    for (int i = par[k]; i >= 0; i = par[DS_IX(i, n)]) L[tri(k, i)] *= inv;
+    for (int i = par[k]; i >= 0; i = par[DS_IX(i, n)]) {
+      const T a = L[tri(k, i)];
+      for (int j = i; j >= 0; j = par[DS_IX(j, n)]) L[tri(i, j)] -= a * L[tri(k, j)];
+    }
+  }
+  return true;
+}
+
+// x <- L^-T x (from the leaves to the root)
+template <typename T>
+DS_HDI void ltl_solve_t(const T* L, T* x, int n, const int* par) {
+  for (int k = n - 1; k >= 0; --k) {
+    const T xk = x[k] / L[tri(k, k)];
+    x[k] = xk;
+    for (int i = par[k]; i >= 0; i = par[DS_IX(i, n)]) x[i] -= L[tri(k, i)] * xk;
+  }
+}
+
+// x <- L^-1 x (from the root to the leaves); M^-1 b = L^-1 L^-T b
+template <typename T>
+DS_HDI void ltl_solve(const T* L, T* x, int n, const int* par) {
+  for (int k = 0; k < n; ++k) {
+    T s = x[k];
+    for (int i = par[k]; i >= 0; i = par[DS_IX(i, n)]) s -= L[tri(k, i)] * x[i];
+    x[k] = s / L[tri(k, k)];
   }
 }
 

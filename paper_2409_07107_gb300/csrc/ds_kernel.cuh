@@ -98,7 +98,7 @@ struct Env : Ncp<NS, T> {
   T S[NV][6];                                // world motion subspace of every dof
   T I[NB][10];                               // world spatial inertia of every body
   T V[NB][6], A[NB][6], VJ[NB][6], IV[NB][6], IA[NB][6], Fc[NB][6];
-  T L[NV * (NV + 1) / 2];                    // Cholesky factor of M (packed lower)
+  T L[NV * (NV + 1) / 2];                    // factor of M = L^T L (packed lower, tree-sparse)
   T v[NV], tau[NV], vdf[NV], vf[NV], vn[NV], astar[NV];
   int slot[NS], body[NS];
   T x[NS][3], c[NS][3], f[NS][3];            // body point, contact point, contact force (world)
@@ -985,7 +985,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     }
   }
 
-  // ---- F3 joint-space inertia by composite inertias (world frame: plain sums) + Cholesky
+  // ---- F3 joint-space inertia by composite inertias (world frame: plain sums), M = L^T L
   {
     T IC[NB][10];
     for (int i = 0; i < NB; ++i)
@@ -1007,12 +1007,12 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     }
     if constexpr (!Env<NB, NV, NS, T>::kDouble) {
       for (int k = 0; k < NV * (NV + 1) / 2; ++k) s.Ld_[k] = double(s.L[k]);
-      if (!chol_packed(s.Ld_, NV)) st |= DS_ENV_NONFINITE;
+      if (!ltl_factor(s.Ld_, NV, m.dof_parent)) st |= DS_ENV_NONFINITE;
     }
-    if (!chol_packed(s.L, NV)) st |= DS_ENV_NONFINITE;
+    if (!ltl_factor(s.L, NV, m.dof_parent)) st |= DS_ENV_NONFINITE;
     for (int k = 0; k < NV; ++k) s.vdf[k] = s.tau[k] - bias[k];
-    fwd_packed(s.L, s.vdf, NV);
-    bwd_packed(s.L, s.vdf, NV);
+    ltl_solve_t(s.L, s.vdf, NV, m.dof_parent);
+    ltl_solve(s.L, s.vdf, NV, m.dof_parent);
     for (int k = 0; k < NV; ++k) s.vf[k] = s.v[k] + T(a.dt) * s.vdf[k];
   }
 
@@ -1105,10 +1105,10 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
     }
   }
 
-  // ---- F6 Delassus matrix G = (L^-1 J^T)^T (L^-1 J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms).
+  // ---- F6 Delassus matrix G = (L^-T J^T)^T (L^-T J^T), Y = M^-1 J^T, g = J v_f (FP64 in both forms).
   for (int r = 0; r < mdim; ++r) {
     for (int k = 0; k < NV; ++k) Yd[r][k] = Jd[r][k];
-    fwd_packed(Ld, Yd[r], NV);
+    ltl_solve_t(Ld, Yd[r], NV, m.dof_parent);
   }
   for (int r = 0; r < mdim; ++r)
     for (int c = 0; c <= r; ++c) {
@@ -1119,7 +1119,7 @@ DS_HD uint32_t env_forward(const DevModel& m, const KArgs& a, const int e, Env<N
       if constexpr (!kD) { s.Gd_[r][c] = t; s.Gd_[c][r] = t; }
     }
   for (int r = 0; r < mdim; ++r) {
-    bwd_packed(Ld, Yd[r], NV);
+    ltl_solve(Ld, Yd[r], NV, m.dof_parent);
     double t = 0.0;
     for (int k = 0; k < NV; ++k) t += Jd[r][k] * double(s.vf[k]);
     s.gt[r] = T(t);
@@ -1510,13 +1510,13 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
         if (blk < 2) {
           T dtau[NV];
           rnea_tangent<NB, NV, NS, T>(m, s, blk, d, dtau);
-          fwd_packed(s.L, dtau, NV);
-          bwd_packed(s.L, dtau, NV);
+          ltl_solve_t(s.L, dtau, NV, m.dof_parent);
+          ltl_solve(s.L, dtau, NV, m.dof_parent);
           for (int k = 0; k < NV; ++k) Dc[k] = -dt * dtau[k] + (blk == 1 && k == d ? T(1) : T(0));
         } else {
           for (int k = 0; k < NV; ++k) Dc[k] = (k == d ? dt : T(0));
-          fwd_packed(s.L, Dc, NV);
-          bwd_packed(s.L, Dc, NV);
+          ltl_solve_t(s.L, Dc, NV, m.dof_parent);
+          ltl_solve(s.L, Dc, NV, m.dof_parent);
         }
         if (by_rows) {
           double rfull[3 * NS];
@@ -1527,7 +1527,8 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
               if (sz[ac] != 0)
-                for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * Dc[k];
+                for (int k = m.iv[DS_IX(s.body[ac], NB)] + m.nd[DS_IX(s.body[ac], NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
+                  t += s.Jc[3 * ac + r][k] * Dc[k];           // J_c rows: the body's ancestor dofs only
               rfull[3 * ac + r] = double(t);
             }
           }
@@ -1546,7 +1547,8 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             fk[2] += baumgarte_d(m, a, s, ac, blk, d);
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
-              for (int k = 0; k < NV; ++k) t += s.Jc[3 * ac + r][k] * Dc[k];
+              for (int k = m.iv[DS_IX(s.body[ac], NB)] + m.nd[DS_IX(s.body[ac], NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
+                t += s.Jc[3 * ac + r][k] * Dc[k];
               r3[r] = double(t);
             }
             if (sz[ac] == 3) {
@@ -1610,12 +1612,14 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
         }
         for (int r = 0; r < mdim; ++r) {
           const T zr = T(zeta[r]);
-          for (int k = 0; k < NV; ++k) ub[k] -= s.Jc[r][k] * zr;
+          const int b = s.body[r / 3];
+          for (int k = m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
+            ub[k] -= s.Jc[r][k] * zr;
         }
       }
       for (int k = 0; k < NV; ++k) w2[k] = ub[k];
-      fwd_packed(s.L, w2, NV);
-      bwd_packed(s.L, w2, NV);
+      ltl_solve_t(s.L, w2, NV, m.dof_parent);
+      ltl_solve(s.L, w2, NV, m.dof_parent);
       const int p0 = (2 * NV * chunk) / nchunk, p1 = (2 * NV * (chunk + 1)) / nchunk;
       for (int blk = 0; blk < 2; ++blk)
         for (int d = 0; d < NV; ++d) {
