@@ -13,7 +13,9 @@ and y = -(sigma + Gamma(sigma)), and lambda = Proj_K(lambda - (sigma + Gamma)/rh
 decomposition is exactly Eq. 1.  It is followed by Newton steps on the equations of the identified
 contact modes (Sec. 3.2, App. A).  A projected Gauss-Seidel solve (pgs), the other solver family
 the paper cites, has the same fixed points; solve_ncp can take either one as its iteration, which
-gives the tests two independent routes to a solution of Eq. 1.
+gives the tests two independent routes to a solution of Eq. 1.  A third route updates the ADMM
+penalty on the way (residual balancing, balance_rho): the adaptive-penalty variant of the same
+iteration, whose fixed points are again those of Eq. 1.
 
 The iteration's parameters are the plain textbook choices (penalty rho = the mean diagonal of G,
 no over-relaxation, stopping test on every iteration).  Eq. 1 can have several solutions (redundant
@@ -56,6 +58,9 @@ def proj_K(x, mu):
 RHO_SCALE = 1.0      # rho = RHO_SCALE * mean diagonal of G
 RELAX = 1.0          # relaxation of the x-step (1: none)
 CHECK_EVERY = 1      # the stopping test runs on every CHECK_EVERY-th iteration
+ADAPT_EVERY = 32     # route "admm_adaptive": iterations between penalty updates
+ADAPT_RATIO = 10.0   # residual imbalance that changes the penalty
+ADAPT_FACTOR = 2.0   # the penalty is multiplied or divided by this
 
 
 def admm_rho(G):
@@ -71,22 +76,46 @@ class AdmmState:
         self.y = np.zeros(m)
         self.sx = np.array(g, dtype=float)     # G x + g at the current x
         self.iters = 0
+        self.rho = None                        # the penalty (set on the first call)
 
 
-def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
+def admm_residuals(x, z, y, sx, mu):
+    """Primal and dual residuals of the ADMM iterate for the penalty update: ||x - z||_inf, and
+    ||y + sigma + Gamma(sigma)||_inf at sigma = G x + g, which vanishes at a fixed point (there
+    y = -(sigma + Gamma(sigma)), module docstring)."""
+    return float(np.max(np.abs(x - z))), float(np.max(np.abs(y + sx + desaxce(sx, mu))))
+
+
+def balance_rho(rho, r_primal, r_dual):
+    """Residual balancing (Boyd et al., Distributed optimization and statistical learning via ADMM,
+    2011, Sec. 3.4.1): a primal residual ADAPT_RATIO times the dual one raises the penalty by
+    ADAPT_FACTOR, the reverse lowers it; otherwise it is kept.  y is the unscaled multiplier, so it
+    needs no rescaling, and the fixed points do not depend on rho."""
+    if r_primal > ADAPT_RATIO * r_dual:
+        return rho * ADAPT_FACTOR
+    if r_dual > ADAPT_RATIO * r_primal:
+        return rho / ADAPT_FACTOR
+    return rho
+
+
+def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None, adapt=False):
     """ADMM iteration for Eq. 1 (reading stated in the module docstring): the De Saxce term is taken
     at the most recent primal iterate x; with RELAX != 1 the x-step is relaxed,
     xh = RELAX x + (1 - RELAX) z, before the z-step and the dual step (the fixed points are
     unchanged).  G x is not recomputed: (G + rho I) x = rhs gives G x = rhs - rho x.  Stops when
     ||x - z||_inf <= eps max(1, ||z||_inf) and rho ||z - z_prev||_inf <= eps max(1, ||g||_inf), or
     when the state has done max_iter iterations in total; the test is evaluated when the cumulative
-    iteration count is a multiple of CHECK_EVERY.  Continues from ``state`` when given.
-    Returns (lambda, iterations, converged, state)."""
+    iteration count is a multiple of CHECK_EVERY.  Continues from ``state`` when given.  With
+    ``adapt`` the penalty is updated by balance_rho after every ADAPT_EVERY-th iteration (counted
+    over the state's life) that did not stop the iteration, and G + rho I is factored again when it
+    changes.  Returns (lambda, iterations, converged, state)."""
     m = len(g)
     st = state or AdmmState(m, g)
     if m == 0:
         return np.zeros(0), 0, True, st
-    rho = admm_rho(G)
+    if st.rho is None:
+        st.rho = admm_rho(G)
+    rho = st.rho
     L = cholesky(G + rho * np.eye(m))
     gs = max(1.0, np.max(np.abs(g)))
     x, z, y, sx = st.x, st.z, st.y, st.sx
@@ -107,7 +136,12 @@ def admm(G, g, mu, eps=1e-12, max_iter=20000, state=None):
         if rp <= eps * max(1.0, np.max(np.abs(z))) and rd <= eps * gs:
             conv = True
             break
-    st.x, st.z, st.y, st.sx = x, z, y, sx
+        if adapt and st.iters % ADAPT_EVERY == 0:
+            new = balance_rho(rho, *admm_residuals(x, z, y, sx, mu))
+            if new != rho:
+                rho = new
+                L = cholesky(G + rho * np.eye(m))
+    st.x, st.z, st.y, st.sx, st.rho = x, z, y, sx, rho
     return z.copy(), st.iters, conv, st
 
 
@@ -176,7 +210,8 @@ def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4
               rounds=4, max_iter=50000, route="admm"):
     """Staged solve of Eq. 1.  When the free motion separates every contact the solution with no
     impulse is returned (module docstring).  Otherwise each stage continues the iteration of the
-    route ("admm", or "pgs": projected Gauss-Seidel sweeps) to a tolerance, identifies the contact
+    route ("admm"; "admm_adaptive": the same with the penalty updated by residual balancing; or
+    "pgs": projected Gauss-Seidel sweeps) to a tolerance, identifies the contact
     modes, and runs up to ``rounds`` active-set rounds of Newton on the mode equations (reclassify +
     retry from the cone projection of the last iterate).  The first candidate whose NCP residual is
     <= tol max(1, ||g||_inf) is accepted.  Returns (lambda, iterations, converged)."""
@@ -189,8 +224,9 @@ def solve_ncp(G, g, mu, eps_sigma=1e-8, eps_lambda=1e-8, tol=1e-12, stages=(1e-4
     best, best_r = None, np.inf
     state, lam, iters = None, None, 0
     for eps in stages:
-        if route == "admm":
-            lam, iters, _, state = admm(G, g, mu, eps=eps, max_iter=max_iter, state=state)
+        if route in ("admm", "admm_adaptive"):
+            lam, iters, _, state = admm(G, g, mu, eps=eps, max_iter=max_iter, state=state,
+                                        adapt=route == "admm_adaptive")
         elif route == "pgs":
             lam, sweeps, _ = pgs(G, g, mu, eps=eps, max_iter=max(1, max_iter - iters), lam0=lam)
             iters += sweeps
