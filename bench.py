@@ -622,28 +622,78 @@ def main():
     # the same step with projected Gauss-Seidel as the NCP iteration (ncp_solver = DS_PGS), FP64,
     # default schedule: same Newton polish and FP64 residual acceptance, so the comparison is at
     # equal NCP residual
-    pgs = None
+    pgs = adaptive = None
     if not vjp:
-        sim = ds.Simulator(wl, precision="fp64", ncp_solver=ds.DS_PGS, **gains)
-        for _ in range(max(2, args.warmup)):
-            one_step(sim)
-        torch.cuda.synchronize()
-        pt = []
-        for _ in range(max(3, min(args.steps, 10))):
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            one_step(sim)
-            e1.record(stream)
+        def variant(**kw):
+            sim = ds.Simulator(wl, precision="fp64", **kw, **gains)
+            for _ in range(max(2, args.warmup)):
+                one_step(sim)
             torch.cuda.synchronize()
-            pt.append(e0.elapsed_time(e1))
-        pit = sim.out["iters"].cpu().numpy().astype(np.int64)
-        pst = sim.out["status"].cpu().numpy()
-        pms = replicas.slowest_ms(float(np.mean(pt)))
-        pgs = {"value": replicas.job_throughput(B, world, pms), "ms_per_step": pms,
-               "sweeps": {"mean": float(pit.mean()), "p50": float(np.median(pit)), "p99": float(np.percentile(pit, 99)),
-                          "max": int(pit.max())},
-               "not_converged": int((pst & 1 != 0).sum())}
+            pt = []
+            for _ in range(max(3, min(args.steps, 10))):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                one_step(sim)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pt.append(e0.elapsed_time(e1))
+            pit = sim.out["iters"].cpu().numpy().astype(np.int64)
+            pst = sim.out["status"].cpu().numpy()
+            pms = replicas.slowest_ms(float(np.mean(pt)))
+            del sim
+            return {"value": replicas.job_throughput(B, world, pms), "ms_per_step": pms,
+                    "iters": {"mean": float(pit.mean()), "p50": float(np.median(pit)),
+                              "p99": float(np.percentile(pit, 99)), "max": int(pit.max())},
+                    "not_converged": int((pst & 1 != 0).sum())}
+        pgs = variant(ncp_solver=ds.DS_PGS)
+        adaptive = variant(admm_rho_adapt=1)
+
+    # the mixed-robot batch as one persistent launch (schedule knob "launch"; mixed precision, the
+    # form it is compiled for) against the workspace pipeline, each eager and replayed from a CUDA
+    # graph; the pipeline runs the tuner's other knobs (or the default schedule without tuning)
+    persist = None
+    if vjp:
+        sim = ds.Simulator(wl, precision="mixed", **gains)
+        tuned = results["mixed"]["schedule"]
+        half = ds.NUM_SCHEDULES // 2              # the launch knob is the highest digit
+        pipe_idx = tuned["index"] % half if tuned else ds.schedule_index()
+        forms = {}
+        try:
+            for form, idx in (("persistent", ds.schedule_index(launch=1)), ("pipeline", pipe_idx)):
+                sim.set_schedule(idx, "vjp")
+                for _ in range(max(2, args.warmup)):
+                    one_step(sim)
+                torch.cuda.synchronize()
+                pt, gt = [], []
+                for _ in range(max(3, min(args.steps, 10))):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    one_step(sim)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    pt.append(e0.elapsed_time(e1))
+                pst = sim.out["status"].cpu().numpy()
+                replay = sim.capture("vjp", vbar)
+                for _ in range(max(3, min(args.steps, 10))):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    replay()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    gt.append(e0.elapsed_time(e1))
+                del replay
+                pms, gms = replicas.slowest_ms(float(np.mean(pt))), replicas.slowest_ms(float(np.mean(gt)))
+                forms[form] = {"value": replicas.job_throughput(B, world, pms), "ms_per_step": pms,
+                               "cuda_graph_replay": {"value": replicas.job_throughput(B, world, gms),
+                                                     "ms_per_step": gms},
+                               "schedule_index": idx, "queue_timeouts": int((pst & 32 != 0).sum())}
+        finally:
+            sim.set_schedule(tuned["index"] if tuned else -1, "vjp")
+        forms["persistent"]["launches_per_step"] = 1
+        persist = forms
         del sim
 
     # end-to-end through the public API with host buffers (pinned), copies inside the timed region
@@ -720,8 +770,18 @@ def main():
                           "env_status": rmx["status"], "stage_roofline": rmx["stage_roofline"],
                           "error_vs_fp64_oracle": None if errors is None else errors["mixed"]},
                 "pgs_fp64": pgs,
+                "adaptive_rho_fp64": adaptive,
+                "adaptive_rho_note": "the FP64 step with the ADMM penalty updated between rounds by residual "
+                                     "balancing (admm_rho_adapt = 1; default schedule), accepted by the same "
+                                     "FP64 NCP residual test; iters = ADMM iterations",
+                "persistent_launch_mixed": persist,
+                "persistent_note": "mixed precision: the step + VJP as one persistent kernel (warps pull chunks "
+                                   "of 32 envs of one model from an atomic queue, one env per lane) and as "
+                                   "the workspace pipeline (the tuner's other knobs), eager and from a CUDA "
+                                   "graph",
                 "pgs_note": "the FP64 step with projected Gauss-Seidel sweeps as the NCP iteration (default "
-                            "schedule), accepted by the same FP64 NCP residual test as the ADMM form",
+                            "schedule), accepted by the same FP64 NCP residual test as the ADMM form; "
+                            "iters = sweeps",
                 "fma_peak_tflops": fma, "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -28,7 +28,8 @@
  *   - modes [ncmax][B]: DS_MODE_* per slot;
  *   - Jacobians dv_dq, dv_dv, dv_dtau [nv][nv][B]: element (row i, col j) at (i*nv + j)*B + e;
  *   - a batch may mix models (model_id): each env reads and writes the leading nq / nv rows of
- *     the arrays for its own model.
+ *     the arrays for its own model; its Jacobians use the leading nv*nv rows of the [nv_max^2][B]
+ *     arrays, element (i, j) at (i*nv + j)*B + e with its own model's nv.
  * All calls are asynchronous on the given stream (a cudaStream_t passed as void*, NULL = default
  * stream).  The return code reports argument and launch errors only; per-environment numerical
  * outcomes go to env_status.  Inputs are never modified.
@@ -72,6 +73,9 @@ enum { DS_MODE_BREAKING = 0, DS_MODE_STICKING = 1, DS_MODE_SLIDING = 2, DS_MODE_
 #define DS_ENV_SINGULAR      4u  /* the reduced implicit system was rank deficient (basic solution used) */
 #define DS_ENV_NEAR_SWITCH   8u  /* mode-classification margin below margin_delta               */
 #define DS_ENV_BAD_SLOT     16u  /* a contact slot beyond the model's declared slot count is in use */
+#define DS_ENV_QUEUE_TIMEOUT 32u  /* persistent launch: not processed, because a wait of the work */
+                                  /* queue ran out (queue_poll_limit); v_next holds NaN and the   */
+                                  /* env's other outputs are not written                          */
 
 /* Host description of a kinematic tree; copied by ds_model_create (the caller keeps ownership).
  * Bodies are numbered in depth-first preorder (parent[i] < i and every subtree is a contiguous
@@ -138,6 +142,17 @@ typedef struct {
                              /* on penetration only), so it may approach the plane by at most   */
                              /* phi within the step.  Negative or non-finite: DS_EINVAL         */
   int32_t ncp_solver;        /* ds_solver (default DS_ADMM); other values: DS_EINVAL             */
+  int32_t queue_poll_limit;  /* persistent launch (a schedule of ds_autotune / ds_set_schedule):  */
+                             /* polls (~256 ns apart) a CTA makes of the work queue's partition */
+                             /* count before it gives up; the envs then left unprocessed get    */
+                             /* DS_ENV_QUEUE_TIMEOUT.  Default 2^22; negative: DS_EINVAL         */
+  int32_t admm_rho_adapt;    /* 1: adaptive ADMM penalty (an ADMM variant among the solver      */
+                             /* alternatives of Sec. 2.2): between the solver's rounds, residual */
+                             /* balancing of rho on each env's iterate (primal ||x - z||, dual   */
+                             /* ||y + sigma + Gamma(sigma)||; a tenfold imbalance doubles or     */
+                             /* halves rho) and K = (G + rho I)^-1 formed again when it changes; */
+                             /* same fixed points, same Newton polish and FP64 acceptance.      */
+                             /* 0 (default): fixed rho.  ADMM only; other values: DS_EINVAL      */
 } ds_options;
 
 /* Fill *opt with the defaults used by the tests and the benchmark (start from these and set the
@@ -270,7 +285,17 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * iterating in the same stage), and whether the setup solves Eq. 1 exactly for the envs whose
  * solution has a single contact in contact and every other contact breaking (the sticking
  * impulse -G_ii^-1 g_i, else Newton on the sliding equations from its cone projection, accepted by
- * the same FP64 NCP residual test as the Newton stage), so that those envs skip the ADMM rounds.
+ * the same FP64 NCP residual test as the Newton stage), so that those envs skip the ADMM rounds;
+ * and whether the step runs as the pipeline above or as one persistent launch: a kernel sized to
+ * the CTAs the GPU keeps resident, whose warps pull chunks of 32 envs of one model from an atomic
+ * work queue (the costliest model's chunks first) and run one env per lane through the whole
+ * step (the fused per-env form of every stage), all models of the batch in the same kernel.  The
+ * persistent launch exists for the shapes compiled into it (a 7-dof arm with 8 contact slots, an
+ * 18-dof quadruped with 4 and a 36-dof humanoid with 16, DS_MIXED only) and at most 4
+ * models; a batch with another shape runs the pipeline under such a schedule.  Its queue can
+ * only be read once every CTA has filed its share of the envs into the per-model lists; a CTA
+ * polls for that at most queue_poll_limit times (ds_options), and when one gives up, every CTA
+ * stops claiming work and the envs left get DS_ENV_QUEUE_TIMEOUT.
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
  * schedule by the second slowest of five runs (so that a schedule whose step time varies from
@@ -289,14 +314,15 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * runs (every accepted impulse passes the same NCP residual test; where Eq. 1 has several
  * solutions, two schedules can return different ones).
  * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
- * the schedule's index (0 .. 14579), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 5 (p +
- * 3 (r + 3 (s + 3 x))))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane
+ * the schedule's index (0 .. 29159), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 5 (p +
+ * 3 (r + 3 (s + 3 (x + 2 u)))))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane
  * round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0
  * cooperative, 1 one thread per env), overlapped finish o (0: after the setup, 1: after round 2,
  * 2: after round 4, 3: after round 5, 4: never), two-warp ADMM p (0: from round 3, 1: from round 5,
  * 2: never), SMs kept
  * free r (0: none, 1: every 8th, 2: every 4th), speculative Newton attempts s (0: from round 3, 1:
- * from round 5, 2: never), single-contact presolve x (0 on, 1 off).  Errors: DS_EINVAL, DS_ECUDA,
+ * from round 5, 2: never), single-contact presolve x (0 on, 1 off), launch u (0 pipeline, 1
+ * persistent).  Errors: DS_EINVAL, DS_ECUDA,
  * those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
@@ -306,7 +332,7 @@ ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_b
 /* Sets the schedule (index as ds_autotune's *chosen) that later calls of `mode` use for batches
  * with this batch's signature, as if ds_autotune had chosen it; index -1 returns the signature to
  * the default schedule (no counterpart in the paper).  For reusing a tuned schedule without timing
- * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 14579). */
+ * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 29159). */
 ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                           const ds_options* opt, int32_t mode, int32_t index);
 

@@ -25,7 +25,7 @@ DS_OK, DS_EINVAL, DS_ECUDA, DS_ENOMEM, DS_EUNSUPPORTED, DS_ETOOLARGE = 0, -1, -2
 DS_FP64, DS_MIXED = 0, 1
 DS_ADMM, DS_PGS = 0, 1
 MODE_BREAKING, MODE_STICKING, MODE_SLIDING, MODE_INACTIVE = 0, 1, 2, 3
-ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT = 1, 2, 4, 8, 16
+ENV_NOT_CONVERGED, ENV_NONFINITE, ENV_SINGULAR, ENV_NEAR_SWITCH, ENV_BAD_SLOT, ENV_QUEUE_TIMEOUT = 1, 2, 4, 8, 16, 32
 
 EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_default",
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
@@ -53,7 +53,8 @@ class ds_options(ctypes.Structure):
                 ("eps_sigma", ctypes.c_double), ("eps_lambda", ctypes.c_double),
                 ("margin_delta", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("baumgarte_kp", ctypes.c_double), ("baumgarte_kd", ctypes.c_double),
-                ("contact_margin", ctypes.c_double), ("ncp_solver", ctypes.c_int32)]
+                ("contact_margin", ctypes.c_double), ("ncp_solver", ctypes.c_int32),
+                ("queue_poll_limit", ctypes.c_int32), ("admm_rho_adapt", ctypes.c_int32)]
 
 
 class ds_step_out(ctypes.Structure):
@@ -247,8 +248,9 @@ SCHEDULE_KNOBS = (
     ("overlapped_finish_keeps_free_every_nth_sm", (None, 8, 4)),
     ("speculative_newton_from_round", (3, 5, None)),
     ("single_contact_presolve", (True, False)),
+    ("launch", ("pipeline", "persistent")),
 )
-NUM_SCHEDULES = 14580
+NUM_SCHEDULES = 29160
 
 
 def describe_schedule(index):
@@ -260,11 +262,12 @@ def describe_schedule(index):
     return d
 
 
-def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=3, pair=1, reserve=1, spec=2, presolve=0):
+def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=3, pair=1, reserve=1, spec=2, presolve=0,
+                   launch=0):
     """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
     defaults give the library's default schedule."""
     idx, mul = 0, 1
-    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec, presolve),
+    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec, presolve, launch),
                               SCHEDULE_KNOBS):
         assert 0 <= pos < len(opts)
         idx += pos * mul

@@ -30,6 +30,18 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _unit_flags(src):
+    """Relocatable device code for the persistent kernel's units (its per-shape steps are device
+    functions of other units, resolved by a device link); the steps' units at the kernel's register
+    budget (128 per thread: __launch_bounds__(128, 4))."""
+    name = os.path.basename(src)
+    if name.startswith("ds_persist_part_"):
+        return ["-rdc=true", "-maxrregcount=128"]
+    if name.startswith("ds_persist"):
+        return ["-rdc=true"]
+    return []
+
+
 def _stale(src, obj):
     if not os.path.exists(obj):
         return True
@@ -49,11 +61,14 @@ def build(verbose=False, jobs=None, check=False):
     nvcc = _nvcc()
     srcs = sources()
     objs = [os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    todo = [(s, o) for s, o in zip(srcs, objs) if _stale(s, o)]
+    # the large units (the humanoid shapes and the persistent kernel) first, so that they do not
+    # start last and set the build's length
+    todo = sorted(((s, o) for s, o in zip(srcs, objs) if _stale(s, o)),
+                  key=lambda so: (not any(t in os.path.basename(so[0]) for t in ("_31_36_", "persist_part")), so[0]))
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc] + ARCH + flags + ["-c", s, "-o", o]
+        cmd = [nvcc] + ARCH + flags + _unit_flags(s) + ["-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (s, r.stdout, r.stderr))
@@ -66,7 +81,17 @@ def build(verbose=False, jobs=None, check=False):
                 if verbose:
                     print("compiled", os.path.basename(s), flush=True)
     if todo or not os.path.exists(lib):
-        cmd = [nvcc] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs + ["-lcudart"]
+        # device link of the relocatable units (the persistent kernel and its per-shape steps)
+        rdc = [o for s, o in zip(srcs, objs) if _unit_flags(s)]
+        link_objs = list(objs)
+        if rdc:
+            dlink = os.path.join(obj_dir, "ds_dlink.o")
+            r = subprocess.run([nvcc] + ARCH + ["-dlink", "-Xcompiler", "-fPIC"] + rdc + ["-o", dlink],
+                               capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError("device link failed:\n%s\n%s" % (r.stdout, r.stderr))
+            link_objs.append(dlink)
+        cmd = [nvcc] + ARCH + ["-shared", "-o", lib + ".tmp"] + link_objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

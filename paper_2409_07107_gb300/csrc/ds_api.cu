@@ -32,6 +32,8 @@ extern "C" void ds_options_default(ds_options* o) {
   o->baumgarte_kd = 0.0;
   o->contact_margin = 0.0;
   o->ncp_solver = DS_ADMM;
+  o->queue_poll_limit = 1 << 22;
+  o->admm_rho_adapt = 0;
 }
 
 extern "C" const char* ds_status_string(ds_status s) {
@@ -202,7 +204,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS, 1};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS, 1, 0};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -229,6 +231,46 @@ static ds_schedule find_schedule(const SchedKey& k) {
   return it == g_sched.end() ? kDefaultSchedule : it->second;
 }
 
+// The whole step as one persistent launch (ds_schedule.persistent) when a persistent kernel with
+// the shape of every model's fitted kernel is compiled; DS_EUNSUPPORTED (nothing launched) when not.
+static ds_status run_persistent(const ds_model* const* models, int32_t nmodels, const ds_batch* b,
+                                const ds_options* o, const ds_kernel_entry* const* kern, int fw_rows, void* ws,
+                                KArgs a, cudaStream_t s) {
+  const ds_persist_entry* pe = nmodels <= DS_PERSIST_MAXMODELS ? ds_persist_kernel(o->precision) : nullptr;
+  if (!pe) return DS_EUNSUPPORTED;
+  PArgs p;
+  std::memset(&p, 0, sizeof(p));
+  long long cost[DS_PERSIST_MAXMODELS];
+  for (int k = 0; k < nmodels; ++k) {
+    int found = -1;
+    for (int i = 0; i < pe->nshapes && found < 0; ++i)
+      if (pe->shape[i][0] == kern[k]->nb && pe->shape[i][1] == kern[k]->nv && pe->shape[i][2] == kern[k]->ns)
+        found = i;
+    if (found < 0) return DS_EUNSUPPORTED;
+    p.model[k] = models[k]->dev;
+    p.shape[k] = found;
+    p.nv[k] = models[k]->host.nv;
+    p.order[k] = k;
+    cost[k] = (long long)kern[k]->nv * kern[k]->nv * (kern[k]->ns + 1);   // rough per-env cost
+  }
+  // the costliest model's chunks first, so that the cheap ones fill in at the end
+  std::sort(p.order, p.order + nmodels, [&](int x, int y) { return cost[x] > cost[y] || (cost[x] == cost[y] && x < y); });
+  ds_workspace_layout(b->ncmax, b->B, ws, &a.ws, nmodels, 0, fw_rows);
+  p.nmodels = nmodels;
+  p.poll_limit = o->queue_poll_limit;
+  p.queue = a.ws.queue;
+  p.lists = a.ws.qlists;
+  a.model = nullptr;
+  a.model_index = 0;
+  a.model_id = b->model_id;
+  a.env_list = nullptr;
+  a.n_env = b->B;
+  if (cudaMemsetAsync(p.queue, 0, sizeof(int32_t) * (DS_Q_COUNT + DS_PERSIST_MAXMODELS), s) != cudaSuccess)
+    return DS_ECUDA;
+  pe->launch(a, p, s);
+  return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ECUDA;
+}
+
 static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_batch* b, const ds_options* o,
                      const ds_step_out* out, int mode, double* dq, double* dv, double* dtau, const double* vbar,
                      const double* qnbar, double* qb, double* vb, double* tb, void* ws, size_t ws_bytes,
@@ -246,6 +288,8 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   if (!std::isfinite(o->baumgarte_kp) || !std::isfinite(o->baumgarte_kd)) return DS_EINVAL;
   if (!(o->contact_margin >= 0.0) || !std::isfinite(o->contact_margin)) return DS_EINVAL;
   if (o->ncp_solver != DS_ADMM && o->ncp_solver != DS_PGS) return DS_EINVAL;
+  if (o->queue_poll_limit < 0) return DS_EINVAL;
+  if (o->admm_rho_adapt != 0 && o->admm_rho_adapt != 1) return DS_EINVAL;
   if (mode == DS_RUN_JAC && (!dq || !dv || !dtau)) return DS_EINVAL;
   if (mode == DS_RUN_VJP && (!vbar || !qb || !vb || !tb)) return DS_EINVAL;
   const ds_kernel_entry* kern[64];
@@ -270,6 +314,7 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   a.dt = o->dt; a.gx = o->gravity[0]; a.gy = o->gravity[1]; a.gz = o->gravity[2];
   a.bkp = o->baumgarte_kp; a.bkd = o->baumgarte_kd; a.cmargin = o->contact_margin;
   a.solver = o->ncp_solver;
+  a.rho_adapt = o->ncp_solver == DS_ADMM && o->admm_rho_adapt;
   a.admm_max_iter = o->admm_max_iter; a.polish_iters = o->polish_iters;
   a.admm_eps = o->admm_eps; a.ncp_tol = o->ncp_tol;
   a.eps_sigma = o->eps_sigma; a.eps_lambda = o->eps_lambda; a.margin_delta = o->margin_delta;
@@ -297,6 +342,10 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
   }
   a.sched = g_force_sched ? *g_force_sched : find_schedule(sched_key(models, nmodels, b, o, mode));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ws && a.sched.persistent) {
+    const ds_status r = run_persistent(models, nmodels, b, o, kern, fw_rows, ws, a, s);
+    if (r != DS_EUNSUPPORTED) return r;
+  }
   HelperStreams* hs = nullptr;
   if (ws && g_allow_helpers && helper_streams(&hs) != DS_OK) return DS_ECUDA;
   a.side = nullptr;
@@ -438,8 +487,8 @@ extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int3
 
 // Schedule knobs and their options.  The index of ds_autotune / ds_set_schedule is the mixed-radix
 // number of the chosen option positions, knob 0 the lowest digit.
-static const int kKnobs = 9, kNumSchedules = 3 * 3 * 3 * 2 * 5 * 3 * 3 * 3 * 2;
-static const int kNopt[kKnobs] = {3, 3, 3, 2, 5, 3, 3, 3, 2};
+static const int kKnobs = 10, kNumSchedules = 3 * 3 * 3 * 2 * 5 * 3 * 3 * 3 * 2 * 2;
+static const int kNopt[kKnobs] = {3, 3, 3, 2, 5, 3, 3, 3, 2, 2};
 static const int kOpt[kKnobs][5] = {{0, 1, 2, 0},          // round-cap table
                                     {3, 5, DS_ROUNDS, 0},  // first row-per-lane ADMM round
                                     {0, 4, 8, 0},          // finish: target CTAs per SM
@@ -448,7 +497,8 @@ static const int kOpt[kKnobs][5] = {{0, 1, 2, 0},          // round-cap table
                                     {3, 5, DS_ROUNDS, 0},  // first two-warp ADMM round
                                     {0, 8, 4, 0},          // overlapped finish: SM stride kept free
                                     {3, 5, DS_ROUNDS, 0},  // speculative Newton attempts from round
-                                    {1, 0, 0, 0}};         // single-contact presolve: on / off
+                                    {1, 0, 0, 0},          // single-contact presolve: on / off
+                                    {0, 1, 0, 0}};         // workspace pipeline / persistent launch
 static int* knob(ds_schedule& c, int d) {
   switch (d) {
     case 0: return &c.caps;
@@ -459,7 +509,8 @@ static int* knob(ds_schedule& c, int d) {
     case 5: return &c.pair_from;
     case 6: return &c.reserve;
     case 7: return &c.spec_from;
-    default: return &c.presolve;
+    case 8: return &c.presolve;
+    default: return &c.persistent;
   }
 }
 static int schedule_index(ds_schedule c) {

@@ -112,7 +112,15 @@ struct WsView {
   int32_t* dlist;         // [B] envs whose NCP solve is complete, in completion order
   int32_t* dcount;        // [2] entries of dlist; a snapshot of it (follows fetch)
   int32_t* claim;         // [1] next unclaimed work item of the overlapped finish (follows dcount)
+  int32_t* queue;         // [DS_Q_COUNT + DS_PERSIST_MAXMODELS] persistent launch: queue words, then
+                          // the length of each model's env list
+  int32_t* qlists;        // [nmodels][B] persistent launch: env indices of each model
 };
+
+// Persistent launch (ds_schedule.persistent): at most this many models in a batch, and the words
+// at the head of WsView.queue.
+#define DS_PERSIST_MAXMODELS 4
+enum { DS_Q_PARTED = 0, DS_Q_ABANDON = 1, DS_Q_NEXT = 2, DS_Q_TIMEOUTS = 3, DS_Q_COUNT = 4 };
 
 // Lays out the workspace for ns contact slots, B envs, nmodels models and fw_rows rows of forward
 // state per env starting at base (may be NULL to size it), and returns its size.  The per-env arrays are shared; every model has its own
@@ -146,6 +154,8 @@ inline size_t ds_workspace_layout(int ns, int B, void* base, WsView* v, int nmod
   w.K = static_cast<double*>(take(sizeof(double) * nc3 * nc3 * size_t(B)));
   w.rho = static_cast<double*>(take(sizeof(double) * size_t(B)));
   w.fw = static_cast<double*>(take(sizeof(double) * size_t(fw_rows) * size_t(B)));
+  w.queue = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_Q_COUNT + DS_PERSIST_MAXMODELS)));
+  w.qlists = static_cast<int32_t*>(take(sizeof(int32_t) * size_t(nmodels) * size_t(B)));
   for (int k = 0; k < nmodels; ++k) {
     int32_t* counts = static_cast<int32_t*>(take(sizeof(int32_t) * (DS_ROUNDS + 1)));
     int32_t* l0 = static_cast<int32_t*>(take(sizeof(int32_t) * B));
@@ -189,6 +199,9 @@ struct ds_schedule {
                       // contact (DS_ROUNDS = never)
   int presolve;       // 1: the setup solves Eq. 1 exactly for the envs whose solution has a single
                       // contact in contact (the others breaking), which then skip the ADMM rounds
+  int persistent;     // 1: the whole step as one persistent launch over an atomic work queue (one
+                      // env per lane, every model of the batch in the same kernel), where a kernel
+                      // with the batch's shapes is compiled; 0: the workspace pipeline
 };
 
 // Everything a launch needs; passed by value.
@@ -206,6 +219,7 @@ struct KArgs {
   double bkp, bkd;         // Baumgarte gains (App. D); 1, 0 (and no margin): no term
   double cmargin;          // activation distance: a slot is active when phi <= cmargin
   int solver;              // ds_solver: the NCP iteration (ADMM or projected Gauss-Seidel)
+  int rho_adapt;           // ADMM penalty updated between rounds by residual balancing
   int admm_max_iter, polish_iters;
   double admm_eps, ncp_tol, eps_sigma, eps_lambda, margin_delta;
   double *v_next, *q_next, *lambda;
@@ -253,6 +267,28 @@ struct ds_kernel_entry {
   ds_launch_fn tape;       // finish only, from a tape (KArgs.tlam / tmodes / tstat)
   unsigned (*check)();     // checked build: reads and clears the shape's bad-index count (else 0)
 };
+// Persistent launch: the models of the batch (device copies), each one's index in the kernel's
+// shape list, the order in which their chunks of envs are numbered, and the queue.
+struct PArgs {
+  const DevModel* model[DS_PERSIST_MAXMODELS];
+  int shape[DS_PERSIST_MAXMODELS];   // index of each model's shape in the kernel's shape list
+  int order[DS_PERSIST_MAXMODELS];   // models in the order their chunks are numbered
+  int nv[DS_PERSIST_MAXMODELS];      // velocity dofs of each model (the NaN preset of v+)
+  int nmodels;
+  int poll_limit;                    // polls of the partition count before a CTA gives up
+  int32_t* queue;                    // WsView.queue
+  int32_t* lists;                    // WsView.qlists
+};
+typedef void (*ds_persist_fn)(const KArgs& a, const PArgs& p, cudaStream_t s);
+struct ds_persist_entry {
+  int precision, nshapes;
+  int shape[DS_PERSIST_MAXMODELS][3];   // {bodies, dofs, contact slots} per shape index
+  ds_persist_fn launch;
+  unsigned (*check)();
+};
+// The persistent kernel of a precision (NULL if none is compiled).
+extern "C++" const ds_persist_entry* ds_persist_kernel(int precision);
+
 // Sum over the compiled shapes of their bad-index counts, cleared (0 in the normal build).
 extern "C++" unsigned long long ds_check_sum();
 extern "C++" const ds_kernel_entry* ds_find_kernel(int nb, int nv, int ns, int precision);

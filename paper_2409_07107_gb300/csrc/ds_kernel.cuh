@@ -405,6 +405,9 @@ struct Pgs {
   T ir[NS];
 
   template <class P>
+  DS_HD void adapt(const P&) {}                // no penalty to adapt
+
+  template <class P>
   DS_HD bool setup(const P& p) {
     bool ok = true;
     for (int i = 0; i < p.na; ++i) {
@@ -449,6 +452,34 @@ struct Pgs {
   }
 };
 
+// Adaptive penalty (options admm_rho_adapt): residual balancing (Boyd et al., Distributed
+// optimization and statistical learning via ADMM, 2011, Sec. 3.4.1), with the residuals of this
+// iteration's fixed point: primal ||x - z||_inf and dual ||y + sigma + Gamma(sigma)||_inf at
+// sigma = sx = G x + g (zero at a solution of Eq. 1, where y = -(sigma + Gamma)).  A primal
+// residual ten times the dual one doubles rho, the reverse halves it.  y is the unscaled
+// multiplier, so it is kept as it is; the fixed points do not depend on rho.  In FP64 in both
+// precisions (the pipeline reads the state from the workspace, the fused path from registers:
+// the same values).
+template <typename V, typename M>
+DS_HDI void admm_residuals(int na, const M* mu, const V* x, const V* z, const V* y, const V* sx, double& rp,
+                           double& rd) {
+  rp = 0.0;
+  rd = 0.0;
+  for (int i = 0; i < na; ++i) {
+    const double s0 = double(sx[3 * i]), s1 = double(sx[3 * i + 1]), s2 = double(sx[3 * i + 2]);
+    const double gam = double(mu[i]) * sqrt(s0 * s0 + s1 * s1);
+    rd = fmax(rd, fmax(fabs(double(y[3 * i]) + s0), fmax(fabs(double(y[3 * i + 1]) + s1),
+                                                       fabs(double(y[3 * i + 2]) + s2 + gam))));
+    for (int r = 0; r < 3; ++r) rp = fmax(rp, fabs(double(x[3 * i + r]) - double(z[3 * i + r])));
+  }
+}
+
+DS_HDI double rho_balance(double rho, double rp, double rd) {
+  if (rp > 10.0 * rd) return 2.0 * rho;
+  if (rd > 10.0 * rp) return 0.5 * rho;
+  return rho;
+}
+
 template <int NS, typename T>
 struct Admm {
   static constexpr int NC3 = 3 * NS;
@@ -466,10 +497,29 @@ struct Admm {
     for (int i = 0; i < m; ++i) trace += p.Gt[i][i];
     rho = T(0.3) * trace / T(m);
     if (!(rho > T(1e-12))) rho = T(1e-12);
-    inv_rho = T(1) / rho;
     for (int i = 0; i < p.na; ++i) inv1pmu2[i] = T(1) / (T(1) + T(p.mu[i]) * T(p.mu[i]));
     gs = T(1);
     for (int i = 0; i < m; ++i) gs = fmax(gs, fabs(p.gt[i]));
+    return factor(p);
+  }
+
+  // Adaptive penalty (KArgs.rho_adapt), between rounds: residual balancing of rho
+  // (rho_balance) on this iterate, and K formed again when rho changes (kept if that fails).
+  template <class P>
+  DS_HD void adapt(const P& p) {
+    double rp = 0.0, rd = 0.0;
+    admm_residuals(p.na, p.mu, x, z, y, sx, rp, rd);
+    const double nr = rho_balance(double(rho), rp, rd);
+    if (nr == double(rho)) return;
+    const T old = rho;
+    rho = T(nr);
+    if (!factor(p)) { rho = old; factor(p); }
+  }
+
+  // K = (G + rho I)^-1 by Cholesky and m solves; 1 / rho.
+  template <class P>
+  DS_HD bool factor(const P& p) {
+    inv_rho = T(1) / rho;
     T Lg[NC3 * (NC3 + 1) / 2];
     for (int i = 0; i < m; ++i)
       for (int j = 0; j <= i; ++j) Lg[tri(i, j)] = p.Gt[i][j] + (i == j ? rho : T(0));
@@ -678,6 +728,7 @@ DS_HD void solve_ncp_with(P& s, const KArgs& a, int& iters, uint32_t& st) {
   const int table = (a.sched.caps >= 0 && a.sched.caps < 3) ? a.sched.caps : 0;
   int stage = 0;
   for (int r = 0; r < DS_ROUNDS; ++r) {
+    if (r > 0 && a.rho_adapt) ad.adapt(s);    // as the pipeline does between its rounds
     const bool final_round = r == DS_ROUNDS - 1;
     const int cap = ds_round_cap(table, r);
     const int lim = final_round ? (a.admm_max_iter > cap ? a.admm_max_iter : cap) : cap;
@@ -2340,6 +2391,49 @@ DS_HD void finish_tape_env(const DevModel& m, const KArgs& a, const int e, int c
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
   env_finish<NB, NV, NS, T>(m, a, e, s, st, 0, chunk, nchunk);
+}
+
+// 2c. adaptive penalty (options admm_rho_adapt), after round a.round's Newton stage: for every env
+//     queued for the next round, residual balancing of rho on its stored ADMM state
+//     (admm_residuals, rho_balance) and, when rho changes, K = (G + rho I)^-1 formed again from the
+//     stored G (the old rho and K are kept if the factorisation fails).  One thread per env.
+template <int NS, typename T>
+__global__ void __launch_bounds__(128) rho_adapt_kernel(KArgs a) {
+  constexpr int NC3 = 3 * NS;
+  const WsView& w = a.ws;
+  const int n = w.counts[a.round + 1];
+  const int32_t* lst = w.list[(a.round + 1) & 1];
+  const int B = a.B;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int e = DS_IX(lst[t], B);
+    const int na = w.na[e];
+    const int m = 3 * na;
+    double x[NC3], z[NC3], y[NC3], sx[NC3], mu[NS];
+    for (int i = 0; i < m; ++i) {
+      x[i] = w.ax[i * B + e];
+      z[i] = w.az[i * B + e];
+      y[i] = w.ay[i * B + e];
+      sx[i] = w.asx[i * B + e];
+    }
+    for (int i = 0; i < na; ++i) mu[i] = w.mu[i * B + e];
+    double rp, rd;
+    admm_residuals(na, mu, x, z, y, sx, rp, rd);
+    const double rho = w.rho[e];
+    const T nr = T(rho_balance(rho, rp, rd));
+    if (double(nr) == rho) continue;
+    T Lg[NC3 * (NC3 + 1) / 2];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j <= i; ++j) Lg[tri(i, j)] = T(w.G[tri(i, j) * B + e]) + (i == j ? nr : T(0));
+    if (!chol_packed(Lg, m)) continue;
+    for (int j = 0; j < m; ++j) {
+      T col[NC3];
+      for (int i = 0; i < m; ++i) col[i] = T(i == j ? 1 : 0);
+      fwd_packed(Lg, col, m);
+      bwd_packed(Lg, col, m);
+      for (int i = 0; i < m; ++i) w.K[(i * NC3 + j) * B + e] = double(col[i]);
+    }
+    w.rho[e] = double(nr);
+  }
 }
 
 template <int NB, int NV, int NS, typename T>

@@ -178,6 +178,11 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     }
     if (!launched) newton_kernel<NS, T><<<nblocks, nthreads, 0, s>>>(a);
     ds_trace_mark(DS_STAGE_NEWTON, 0, s);
+    if (a0.rho_adapt && !a.final_round) {
+      ds_trace_mark(DS_STAGE_ADMM, 1, s);
+      rho_adapt_kernel<NS, T><<<blocks < ds_sm_count() * 8 ? blocks : ds_sm_count() * 8, threads, 0, s>>>(a);
+      ds_trace_mark(DS_STAGE_ADMM, 0, s);
+    }
     if (overlap && r == sc.overlap_from) fork_finish();
   }
   if (overlap) {

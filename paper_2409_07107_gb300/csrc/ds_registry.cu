@@ -41,8 +41,16 @@ const ds_kernel_entry* ds_fit_kernel(int nb, int nv, int slots, int ncmax, int p
   return best;
 }
 
+const ds_persist_entry* ds_persist_mix();
+
+// The persistent kernel is compiled for the mixed-precision form only.
+const ds_persist_entry* ds_persist_kernel(int precision) {
+  return precision == DS_MIXED ? ds_persist_mix() : nullptr;
+}
+
 unsigned long long ds_check_sum() {
   unsigned long long n = 0;
   for (const ds_kernel_entry& k : kTable) n += k.check();
+  n += ds_persist_mix()->check();
   return n;
 }

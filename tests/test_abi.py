@@ -42,9 +42,11 @@ def test_status_strings_and_defaults(L):
     # the last fields of ds_options sit where the binding expects them (the C default fills them)
     assert o.margin_delta == 1e-3 and o.baumgarte_kp == 1.0 and o.baumgarte_kd == 0.0
     raw = ds.ds_options()
-    raw.contact_margin = 7.0                 # the C default must overwrite the binding's last field
+    raw.contact_margin = 7.0
+    raw.queue_poll_limit = 7
+    raw.admm_rho_adapt = 7                   # the C default must overwrite the binding's last field
     L.ds_options_default(ctypes.byref(raw))
-    assert raw.contact_margin == 0.0
+    assert raw.contact_margin == 0.0 and raw.queue_poll_limit == 1 << 22 and raw.admm_rho_adapt == 0
 
 
 def _desc(nb=2, parent=(-1, 0), jtype=(0, 0), axis=None):

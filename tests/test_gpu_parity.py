@@ -553,6 +553,37 @@ def test_pgs_solver(torch_cuda, precision, tol_v, tol_j, pipeline):
         assert not (g["status"] & 1).any()
 
 
+@pytest.mark.parametrize("precision,tol_v,tol_j", [("fp64", 1e-9, 1e-9), ("mixed", 1e-4, 1e-3)])
+@pytest.mark.parametrize("pipeline", [True, False])
+def test_adaptive_rho(torch_cuda, precision, tol_v, tol_j, pipeline):
+    """The adaptive-penalty ADMM (admm_rho_adapt = 1: residual balancing of rho between rounds, K
+    formed again): v+, modes and the Jacobians against the oracle (whose third route is the same
+    variant, with its own update points), in the pipeline (ragged batch of 300, every env through
+    the ADMM rounds) and in the fused kernel; the penalty changes the iterates (iteration counts
+    differ from the fixed-rho run) but not the accepted solutions."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_cube(65536)
+    sub = scenes.Workload(wl.name, wl.models, wl.batch.take(np.arange(300)), wl.options)
+    outs = []
+    for adapt in (0, 1):
+        sim = ds.Simulator(sub, precision=precision, pipeline=pipeline, admm_rho_adapt=adapt)
+        sim.set_schedule(ds.schedule_index(presolve=1))
+        try:
+            out = sim.step_jac()
+            torch.cuda.synchronize()
+        finally:
+            sim.set_schedule(-1)
+        outs.append({k: v.cpu().numpy() for k, v in out.items()})
+    fixed, g = outs
+    assert (g["iters"] != fixed["iters"]).sum() >= 20
+    envs = list(range(0, 300, 3))
+    refs = run_oracle(sub, envs, routes=("admm", "pgs", "admm_adaptive"))
+    _compare(sub, g, refs, envs, tol_v, tol_j, min_checked=60)
+    if precision == "fp64":
+        assert not (g["status"] & 1).any()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_single_contact_presolve(torch_cuda, precision):
     """The setup's exact solve for single-contact solutions (default schedule) against the same

@@ -24,9 +24,10 @@ def test_schedule_index_round_trip():
 def test_default_schedule_index():
     # the library's default: default caps, row-per-lane from round 5, 4 finish CTAs per SM,
     # cooperative Newton, overlapped finish after round 5 keeping every 8th SM free, two-warp ADMM
-    # rounds from round 5, no speculative Newton attempts, the single-contact presolve
+    # rounds from round 5, no speculative Newton attempts, the single-contact presolve, the pipeline
+    # (not the persistent launch)
     d = ds.describe_schedule(ds.schedule_index())
     assert d == {"round_caps": "default", "row_per_lane_admm_from_round": 5, "finish_ctas_per_sm": 4,
                  "newton": "cooperative", "overlapped_finish_after_round": 5, "two_warp_admm_from_round": 5,
                  "overlapped_finish_keeps_free_every_nth_sm": 8, "speculative_newton_from_round": None,
-                 "single_contact_presolve": True}
+                 "single_contact_presolve": True, "launch": "pipeline"}
