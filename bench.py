@@ -656,8 +656,9 @@ def main():
     if vjp:
         sim = ds.Simulator(wl, precision="mixed", **gains)
         tuned = results["mixed"]["schedule"]
-        half = ds.NUM_SCHEDULES // 2              # the launch knob is the highest digit
-        pipe_idx = tuned["index"] % half if tuned else ds.schedule_index()
+        launch_digit = ds.NUM_SCHEDULES // 4      # the launch knob: the second-highest digit
+        idx = tuned["index"] if tuned else ds.schedule_index()
+        pipe_idx = idx - ((idx // launch_digit) % 2) * launch_digit
         forms = {}
         try:
             for form, idx in (("persistent", ds.schedule_index(launch=1)), ("pipeline", pipe_idx)):

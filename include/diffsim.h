@@ -295,7 +295,14 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * models; a batch with another shape runs the pipeline under such a schedule.  Its queue can
  * only be read once every CTA has filed its share of the envs into the per-model lists; a CTA
  * polls for that at most queue_poll_limit times (ds_options), and when one gives up, every CTA
- * stops claiming work and the envs left get DS_ENV_QUEUE_TIMEOUT.
+ * stops claiming work and the envs left get DS_ENV_QUEUE_TIMEOUT.  And the finish's form: one
+ * kernel whose threads each hold an env (or a share of its columns) in registers and local
+ * memory, or two: a prep kernel, one thread per env, that does the step's outputs, the reduced
+ * implicit system and its factor and the rows of the implicit part (Jacobians) or the adjoint
+ * vectors (VJP), and stores what the columns read in the workspace; then a column kernel, one
+ * warp per env, that stages that state in shared memory and spreads the 3 nv Jacobian columns
+ * (the VJP's 2 nv dof passes) over its lanes (in the mixed form the implicit part is then applied
+ * in FP32 instead of FP64).
  * ds_autotune runs `mode` (0 = sim_step, 1 = sim_step_jac with o0..o2 = dv_dq, dv_dv, dv_dtau,
  * 2 = sim_step_vjp with v_next_bar and o0..o2 = q_bar, v_bar, tau_bar) on this batch, timing each
  * schedule by the second slowest of five runs (so that a schedule whose step time varies from
@@ -314,15 +321,15 @@ ds_status sim_step_jac_noalloc(const ds_model* const* models, int32_t nmodels, c
  * runs (every accepted impulse passes the same NCP residual test; where Eq. 1 has several
  * solutions, two schedules can return different ones).
  * Blocking: it synchronises on `stream`.  The workspace is required.  *chosen (may be NULL) gets
- * the schedule's index (0 .. 29159), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 5 (p +
- * 3 (r + 3 (s + 3 (x + 2 u)))))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane
+ * the schedule's index (0 .. 58319), the mixed-radix number c + 3 (w + 3 (f + 3 (n + 2 (o + 5 (p +
+ * 3 (r + 3 (s + 3 (x + 2 (u + 2 h))))))))): round caps c (0 default, 1 halved, 2 doubled), first row-per-lane
  * round w (0: 3, 1: 5, 2: never), finish target f (0, 4, 8 CTAs per SM as 0, 1, 2), Newton n (0
  * cooperative, 1 one thread per env), overlapped finish o (0: after the setup, 1: after round 2,
  * 2: after round 4, 3: after round 5, 4: never), two-warp ADMM p (0: from round 3, 1: from round 5,
  * 2: never), SMs kept
  * free r (0: none, 1: every 8th, 2: every 4th), speculative Newton attempts s (0: from round 3, 1:
  * from round 5, 2: never), single-contact presolve x (0 on, 1 off), launch u (0 pipeline, 1
- * persistent).  Errors: DS_EINVAL, DS_ECUDA,
+ * persistent), finish h (0 one kernel, 1 prep + column kernels).  Errors: DS_EINVAL, DS_ECUDA,
  * those of the call. */
 ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                       const ds_options* opt, int32_t mode, const double* v_next_bar, const ds_step_out* out,
@@ -332,7 +339,7 @@ ds_status ds_autotune(const ds_model* const* models, int32_t nmodels, const ds_b
 /* Sets the schedule (index as ds_autotune's *chosen) that later calls of `mode` use for batches
  * with this batch's signature, as if ds_autotune had chosen it; index -1 returns the signature to
  * the default schedule (no counterpart in the paper).  For reusing a tuned schedule without timing
- * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 29159). */
+ * again, and for running a given kernel form.  Errors: DS_EINVAL (index outside -1 .. 58319). */
 ds_status ds_set_schedule(const ds_model* const* models, int32_t nmodels, const ds_batch* batch,
                           const ds_options* opt, int32_t mode, int32_t index);
 

@@ -249,8 +249,9 @@ SCHEDULE_KNOBS = (
     ("speculative_newton_from_round", (3, 5, None)),
     ("single_contact_presolve", (True, False)),
     ("launch", ("pipeline", "persistent")),
+    ("finish", ("one kernel", "split")),
 )
-NUM_SCHEDULES = 29160
+NUM_SCHEDULES = 58320
 
 
 def describe_schedule(index):
@@ -263,11 +264,11 @@ def describe_schedule(index):
 
 
 def schedule_index(round_caps=0, wide=1, finish=1, newton=0, overlap=3, pair=1, reserve=1, spec=2, presolve=0,
-                   launch=0):
+                   launch=0, split=0):
     """Schedule index from option positions (each the position in its SCHEDULE_KNOBS tuple); the
     defaults give the library's default schedule."""
     idx, mul = 0, 1
-    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec, presolve, launch),
+    for pos, (_, opts) in zip((round_caps, wide, finish, newton, overlap, pair, reserve, spec, presolve, launch, split),
                               SCHEDULE_KNOBS):
         assert 0 <= pos < len(opts)
         idx += pos * mul

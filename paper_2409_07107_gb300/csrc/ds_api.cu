@@ -148,7 +148,7 @@ static int forward_rows(const ds_model* const* models, int32_t nmodels, const ds
     if (slots < 0 || slots > b->ncmax) return -1;
     const ds_kernel_entry* ke = ds_fit_kernel(models[k]->host.nb, models[k]->host.nv, slots, b->ncmax, o->precision);
     if (!ke) return -1;
-    const int r = ds_forward_rows(ke->nb, ke->nv, ke->ns);
+    const int r = std::max(ds_forward_rows(ke->nb, ke->nv, ke->ns), ds_colstate_rows(ke->nb, ke->nv, ke->ns));
     if (r > rows) rows = r;
   }
   return rows;
@@ -204,7 +204,7 @@ static ds_status helper_streams(HelperStreams** out) {
 }
 
 // Schedules chosen by ds_autotune, per batch signature; calls without an entry use the default.
-static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS, 1, 0};
+static const ds_schedule kDefaultSchedule = {0, 5, 4, 0, 5, 5, 8, DS_ROUNDS, 1, 0, 0};
 struct SchedKey {
   int nmodels, nb0, nv0, ncmax, precision, mode, bbucket;
   bool operator<(const SchedKey& o) const {
@@ -300,7 +300,8 @@ static ds_status run(const ds_model* const* models, int32_t nmodels, const ds_ba
     if (slots < 0 || slots > b->ncmax) return DS_EINVAL;
     kern[k] = ds_fit_kernel(models[k]->host.nb, models[k]->host.nv, slots, b->ncmax, o->precision);
     if (!kern[k]) return DS_EUNSUPPORTED;
-    const int r = ds_forward_rows(kern[k]->nb, kern[k]->nv, kern[k]->ns);
+    const int r = std::max(ds_forward_rows(kern[k]->nb, kern[k]->nv, kern[k]->ns),
+                           ds_colstate_rows(kern[k]->nb, kern[k]->nv, kern[k]->ns));
     if (r > fw_rows) fw_rows = r;
   }
   if (ws && (ws_bytes < ds_workspace_layout(b->ncmax, b->B, nullptr, nullptr, nmodels, 0, fw_rows) ||
@@ -487,8 +488,8 @@ extern "C" ds_status ds_cotangent_to_tangent(const ds_model* const* models, int3
 
 // Schedule knobs and their options.  The index of ds_autotune / ds_set_schedule is the mixed-radix
 // number of the chosen option positions, knob 0 the lowest digit.
-static const int kKnobs = 10, kNumSchedules = 3 * 3 * 3 * 2 * 5 * 3 * 3 * 3 * 2 * 2;
-static const int kNopt[kKnobs] = {3, 3, 3, 2, 5, 3, 3, 3, 2, 2};
+static const int kKnobs = 11, kNumSchedules = 3 * 3 * 3 * 2 * 5 * 3 * 3 * 3 * 2 * 2 * 2;
+static const int kNopt[kKnobs] = {3, 3, 3, 2, 5, 3, 3, 3, 2, 2, 2};
 static const int kOpt[kKnobs][5] = {{0, 1, 2, 0},          // round-cap table
                                     {3, 5, DS_ROUNDS, 0},  // first row-per-lane ADMM round
                                     {0, 4, 8, 0},          // finish: target CTAs per SM
@@ -498,7 +499,8 @@ static const int kOpt[kKnobs][5] = {{0, 1, 2, 0},          // round-cap table
                                     {0, 8, 4, 0},          // overlapped finish: SM stride kept free
                                     {3, 5, DS_ROUNDS, 0},  // speculative Newton attempts from round
                                     {1, 0, 0, 0},          // single-contact presolve: on / off
-                                    {0, 1, 0, 0}};         // workspace pipeline / persistent launch
+                                    {0, 1, 0, 0},          // workspace pipeline / persistent launch
+                                    {0, 1, 0, 0}};         // finish: one kernel / prep + column kernels
 static int* knob(ds_schedule& c, int d) {
   switch (d) {
     case 0: return &c.caps;
@@ -510,7 +512,8 @@ static int* knob(ds_schedule& c, int d) {
     case 6: return &c.reserve;
     case 7: return &c.spec_from;
     case 8: return &c.presolve;
-    default: return &c.persistent;
+    case 9: return &c.persistent;
+    default: return &c.finish_split;
   }
 }
 static int schedule_index(ds_schedule c) {

@@ -89,6 +89,14 @@ DS_HDI int ds_forward_rows(int nb, int nv, int ns) {
   return 8 * nv + 28 * nb + nv * (nv + 1) / 2 + 6 * ns * nv + 9 * ns;
 }
 
+// Rows (of B doubles) of the split finish's per-env column state (order: ColState::visit), for
+// a model of nb bodies, nv dofs and ns contact slots; stored in the forward-state rows, which
+// are sized for the larger of the two.
+DS_HDI constexpr int ds_colstate_rows(int nb, int nv, int ns) {
+  return 6 * nv + 2 * nv + 10 * nb + 7 * 6 * nb + nv * (nv + 1) / 2 + 9 * ns + 9 + 3 * ns * nv + nv * 3 * ns +
+         2 * nv + 3 * ns + ns + nv + ns + ns + 2;
+}
+
 struct WsView {
   int32_t* counts;        // [DS_ROUNDS + 1] envs queued for each round
   int32_t* list[2];       // [B] ping-pong work lists of env indices
@@ -202,6 +210,9 @@ struct ds_schedule {
   int persistent;     // 1: the whole step as one persistent launch over an atomic work queue (one
                       // env per lane, every model of the batch in the same kernel), where a kernel
                       // with the batch's shapes is compiled; 0: the workspace pipeline
+  int finish_split;   // 1: the finish as a prep kernel (one thread per env) and a column kernel
+                      // (one warp per env, its state in shared memory); 0: one kernel, an env's
+                      // columns over finish_ctas-derived threads
 };
 
 // Everything a launch needs; passed by value.

@@ -770,8 +770,8 @@ namespace ds {
 // along one dof: kind 0 = tangent of q (the subtree of the dof's body moves by the rigid twist
 // xi = S_d), kind 1 = unit change of the dof's velocity.  Uses the stored pass values V, A, VJ,
 // IV, IA, Fc of the a* pass.  Writes dtau[NV].
-template <int NB, int NV, int NS, typename T>
-DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind, int d, T* dtau) {
+template <int NB, int NV, int NS, typename T, class E>
+DS_HD void rnea_tangent(const DevModel& m, const E& s, int kind, int d, T* dtau) {
   const int j = m.dof_body[DS_IX(d, NV)];
   const int jend = m.sub_end[DS_IX(j, NB)];
   const T* xi = s.S[d];
@@ -845,8 +845,8 @@ DS_HD void rnea_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, int kind
 
 // d(J_c v+)/dq_d for contact a at fixed v+ (App. D's FKV term, including the motion of the
 // contact point with the body): Vp = body velocities under v+.
-template <int NB, int NV, int NS, typename T>
-DS_HDI void fkv_tangent(const DevModel& m, const Env<NB, NV, NS, T>& s, const T (*Vp)[6],
+template <int NB, int NV, int NS, typename T, class E>
+DS_HDI void fkv_tangent(const DevModel& m, const E& s, const T (*Vp)[6],
                                             int a, int d, T* out) {
   const int j = m.dof_body[DS_IX(d, NV)];
   const int b = s.body[a];
@@ -892,8 +892,8 @@ DS_HDI void baumgarte_g(const KArgs& a, const int e, const double (*Jd)[NV], Env
 // d/dq_d: (1 - kp)/dt dphi/dq_d (1/dt where phi >= 0: [x]_- is flat there) - kd d(J_c v)_N/dq_d
 // (dphi/dq_d = (J_c)_N,d for a body-fixed contact point; the second term is the FKV derivative at
 // v); d/dv_d: -kd (J_c)_N,d; d/dtau: 0.
-template <int NB, int NV, int NS, typename T>
-DS_HDI T baumgarte_d(const DevModel& m, const KArgs& a, const Env<NB, NV, NS, T>& s, int ac, int blk, int d) {
+template <int NB, int NV, int NS, typename T, class E>
+DS_HDI T baumgarte_d(const DevModel& m, const KArgs& a, const E& s, int ac, int blk, int d) {
   if (!gap_term(a) || blk == 2) return T(0);
   const T jn = s.Jc[3 * ac + 2][d];
   if (blk == 1) return -T(a.bkd) * jn;
@@ -1347,6 +1347,222 @@ DS_HDI void integrate_adjoint(const DevModel& m, const double* vn, double dt, co
   }
 }
 
+// Reduced implicit system of an env (App. B): offset and size of each contact's block (3 rows
+// sticking, 2 sliding, 0 breaking), the sliding contacts' R and R^T P, and its dimension md.
+template <int NS>
+struct Reduced {
+  int off[NS], sz[NS];
+  double Rm[NS][3][2], RP[NS][2][3];
+  int md;
+};
+
+// The part of the finish before the derivative columns: the B1 pass of
+// tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces (s.astar, s.f, s.A,
+// s.IA, s.Fc), the body velocities under v+ (Vp), and the reduced system A = B G C + blkdiag(0, Q)
+// (App. B) built and factored in s.lu (DS_ENV_SINGULAR when rank deficient).
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_reduced(const DevModel& m, const KArgs& a, Env<NB, NV, NS, T>& s, T (*Vp)[6], Reduced<NS>& rd,
+                          uint32_t& st) {
+  const int mdim = 3 * s.na;
+  const T grav[3] = {T(a.gx), T(a.gy), T(a.gz)};
+  int(&off)[NS] = rd.off;
+  int(&sz)[NS] = rd.sz;
+  double(&Rm)[NS][3][2] = rd.Rm;
+  double(&RP)[NS][2][3] = rd.RP;
+  int& md = rd.md;
+  // ---- B1 pass of tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces
+  for (int k = 0; k < NV; ++k) {
+    T t = s.vdf[k];
+    for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
+    s.astar[k] = t;
+  }
+  for (int ac = 0; ac < s.na; ++ac)
+    for (int k = 0; k < 3; ++k)
+      s.f[ac][k] = T((double(s.fr[0][k]) * s.lam[3 * ac] + double(s.fr[1][k]) * s.lam[3 * ac + 1] +
+                      double(s.fr[2][k]) * s.lam[3 * ac + 2]) / a.dt);
+  for (int i = 0; i < NB; ++i) {
+    const int par = m.parent[i];
+    T t[6];
+    mcross(s.V[i], s.VJ[i], t);
+    for (int k = 0; k < 6; ++k) s.A[i][k] = (par >= 0 ? s.A[DS_IX(par, NB)][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
+    for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
+      for (int k = 0; k < 6; ++k) s.A[i][k] += s.S[DS_IX(dd, NV)][k] * s.astar[DS_IX(dd, NV)];
+    iapply(s.I[i], s.A[i], s.IA[i]);
+    fcross(s.V[i], s.IV[i], t);
+    for (int k = 0; k < 6; ++k) s.Fc[i][k] = s.IA[i][k] + t[k];
+    for (int ac = 0; ac < s.na; ++ac) {
+      if (s.body[ac] != i) continue;
+      T cf[3];
+      cross3(s.c[ac], s.f[ac], cf);
+      for (int k = 0; k < 3; ++k) { s.Fc[i][k] -= s.f[ac][k]; s.Fc[i][3 + k] -= cf[k]; }
+    }
+  }
+  for (int i = NB - 1; i > 0; --i) {
+    const int par = m.parent[i];
+    if (par >= 0)
+      for (int k = 0; k < 6; ++k) s.Fc[DS_IX(par, NB)][k] += s.Fc[i][k];
+  }
+  // body velocities under v+ (for the FKV term)
+  for (int i = 0; i < NB; ++i) {
+    const int par = m.parent[i];
+    for (int k = 0; k < 6; ++k) Vp[i][k] = (par >= 0 ? Vp[DS_IX(par, NB)][k] : T(0));
+    for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
+      for (int k = 0; k < 6; ++k) Vp[i][k] += s.S[DS_IX(dd, NV)][k] * s.vn[DS_IX(dd, NV)];
+  }
+
+  // ---- B3/B4 reduced implicit system A = B G C + blkdiag(0, Q) (App. B), FP64
+  md = 0;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int ac = 0; ac < s.na; ++ac) {
+      const int want = pass == 0 ? DS_MODE_STICKING : DS_MODE_SLIDING;
+      if (s.mode[ac] != want) continue;
+      off[ac] = md;
+      sz[ac] = pass == 0 ? 3 : 2;
+      md += sz[ac];
+    }
+  for (int ac = 0; ac < s.na; ++ac) {
+    if (s.mode[ac] == DS_MODE_BREAKING) { sz[ac] = 0; off[ac] = 0; }
+    if (s.mode[ac] != DS_MODE_SLIDING) continue;
+    double sg[3];
+    for (int k = 0; k < 3; ++k) {
+      double t = s.gd[3 * ac + k];
+      for (int j = 0; j < mdim; ++j) t += s.G(3 * ac + k, j) * s.lam[j];
+      sg[k] = t;
+    }
+    const double* l = s.lam + 3 * ac;
+    const double ns = sqrt(sg[0] * sg[0] + sg[1] * sg[1]);
+    const double u[2] = {sg[0] / ns, sg[1] / ns};
+    const double nl = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    const double r1[3] = {l[0] / nl, l[1] / nl, l[2] / nl};
+    const double r2[3] = {-u[1], u[0], 0.0};
+    const double ia = s.mu[ac] * l[2] / ns;   // 1/alpha
+    for (int k = 0; k < 3; ++k) { Rm[ac][k][0] = r1[k]; Rm[ac][k][1] = r2[k]; }
+    // R^T P with P = diag(H/alpha, 1), H = I - u u^T
+    const double H[2][2] = {{1 - u[0] * u[0], -u[0] * u[1]}, {-u[1] * u[0], 1 - u[1] * u[1]}};
+    const double* rr[2] = {r1, r2};
+    for (int c = 0; c < 2; ++c) {
+      RP[ac][c][0] = ia * (rr[c][0] * H[0][0] + rr[c][1] * H[1][0]);
+      RP[ac][c][1] = ia * (rr[c][0] * H[0][1] + rr[c][1] * H[1][1]);
+      RP[ac][c][2] = rr[c][2];
+    }
+  }
+  s.lu.r = md;
+  s.lu.c = md;
+  for (int ra = 0; ra < s.na; ++ra) {
+    if (sz[ra] == 0) continue;
+    for (int cb = 0; cb < s.na; ++cb) {
+      if (sz[cb] == 0) continue;
+      double Gb[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Gb[r][c] = s.G(3 * ra + r, 3 * cb + c);
+      double LG[3][3];   // left (I or R^T P) times G block
+      for (int r = 0; r < sz[ra]; ++r)
+        for (int c = 0; c < 3; ++c)
+          LG[r][c] = sz[ra] == 3 ? Gb[r][c] : RP[ra][r][0] * Gb[0][c] + RP[ra][r][1] * Gb[1][c] + RP[ra][r][2] * Gb[2][c];
+      for (int r = 0; r < sz[ra]; ++r)
+        for (int c = 0; c < sz[cb]; ++c) {
+          double t = sz[cb] == 3 ? LG[r][c] : LG[r][0] * Rm[cb][0][c] + LG[r][1] * Rm[cb][1][c] + LG[r][2] * Rm[cb][2][c];
+          if (ra == cb && sz[ra] == 2 && r == 1 && c == 1) t += 1.0;   // Q = diag(0, 1)
+          s.lu.a[off[ra] + r][off[cb] + c] = t;
+        }
+    }
+  }
+  if (md > 0) {
+    s.lu.factor(1e-12);
+    s.lu.nullspace();
+    if (s.lu.rank < md) st |= DS_ENV_SINGULAR;
+  }
+}
+
+// Rows of the implicit part of the Jacobian: P_k = B^T (A^-)^T C^T Y^T e_k for every output row k
+// (one transposed minimum-norm solve each), so that column c of Y C A^- B (J_c D + F) is
+// sum_j P[k][j] (J_c D + F)_j.  Rows of breaking contacts are 0.
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_rows(Env<NB, NV, NS, T>& s, const Reduced<NS>& rd, double (*P)[3 * NS]) {
+  const int(&off)[NS] = rd.off;
+  const int(&sz)[NS] = rd.sz;
+  const double(&Rm)[NS][3][2] = rd.Rm;
+  const double(&RP)[NS][2][3] = rd.RP;
+  for (int k = 0; k < NV; ++k) {
+    double u[3 * NS], z[3 * NS];
+    for (int ac = 0; ac < s.na; ++ac) {
+      if (sz[ac] == 0) continue;
+      if (sz[ac] == 3) {
+        for (int r = 0; r < 3; ++r) u[off[ac] + r] = double(s.Y[3 * ac + r][k]);
+      } else {
+        for (int c = 0; c < 2; ++c)
+          u[off[ac] + c] = Rm[ac][0][c] * double(s.Y[3 * ac][k]) + Rm[ac][1][c] * double(s.Y[3 * ac + 1][k]) +
+                           Rm[ac][2][c] * double(s.Y[3 * ac + 2][k]);
+      }
+    }
+    s.lu.solve_t_mn(u, z);
+    for (int ac = 0; ac < s.na; ++ac) {
+      for (int r = 0; r < 3; ++r) {
+        double p = 0.0;
+        if (sz[ac] == 3) p = z[off[ac] + r];
+        else if (sz[ac] == 2) p = RP[ac][0][r] * z[off[ac]] + RP[ac][1][r] * z[off[ac] + 1];
+        P[k][3 * ac + r] = p;
+      }
+    }
+  }
+}
+
+// The VJP's adjoint vectors (B7, B8): with v_bar (and the position update's adjoint chained in
+// when there is a cotangent of q+: qadd), z = A^-T C^T Y^T v_bar, zeta = B^T z,
+// ub = v_bar - J_c^T zeta and w2 = M^-1 ub.
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_vjp_head(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s,
+                           const Reduced<NS>& rd, T* ub, T* w2, double* zeta, double* qadd) {
+  const int B = a.B;
+  const int mdim = 3 * s.na;
+  const int(&off)[NS] = rd.off;
+  const int(&sz)[NS] = rd.sz;
+  const double(&Rm)[NS][3][2] = rd.Rm;
+  const double(&RP)[NS][2][3] = rd.RP;
+  const int md = rd.md;
+  T vb[NV];
+  double qn[NV], vadd[NV];
+  if (a.qnbar) {
+    double vnd[NV];
+    for (int k = 0; k < NV; ++k) { qn[k] = a.qnbar[k * B + e]; vnd[k] = double(s.vn[k]); }
+    integrate_adjoint(m, vnd, a.dt, qn, vadd, qadd);
+  }
+  for (int k = 0; k < NV; ++k) {
+    vb[k] = T(a.qnbar ? a.vbar[k * B + e] + vadd[k] : a.vbar[k * B + e]);
+    ub[k] = vb[k];
+  }
+  for (int r = 0; r < mdim; ++r) zeta[r] = 0.0;
+  if (md > 0) {
+    double wv[3 * NS], z[3 * NS];
+    for (int ac = 0; ac < s.na; ++ac) {
+      if (sz[ac] == 0) continue;
+      double y3[3];
+      for (int r = 0; r < 3; ++r) {
+        T t = T(0);
+        for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
+        y3[r] = double(t);
+      }
+      if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) wv[off[ac] + r] = y3[r]; }
+      else { for (int c = 0; c < 2; ++c) wv[off[ac] + c] = Rm[ac][0][c] * y3[0] + Rm[ac][1][c] * y3[1] + Rm[ac][2][c] * y3[2]; }
+    }
+    s.lu.solve_t_mn(wv, z);
+    for (int ac = 0; ac < s.na; ++ac) {
+      if (sz[ac] == 0) continue;
+      if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) zeta[3 * ac + r] = z[off[ac] + r]; }
+      else { for (int r = 0; r < 3; ++r) zeta[3 * ac + r] = RP[ac][0][r] * z[off[ac]] + RP[ac][1][r] * z[off[ac] + 1]; }
+    }
+    for (int r = 0; r < mdim; ++r) {
+      const T zr = T(zeta[r]);
+      const int b = s.body[r / 3];
+      for (int k = m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
+        ub[k] -= s.Jc[r][k] * zr;
+    }
+  }
+  for (int k = 0; k < NV; ++k) w2[k] = ub[k];
+  ltl_solve_t(s.L, w2, NV, m.dof_parent);
+  ltl_solve(s.L, w2, NV, m.dof_parent);
+}
+
 template <int NB, int NV, int NS, typename T>
 DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, uint32_t st, int iters,
                       int chunk = 0, int nchunk = 1) {
@@ -1415,111 +1631,14 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
   }
 
   if (a.run != DS_RUN_STEP && !(st & DS_ENV_NONFINITE)) {
-    // ---- B1 pass of tau = RNEA(q, v, a*) - J_c^T f at a* = (v+ - v)/dt with the contact forces
-    for (int k = 0; k < NV; ++k) {
-      T t = s.vdf[k];
-      for (int r = 0; r < mdim; ++r) t += s.Y[r][k] * T(s.lam[r] / a.dt);
-      s.astar[k] = t;
-    }
-    for (int ac = 0; ac < s.na; ++ac)
-      for (int k = 0; k < 3; ++k)
-        s.f[ac][k] = T((double(s.fr[0][k]) * s.lam[3 * ac] + double(s.fr[1][k]) * s.lam[3 * ac + 1] +
-                        double(s.fr[2][k]) * s.lam[3 * ac + 2]) / a.dt);
-    for (int i = 0; i < NB; ++i) {
-      const int par = m.parent[i];
-      T t[6];
-      mcross(s.V[i], s.VJ[i], t);
-      for (int k = 0; k < 6; ++k) s.A[i][k] = (par >= 0 ? s.A[DS_IX(par, NB)][k] : (k < 3 ? -grav[k] : T(0))) + t[k];
-      for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
-        for (int k = 0; k < 6; ++k) s.A[i][k] += s.S[DS_IX(dd, NV)][k] * s.astar[DS_IX(dd, NV)];
-      iapply(s.I[i], s.A[i], s.IA[i]);
-      fcross(s.V[i], s.IV[i], t);
-      for (int k = 0; k < 6; ++k) s.Fc[i][k] = s.IA[i][k] + t[k];
-      for (int ac = 0; ac < s.na; ++ac) {
-        if (s.body[ac] != i) continue;
-        T cf[3];
-        cross3(s.c[ac], s.f[ac], cf);
-        for (int k = 0; k < 3; ++k) { s.Fc[i][k] -= s.f[ac][k]; s.Fc[i][3 + k] -= cf[k]; }
-      }
-    }
-    for (int i = NB - 1; i > 0; --i) {
-      const int par = m.parent[i];
-      if (par >= 0)
-        for (int k = 0; k < 6; ++k) s.Fc[DS_IX(par, NB)][k] += s.Fc[i][k];
-    }
-    // body velocities under v+ (for the FKV term)
     T Vp[NB][6];
-    for (int i = 0; i < NB; ++i) {
-      const int par = m.parent[i];
-      for (int k = 0; k < 6; ++k) Vp[i][k] = (par >= 0 ? Vp[DS_IX(par, NB)][k] : T(0));
-      for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd)
-        for (int k = 0; k < 6; ++k) Vp[i][k] += s.S[DS_IX(dd, NV)][k] * s.vn[DS_IX(dd, NV)];
-    }
-
-    // ---- B3/B4 reduced implicit system A = B G C + blkdiag(0, Q) (App. B), FP64
-    int off[NS], sz[NS];
-    double Rm[NS][3][2], RP[NS][2][3];
-    int md = 0;
-    for (int pass = 0; pass < 2; ++pass)
-      for (int ac = 0; ac < s.na; ++ac) {
-        const int want = pass == 0 ? DS_MODE_STICKING : DS_MODE_SLIDING;
-        if (s.mode[ac] != want) continue;
-        off[ac] = md;
-        sz[ac] = pass == 0 ? 3 : 2;
-        md += sz[ac];
-      }
-    for (int ac = 0; ac < s.na; ++ac) {
-      if (s.mode[ac] == DS_MODE_BREAKING) { sz[ac] = 0; off[ac] = 0; }
-      if (s.mode[ac] != DS_MODE_SLIDING) continue;
-      double sg[3];
-      for (int k = 0; k < 3; ++k) {
-        double t = s.gd[3 * ac + k];
-        for (int j = 0; j < mdim; ++j) t += s.G(3 * ac + k, j) * s.lam[j];
-        sg[k] = t;
-      }
-      const double* l = s.lam + 3 * ac;
-      const double ns = sqrt(sg[0] * sg[0] + sg[1] * sg[1]);
-      const double u[2] = {sg[0] / ns, sg[1] / ns};
-      const double nl = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
-      const double r1[3] = {l[0] / nl, l[1] / nl, l[2] / nl};
-      const double r2[3] = {-u[1], u[0], 0.0};
-      const double ia = s.mu[ac] * l[2] / ns;   // 1/alpha
-      for (int k = 0; k < 3; ++k) { Rm[ac][k][0] = r1[k]; Rm[ac][k][1] = r2[k]; }
-      // R^T P with P = diag(H/alpha, 1), H = I - u u^T
-      const double H[2][2] = {{1 - u[0] * u[0], -u[0] * u[1]}, {-u[1] * u[0], 1 - u[1] * u[1]}};
-      const double* rr[2] = {r1, r2};
-      for (int c = 0; c < 2; ++c) {
-        RP[ac][c][0] = ia * (rr[c][0] * H[0][0] + rr[c][1] * H[1][0]);
-        RP[ac][c][1] = ia * (rr[c][0] * H[0][1] + rr[c][1] * H[1][1]);
-        RP[ac][c][2] = rr[c][2];
-      }
-    }
-    s.lu.r = md;
-    s.lu.c = md;
-    for (int ra = 0; ra < s.na; ++ra) {
-      if (sz[ra] == 0) continue;
-      for (int cb = 0; cb < s.na; ++cb) {
-        if (sz[cb] == 0) continue;
-        double Gb[3][3];
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) Gb[r][c] = s.G(3 * ra + r, 3 * cb + c);
-        double LG[3][3];   // left (I or R^T P) times G block
-        for (int r = 0; r < sz[ra]; ++r)
-          for (int c = 0; c < 3; ++c)
-            LG[r][c] = sz[ra] == 3 ? Gb[r][c] : RP[ra][r][0] * Gb[0][c] + RP[ra][r][1] * Gb[1][c] + RP[ra][r][2] * Gb[2][c];
-        for (int r = 0; r < sz[ra]; ++r)
-          for (int c = 0; c < sz[cb]; ++c) {
-            double t = sz[cb] == 3 ? LG[r][c] : LG[r][0] * Rm[cb][0][c] + LG[r][1] * Rm[cb][1][c] + LG[r][2] * Rm[cb][2][c];
-            if (ra == cb && sz[ra] == 2 && r == 1 && c == 1) t += 1.0;   // Q = diag(0, 1)
-            s.lu.a[off[ra] + r][off[cb] + c] = t;
-          }
-      }
-    }
-    if (md > 0) {
-      s.lu.factor(1e-12);
-      s.lu.nullspace();
-      if (s.lu.rank < md) st |= DS_ENV_SINGULAR;
-    }
+    Reduced<NS> rd;
+    finish_reduced<NB, NV, NS, T>(m, a, s, Vp, rd, st);
+    const int(&off)[NS] = rd.off;
+    const int(&sz)[NS] = rd.sz;
+    const double(&Rm)[NS][3][2] = rd.Rm;
+    const double(&RP)[NS][2][3] = rd.RP;
+    const int md = rd.md;
 
     const T dt = T(a.dt);
     if (a.run == DS_RUN_JAC) {
@@ -1531,30 +1650,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       const int c0 = (3 * NV * chunk) / nchunk, c1 = (3 * NV * (chunk + 1)) / nchunk;
       const bool by_rows = md > 0 && NV < c1 - c0;
       double P[NV][3 * NS];
-      if (by_rows) {
-        for (int k = 0; k < NV; ++k) {
-          double u[3 * NS], z[3 * NS];
-          for (int ac = 0; ac < s.na; ++ac) {
-            if (sz[ac] == 0) continue;
-            if (sz[ac] == 3) {
-              for (int r = 0; r < 3; ++r) u[off[ac] + r] = double(s.Y[3 * ac + r][k]);
-            } else {
-              for (int c = 0; c < 2; ++c)
-                u[off[ac] + c] = Rm[ac][0][c] * double(s.Y[3 * ac][k]) + Rm[ac][1][c] * double(s.Y[3 * ac + 1][k]) +
-                                 Rm[ac][2][c] * double(s.Y[3 * ac + 2][k]);
-            }
-          }
-          s.lu.solve_t_mn(u, z);
-          for (int ac = 0; ac < s.na; ++ac) {
-            for (int r = 0; r < 3; ++r) {
-              double p = 0.0;
-              if (sz[ac] == 3) p = z[off[ac] + r];
-              else if (sz[ac] == 2) p = RP[ac][0][r] * z[off[ac]] + RP[ac][1][r] * z[off[ac] + 1];
-              P[k][3 * ac + r] = p;
-            }
-          }
-        }
-      }
+      if (by_rows) finish_rows<NB, NV, NS, T>(s, rd, P);
       for (int col = c0; col < c1; ++col) {
         const int blk = col / NV, d = col % NV;
         T Dc[NV];
@@ -1574,7 +1670,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
           for (int ac = 0; ac < s.na; ++ac) {
             T fk[3] = {T(0), T(0), T(0)};
             if (sz[ac] != 0 && blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
-            if (sz[ac] != 0) fk[2] += baumgarte_d(m, a, s, ac, blk, d);
+            if (sz[ac] != 0) fk[2] += baumgarte_d<NB, NV, NS, T>(m, a, s, ac, blk, d);
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
               if (sz[ac] != 0)
@@ -1595,7 +1691,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             double r3[3];
             T fk[3] = {T(0), T(0), T(0)};
             if (blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
-            fk[2] += baumgarte_d(m, a, s, ac, blk, d);
+            fk[2] += baumgarte_d<NB, NV, NS, T>(m, a, s, ac, blk, d);
             for (int r = 0; r < 3; ++r) {
               T t = fk[r];
               for (int k = m.iv[DS_IX(s.body[ac], NB)] + m.nd[DS_IX(s.body[ac], NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
@@ -1629,48 +1725,9 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
       // z = A^-T C^T Y^T vbar, zeta = B^T z, ubar = vbar - J_c^T zeta, w = M^-1 ubar,
       // q_bar = -dt dtau_q . w - F^T zeta, v_bar = ubar - dt dtau_v . w, tau_bar = dt w.
       // With a cotangent of q+ as well, the position update's adjoint is chained in first (B8).
-      T vb[NV], ub[NV], w2[NV];
-      double qn[NV], vadd[NV], qadd[NV];
-      if (a.qnbar) {
-        double vnd[NV];
-        for (int k = 0; k < NV; ++k) { qn[k] = a.qnbar[k * B + e]; vnd[k] = double(s.vn[k]); }
-        integrate_adjoint(m, vnd, a.dt, qn, vadd, qadd);
-      }
-      for (int k = 0; k < NV; ++k) {
-        vb[k] = T(a.qnbar ? a.vbar[k * B + e] + vadd[k] : a.vbar[k * B + e]);
-        ub[k] = vb[k];
-      }
-      double zeta[3 * NS];
-      for (int r = 0; r < mdim; ++r) zeta[r] = 0.0;
-      if (md > 0) {
-        double wv[3 * NS], z[3 * NS];
-        for (int ac = 0; ac < s.na; ++ac) {
-          if (sz[ac] == 0) continue;
-          double y3[3];
-          for (int r = 0; r < 3; ++r) {
-            T t = T(0);
-            for (int k = 0; k < NV; ++k) t += s.Y[3 * ac + r][k] * vb[k];
-            y3[r] = double(t);
-          }
-          if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) wv[off[ac] + r] = y3[r]; }
-          else { for (int c = 0; c < 2; ++c) wv[off[ac] + c] = Rm[ac][0][c] * y3[0] + Rm[ac][1][c] * y3[1] + Rm[ac][2][c] * y3[2]; }
-        }
-        s.lu.solve_t_mn(wv, z);
-        for (int ac = 0; ac < s.na; ++ac) {
-          if (sz[ac] == 0) continue;
-          if (sz[ac] == 3) { for (int r = 0; r < 3; ++r) zeta[3 * ac + r] = z[off[ac] + r]; }
-          else { for (int r = 0; r < 3; ++r) zeta[3 * ac + r] = RP[ac][0][r] * z[off[ac]] + RP[ac][1][r] * z[off[ac] + 1]; }
-        }
-        for (int r = 0; r < mdim; ++r) {
-          const T zr = T(zeta[r]);
-          const int b = s.body[r / 3];
-          for (int k = m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
-            ub[k] -= s.Jc[r][k] * zr;
-        }
-      }
-      for (int k = 0; k < NV; ++k) w2[k] = ub[k];
-      ltl_solve_t(s.L, w2, NV, m.dof_parent);
-      ltl_solve(s.L, w2, NV, m.dof_parent);
+      T ub[NV], w2[NV];
+      double zeta[3 * NS], qadd[NV];
+      finish_vjp_head<NB, NV, NS, T>(m, a, e, s, rd, ub, w2, zeta, qadd);
       const int p0 = (2 * NV * chunk) / nchunk, p1 = (2 * NV * (chunk + 1)) / nchunk;
       for (int blk = 0; blk < 2; ++blk)
         for (int d = 0; d < NV; ++d) {
@@ -1686,7 +1743,7 @@ DS_HD void env_finish(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
             if (sz[ac] == 0) continue;
             T fk[3] = {T(0), T(0), T(0)};
             if (blk == 0) fkv_tangent<NB, NV, NS, T>(m, s, Vp, ac, d, fk);
-            fk[2] += baumgarte_d(m, a, s, ac, blk, d);
+            fk[2] += baumgarte_d<NB, NV, NS, T>(m, a, s, ac, blk, d);
             for (int rr = 0; rr < 3; ++rr) r -= fk[rr] * T(zeta[3 * ac + rr]);
           }
           double* out = blk == 0 ? a.q_bar : a.v_bar;
@@ -2391,6 +2448,251 @@ DS_HD void finish_tape_env(const DevModel& m, const KArgs& a, const int e, int c
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
   env_finish<NB, NV, NS, T>(m, a, e, s, st, 0, chunk, nchunk);
+}
+
+// ------------------------------------------------------------------------ split finish
+// The finish in two kernels (schedule finish_split): a prep kernel, one thread per env, does F9,
+// the B1 pass, the reduced system and its factor, and either the rows P of the implicit part
+// (Jacobians) or the adjoint vectors (VJP), and stores what the derivative columns read (a
+// ColState) in the env's column of the workspace's forward-state rows, which it has just read.  A
+// column kernel then runs one warp per env: the warp stages the env's ColState in shared memory
+// and its lanes take the 3 nv Jacobian columns (2 nv dof passes of the VJP), so that the tree
+// passes of the columns read shared memory instead of a per-thread copy of the env in local
+// memory.  An env's columns are the per-thread finish's by-rows columns, term for term; in the
+// mixed form P is applied in FP32 (the per-thread finish applies it in FP64).
+template <int NB, int NV, int NS, typename T>
+struct ColState {
+  static constexpr int NC3 = 3 * NS;
+  T S[NV][6];
+  T v[NV], astar[NV];
+  T I[NB][10];
+  T V[NB][6], A[NB][6], VJ[NB][6], IV[NB][6], IA[NB][6], Fc[NB][6], Vp[NB][6];
+  T L[NV * (NV + 1) / 2];
+  T x[NS][3], c[NS][3], f[NS][3];
+  T fr[3][3];
+  T Jc[NC3][NV];
+  T P[NV][NC3];                 // Jacobians: rows of the implicit part
+  T w2[NV], ub[NV], zeta[NC3];  // VJP: adjoint vectors
+  double phi[NS];
+  double qadd[NV];              // VJP: the position update's adjoint (with a cotangent of q+)
+  int body[NS];
+  int act[NS];                  // 1: the contact is in the reduced system (sticking or sliding)
+  int na;
+  int md;
+
+  // Every member as (pointer, count), in storage order: the rows of the stored form.
+  template <class F>
+  DS_HD void visit(F&& fn) {
+    fn(&S[0][0], NV * 6); fn(v, NV); fn(astar, NV); fn(&I[0][0], NB * 10);
+    fn(&V[0][0], NB * 6); fn(&A[0][0], NB * 6); fn(&VJ[0][0], NB * 6); fn(&IV[0][0], NB * 6);
+    fn(&IA[0][0], NB * 6); fn(&Fc[0][0], NB * 6); fn(&Vp[0][0], NB * 6);
+    fn(L, NV * (NV + 1) / 2); fn(&x[0][0], NS * 3); fn(&c[0][0], NS * 3); fn(&f[0][0], NS * 3);
+    fn(&fr[0][0], 9); fn(&Jc[0][0], NC3 * NV); fn(&P[0][0], NV * NC3); fn(w2, NV); fn(ub, NV); fn(zeta, NC3);
+    fn(phi, NS); fn(qadd, NV); fn(body, NS); fn(act, NS); fn(&na, 1); fn(&md, 1);
+  }
+  static constexpr int kRows = ds_colstate_rows(NB, NV, NS);
+};
+
+// Prep for env e (one thread): F9 and the outputs of the step as the per-thread finish writes
+// them, then the ColState into the env's forward-state rows (status, with the derivative part's
+// bits, written by the column kernel).
+template <int NB, int NV, int NS, typename T>
+DS_HD void finish_prep_env(const DevModel& m, const KArgs& a, const int e) {
+  Env<NB, NV, NS, T> s;
+  load_forward<NB, NV, NS, T>(m, a, e, s);
+  const WsView& w = a.ws;
+  const int B = a.B;
+  const int mm = 3 * s.na;
+  for (int i = 0; i < mm; ++i) s.lam[i] = w.lam[i * B + e];
+  if (mm > 0 && !(w.st[e] & DS_ENV_NONFINITE)) {
+    for (int i = 0; i < s.na; ++i) s.mode[i] = w.mode[i * B + e];
+  } else {
+    s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
+  }
+  KArgs a1 = a;
+  a1.run = DS_RUN_STEP;                       // F9 and the step's outputs only
+  a1.status = nullptr;
+  uint32_t st = w.st[e];
+  env_finish<NB, NV, NS, T>(m, a1, e, s, st, w.iters[e]);
+  for (int k = 0; k < NV; ++k)
+    if (!isfinite(double(s.vn[k]))) st |= DS_ENV_NONFINITE;
+  ColState<NB, NV, NS, T> cs;
+  cs.na = s.na;
+  cs.md = 0;
+  if (!(st & DS_ENV_NONFINITE)) {
+    T Vp[NB][6];
+    Reduced<NS> rd;
+    finish_reduced<NB, NV, NS, T>(m, a, s, Vp, rd, st);
+    cs.md = rd.md;
+    for (int i = 0; i < NB; ++i)
+      for (int k = 0; k < 6; ++k) cs.Vp[i][k] = Vp[i][k];
+    for (int ac = 0; ac < NS; ++ac) cs.act[ac] = ac < s.na && rd.sz[ac] != 0;
+    if (a.run == DS_RUN_JAC) {
+      double P[NV][3 * NS];
+      if (rd.md > 0) finish_rows<NB, NV, NS, T>(s, rd, P);
+      for (int k = 0; k < NV; ++k)
+        for (int j = 0; j < 3 * NS; ++j) cs.P[k][j] = T(rd.md > 0 && j < mm ? P[k][j] : 0.0);
+    } else {
+      double zeta[3 * NS], qadd[NV];
+      finish_vjp_head<NB, NV, NS, T>(m, a, e, s, rd, cs.ub, cs.w2, zeta, qadd);
+      for (int j = 0; j < 3 * NS; ++j) cs.zeta[j] = T(j < mm ? zeta[j] : 0.0);
+      for (int k = 0; k < NV; ++k) cs.qadd[k] = a.qnbar ? qadd[k] : 0.0;
+    }
+  }
+  // the status of the derivative part travels in w.st (read by the column kernel)
+  w.st[e] = st;
+  for (int k = 0; k < NV; ++k) {
+    for (int j = 0; j < 6; ++j) cs.S[k][j] = s.S[k][j];
+    cs.v[k] = s.v[k];
+    cs.astar[k] = s.astar[k];
+  }
+  for (int i = 0; i < NB; ++i) {
+    for (int k = 0; k < 10; ++k) cs.I[i][k] = s.I[i][k];
+    for (int k = 0; k < 6; ++k) {
+      cs.V[i][k] = s.V[i][k]; cs.A[i][k] = s.A[i][k]; cs.VJ[i][k] = s.VJ[i][k];
+      cs.IV[i][k] = s.IV[i][k]; cs.IA[i][k] = s.IA[i][k]; cs.Fc[i][k] = s.Fc[i][k];
+    }
+  }
+  for (int k = 0; k < NV * (NV + 1) / 2; ++k) cs.L[k] = s.L[k];
+  for (int ac = 0; ac < NS; ++ac) {
+    for (int k = 0; k < 3; ++k) { cs.x[ac][k] = s.x[ac][k]; cs.c[ac][k] = s.c[ac][k]; cs.f[ac][k] = s.f[ac][k]; }
+    cs.phi[ac] = s.phi[ac];
+    cs.body[ac] = s.body[ac];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k) cs.fr[r][k] = s.fr[r][k];
+  for (int r = 0; r < 3 * NS; ++r)
+    for (int k = 0; k < NV; ++k) cs.Jc[r][k] = s.Jc[r][k];
+  int row = 0;
+  double* fw = w.fw;
+  cs.visit([&](auto* ptr, int n) {
+    for (int i = 0; i < n; ++i) fw[size_t(row + i) * B + e] = double(ptr[i]);
+    row += n;
+  });
+}
+
+// Jacobian column (blk, d) of the env in cs: D's column (tree tangent pass, M^-1) minus the
+// implicit part sum_j P[k][j] (J_c D + F)_j (Dc, nv entries).
+template <int NB, int NV, int NS, typename T>
+DS_HD void split_jac_column(const DevModel& m, const KArgs& a, const ColState<NB, NV, NS, T>& cs, int blk, int d,
+                            T* Dc) {
+  const T dt = T(a.dt);
+  if (blk < 2) {
+    T dtau[NV];
+    rnea_tangent<NB, NV, NS, T>(m, cs, blk, d, dtau);
+    ltl_solve_t(cs.L, dtau, NV, m.dof_parent);
+    ltl_solve(cs.L, dtau, NV, m.dof_parent);
+    for (int k = 0; k < NV; ++k) Dc[k] = -dt * dtau[k] + (blk == 1 && k == d ? T(1) : T(0));
+  } else {
+    for (int k = 0; k < NV; ++k) Dc[k] = (k == d ? dt : T(0));
+    ltl_solve_t(cs.L, Dc, NV, m.dof_parent);
+    ltl_solve(cs.L, Dc, NV, m.dof_parent);
+  }
+  if (cs.md == 0) return;
+  const int mdim = 3 * cs.na;
+  T rfull[3 * NS];
+  for (int ac = 0; ac < cs.na; ++ac) {
+    T fk[3] = {T(0), T(0), T(0)};
+    if (cs.act[ac] && blk == 0) fkv_tangent<NB, NV, NS, T>(m, cs, cs.Vp, ac, d, fk);
+    if (cs.act[ac]) fk[2] += baumgarte_d<NB, NV, NS, T>(m, a, cs, ac, blk, d);
+    for (int r = 0; r < 3; ++r) {
+      T t = fk[r];
+      if (cs.act[ac])
+        for (int k = m.iv[DS_IX(cs.body[ac], NB)] + m.nd[DS_IX(cs.body[ac], NB)] - 1; k >= 0; k = m.dof_parent[DS_IX(k, NV)])
+          t += cs.Jc[3 * ac + r][k] * Dc[k];
+      rfull[3 * ac + r] = t;
+    }
+  }
+  for (int k = 0; k < NV; ++k) {
+    T t = T(0);
+    for (int j = 0; j < mdim; ++j) t += cs.P[k][j] * rfull[j];
+    Dc[k] -= t;
+  }
+}
+
+// VJP entry p (blk = p / nv, dof d = p % nv) of the env in cs: q_bar or v_bar.
+template <int NB, int NV, int NS, typename T>
+DS_HD double split_vjp_entry(const DevModel& m, const KArgs& a, const ColState<NB, NV, NS, T>& cs, int blk, int d) {
+  const T dt = T(a.dt);
+  T dtau[NV];
+  rnea_tangent<NB, NV, NS, T>(m, cs, blk, d, dtau);
+  T r = T(0);
+  for (int k = 0; k < NV; ++k) r += dtau[k] * cs.w2[k];
+  r = -dt * r;
+  if (blk == 1) r += cs.ub[d];
+  const bool stab = gap_term(a);
+  for (int ac = 0; ac < cs.na && (blk == 0 || stab); ++ac) {
+    if (!cs.act[ac]) continue;
+    T fk[3] = {T(0), T(0), T(0)};
+    if (blk == 0) fkv_tangent<NB, NV, NS, T>(m, cs, cs.Vp, ac, d, fk);
+    fk[2] += baumgarte_d<NB, NV, NS, T>(m, a, cs, ac, blk, d);
+    for (int rr = 0; rr < 3; ++rr) r -= fk[rr] * cs.zeta[3 * ac + rr];
+  }
+  return (blk == 0 && a.qnbar) ? double(r) + cs.qadd[d] : double(r);
+}
+
+// Prep kernel: one thread per env of the launch's range (as finish_kernel's, without splitting),
+// in CTAs of one warp, so that a batch of a few thousand envs still spreads over every SM.
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(32, 16) finish_prep_kernel(KArgs a) {
+  __shared__ DevModel sm;
+  load_model(sm, a.model);
+  const int lo = a.flo ? *a.flo : 0;
+  const int n = a.fhi ? *a.fhi - lo : a.n_env;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int e = DS_IX(a.fhi ? a.ws.dlist[lo + t] : (a.env_list ? a.env_list[t] : t), a.B);
+    if (a.model_id && a.model_id[e] != a.model_index) continue;
+    finish_prep_env<NB, NV, NS, T>(sm, a, e);
+  }
+}
+
+// Column kernel: one warp per env (blockDim = 32 x envs per block, dynamic shared memory = one
+// ColState per warp); warps stride over the range's envs.
+template <int NB, int NV, int NS, typename T>
+__global__ void __launch_bounds__(128) finish_cols_kernel(KArgs a) {
+  using CS = ColState<NB, NV, NS, T>;
+  __shared__ DevModel sm;
+  extern __shared__ __align__(16) unsigned char ds_cs_smem[];
+  load_model(sm, a.model);
+  CS& cs = reinterpret_cast<CS*>(ds_cs_smem)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int lo = a.flo ? *a.flo : 0;
+  const int n = a.fhi ? *a.fhi - lo : a.n_env;
+  const int B = a.B;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nwarps) {
+    const int e = DS_IX(a.fhi ? a.ws.dlist[lo + t] : (a.env_list ? a.env_list[t] : t), B);
+    if (a.model_id && a.model_id[e] != a.model_index) continue;      // uniform over the warp
+    const uint32_t st = a.ws.st[e];
+    if (!(st & DS_ENV_NONFINITE)) {
+      int row = 0;
+      const double* fw = a.ws.fw;
+      cs.visit([&](auto* ptr, int cnt) {
+        using V = typename std::remove_reference<decltype(*ptr)>::type;
+        for (int i = lane; i < cnt; i += 32) ptr[i] = V(fw[size_t(row + i) * B + e]);
+        row += cnt;
+      });
+      __syncwarp();
+      if (a.run == DS_RUN_JAC) {
+        for (int col = lane; col < 3 * NV; col += 32) {
+          const int blk = col / NV, d = col % NV;
+          T Dc[NV];
+          split_jac_column<NB, NV, NS, T>(sm, a, cs, blk, d, Dc);
+          double* out = blk == 0 ? a.dv_dq : (blk == 1 ? a.dv_dv : a.dv_dtau);
+          for (int k = 0; k < NV; ++k) out[(k * NV + d) * B + e] = double(Dc[k]);
+        }
+      } else {
+        for (int p = lane; p < 2 * NV; p += 32) {
+          const int blk = p / NV, d = p % NV;
+          double* out = blk == 0 ? a.q_bar : a.v_bar;
+          out[d * B + e] = split_vjp_entry<NB, NV, NS, T>(sm, a, cs, blk, d);
+        }
+        for (int k = lane; k < NV; k += 32) a.tau_bar[k * B + e] = double(T(a.dt) * cs.w2[k]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0 && a.status) a.status[e] = st;
+  }
 }
 
 // 2c. adaptive penalty (options admm_rho_adapt), after round a.round's Newton stage: for every env

@@ -44,6 +44,33 @@ inline int finish_blocks(int n, int nchunk, int threads) {
   return int(b < (1 << 20) ? (b > 0 ? b : 1) : (1 << 20));
 }
 
+// The split finish (schedule finish_split) over the envs of fa (its range flo/fhi, or all): the
+// prep kernel (CTAs of one warp), then the column kernel with up to 4 envs per CTA as fit in
+// 200 KB of shared memory (at least one), CTAs for the SMs' resident capacity.
+template <int NB, int NV, int NS, typename T>
+void launch_finish_split(const KArgs& fa, cudaStream_t s) {
+  const int pblocks = (fa.n_env + 31) / 32;
+  if (pblocks <= 0) return;
+  ds_trace_mark(DS_STAGE_FINISH, 1, s);
+  finish_prep_kernel<NB, NV, NS, T><<<pblocks, 32, 0, s>>>(fa);
+  constexpr size_t cs_bytes = sizeof(ColState<NB, NV, NS, T>);
+  constexpr int epb = cs_bytes * 4 <= 200 * 1024 ? 4 : (cs_bytes * 2 <= 200 * 1024 ? 2 : 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(finish_cols_kernel<NB, NV, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(epb * cs_bytes));
+    attr = true;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, finish_cols_kernel<NB, NV, NS, T>, 32 * epb, epb * cs_bytes);
+  if (per_sm <= 0) per_sm = 1;
+  int cblocks = ds_sm_count() * per_sm;
+  const int need = (fa.n_env + epb - 1) / epb;
+  if (cblocks > need) cblocks = need;
+  finish_cols_kernel<NB, NV, NS, T><<<cblocks, 32 * epb, epb * cs_bytes, s>>>(fa);
+  ds_trace_mark(DS_STAGE_FINISH, 0, s);
+}
+
 template <int NB, int NV, int NS, typename T>
 void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   const int threads = 128;
@@ -126,6 +153,7 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
   // stream while the later ADMM rounds run; the rest are finished at the end.  Overlap round -1:
   // right after the setup (the envs it solved: no contact, separating, presolved).
   const bool overlap = a0.side && sc.overlap_from < DS_ROUNDS - 1;
+  const bool split = sc.finish_split && a0.run != DS_RUN_STEP;
   auto fork_finish = [&]() {
     ds_trace_mark(DS_STAGE_FINISH, 1, s);
     dcount_snapshot_kernel<<<1, 1, 0, s>>>(a0.ws.dcount);
@@ -145,9 +173,15 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
       fa.fin_reserve = sc.reserve;
       fa.claim = a0.ws.claim;
     }
-    ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
-    finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
-    ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);
+    if (split) {
+      fa.fin_reserve = 0;
+      fa.claim = nullptr;
+      launch_finish_split<NB, NV, NS, T>(fa, a0.side);
+    } else {
+      ds_trace_mark(DS_STAGE_FINISH, 1, a0.side);
+      finish_kernel<NB, NV, NS, T><<<fb, threads, 0, a0.side>>>(fa);
+      ds_trace_mark(DS_STAGE_FINISH, 0, a0.side);
+    }
     cudaEventRecord(a0.ev_join, a0.side);
   };
   if (overlap && sc.overlap_from < 0) fork_finish();
@@ -192,10 +226,18 @@ void launch_pipeline(const KArgs& a0, cudaStream_t s) {
     fb_args.flo = a0.ws.dcount + 1;
     fb_args.fhi = a0.ws.dcount;
     const int fb = finish_blocks(a0.n_env, fb_args.nchunk, threads);
-    ds_trace_mark(DS_STAGE_FINISH, 1, s);
-    finish_kernel<NB, NV, NS, T><<<fb, threads, 0, s>>>(fb_args);
-    ds_trace_mark(DS_STAGE_FINISH, 0, s);
+    if (split) {
+      launch_finish_split<NB, NV, NS, T>(fb_args, s);
+    } else {
+      ds_trace_mark(DS_STAGE_FINISH, 1, s);
+      finish_kernel<NB, NV, NS, T><<<fb, threads, 0, s>>>(fb_args);
+      ds_trace_mark(DS_STAGE_FINISH, 0, s);
+    }
     cudaStreamWaitEvent(s, a0.ev_join, 0);
+    return;
+  }
+  if (split) {
+    launch_finish_split<NB, NV, NS, T>(af, s);
     return;
   }
   const int fblocks = finish_blocks(a0.n_env, af.nchunk, threads);

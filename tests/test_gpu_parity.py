@@ -616,3 +616,64 @@ def test_single_contact_presolve(torch_cuda, precision):
     refs = run_oracle(sub, list(range(len(envs))))
     tol_v, tol_j = (1e-9, 1e-9) if precision == "fp64" else (1e-4, 1e-3)
     _compare(sub, g, refs, list(range(len(envs))), tol_v, tol_j, min_checked=25)
+
+
+def _rel_per_env(got, ref):
+    axes = tuple(range(got.ndim - 1))
+    return (got - ref).abs().amax(axes) / ref.abs().amax(axes).clamp_min(1e-6)
+
+
+@pytest.mark.parametrize("name,B", [("arm_cube", 600), ("humanoid_feet", 300), ("quadruped_feet", 300)])
+@pytest.mark.parametrize("precision,tol_v,tol_j,tol_same", [("fp64", 1e-9, 1e-9, 1e-8), ("mixed", 1e-4, 1e-3, 1e-3)])
+def test_split_finish(torch_cuda, name, B, precision, tol_v, tol_j, tol_same):
+    """The finish as a prep kernel and a column kernel (schedule finish = split: one warp per env,
+    its state in shared memory, the columns over the lanes).  The step's outputs are the one-kernel
+    finish's exactly (same solve, same F9); the Jacobians agree with it to rounding (the implicit
+    part applied by rows, in FP32 in the mixed form) and with the oracle on sampled envs."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = getattr(scenes, name)(B)
+    sim = ds.Simulator(wl, precision=precision)
+    ref = {k: v.clone() for k, v in sim.step_jac().items()}
+    sim.set_schedule(ds.schedule_index(split=1))
+    try:
+        got = {k: v.clone() for k, v in sim.step_jac().items()}
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1)
+    for key in ("v_next", "modes", "status", "iters"):
+        assert torch.equal(got[key], ref[key]), key
+    ok = (ref["status"] & 2) == 0
+    for key in ("dv_dq", "dv_dv", "dv_dtau"):
+        err = _rel_per_env(got[key], ref[key])[ok]
+        assert err.max().item() <= tol_same, (key, err.max().item())
+    envs = list(range(0, B, max(1, B // 40)))
+    g = {k: v.cpu().numpy() for k, v in got.items()}
+    refs = run_oracle(wl, envs)
+    _compare(wl, g, refs, envs, tol_v, tol_j, min_checked=max(10, len(envs) // 3))
+
+
+@pytest.mark.parametrize("precision,tol_same", [("fp64", 1e-8), ("mixed", 1e-3)])
+def test_split_finish_vjp(torch_cuda, precision, tol_same):
+    """The split finish under sim_step_vjp on the mixed-robot batch (each model's pipeline): q_bar,
+    v_bar, tau_bar against the one-kernel finish's, with a cotangent of q+ as well."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.uneven(300)
+    sim = ds.Simulator(wl, precision=precision)
+    rng = np.random.default_rng(41)
+    vb = torch.as_tensor(rng.normal(size=wl.batch.v.shape), dtype=torch.float64, device="cuda")
+    qb = torch.as_tensor(rng.normal(size=wl.batch.v.shape), dtype=torch.float64, device="cuda")
+    ref = {k: v.clone() for k, v in sim.step_vjp(vb, q_next_bar=qb).items()}
+    sim.set_schedule(ds.schedule_index(split=1), "vjp")
+    try:
+        got = {k: v.clone() for k, v in sim.step_vjp(vb, q_next_bar=qb).items()}
+        torch.cuda.synchronize()
+    finally:
+        sim.set_schedule(-1, "vjp")
+    for key in ("v_next", "modes", "status"):
+        assert torch.equal(got[key], ref[key]), key
+    ok = (ref["status"] & 2) == 0
+    for key in ("q_bar", "v_bar", "tau_bar"):
+        err = _rel_per_env(got[key], ref[key])[ok]
+        assert err.max().item() <= tol_same, (key, err.max().item())

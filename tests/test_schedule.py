@@ -30,4 +30,5 @@ def test_default_schedule_index():
     assert d == {"round_caps": "default", "row_per_lane_admm_from_round": 5, "finish_ctas_per_sm": 4,
                  "newton": "cooperative", "overlapped_finish_after_round": 5, "two_warp_admm_from_round": 5,
                  "overlapped_finish_keeps_free_every_nth_sm": 8, "speculative_newton_from_round": None,
-                 "single_contact_presolve": True, "launch": "pipeline"}
+                 "single_contact_presolve": True, "launch": "pipeline",
+                 "finish": "one kernel"}
