@@ -254,7 +254,7 @@ ds_status ds_cotangent_to_raw(const ds_model* const* models, int32_t nmodels, in
  * (16 MiB) that the library holds on every device that loads it, until the process exits.  It
  * calls no cudaMalloc / cudaFree and no allocating routine.
  *   - Batches whose ds_workspace_size() exceeds the array are rejected with DS_ETOOLARGE
- *     (about 2650 envs of the 7-dof arm with 4 contact slots).
+ *     (about 2070 envs of the 7-dof arm with 4 contact slots).
  *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress);
  *     make that first call outside any stream capture.
  *   - Every call shares the one array and leaves its contents behind; the counters that must
