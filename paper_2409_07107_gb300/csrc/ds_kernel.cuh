@@ -1474,16 +1474,16 @@ DS_HD void finish_reduced(const DevModel& m, const KArgs& a, Env<NB, NV, NS, T>&
   }
 }
 
-// Rows of the implicit part of the Jacobian: P_k = B^T (A^-)^T C^T Y^T e_k for every output row k
-// (one transposed minimum-norm solve each), so that column c of Y C A^- B (J_c D + F) is
-// sum_j P[k][j] (J_c D + F)_j.  Rows of breaking contacts are 0.
+// Rows of the implicit part of the Jacobian: P_k = B^T (A^-)^T C^T Y^T e_k for the output rows
+// k = k0, k0 + kstep, ... (one transposed minimum-norm solve each), so that column c of
+// Y C A^- B (J_c D + F) is sum_j P[k][j] (J_c D + F)_j.  Rows of breaking contacts are 0.
 template <int NB, int NV, int NS, typename T>
-DS_HD void finish_rows(Env<NB, NV, NS, T>& s, const Reduced<NS>& rd, double (*P)[3 * NS]) {
+DS_HD void finish_rows(Env<NB, NV, NS, T>& s, const Reduced<NS>& rd, double (*P)[3 * NS], int k0 = 0, int kstep = 1) {
   const int(&off)[NS] = rd.off;
   const int(&sz)[NS] = rd.sz;
   const double(&Rm)[NS][3][2] = rd.Rm;
   const double(&RP)[NS][2][3] = rd.RP;
-  for (int k = 0; k < NV; ++k) {
+  for (int k = k0; k < NV; k += kstep) {
     double u[3 * NS], z[3 * NS];
     for (int ac = 0; ac < s.na; ++ac) {
       if (sz[ac] == 0) continue;
@@ -2493,12 +2493,14 @@ struct ColState {
   static constexpr int kRows = ds_colstate_rows(NB, NV, NS);
 };
 
-// Prep for env e (one thread): F9 and the outputs of the step as the per-thread finish writes
-// them, then the ColState into the env's forward-state rows (status, with the derivative part's
-// bits, written by the column kernel).
+// Prep for env e, in two parts around a warp barrier: prep_load reads the env's forward state
+// (and its impulse and modes); prep_store, after every thread of the env has read it, writes the
+// ColState over the same rows.  With nch > 1 threads per env (Jacobians), chunk c computes the
+// rows k = c, c + nch, ... of P (each chunk factors the reduced system itself) and chunk 0 does F9,
+// the step's outputs and the rest of the ColState; the status of the derivative part travels in
+// w.st to the column kernel, which writes it.
 template <int NB, int NV, int NS, typename T>
-DS_HD void finish_prep_env(const DevModel& m, const KArgs& a, const int e) {
-  Env<NB, NV, NS, T> s;
+DS_HD void prep_load(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s) {
   load_forward<NB, NV, NS, T>(m, a, e, s);
   const WsView& w = a.ws;
   const int B = a.B;
@@ -2509,14 +2511,26 @@ DS_HD void finish_prep_env(const DevModel& m, const KArgs& a, const int e) {
   } else {
     s.margin = classify(s, s.lam, a.eps_sigma, a.eps_lambda, s.mode);
   }
+}
+
+template <int NB, int NV, int NS, typename T>
+DS_HD void prep_store(const DevModel& m, const KArgs& a, const int e, Env<NB, NV, NS, T>& s, int chunk, int nch) {
+  using CS = ColState<NB, NV, NS, T>;
+  const WsView& w = a.ws;
+  const int B = a.B;
+  const int mm = 3 * s.na;
+  const bool lead = chunk == 0;
   KArgs a1 = a;
-  a1.run = DS_RUN_STEP;                       // F9 and the step's outputs only
+  a1.run = DS_RUN_STEP;                       // F9 (and, from chunk 0, the step's outputs) only
   a1.status = nullptr;
   uint32_t st = w.st[e];
-  env_finish<NB, NV, NS, T>(m, a1, e, s, st, w.iters[e]);
+  const int iters = w.iters[e];
+  env_finish<NB, NV, NS, T>(m, a1, e, s, st, iters, chunk, nch);
   for (int k = 0; k < NV; ++k)
     if (!isfinite(double(s.vn[k]))) st |= DS_ENV_NONFINITE;
-  ColState<NB, NV, NS, T> cs;
+  double* fw = w.fw;
+  constexpr int kOffP = 6 * NV + 2 * NV + 10 * NB + 7 * 6 * NB + NV * (NV + 1) / 2 + 9 * NS + 9 + 3 * NS * NV;
+  CS cs;
   cs.na = s.na;
   cs.md = 0;
   if (!(st & DS_ENV_NONFINITE)) {
@@ -2529,17 +2543,18 @@ DS_HD void finish_prep_env(const DevModel& m, const KArgs& a, const int e) {
     for (int ac = 0; ac < NS; ++ac) cs.act[ac] = ac < s.na && rd.sz[ac] != 0;
     if (a.run == DS_RUN_JAC) {
       double P[NV][3 * NS];
-      if (rd.md > 0) finish_rows<NB, NV, NS, T>(s, rd, P);
-      for (int k = 0; k < NV; ++k)
-        for (int j = 0; j < 3 * NS; ++j) cs.P[k][j] = T(rd.md > 0 && j < mm ? P[k][j] : 0.0);
-    } else {
+      if (rd.md > 0) finish_rows<NB, NV, NS, T>(s, rd, P, chunk, nch);
+      for (int k = chunk; k < NV; k += nch)
+        for (int j = 0; j < 3 * NS; ++j)
+          fw[size_t(kOffP + k * 3 * NS + j) * B + e] = double(T(rd.md > 0 && j < mm ? P[k][j] : 0.0));
+    } else if (lead) {
       double zeta[3 * NS], qadd[NV];
       finish_vjp_head<NB, NV, NS, T>(m, a, e, s, rd, cs.ub, cs.w2, zeta, qadd);
       for (int j = 0; j < 3 * NS; ++j) cs.zeta[j] = T(j < mm ? zeta[j] : 0.0);
       for (int k = 0; k < NV; ++k) cs.qadd[k] = a.qnbar ? qadd[k] : 0.0;
     }
   }
-  // the status of the derivative part travels in w.st (read by the column kernel)
+  if (!lead) return;
   w.st[e] = st;
   for (int k = 0; k < NV; ++k) {
     for (int j = 0; j < 6; ++j) cs.S[k][j] = s.S[k][j];
@@ -2564,9 +2579,13 @@ DS_HD void finish_prep_env(const DevModel& m, const KArgs& a, const int e) {
   for (int r = 0; r < 3 * NS; ++r)
     for (int k = 0; k < NV; ++k) cs.Jc[r][k] = s.Jc[r][k];
   int row = 0;
-  double* fw = w.fw;
+  const void* skip = (a.run == DS_RUN_JAC) ? static_cast<const void*>(&cs.P[0][0]) : nullptr;
   cs.visit([&](auto* ptr, int n) {
-    for (int i = 0; i < n; ++i) fw[size_t(row + i) * B + e] = double(ptr[i]);
+    if (static_cast<const void*>(ptr) != skip) {      // the rows of P were written by their chunks
+      for (int i = 0; i < n; ++i) fw[size_t(DS_IX(row + i, CS::kRows)) * B + e] = double(ptr[i]);
+    } else if (row != kOffP) {
+      (void)DS_IX(-1, 1);                              // checked build: the layout disagrees
+    }
     row += n;
   });
 }
@@ -2631,18 +2650,33 @@ DS_HD double split_vjp_entry(const DevModel& m, const KArgs& a, const ColState<N
   return (blk == 0 && a.qnbar) ? double(r) + cs.qadd[d] : double(r);
 }
 
-// Prep kernel: one thread per env of the launch's range (as finish_kernel's, without splitting),
-// in CTAs of one warp, so that a batch of a few thousand envs still spreads over every SM.
+// Prep kernel: a.nchunk threads per env of the launch's range (a power of two <= 32, so that an
+// env's threads share a warp), in CTAs of one warp, so that a batch of a few thousand envs still
+// spreads over every SM.  Every lane runs the same trips, so the warp barrier between reading the
+// forward state and overwriting it with the ColState is reached by all 32.
 template <int NB, int NV, int NS, typename T>
 __global__ void __launch_bounds__(32, 16) finish_prep_kernel(KArgs a) {
   __shared__ DevModel sm;
   load_model(sm, a.model);
   const int lo = a.flo ? *a.flo : 0;
   const int n = a.fhi ? *a.fhi - lo : a.n_env;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int e = DS_IX(a.fhi ? a.ws.dlist[lo + t] : (a.env_list ? a.env_list[t] : t), a.B);
-    if (a.model_id && a.model_id[e] != a.model_index) continue;
-    finish_prep_env<NB, NV, NS, T>(sm, a, e);
+  const int nch = a.nchunk;
+  const long long total = (long long)n * nch;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * 32; base < total; base += (long long)gridDim.x * 32) {
+    const long long t = base + lane;
+    int e = 0, chunk = 0;
+    bool mine = t < total;
+    if (mine) {
+      const int ti = int(t / nch);
+      chunk = int(t - (long long)ti * nch);
+      e = DS_IX(a.fhi ? a.ws.dlist[lo + ti] : (a.env_list ? a.env_list[ti] : ti), a.B);
+      mine = !a.model_id || a.model_id[e] == a.model_index;
+    }
+    Env<NB, NV, NS, T> s;
+    if (mine) prep_load<NB, NV, NS, T>(sm, a, e, s);
+    __syncwarp();
+    if (mine) prep_store<NB, NV, NS, T>(sm, a, e, s, chunk, nch);
   }
 }
 

@@ -49,10 +49,19 @@ inline int finish_blocks(int n, int nchunk, int threads) {
 // 200 KB of shared memory (at least one), CTAs for the SMs' resident capacity.
 template <int NB, int NV, int NS, typename T>
 void launch_finish_split(const KArgs& fa, cudaStream_t s) {
-  const int pblocks = (fa.n_env + 31) / 32;
+  // prep threads per env (Jacobians): enough to fill the SMs' 16 resident warps (128 registers a
+  // thread), at most 8
+  KArgs pa = fa;
+  pa.nchunk = 1;
+  if (fa.run == DS_RUN_JAC) {
+    const int want = fa.n_env > 0 ? (ds_sm_count() * 16 * 32) / fa.n_env : 1;
+    pa.nchunk = want >= 8 ? 8 : (want >= 4 ? 4 : (want >= 2 ? 2 : 1));
+  }
+  const long long items = (long long)fa.n_env * pa.nchunk;
+  const int pblocks = int((items + 31) / 32);
   if (pblocks <= 0) return;
   ds_trace_mark(DS_STAGE_FINISH, 1, s);
-  finish_prep_kernel<NB, NV, NS, T><<<pblocks, 32, 0, s>>>(fa);
+  finish_prep_kernel<NB, NV, NS, T><<<pblocks, 32, 0, s>>>(pa);
   constexpr size_t cs_bytes = sizeof(ColState<NB, NV, NS, T>);
   constexpr int epb = cs_bytes * 4 <= 200 * 1024 ? 4 : (cs_bytes * 2 <= 200 * 1024 ? 2 : 1);
   static bool attr = false;
