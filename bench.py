@@ -28,10 +28,11 @@ from paper_2409_07107_gb300 import replicas, scenes  # noqa: E402
 WORKLOAD_B = 65536
 
 # DRAM bytes (read + write) per env and launch of the FP64 ADMM round kernels on the arm + cube
-# workload, from one ncu capture of a default-schedule step at 16384 envs (nine launches, 117.2 MB);
-# the workspace traffic grows with the envs.  Valid only for the kernel sources it was taken on.
-ADMM_TRAFFIC = {"bytes_per_env_launch": 117.2e6 / 9 / 16384,
-                "sources_sha256_16": {"ds_kernel.cuh": "2b4374f85ab650f4", "ds_common.cuh": "c6a81f42512c998f"}}
+# workload, from one ncu capture of a default-schedule step at 16384 envs (nine launches,
+# 103.1 MB); the workspace traffic grows with the envs.  Valid only while the kernel sources hash
+# as recorded here (the ADMM kernels in them are the captured ones).
+ADMM_TRAFFIC = {"bytes_per_env_launch": 103.136512e6 / 9 / 16384,
+                "sources_sha256_16": {"ds_kernel.cuh": "a0bf8530487f801b", "ds_common.cuh": "d9ed443c0376b110"}}
 
 
 def _admm_traffic_valid():
@@ -211,7 +212,7 @@ def _oracle_rec(args):
         import types
         opt = types.SimpleNamespace(**dict(vars(opt), ncp_route=args[3]))
     st = S.step_jac(model, env, opt)
-    return {k: st[k] for k in ("v_next", "modes", "margin", "slots", "dv_dq", "dv_dv", "dv_dtau")}
+    return {k: st[k] for k in ("v_next", "modes", "margin", "slots", "dv_dq", "dv_dv", "dv_dtau", "G", "g", "mu")}
 
 
 def oracle_alternatives(wl, snaps, recs, processes=None):
@@ -294,10 +295,17 @@ def error_stats(wl, snap, recs, vbar=None, delta=1e-3, alt=None):
     counts of mode disagreements, of envs near a mode switch (oracle margin < delta) and of envs
     whose v+ differs from the oracle's by more than 1e-6 (an error).  The reference of an env is
     the nearer (in v+) of the oracle's ADMM-route solution and, where given in ``alt``, its PGS-route
-    one (Eq. 1 can have several solutions); envs that took the second are counted."""
+    one (Eq. 1 can have several solutions); envs that took the second are counted.  An env whose v+
+    is beyond the form's tolerance (1e-6 FP64, 1e-4 mixed) from both but whose impulse satisfies
+    Eq. 1 for the oracle's G, g, mu (NCP residual <= 1e-9 max(1, |g|)) reached yet another solution:
+    it is counted, with its v+ difference, under other_solution_of_eq1 and left out of the
+    statistics (as the parity tests accept it)."""
+    from oracle.ncp import ncp_residual
     keys = ("q_bar", "v_bar", "tau_bar") if vbar is not None else ("dv_dq", "dv_dv", "dv_dtau")
     err = {k: [] for k in ("v_next",) + keys}
     mode_dis = near = far = second = 0
+    other = []
+    tol = 1e-4 if snap.get("_form") == "mixed" else 1e-6
     for e, r in enumerate(recs):
         nv = _model_of(wl, e).nv
         ev = _rel(snap["v_next"][:nv, e], r["v_next"])
@@ -306,6 +314,14 @@ def error_stats(wl, snap, recs, vbar=None, delta=1e-3, alt=None):
             if ea < ev:
                 r, ev = alt[e], ea
                 second += 1
+        if ev > tol and len(r["slots"]) and "lambda" in snap:
+            # neither oracle route's solution: does the GPU impulse solve Eq. 1 for the oracle's
+            # problem data (another member of the solution set)?
+            lam = np.concatenate([snap["lambda"][3 * k:3 * k + 3, e] for k in r["slots"]])
+            scale = max(1.0, float(np.max(np.abs(r["g"]))))
+            if ncp_residual(r["G"], r["g"], r["mu"], lam) <= 1e-9 * scale:
+                other.append(ev)
+                continue
         err["v_next"].append(ev)
         far += ev > 1e-6
         if r["margin"] < delta:
@@ -324,7 +340,8 @@ def error_stats(wl, snap, recs, vbar=None, delta=1e-3, alt=None):
         return ({"max": float(np.max(v)), "p99": float(np.percentile(v, 99)), "median": float(np.median(v)),
                  "envs": len(v)} if len(v) else None)
     return dict({k: q(v) for k, v in err.items()}, envs=len(recs), mode_disagreements=mode_dis,
-                near_switch=near, v_next_off_by_1e6=int(far), second_route_solution=int(second))
+                near_switch=near, v_next_off_by_1e6=int(far), second_route_solution=int(second),
+                other_solution_of_eq1={"envs": len(other), "v_next_max_diff": float(max(other)) if other else None})
 
 
 # -------------------------------------------------------------------------------------- rollout
@@ -619,6 +636,7 @@ def main():
             key = "".join("bks"[int(x)] for x in sorted(modes[:, e]) if x != 3) or "-"
             pat[key] = pat.get(key, 0) + 1
         snaps[prec] = {k: v[..., :1024].cpu().numpy() for k, v in one_out.items()}
+        snaps[prec]["_form"] = prec
         traffic = None
         if prec == "fp64" and wl_name == "arm7-cube" and _admm_traffic_valid():
             traffic = ADMM_TRAFFIC["bytes_per_env_launch"] * B
