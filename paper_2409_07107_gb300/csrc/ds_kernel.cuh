@@ -843,6 +843,97 @@ DS_HD void rnea_tangent(const DevModel& m, const E& s, int kind, int d, T* dtau)
     for (int dd = m.iv[DS_IX(b, NB)]; dd < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++dd) dtau[DS_IX(dd, NV)] = dot6(s.S[DS_IX(dd, NV)], dF[DS_IX(j, NB)]);
 }
 
+// The same directional derivative as rnea_tangent, with the subtree of the dof's body walked
+// depth first on an explicit stack: a body's dV, dA and accumulated dF live on the stack only while
+// it lies on the path from the dof's body to the body being visited, and a body's dF is final (its
+// subtree's included) when it is popped, at which point its dofs' entries are formed and it is
+// added into its parent's.  The per-column scratch it touches is the path's depth, not the whole
+// tree; the sums over children run in preorder (rnea_tangent sums them in reverse), so the two
+// agree to rounding.
+template <int NB, int NV, int NS, typename T, class E>
+DS_HD void rnea_tangent_stack(const DevModel& m, const E& s, int kind, int d, T* dtau) {
+  const int j = m.dof_body[DS_IX(d, NV)];
+  const int jend = m.sub_end[DS_IX(j, NB)];
+  const T* xi = s.S[d];
+  int sb[NB] = {};
+  T sV[NB][6], sA[NB][6], sF[NB][6];
+  int top = -1;
+  for (int k = 0; k < NV; ++k) dtau[k] = T(0);
+  // pop the top body: its dofs' entries from its final dF, then dF into its parent's (on the stack)
+  auto pop = [&]() {
+    const int b = sb[DS_IX(top, NB)];
+    for (int dd = m.iv[DS_IX(b, NB)]; dd < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++dd) {
+      T r = dot6(s.S[DS_IX(dd, NV)], sF[DS_IX(top, NB)]);
+      if (kind == 0) {
+        T dS[6];
+        mcross(xi, s.S[DS_IX(dd, NV)], dS);
+        r += dot6(dS, s.Fc[DS_IX(b, NB)]);
+      }
+      dtau[DS_IX(dd, NV)] = r;
+    }
+    if (top > 0)
+      for (int k = 0; k < 6; ++k) sF[DS_IX(top - 1, NB)][k] += sF[DS_IX(top, NB)][k];
+    --top;
+  };
+  for (int i = j; i < jend; ++i) {
+    const int par = m.parent[i];
+    while (top >= 0 && sb[DS_IX(top, NB)] != par) pop();
+    const bool inside = top >= 0;
+    T dVJ[6] = {0, 0, 0, 0, 0, 0}, dSa[6] = {0, 0, 0, 0, 0, 0};
+    if (kind == 0) {
+      for (int dd = m.iv[i]; dd < m.iv[i] + m.nd[i]; ++dd) {
+        T dS[6];
+        mcross(xi, s.S[DS_IX(dd, NV)], dS);
+        for (int k = 0; k < 6; ++k) { dVJ[k] += dS[k] * s.v[DS_IX(dd, NV)]; dSa[k] += dS[k] * s.astar[DS_IX(dd, NV)]; }
+      }
+    } else if (i == j) {
+      for (int k = 0; k < 6; ++k) dVJ[k] = xi[k];
+    }
+    ++top;
+    T* dV = sV[DS_IX(top, NB)];
+    T* dA = sA[DS_IX(top, NB)];
+    sb[DS_IX(top, NB)] = i;
+    T t1[6], t2[6];
+    for (int k = 0; k < 6; ++k) dV[k] = (inside ? sV[DS_IX(top - 1, NB)][k] : T(0)) + dVJ[k];
+    mcross(dV, s.VJ[i], t1);
+    mcross(s.V[i], dVJ, t2);
+    for (int k = 0; k < 6; ++k) dA[k] = (inside ? sA[DS_IX(top - 1, NB)][k] : T(0)) + dSa[k] + t1[k] + t2[k];
+    T u[6], w[6];
+    iapply(s.I[i], dA, u);
+    fcross(dV, s.IV[i], t1);
+    for (int k = 0; k < 6; ++k) u[k] += t1[k];
+    iapply(s.I[i], dV, w);
+    if (kind == 0) {
+      T xa[6], ixa[6];
+      fcross(xi, s.IA[i], t1);
+      mcross(xi, s.A[i], xa);
+      iapply(s.I[i], xa, ixa);
+      for (int k = 0; k < 6; ++k) u[k] += t1[k] - ixa[k];
+      fcross(xi, s.IV[i], t1);
+      mcross(xi, s.V[i], xa);
+      iapply(s.I[i], xa, ixa);
+      for (int k = 0; k < 6; ++k) w[k] += t1[k] - ixa[k];
+      for (int a = 0; a < s.na; ++a) {
+        if (s.body[a] != i) continue;
+        T dc[3], t[3];
+        cross3(xi + 3, s.x[a], t);
+        for (int k = 0; k < 3; ++k) dc[k] = xi[k] + t[k];
+        cross3(dc, s.f[a], t);
+        for (int k = 0; k < 3; ++k) u[3 + k] -= t[k];
+      }
+    }
+    fcross(s.V[i], w, t1);
+    for (int k = 0; k < 6; ++k) sF[DS_IX(top, NB)][k] = u[k] + t1[k];
+  }
+  T Fj[6];
+  while (top > 0) pop();
+  for (int k = 0; k < 6; ++k) Fj[k] = sF[0][k];     // the dof's body, its whole subtree included
+  pop();
+  for (int b = m.parent[DS_IX(j, NB)]; b >= 0; b = m.parent[DS_IX(b, NB)])
+    for (int dd = m.iv[DS_IX(b, NB)]; dd < m.iv[DS_IX(b, NB)] + m.nd[DS_IX(b, NB)]; ++dd)
+      dtau[DS_IX(dd, NV)] = dot6(s.S[DS_IX(dd, NV)], Fj);
+}
+
 // d(J_c v+)/dq_d for contact a at fixed v+ (App. D's FKV term, including the motion of the
 // contact point with the body): Vp = body velocities under v+.
 template <int NB, int NV, int NS, typename T, class E>
@@ -2598,7 +2689,7 @@ DS_HD void split_jac_column(const DevModel& m, const KArgs& a, const ColState<NB
   const T dt = T(a.dt);
   if (blk < 2) {
     T dtau[NV];
-    rnea_tangent<NB, NV, NS, T>(m, cs, blk, d, dtau);
+    rnea_tangent_stack<NB, NV, NS, T>(m, cs, blk, d, dtau);
     ltl_solve_t(cs.L, dtau, NV, m.dof_parent);
     ltl_solve(cs.L, dtau, NV, m.dof_parent);
     for (int k = 0; k < NV; ++k) Dc[k] = -dt * dtau[k] + (blk == 1 && k == d ? T(1) : T(0));
@@ -2634,7 +2725,7 @@ template <int NB, int NV, int NS, typename T>
 DS_HD double split_vjp_entry(const DevModel& m, const KArgs& a, const ColState<NB, NV, NS, T>& cs, int blk, int d) {
   const T dt = T(a.dt);
   T dtau[NV];
-  rnea_tangent<NB, NV, NS, T>(m, cs, blk, d, dtau);
+  rnea_tangent_stack<NB, NV, NS, T>(m, cs, blk, d, dtau);
   T r = T(0);
   for (int k = 0; k < NV; ++k) r += dtau[k] * cs.w2[k];
   r = -dt * r;
