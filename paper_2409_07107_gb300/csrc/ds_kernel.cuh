@@ -2771,35 +2771,55 @@ __global__ void __launch_bounds__(32, 16) finish_prep_kernel(KArgs a) {
   }
 }
 
-// Column kernel: one warp per env (blockDim = 32 x envs per block, dynamic shared memory = one
-// ColState per warp); warps stride over the range's envs.
+// Warps per env of the column kernel: two when an env has more than 32 columns (Jacobians) or dof
+// passes (VJP) to spread, so that more warps are in flight for the same shared memory.
+template <int NV>
+struct ColsShape {
+  static constexpr int WPE = 3 * NV > 32 ? 2 : 1;
+};
+
+// Column kernel: ColsShape::WPE warps per env (blockDim = 32 WPE x envs per block, dynamic shared
+// memory = one ColState per env); the CTAs stride over the range's envs, a CTA's envs in step, with
+// a CTA barrier between staging the states and reading them (every thread runs the same trips).
 template <int NB, int NV, int NS, typename T>
-__global__ void __launch_bounds__(128) finish_cols_kernel(KArgs a) {
+__global__ void __launch_bounds__(256, 2) finish_cols_kernel(KArgs a) {
   using CS = ColState<NB, NV, NS, T>;
+  constexpr int WPE = ColsShape<NV>::WPE;
+  constexpr int GL = 32 * WPE;                         // lanes per env
   __shared__ DevModel sm;
   extern __shared__ __align__(16) unsigned char ds_cs_smem[];
   load_model(sm, a.model);
-  CS& cs = reinterpret_cast<CS*>(ds_cs_smem)[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
+  const int slot = int(threadIdx.x) / GL;
+  const int li = int(threadIdx.x) - slot * GL;
+  const int epb = int(blockDim.x) / GL;
+  CS& cs = reinterpret_cast<CS*>(ds_cs_smem)[slot];
   const int lo = a.flo ? *a.flo : 0;
   const int n = a.fhi ? *a.fhi - lo : a.n_env;
   const int B = a.B;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nwarps) {
-    const int e = DS_IX(a.fhi ? a.ws.dlist[lo + t] : (a.env_list ? a.env_list[t] : t), B);
-    if (a.model_id && a.model_id[e] != a.model_index) continue;      // uniform over the warp
-    const uint32_t st = a.ws.st[e];
-    if (!(st & DS_ENV_NONFINITE)) {
+  for (int base = int(blockIdx.x) * epb; base < n; base += int(gridDim.x) * epb) {
+    const int t = base + slot;
+    int e = 0;
+    bool mine = t < n;
+    uint32_t st = 0;
+    if (mine) {
+      e = DS_IX(a.fhi ? a.ws.dlist[lo + t] : (a.env_list ? a.env_list[t] : t), B);
+      mine = !a.model_id || a.model_id[e] == a.model_index;
+    }
+    if (mine) st = a.ws.st[e];
+    const bool cols = mine && !(st & DS_ENV_NONFINITE);
+    if (cols) {
       int row = 0;
       const double* fw = a.ws.fw;
       cs.visit([&](auto* ptr, int cnt) {
         using V = typename std::remove_reference<decltype(*ptr)>::type;
-        for (int i = lane; i < cnt; i += 32) ptr[i] = V(fw[size_t(row + i) * B + e]);
+        for (int i = li; i < cnt; i += GL) ptr[i] = V(fw[size_t(row + i) * B + e]);
         row += cnt;
       });
-      __syncwarp();
+    }
+    __syncthreads();
+    if (cols) {
       if (a.run == DS_RUN_JAC) {
-        for (int col = lane; col < 3 * NV; col += 32) {
+        for (int col = li; col < 3 * NV; col += GL) {
           const int blk = col / NV, d = col % NV;
           T Dc[NV];
           split_jac_column<NB, NV, NS, T>(sm, a, cs, blk, d, Dc);
@@ -2807,16 +2827,16 @@ __global__ void __launch_bounds__(128) finish_cols_kernel(KArgs a) {
           for (int k = 0; k < NV; ++k) out[(k * NV + d) * B + e] = double(Dc[k]);
         }
       } else {
-        for (int p = lane; p < 2 * NV; p += 32) {
+        for (int p = li; p < 2 * NV; p += GL) {
           const int blk = p / NV, d = p % NV;
           double* out = blk == 0 ? a.q_bar : a.v_bar;
           out[d * B + e] = split_vjp_entry<NB, NV, NS, T>(sm, a, cs, blk, d);
         }
-        for (int k = lane; k < NV; k += 32) a.tau_bar[k * B + e] = double(T(a.dt) * cs.w2[k]);
+        for (int k = li; k < NV; k += GL) a.tau_bar[k * B + e] = double(T(a.dt) * cs.w2[k]);
       }
-      __syncwarp();
     }
-    if (lane == 0 && a.status) a.status[e] = st;
+    if (mine && li == 0 && a.status) a.status[e] = st;
+    __syncthreads();
   }
 }
 

@@ -46,7 +46,8 @@ inline int finish_blocks(int n, int nchunk, int threads) {
 
 // The split finish (schedule finish_split) over the envs of fa (its range flo/fhi, or all): the
 // prep kernel (CTAs of one warp), then the column kernel with up to 4 envs per CTA as fit in
-// 200 KB of shared memory (at least one), CTAs for the SMs' resident capacity.
+// 200 KB of shared memory (at least one), ColsShape::WPE warps per env, CTAs for the SMs'
+// resident capacity.
 template <int NB, int NV, int NS, typename T>
 void launch_finish_split(const KArgs& fa, cudaStream_t s) {
   // prep threads per env (Jacobians): enough to fill the SMs' 16 resident warps (128 registers a
@@ -64,6 +65,7 @@ void launch_finish_split(const KArgs& fa, cudaStream_t s) {
   finish_prep_kernel<NB, NV, NS, T><<<pblocks, 32, 0, s>>>(pa);
   constexpr size_t cs_bytes = sizeof(ColState<NB, NV, NS, T>);
   constexpr int epb = cs_bytes * 4 <= 200 * 1024 ? 4 : (cs_bytes * 2 <= 200 * 1024 ? 2 : 1);
+  constexpr int cthreads = 32 * ColsShape<NV>::WPE * epb;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(finish_cols_kernel<NB, NV, NS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -71,12 +73,12 @@ void launch_finish_split(const KArgs& fa, cudaStream_t s) {
     attr = true;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, finish_cols_kernel<NB, NV, NS, T>, 32 * epb, epb * cs_bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, finish_cols_kernel<NB, NV, NS, T>, cthreads, epb * cs_bytes);
   if (per_sm <= 0) per_sm = 1;
   int cblocks = ds_sm_count() * per_sm;
   const int need = (fa.n_env + epb - 1) / epb;
   if (cblocks > need) cblocks = need;
-  finish_cols_kernel<NB, NV, NS, T><<<cblocks, 32 * epb, epb * cs_bytes, s>>>(fa);
+  finish_cols_kernel<NB, NV, NS, T><<<cblocks, cthreads, epb * cs_bytes, s>>>(fa);
   ds_trace_mark(DS_STAGE_FINISH, 0, s);
 }
 
