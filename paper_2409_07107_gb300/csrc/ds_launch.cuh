@@ -51,12 +51,17 @@ inline int finish_blocks(int n, int nchunk, int threads) {
 template <int NB, int NV, int NS, typename T>
 void launch_finish_split(const KArgs& fa, cudaStream_t s) {
   // prep threads per env (Jacobians): enough to fill the SMs' 16 resident warps (128 registers a
-  // thread), at most 8
+  // thread), a power of two with at least 8 rows of P each (every thread holds its own copy of the
+  // env's state, so more of them cost local-memory traffic: measured, 8 threads per env slowed the
+  // quadruped's prep at 8192 envs and sped the humanoid's at 4096)
   KArgs pa = fa;
   pa.nchunk = 1;
   if (fa.run == DS_RUN_JAC) {
     const int want = fa.n_env > 0 ? (ds_sm_count() * 16 * 32) / fa.n_env : 1;
-    pa.nchunk = want >= 8 ? 8 : (want >= 4 ? 4 : (want >= 2 ? 2 : 1));
+    int cap = 1;
+    while (cap * 2 * 8 <= NV && cap < 8) cap *= 2;
+    int c = want >= 8 ? 8 : (want >= 4 ? 4 : (want >= 2 ? 2 : 1));
+    pa.nchunk = c < cap ? c : cap;
   }
   const long long items = (long long)fa.n_env * pa.nchunk;
   const int pblocks = int((items + 31) / 32);
