@@ -169,9 +169,10 @@ typedef struct {
 } ds_step_out;
 
 /* Bytes of device workspace that sim_step / sim_step_jac / sim_step_vjp can use for this batch
- * (about 6.3 KB per env for the 7-dof arm with 4 contact slots, 2.4 KB of it the contact
- * problem and the solver state, the rest the forward quantities the setup keeps for the finish;
- * about 30 KB for the 36-dof humanoid with 8).  With a workspace the step runs as a pipeline of
+ * (about 8.1 KB per env for the 7-dof arm with 4 contact slots, 2.4 KB of it the contact
+ * problem and the solver state, the rest the forward quantities the setup keeps for the finish,
+ * in rows sized also for the split finish's column state; about 45 KB for the 36-dof humanoid
+ * with 8).  With a workspace the step runs as a pipeline of
  * kernels (setup, NCP solve in compacted ADMM rounds, finish) that keeps warps busy when the
  * per-env iteration counts differ; without one (workspace = NULL) a single fused kernel does
  * everything.  Both compute the same step; they differ only by rounding (the NCP solve is
