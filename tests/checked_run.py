@@ -36,6 +36,26 @@ def run_all():
     wl = scenes.arm_cube(48)
     sim = ds.Simulator(wl, precision="fp64", ncp_solver=ds.DS_PGS)
     take("arm_cube_pgs", sim.step_jac())
+    sim = ds.Simulator(wl, precision="fp64", admm_rho_adapt=1)
+    take("arm_cube_adaptive", sim.step_jac())
+    # the split finish (prep + column kernels) and the persistent launch, on batch sizes of their
+    # own (a schedule is kept per batch signature) and set back to the default afterwards
+    for tag, wl, prec in (("quadruped_split", scenes.quadruped_feet(100), "fp64"),
+                          ("humanoid_split", scenes.humanoid_feet(24), "mixed")):
+        sim = ds.Simulator(wl, precision=prec)
+        sim.set_schedule(ds.schedule_index(split=1))
+        try:
+            take(tag, sim.step_jac())
+        finally:
+            sim.set_schedule(-1)
+    wl = scenes.uneven(33)
+    sim = ds.Simulator(wl, precision="mixed")
+    vb = torch.as_tensor(np.random.default_rng(6).normal(size=wl.batch.v.shape), **f64)
+    sim.set_schedule(ds.schedule_index(launch=1), "vjp")
+    try:
+        take("uneven_persistent", sim.step_vjp(vb))
+    finally:
+        sim.set_schedule(-1, "vjp")
     torch.cuda.synchronize()
     return out
 

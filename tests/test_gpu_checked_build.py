@@ -1,7 +1,8 @@
 """The checked build of the library (compiled with DS_CHECK: every tree index, work-list env index
 and shared-memory group index is checked, and one out of range is counted instead of faulting)
-on small batches of every workload, pipeline and fused kernels, FP64 and mixed, VJP and the PGS
-iteration: no index out of range, and the same results as the normal build.  The counting itself
+on small batches of every workload, pipeline and fused kernels, FP64 and mixed, VJP, the PGS
+iteration, the adaptive penalty, the split finish and the persistent launch: no index out of
+range, and the same results as the normal build.  The counting itself
 is tested with one check of an index outside and one inside its range."""
 import os
 import subprocess
@@ -13,7 +14,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-MIXED_CASES = ("arm_cube_mixed", "humanoid")       # the cases of checked_run in the mixed form
+MIXED_CASES = ("arm_cube_mixed", "humanoid", "humanoid_split", "uneven_persistent")  # checked_run's mixed-form cases
 
 
 def test_checked_build_matches_and_finds_no_bad_index(tmp_path):
