@@ -147,3 +147,24 @@ def test_persistent_cuda_graph(torch_cuda):
     got = dict(sim.out, q_bar=sim.vjp_out[0], v_bar=sim.vjp_out[1], tau_bar=sim.vjp_out[2])
     for key in ("v_next", "q_bar", "v_bar", "tau_bar", "status", "modes"):
         assert torch.equal(got[key], eager[key]), key
+
+
+def test_persistent_schedule_falls_back_to_the_pipeline(torch_cuda):
+    """The persistent kernel is compiled for the mixed form of the three mixed-batch shapes; under a
+    persistent schedule an FP64 batch, or a model whose fitted shape is not among them (the arm with
+    4 slots), runs the workspace pipeline: the results are the default schedule's, bit for bit."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    arm = scenes.arm_cube(65536)
+    for wl, prec in ((scenes.uneven(90), "fp64"),
+                     (scenes.Workload(arm.name, arm.models, arm.batch.take(np.arange(200)), arm.options), "mixed")):
+        sim = ds.Simulator(wl, precision=prec)
+        ref = {k: v.clone() for k, v in sim.step().items()}
+        _persistent(sim, "step")
+        try:
+            got = {k: v.clone() for k, v in sim.step().items()}
+            torch.cuda.synchronize()
+        finally:
+            sim.set_schedule(-1, "step")
+        for key in ("v_next", "q_next", "lambda", "modes", "status", "iters"):
+            assert torch.equal(got[key], ref[key]), (prec, key)
