@@ -677,3 +677,20 @@ def test_split_finish_vjp(torch_cuda, precision, tol_same):
     for key in ("q_bar", "v_bar", "tau_bar"):
         err = _rel_per_env(got[key], ref[key])[ok]
         assert err.max().item() <= tol_same, (key, err.max().item())
+
+
+@pytest.mark.parametrize("field,value", [("queue_poll_limit", -1), ("admm_rho_adapt", 2), ("ncp_solver", 7),
+                                         ("contact_margin", -1e-3), ("baumgarte_kp", float("nan"))])
+def test_option_validation(torch_cuda, field, value):
+    """Out-of-range options are refused by the call (DS_EINVAL) before any kernel runs; the next call
+    with valid options works."""
+    import paper_2409_07107_gb300 as ds
+    torch = torch_cuda
+    wl = scenes.arm_sphere(16)
+    bad = ds.Simulator(wl, precision="fp64", **{field: value})
+    with pytest.raises(ds.DiffsimError, match="invalid"):
+        bad.step()
+    good = ds.Simulator(wl, precision="fp64")
+    good.step()
+    torch.cuda.synchronize()
+    assert not (good.out["status"] & 2).any()
