@@ -2582,6 +2582,8 @@ struct ColState {
     fn(phi, NS); fn(qadd, NV); fn(body, NS); fn(act, NS); fn(&na, 1); fn(&md, 1);
   }
   static constexpr int kRows = ds_colstate_rows(NB, NV, NS);
+  // first row of P in the stored form (the members visit() lists before it)
+  static constexpr int kOffP = 6 * NV + 2 * NV + 10 * NB + 7 * 6 * NB + NV * (NV + 1) / 2 + 9 * NS + 9 + 3 * NS * NV;
 };
 
 // Prep for env e, in two parts around a warp barrier: prep_load reads the env's forward state
@@ -2620,7 +2622,7 @@ DS_HD void prep_store(const DevModel& m, const KArgs& a, const int e, Env<NB, NV
   for (int k = 0; k < NV; ++k)
     if (!isfinite(double(s.vn[k]))) st |= DS_ENV_NONFINITE;
   double* fw = w.fw;
-  constexpr int kOffP = 6 * NV + 2 * NV + 10 * NB + 7 * 6 * NB + NV * (NV + 1) / 2 + 9 * NS + 9 + 3 * NS * NV;
+  constexpr int kOffP = CS::kOffP;
   CS cs;
   cs.na = s.na;
   cs.md = 0;
