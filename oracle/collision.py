@@ -1,0 +1,216 @@
+"""Collision detection between convex shapes and its derivative by randomized smoothing (oracle).
+Test infrastructure only; not yet wired into the step (which keeps primitive-versus-plane
+contacts, contact.py).
+
+Sec. 2.1: given two convex shapes and their poses, collision detection returns a contact point and
+a contact normal, the direction separating the shapes with minimal displacement; the contact frame
+has its origin at the contact point and its Z axis along the normal.  App. C writes the contact
+placement as 0M_c = CD(0M_1, 0M_2) and needs dCD/dM_i, which the paper takes from a randomized
+smoothing estimator (zero-order: the expectation of CD's response to random tangent perturbations
+of the poses).
+
+The plain definition is computed here, not GJK/EPA's iteration.  Every shape is a core (a point,
+a segment or a convex polytope given by its vertices) swept by a radius r >= 0 (sphere = point + r,
+capsule = segment + r, box = its 8 corners + 0).  The signed distance of A and B is the distance of
+their cores minus rA + rB when the cores are apart, and minus (penetration depth of the cores +
+rA + rB) when they overlap.  Between cores it is computed from the Minkowski difference
+D = core_A - core_B:
+
+* apart: the closest point of D to the origin, -n d with d = dist(0, D), gives the witness points
+  (the same convex weights on A's and B's points) and the normal n (unit, from A towards B);
+* overlapping (a polytope core on either side): the facet of conv(D) nearest the origin gives the
+  depth and the normal (n is that facet's outward normal: translating A by -depth n separates the
+  cores), and the projection of the origin onto that facet the witness points.
+
+Points and segments use their closed forms; a polytope core uses the convex hull of D (scipy's
+Qhull) and the exact closest point of each hull triangle to the origin.  The contact point is the
+midpoint of the two witness points moved to the shapes' surfaces (pA + rA n, pB - rB n)."""
+import numpy as np
+from scipy.spatial import ConvexHull
+
+
+class Shape:
+    """A convex shape: core points in the body frame (1 = point, 2 = segment, >= 4 = polytope
+    vertices) and a radius."""
+
+    def __init__(self, core, radius=0.0):
+        self.core = np.atleast_2d(np.asarray(core, dtype=float))
+        self.radius = float(radius)
+
+
+def sphere(r):
+    return Shape([[0.0, 0.0, 0.0]], r)
+
+
+def capsule(half_length, r):
+    """Segment along the body z axis from -half_length to +half_length, swept by r."""
+    return Shape([[0.0, 0.0, -half_length], [0.0, 0.0, half_length]], r)
+
+
+def box(hx, hy, hz):
+    return Shape([[sx * hx, sy * hy, sz * hz] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)], 0.0)
+
+
+def world_core(shape, R, p):
+    return shape.core @ np.asarray(R, float).T + np.asarray(p, float)
+
+
+def closest_on_segment(a, b, x):
+    """Closest point of segment [a, b] to x and its parameter t in [0, 1]."""
+    ab = b - a
+    den = ab @ ab
+    t = 0.0 if den == 0.0 else min(1.0, max(0.0, (x - a) @ ab / den))
+    return a + t * ab, t
+
+
+def closest_segments(p1, q1, p2, q2):
+    """Closest points of segments [p1, q1] and [p2, q2]: the minimum of |p1 + s d1 - p2 - t d2|^2
+    over [0, 1]^2 is the unconstrained minimum when it lies inside the square, else on one of the
+    square's four edges, where it is a point-to-segment problem."""
+    d1, d2 = q1 - p1, q2 - p2
+    a, b, e = d1 @ d1, d1 @ d2, d2 @ d2
+    r = p1 - p2
+    den = a * e - b * b
+    if den > 1e-14 * max(a * e, 1e-300):
+        s = (b * (d2 @ r) - e * (d1 @ r)) / den
+        t = (a * (d2 @ r) - b * (d1 @ r)) / den
+        if 0.0 <= s <= 1.0 and 0.0 <= t <= 1.0:
+            return p1 + s * d1, p2 + t * d2
+    best = None
+    for x, (ya, yb), first in ((p1, (p2, q2), True), (q1, (p2, q2), True), (p2, (p1, q1), False), (q2, (p1, q1), False)):
+        y, _ = closest_on_segment(ya, yb, x)
+        dist = np.sum((x - y) ** 2)
+        if best is None or dist < best[0]:
+            best = (dist, (x, y) if first else (y, x))
+    return best[1][0].copy(), best[1][1].copy()
+
+
+def closest_on_triangle(a, b, c, x=np.zeros(3)):
+    """Barycentric weights (wa, wb, wc) of the closest point of triangle abc to x: the projection of
+    x on the triangle's plane when it falls inside the triangle, else the nearest of the closest
+    points on the three edges."""
+    ab, ac = b - a, c - a
+    nrm = np.cross(ab, ac)
+    nn = nrm @ nrm
+    if nn > 1e-300:
+        # barycentric coordinates of the projection of x
+        v = np.cross(x - a, ac) @ nrm / nn
+        w = np.cross(ab, x - a) @ nrm / nn
+        if v >= 0.0 and w >= 0.0 and v + w <= 1.0:
+            return np.array([1.0 - v - w, v, w])
+    best = None
+    for (i, j) in ((0, 1), (1, 2), (0, 2)):
+        pts = (a, b, c)
+        y, t = closest_on_segment(pts[i], pts[j], x)
+        dist = np.sum((x - y) ** 2)
+        if best is None or dist < best[0]:
+            wts = np.zeros(3)
+            wts[i], wts[j] = 1.0 - t, t
+            best = (dist, wts)
+    return best[1]
+
+
+def _hull_core_distance(ca, cb):
+    """Signed distance of two cores of which one is a polytope, their witness points and the normal
+    from A to B, from the convex hull of their Minkowski difference."""
+    ia, ib = np.meshgrid(np.arange(len(ca)), np.arange(len(cb)), indexing="ij")
+    ia, ib = ia.ravel(), ib.ravel()
+    D = ca[ia] - cb[ib]
+    hull = ConvexHull(D)
+    off = hull.equations[:, 3]                       # n.x + off <= 0 inside, |n| = 1
+    if np.all(off <= 0.0):
+        # overlapping: the nearest facet plane (origin inside conv(D))
+        k = int(np.argmax(off))
+        m = hull.equations[k, :3]
+        depth = -off[k]
+        y = depth * m
+        best = None
+        for f, simplex in enumerate(hull.simplices):
+            if not np.allclose(hull.equations[f], hull.equations[k], atol=1e-12):
+                continue
+            w = closest_on_triangle(*D[simplex], x=y)
+            err = np.sum((w @ D[simplex] - y) ** 2)
+            if best is None or err < best[0]:
+                best = (err, simplex, w)
+        _, simplex, w = best
+        return -depth, w @ ca[ia[simplex]], w @ cb[ib[simplex]], m
+    best = None
+    for simplex in hull.simplices:
+        w = closest_on_triangle(*D[simplex])
+        y = w @ D[simplex]
+        d2 = y @ y
+        if best is None or d2 < best[0]:
+            best = (d2, simplex, w, y)
+    d2, simplex, w, y = best
+    d = np.sqrt(d2)
+    return d, w @ ca[ia[simplex]], w @ cb[ib[simplex]], -y / d
+
+
+def core_distance(ca, cb):
+    """Signed distance of cores ca, cb (world points: 1 = point, 2 = segment, more = polytope), the
+    witness points on each and the unit normal from A to B.  Touching or crossing point and segment
+    cores have no defined normal; the world z axis is returned for them."""
+    if len(ca) <= 2 and len(cb) <= 2:
+        sa = (ca[0], ca[-1])
+        sb = (cb[0], cb[-1])
+        pa, pb = closest_segments(sa[0], sa[1], sb[0], sb[1])
+        d = np.sqrt(np.sum((pb - pa) ** 2))
+        n = (pb - pa) / d if d > 1e-300 else np.array([0.0, 0.0, 1.0])
+        return d, pa, pb, n
+    return _hull_core_distance(ca, cb)
+
+
+def tangent_basis(n):
+    """Tangent axes of the contact frame for the unit normal n (the rule of contact.py: t1 =
+    normalize(e_x - (n.e_x) n), e_y when |n_x| > 0.9; t2 = n x t1)."""
+    e = np.array([1.0, 0.0, 0.0]) if abs(n[0]) <= 0.9 else np.array([0.0, 1.0, 0.0])
+    t1 = e - (n @ e) * n
+    t1 = t1 / np.sqrt(t1 @ t1)
+    return t1, np.cross(n, t1)
+
+
+def collide(shape_a, Ra, pa, shape_b, Rb, pb):
+    """Collision detection of Sec. 2.1 for shapes A and B at world poses (R, p): returns a dict with
+    the signed distance phi (< 0: penetration), the witness points on the shapes' surfaces, the
+    contact point c (their midpoint), the unit normal n from A to B, and the contact frame's
+    rotation Rc (columns t1, t2, n: Z along the normal)."""
+    ca, cb = world_core(shape_a, Ra, pa), world_core(shape_b, Rb, pb)
+    d, wa, wb, n = core_distance(ca, cb)
+    phi = d - shape_a.radius - shape_b.radius
+    sa, sb = wa + shape_a.radius * n, wb - shape_b.radius * n
+    t1, t2 = tangent_basis(n)
+    return {"phi": phi, "pa": sa, "pb": sb, "c": 0.5 * (sa + sb), "n": n,
+            "Rc": np.stack([t1, t2, n], axis=1)}
+
+
+def twist_pose(R, p, xi):
+    """The pose (R, p) moved by the world-frame twist xi = (u, w) (linear, angular at the world
+    origin): x -> exp([w]) x + V(w) u, i.e. R' = exp([w]) R, p' = exp([w]) p + V(w) u."""
+    u, w = np.asarray(xi[:3], float), np.asarray(xi[3:], float)
+    th = np.sqrt(w @ w)
+    W = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if th < 1e-12:
+        E, V = np.eye(3) + W, np.eye(3) + 0.5 * W
+    else:
+        E = np.eye(3) + np.sin(th) / th * W + (1 - np.cos(th)) / th ** 2 * W @ W
+        V = np.eye(3) + (1 - np.cos(th)) / th ** 2 * W + (th - np.sin(th)) / th ** 3 * W @ W
+    return E @ R, E @ p + V @ u
+
+
+def cd_features(res):
+    """The smoothed quantities: phi, the contact point and the normal (7 numbers)."""
+    return np.concatenate([[res["phi"]], res["c"], res["n"]])
+
+
+def randomized_smoothing_jacobian(shape_a, Ra, pa, shape_b, Rb, pb, sigma, samples, rng):
+    """Zero-order randomized-smoothing estimate of the derivative of (phi, c, n) with respect to the
+    world-frame twists of A's and B's poses (7 x 12; columns: A's (u, w), then B's): with eps ~
+    N(0, sigma^2 I_12) the expectation of (f(eps) - f(-eps)) eps^T / (2 sigma^2), the gradient of
+    the Gaussian-smoothed f (antithetic pairs; unbiased for the smoothed function)."""
+    acc = np.zeros((7, 12))
+    for _ in range(samples):
+        eps = rng.normal(0.0, sigma, size=12)
+        fp = cd_features(collide(shape_a, *twist_pose(Ra, pa, eps[:6]), shape_b, *twist_pose(Rb, pb, eps[6:])))
+        fm = cd_features(collide(shape_a, *twist_pose(Ra, pa, -eps[:6]), shape_b, *twist_pose(Rb, pb, -eps[6:])))
+        acc += np.outer(fp - fm, eps)
+    return acc / (2.0 * sigma ** 2 * samples)
