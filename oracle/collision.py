@@ -214,3 +214,116 @@ def randomized_smoothing_jacobian(shape_a, Ra, pa, shape_b, Rb, pb, sigma, sampl
         fm = cd_features(collide(shape_a, *twist_pose(Ra, pa, -eps[:6]), shape_b, *twist_pose(Rb, pb, -eps[6:])))
         acc += np.outer(fp - fm, eps)
     return acc / (2.0 * sigma ** 2 * samples)
+
+
+# ------------------------------------------------------------------- contacts between two bodies
+# App. C: a contact between body 1 and body 2 has J_c = E (cX_1 J_1 - cX_2 J_2) (E: the linear
+# part, J_i body Jacobians in body coordinates, cX_i the motion transform from body i to the
+# contact frame).  Here body A is 1's counterpart with the opposite sign: J_c v is the velocity of
+# B's material point at the contact point relative to A's, in the contact frame whose Z axis is the
+# normal from A to B, so sigma_N > 0 separates (the convention of the plane contacts, where A is the
+# plane).  A body index of -1 is the fixed world.
+
+def _skew(a):
+    return np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+
+
+def motion_transform(E, r):
+    """6x6 transform of motion vectors (linear, angular) from a frame to the frame at (E, r) in it."""
+    Et = E.T
+    return np.block([[Et, -Et @ _skew(r)], [np.zeros((3, 3)), Et]])
+
+
+def motion_cross(a, b):
+    """Spatial motion cross product a x b, vectors (linear, angular)."""
+    return np.concatenate([np.cross(a[3:], b[:3]) + np.cross(a[:3], b[3:]), np.cross(a[3:], b[3:])])
+
+
+def body_pose(model, q, body):
+    from .rigid import fk
+    if body < 0:
+        return np.eye(3), np.zeros(3)
+    R, p = fk(model, q)[1][body]
+    return np.asarray(R, float), np.asarray(p, float)
+
+
+def pair_placement(model, q, pair, poses=None):
+    """Contact placement (Rc, c) and the collision result of pair = (shape_a, body_a, (Ea, ra),
+    shape_b, body_b, (Eb, rb)), each shape at placement (E, r) in its body; poses, when given,
+    replaces the bodies' world poses [(Ra, pa), (Rb, pb)]."""
+    sa, ba, (Ea, ra), sb, bb, (Eb, rb) = pair
+    (Ra, pa), (Rb, pb) = poses if poses is not None else (body_pose(model, q, ba), body_pose(model, q, bb))
+    res = collide(sa, Ra @ Ea, pa + Ra @ ra, sb, Rb @ Eb, pb + Rb @ rb)
+    return res["Rc"], res["c"], res
+
+
+def pair_jcv(model, q, v, pair):
+    """J_c v of the pair at (q, v): the linear part of cX_b V_b - cX_a V_a (V_i = J_i v, body
+    coordinates; 0 for the world)."""
+    from .rigid import body_velocities
+    Rc, c, _ = pair_placement(model, q, pair)
+    vel = body_velocities(model, q, v)
+    out = np.zeros(3)
+    for body, sign in ((pair[1], -1.0), (pair[4], 1.0)):
+        if body < 0:
+            continue
+        R, p = body_pose(model, q, body)
+        X = motion_transform(R.T @ Rc, R.T @ (c - p))
+        out += sign * (X @ vel[body])[:3]
+    return out
+
+
+def local_twist(R0, p0, R1, p1):
+    """First-order local twist taking (R0, p0) to (R1, p1): (R0^T (p1 - p0), vee(R0^T R1 - I))."""
+    W = R0.T @ R1 - np.eye(3)
+    return np.concatenate([R0.T @ (p1 - p0), 0.5 * np.array([W[2, 1] - W[1, 2], W[0, 2] - W[2, 0], W[1, 0] - W[0, 1]])])
+
+
+def dcd_dbody(model, q, pair, which, h=1e-6):
+    """dCD/dM_i (6 x 6) by central differences: the local twist of the contact placement per local
+    twist of body i's pose (which = 0: A, 1: B), M_i -> M_i exp(delta)."""
+    poses = [body_pose(model, q, pair[1]), body_pose(model, q, pair[4])]
+    Rc, c, _ = pair_placement(model, q, pair, poses)
+    out = np.zeros((6, 6))
+    for j in range(6):
+        cols = []
+        for s in (h, -h):
+            R, p = poses[which]
+            d = np.zeros(6)
+            d[j] = s
+            # local twist of the body frame: R' = R exp([w]), p' = p + R u (first order is enough
+            # for central differences of a smooth map)
+            R2, p2 = twist_pose(np.eye(3), np.zeros(3), d)
+            moved = list(poses)
+            moved[which] = (R @ R2, p + R @ p2)
+            Rc2, c2, _ = pair_placement(model, q, pair, moved)
+            cols.append(local_twist(Rc, c, Rc2, c2))
+        out[:, j] = (cols[0] - cols[1]) / (2 * h)
+    return out
+
+
+def appc_dJcv_dq(model, q, v, pair, dcd):
+    """App. C's contact-placement terms of d(J_c v)/dq at fixed v and fixed body velocities V_i:
+    sum over the two bodies of the sign times E [ (cX_i V_i) x dCD/dM_i J_i - cX_i (V_i x J_i) ],
+    the contact frame's twist collecting both bodies' contributions (nv columns).  dcd = (dCD/dM_a,
+    dCD/dM_b)."""
+    from .rigid import body_jacobians, body_velocities
+    Rc, c, _ = pair_placement(model, q, pair)
+    Js = body_jacobians(model, q)
+    vel = body_velocities(model, q, v)
+    nv = Js[0].shape[1]
+    dc = np.zeros((6, nv))                       # local twist of the contact frame per dof
+    for which, body in ((0, pair[1]), (1, pair[4])):
+        if body >= 0:
+            dc += dcd[which] @ Js[body]
+    out = np.zeros((3, nv))
+    for which, body, sign in ((0, pair[1], -1.0), (1, pair[4], 1.0)):
+        if body < 0:
+            continue
+        R, p = body_pose(model, q, body)
+        X = motion_transform(R.T @ Rc, R.T @ (c - p))
+        W = X @ vel[body]
+        for k in range(nv):
+            term = motion_cross(W, dc[:, k]) - X @ motion_cross(vel[body], Js[body][:, k])
+            out[:, k] += sign * term[:3]
+    return out

@@ -9,7 +9,11 @@ randomized-smoothing derivative (App. C), no GPU.
 * invariances: a rigid motion of both shapes moves c and n with it and keeps phi; swapping the
   shapes keeps phi and c and flips n;
 * the smoothing estimator against the analytic derivative of phi and n for two spheres (a smooth
-  pair), with a small sigma.
+  pair), with a small sigma;
+* App. C's contact-placement terms of d(J_c v)/dq for contacts between two bodies of an arm and
+  between an arm link and a fixed box: with the bodies' velocity change they sum to central
+  differences of q -> J_c(q) v, the contact frame recomputed by collision detection at every q
+  (a flipped sign or swapped cross product in the terms fails it).
 """
 import numpy as np
 import pytest
@@ -157,3 +161,52 @@ def test_smoothing_jacobian_of_two_spheres():
     scale = max(np.abs(dphi).max(), np.abs(dn).max())
     assert np.abs(J[0] - dphi).max() <= 0.05 * scale
     assert np.abs(J[4:7] - dn).max() <= 0.05 * scale
+
+
+def _arm_pair(rng, kind):
+    from paper_2409_07107_gb300 import scenes
+    model, tip = scenes.arm7(rng)
+    q = rng.uniform(-np.pi, np.pi, size=7)
+    v = rng.normal(size=7)
+    if kind == "self":
+        # a sphere at the tip of link 7 and a box on link 3, both on the arm
+        pair = (C.sphere(0.05), 6, (I3, np.asarray(tip, float)), C.box(0.05, 0.08, 0.06), 2, (_rot(rng), np.zeros(3)))
+    else:
+        # a capsule on link 5 against a fixed box in the world
+        pair = (C.capsule(0.05, 0.03), 4, (_rot(rng), np.zeros(3)), C.box(0.3, 0.3, 0.1), -1, (I3, np.array([0.0, 0.0, -0.5])))
+    return model, q, v, pair
+
+
+@pytest.mark.parametrize("kind", ["self", "world"])
+def test_appc_contact_placement_terms(kind):
+    """App. C: with the contact frame moving with the collision detection, d(J_c v)/dq at fixed v is
+    the bodies' velocity change seen in the contact frame plus the placement terms
+    E[(cX_i V_i) x dCD/dM_i J_i - cX_i (V_i x J_i)] (signed per body); their sum equals central
+    differences of q -> J_c(q) v, the contact frame recomputed at every q."""
+    from oracle import rigid
+    rng = np.random.default_rng(8 if kind == "self" else 9)
+    model, q, v, pair = _arm_pair(rng, kind)
+    h = 1e-6
+    nv = 7
+    fd = np.zeros((3, nv))
+    vel_fd = []
+    for k in range(nv):
+        e = np.zeros(nv)
+        e[k] = h
+        qp, qm = rigid.integrate(model, q, e), rigid.integrate(model, q, -e)
+        fd[:, k] = (C.pair_jcv(model, qp, v, pair) - C.pair_jcv(model, qm, v, pair)) / (2 * h)
+        vp, vm = rigid.body_velocities(model, qp, v), rigid.body_velocities(model, qm, v)
+        vel_fd.append([(a - b) / (2 * h) for a, b in zip(vp, vm)])
+    dcd = (C.dcd_dbody(model, q, pair, 0), C.dcd_dbody(model, q, pair, 1))
+    terms = C.appc_dJcv_dq(model, q, v, pair, dcd)
+    Rc, c, _ = C.pair_placement(model, q, pair)
+    for body, sign in ((pair[1], -1.0), (pair[4], 1.0)):
+        if body < 0:
+            continue
+        R, p = C.body_pose(model, q, body)
+        X = C.motion_transform(R.T @ Rc, R.T @ (c - p))
+        for k in range(nv):
+            terms[:, k] += sign * (X @ vel_fd[k][body])[:3]
+    assert np.abs(terms - fd).max() <= 1e-5 * max(1.0, np.abs(fd).max())
+    # and the placement terms matter: without them the sum is off
+    assert np.abs(C.appc_dJcv_dq(model, q, v, pair, dcd)).max() > 1e-3
