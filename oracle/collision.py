@@ -327,3 +327,45 @@ def appc_dJcv_dq(model, q, v, pair, dcd):
             term = motion_cross(W, dc[:, k]) - X @ motion_cross(vel[body], Js[body][:, k])
             out[:, k] += sign * term[:3]
     return out
+
+
+def pair_transforms(model, q, pair):
+    """The motion transforms cX_a, cX_b from the bodies to the contact frame at q (None for the
+    world)."""
+    Rc, c, _ = pair_placement(model, q, pair)
+    out = []
+    for body in (pair[1], pair[4]):
+        if body < 0:
+            out.append(None)
+            continue
+        R, p = body_pose(model, q, body)
+        out.append(motion_transform(R.T @ Rc, R.T @ (c - p)))
+    return out
+
+
+def pair_jc(model, q, pair, transforms=None):
+    """J_c (3 x nv) of the pair: column k is pair_jcv at v = e_k.  With ``transforms`` (cX_a, cX_b,
+    as pair_transforms returns them) held, only the bodies' Jacobians J_i(q) vary with q."""
+    from .rigid import body_jacobians
+    Xs = transforms if transforms is not None else pair_transforms(model, q, pair)
+    Js = body_jacobians(model, q)
+    out = np.zeros((3, Js[0].shape[1]))
+    for X, body, sign in ((Xs[0], pair[1], -1.0), (Xs[1], pair[4], 1.0)):
+        if body < 0:
+            continue
+        out += sign * (X @ Js[body])[:3]
+    return out
+
+
+def appc_dJctlam_dq(model, q, lam, pair, dcd):
+    """App. C's contact-placement terms of d(J_c^T lambda)/dq (nv x nv), from the duality
+    <d(J_c^T lambda) dq, v> = <lambda, d(J_c v) dq> for every v: entry (j, k) is
+    lambda . (placement terms of d(J_c e_j)/dq_k)."""
+    from .rigid import index_maps
+    nv = index_maps(model)[3]
+    out = np.zeros((nv, nv))
+    for j in range(nv):
+        e = np.zeros(nv)
+        e[j] = 1.0
+        out[j] = np.asarray(lam, float) @ appc_dJcv_dq(model, q, e, pair, dcd)
+    return out

@@ -13,7 +13,9 @@ randomized-smoothing derivative (App. C), no GPU.
 * App. C's contact-placement terms of d(J_c v)/dq for contacts between two bodies of an arm and
   between an arm link and a fixed box: with the bodies' velocity change they sum to central
   differences of q -> J_c(q) v, the contact frame recomputed by collision detection at every q
-  (a flipped sign or swapped cross product in the terms fails it).
+  (a flipped sign or swapped cross product in the terms fails it); and the second term,
+  d(J_c^T lambda)/dq, by duality, against central differences of J_c(q)^T lambda with and without
+  the body-to-contact transforms held.
 """
 import numpy as np
 import pytest
@@ -210,3 +212,29 @@ def test_appc_contact_placement_terms(kind):
     assert np.abs(terms - fd).max() <= 1e-5 * max(1.0, np.abs(fd).max())
     # and the placement terms matter: without them the sum is off
     assert np.abs(C.appc_dJcv_dq(model, q, v, pair, dcd)).max() > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["self", "world"])
+def test_appc_transposed_terms(kind):
+    """The second App. C term, d(J_c^T lambda)/dq from the contact placement, by duality with the
+    first: it equals central differences of q -> J_c(q)^T lambda with the contact frame recomputed
+    at every q minus those with the transforms cX_i held (only the bodies' Jacobians J_i(q)
+    varying, the part App. C leaves to the other terms); J_c v agrees with J_c times v."""
+    from oracle import rigid
+    rng = np.random.default_rng(10 if kind == "self" else 11)
+    model, q, v, pair = _arm_pair(rng, kind)
+    lam = rng.normal(size=3)
+    assert np.allclose(C.pair_jc(model, q, pair) @ v, C.pair_jcv(model, q, v, pair), atol=1e-12)
+    transforms = C.pair_transforms(model, q, pair)
+    h, nv = 1e-6, 7
+    moving = np.zeros((nv, nv))
+    held = np.zeros((nv, nv))
+    for k in range(nv):
+        e = np.zeros(nv)
+        e[k] = h
+        qp, qm = rigid.integrate(model, q, e), rigid.integrate(model, q, -e)
+        moving[:, k] = (C.pair_jc(model, qp, pair).T @ lam - C.pair_jc(model, qm, pair).T @ lam) / (2 * h)
+        held[:, k] = (C.pair_jc(model, qp, pair, transforms).T @ lam - C.pair_jc(model, qm, pair, transforms).T @ lam) / (2 * h)
+    dcd = (C.dcd_dbody(model, q, pair, 0), C.dcd_dbody(model, q, pair, 1))
+    terms = C.appc_dJctlam_dq(model, q, lam, pair, dcd)
+    assert np.abs(terms - (moving - held)).max() <= 1e-5 * max(1.0, np.abs(moving).max())
