@@ -6,7 +6,9 @@ no code with the CUDA path (``paper_2409_07107_gb300/csrc``) and imports nothing
 
 Everything is plain NumPy, written for clarity, not speed: textbook recursive rigid-body algorithms
 in body coordinates (``rigid``), the contact geometry (``contact``), the Coulomb-cone NCP and its
-ADMM solve (``ncp``), and the implicit derivatives by two independent routes (``implicit``).  Every
+ADMM solve (``ncp``), and the implicit derivatives by two independent routes (``implicit``);
+collision detection between convex shapes with App. C's contact-placement terms (``collision``) and
+a step with contacts between two bodies built on it (``pair_step``).  Every
 function is written so that it also accepts complex arrays: partial derivatives are taken by the
 complex-step method (Squire & Trapp 1998), which gives them to machine precision without any
 hand-derived derivative formula.

@@ -349,7 +349,7 @@ def pair_jc(model, q, pair, transforms=None):
     from .rigid import body_jacobians
     Xs = transforms if transforms is not None else pair_transforms(model, q, pair)
     Js = body_jacobians(model, q)
-    out = np.zeros((3, Js[0].shape[1]))
+    out = np.zeros((3, Js[0].shape[1]), dtype=np.result_type(Js[0], 1.0))
     for X, body, sign in ((Xs[0], pair[1], -1.0), (Xs[1], pair[4], 1.0)):
         if body < 0:
             continue
