@@ -365,6 +365,36 @@ ds_status ds_check_self_test(int32_t index, int32_t n, uint64_t* count);
 ds_status ds_profile(int32_t enable);
 ds_status ds_profile_read(double* ms, int32_t* launches);
 
+/* ---------------------------------------------------------------------------------------------
+ * Collision detection between convex shapes (Sec. 2.1; App. C writes it as the contact placement
+ * 0M_c = CD(0M_1, 0M_2)).  Not yet used by the step, whose contacts are primitive-versus-plane.
+ *
+ * A shape is a type and three sizes: DS_CONVEX_SPHERE (radius, -, -), DS_CONVEX_CAPSULE (half
+ * length, radius, -; the segment runs along the body z axis from -half length to +half length),
+ * DS_CONVEX_BOX (half extents hx, hy, hz).  A pose is 12 numbers: the rotation R (row-major, body
+ * to world) and the position p.  For each of n_pairs pairs (A, B) ds_collide writes DS_COLLIDE_OUT
+ * numbers to out[DS_COLLIDE_OUT * k ...]: the signed distance phi (< 0: penetration), the contact
+ * point c[3] (the midpoint of the witness points), the unit normal n[3] from A to B, the tangent
+ * axes t1[3], t2[3] of the contact frame (Z along n; t1 = normalize(e_x - (n.e_x) n), e_y in place
+ * of e_x when |n_x| > 0.9; t2 = n x t1) and the witness points on A's and B's surfaces sa[3],
+ * sb[3].  Separated shapes take the closest points of their cores (point, segment or box corners)
+ * by GJK; overlapping ones the penetration depth of the cores along the nearest facet of their
+ * Minkowski difference.  Touching or crossing point and segment cores (sphere and capsule cores)
+ * have no normal: n is the world z axis there.  Where the witness points are not unique (parallel
+ * faces or edges in contact) one of them is returned.
+ *
+ * Pointers: type_a, type_b (int32, n_pairs), size_a, size_b (FP64, 3 n_pairs), pose_a, pose_b
+ * (FP64, 12 n_pairs) and out (FP64, DS_COLLIDE_OUT n_pairs) are device pointers, read and written
+ * on `stream` (a cudaStream_t, NULL = the default stream); the call returns after the launch.
+ * The caller owns every buffer.  Errors: DS_EINVAL (n_pairs < 0, or a NULL pointer with
+ * n_pairs > 0), DS_ECUDA (launch failure).  A pair with an unknown type gets NaN in all its
+ * outputs.  n_pairs = 0 launches nothing. */
+enum { DS_CONVEX_SPHERE = 0, DS_CONVEX_CAPSULE = 1, DS_CONVEX_BOX = 2 };
+#define DS_COLLIDE_OUT 19
+ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const double* size_a, const double* pose_a,
+                     const int32_t* type_b, const double* size_b, const double* pose_b, double* out,
+                     void* stream);
+
 /* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
  * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per
  * thread to out[blocks*256] (device, FP64).  Used to measure the CUDA-core FMA peak that bounds

@@ -31,7 +31,7 @@ EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_d
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
            "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape", "ds_set_schedule", "ds_check_bad_indices",
-           "ds_check_self_test")
+           "ds_check_self_test", "ds_collide")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
         L.ds_profile.argtypes = [i32]
         L.ds_profile_read.argtypes = [vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
+        L.ds_collide.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
         for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
@@ -307,6 +308,23 @@ def sim_step_vjp_tape(models, batch, opt, v_next_bar, tape, out, q_bar, v_bar, t
 def fma_peak(out, blocks, iters, fp64, stream=None):
     """Launch the FMA-throughput probe (2 * 8 * iters * blocks * 256 flops)."""
     _check(lib().ds_fma_peak(_ptr(out), blocks, iters, 1 if fp64 else 0, _stream(stream)))
+
+
+CONVEX_SPHERE, CONVEX_CAPSULE, CONVEX_BOX = 0, 1, 2
+COLLIDE_OUT = 19
+
+
+def collide(type_a, size_a, pose_a, type_b, size_b, pose_b, out=None, stream=None):
+    """Collision detection between convex shapes (ds_collide), one pair per row: type (int32, n),
+    size (FP64, n x 3), pose (FP64, n x 12: R row-major, then p), all CUDA tensors.  Returns out
+    (FP64, n x 19): phi, c, n, t1, t2, the witness points on A's and B's surfaces."""
+    import torch
+    n = type_a.shape[0]
+    if out is None:
+        out = torch.empty((n, COLLIDE_OUT), dtype=torch.float64, device=type_a.device)
+    _check(lib().ds_collide(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
+                            _ptr(pose_b), _ptr(out), _stream(stream)))
+    return out
 
 
 STAGES = ("setup", "admm", "newton", "finish", "fused")

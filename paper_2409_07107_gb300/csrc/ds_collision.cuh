@@ -1,0 +1,438 @@
+// Collision detection between convex shapes (Sec. 2.1): the signed distance, the witness points,
+// the contact point and the contact frame (Z along the normal from A to B) of two shapes at given
+// world poses.  FP64, host- and device-callable, one pair per thread.
+//
+// Every shape is a core swept by a radius: a sphere is a point + r, a capsule a segment along its
+// body z axis (from -half_length to +half_length) + r, a box its 8 corners + 0.  The signed
+// distance is the distance of the cores minus rA + rB when the cores are apart, and minus
+// (penetration depth of the cores + rA + rB) when they overlap.
+//
+// * Cores apart: GJK (Gilbert, Johnson & Keerthi 1988) on the Minkowski difference D = A - B with
+//   the closest point of each simplex to the origin found by region tests (Ericson, Real-Time
+//   Collision Detection, 2005, Sec. 5.1.5 for the triangle); the final simplex's barycentric
+//   weights give the witness points on A and B.
+// * Cores overlapping: the penetration depth is min over unit m of h_D(m) (h the support
+//   function), attained at a facet normal of D.  Every facet of a Minkowski sum of a box with a
+//   box, segment or point has as normal a face normal of a box or the cross product of an edge
+//   direction of each core, so the minimum over those (15 axes for two boxes, 6 for a segment and
+//   a box, 3 for a point and a box) is the depth (the separating-axis form; GJK/EPA's polytope
+//   expansion reaches the same facet).  The witness points are the projection of the origin on
+//   that facet, split over the two cores' support features.
+// * The contact point is the midpoint of the witness points moved to the surfaces (pA + rA n,
+//   pB - rB n); the tangent axes follow the plane contacts' rule: t1 = normalize(e_x - (n.e_x) n),
+//   e_y in place of e_x when |n_x| > 0.9, t2 = n x t1.
+#pragma once
+#include <cmath>
+
+#include "ds_common.cuh"
+
+namespace ds {
+namespace cd {
+
+constexpr int kGjkMaxIter = 64;
+
+// A core in world coordinates: 1 point, 2 segment end points, or 8 box corners, plus the radius
+// and (for a box) its axes, the directions of its faces and edges.
+struct Core {
+  int nv;
+  double v[8][3];
+  double r;
+  double axis[3][3];   // box: the columns of R; segment: axis[0] = its direction
+  int naxis;           // 3 for a box, 1 for a segment, 0 for a point
+};
+
+DS_HDI void sub3(const double* a, const double* b, double* o) {
+  o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+
+DS_HDI void copy3(const double* a, double* o) { o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; }
+
+// Build the world core of shape (type, size) at pose (R row-major, p).  Returns false for an
+// unknown type.
+DS_HDI bool make_core(int type, const double* size, const double* R, const double* p, Core& c) {
+  if (type == DS_CONVEX_SPHERE) {
+    c.nv = 1; c.naxis = 0; c.r = size[0];
+    copy3(p, c.v[0]);
+    return true;
+  }
+  if (type == DS_CONVEX_CAPSULE) {
+    const double h = size[0];
+    c.nv = 2; c.naxis = 1; c.r = size[1];
+    for (int k = 0; k < 3; ++k) {
+      const double z = R[3 * k + 2];
+      c.v[0][k] = p[k] - h * z;
+      c.v[1][k] = p[k] + h * z;
+      c.axis[0][k] = z;
+    }
+    return true;
+  }
+  if (type == DS_CONVEX_BOX) {
+    c.nv = 8; c.naxis = 3; c.r = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      const double s0 = (i & 4) ? size[0] : -size[0];
+      const double s1 = (i & 2) ? size[1] : -size[1];
+      const double s2 = (i & 1) ? size[2] : -size[2];
+      for (int k = 0; k < 3; ++k) c.v[i][k] = p[k] + R[3 * k] * s0 + R[3 * k + 1] * s1 + R[3 * k + 2] * s2;
+    }
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) c.axis[j][k] = R[3 * k + j];
+    return true;
+  }
+  return false;
+}
+
+// Index of the core vertex with the largest d . v (the first of equals).
+DS_HDI int support(const Core& c, const double* d) {
+  int best = 0;
+  double bv = dot3(d, c.v[0]);
+  for (int i = 1; i < c.nv; ++i) {
+    const double x = dot3(d, c.v[i]);
+    if (x > bv) { bv = x; best = i; }
+  }
+  return best;
+}
+
+// ------------------------------------------------------------------------------------------ GJK
+// A simplex of D: up to 4 points w_j = A.v[ia_j] - B.v[ib_j] with barycentric weights.
+struct Simplex {
+  int n;
+  double w[4][3];
+  int ia[4], ib[4];
+  double lam[4];
+};
+
+// Weights (1 - t, t) of the point of segment ab closest to the origin.
+DS_HDI void seg_weights(const double* a, const double* b, double* l) {
+  double ab[3];
+  sub3(b, a, ab);
+  const double den = dot3(ab, ab);
+  double t = den > 0.0 ? -dot3(a, ab) / den : 0.0;
+  t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  l[0] = 1.0 - t;
+  l[1] = t;
+}
+
+// Weights of the point of triangle abc closest to the origin: the vertex, edge and face regions
+// tested in turn (Ericson 2005, Sec. 5.1.5).  A degenerate (collinear) triangle takes the best of
+// its edges.
+DS_HDI void tri_weights(const double* a, const double* b, const double* c, double* l) {
+  double ab[3], ac[3];
+  sub3(b, a, ab);
+  sub3(c, a, ac);
+  const double d1 = -dot3(ab, a), d2 = -dot3(ac, a);
+  if (d1 <= 0.0 && d2 <= 0.0) { l[0] = 1.0; l[1] = 0.0; l[2] = 0.0; return; }
+  const double d3 = -dot3(ab, b), d4 = -dot3(ac, b);
+  if (d3 >= 0.0 && d4 <= d3) { l[0] = 0.0; l[1] = 1.0; l[2] = 0.0; return; }
+  const double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    const double t = d1 / (d1 - d3);
+    l[0] = 1.0 - t; l[1] = t; l[2] = 0.0;
+    return;
+  }
+  const double d5 = -dot3(ab, c), d6 = -dot3(ac, c);
+  if (d6 >= 0.0 && d5 <= d6) { l[0] = 0.0; l[1] = 0.0; l[2] = 1.0; return; }
+  const double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    const double t = d2 / (d2 - d6);
+    l[0] = 1.0 - t; l[1] = 0.0; l[2] = t;
+    return;
+  }
+  const double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && d4 - d3 >= 0.0 && d5 - d6 >= 0.0) {
+    const double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    l[0] = 0.0; l[1] = 1.0 - t; l[2] = t;
+    return;
+  }
+  const double den = va + vb + vc;
+  if (den > 0.0) {
+    l[1] = vb / den;
+    l[2] = vc / den;
+    l[0] = 1.0 - l[1] - l[2];
+    return;
+  }
+  // collinear: the nearest of the three edges
+  const double* P[3] = {a, b, c};
+  double best = -1.0;
+  for (int e = 0; e < 3; ++e) {
+    const int i = e, j = (e + 1) % 3;
+    double le[2], x[3];
+    seg_weights(P[i], P[j], le);
+    for (int k = 0; k < 3; ++k) x[k] = le[0] * P[i][k] + le[1] * P[j][k];
+    const double d = dot3(x, x);
+    if (best < 0.0 || d < best) {
+      best = d;
+      l[0] = l[1] = l[2] = 0.0;
+      l[i] = le[0];
+      l[j] = le[1];
+    }
+  }
+}
+
+// Keep the simplex points listed in idx[0..m) with weights l (in that order).
+DS_HDI void keep(Simplex& s, const int* idx, const double* l, int m) {
+  Simplex t;
+  t.n = m;
+  for (int j = 0; j < m; ++j) {
+    copy3(s.w[idx[j]], t.w[j]);
+    t.ia[j] = s.ia[idx[j]];
+    t.ib[j] = s.ib[idx[j]];
+    t.lam[j] = l[j];
+  }
+  s = t;
+}
+
+// Replace the simplex by the smallest face carrying its point closest to the origin (weights > 0)
+// and return that point in v.  Returns true when the origin lies inside a tetrahedron.
+DS_HDI bool closest_reduce(Simplex& s, double* v) {
+  double l[4] = {1.0, 0.0, 0.0, 0.0};
+  int idx[4] = {0, 1, 2, 3};
+  int m = s.n;
+  if (s.n == 2) {
+    seg_weights(s.w[0], s.w[1], l);
+  } else if (s.n == 3) {
+    tri_weights(s.w[0], s.w[1], s.w[2], l);
+  } else if (s.n == 4) {
+    // faces (i, j, k) with the opposite vertex o; the origin is outside a face when it lies on
+    // the other side of the face's plane from o (a flat tetrahedron has every face outside)
+    const int F[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
+    bool inside = true;
+    double best = -1.0;
+    for (int f = 0; f < 4; ++f) {
+      const double *wi = s.w[F[f][0]], *wj = s.w[F[f][1]], *wk = s.w[F[f][2]], *wo = s.w[F[f][3]];
+      double e1[3], e2[3], nrm[3], eo[3];
+      sub3(wj, wi, e1);
+      sub3(wk, wi, e2);
+      cross3(e1, e2, nrm);
+      sub3(wo, wi, eo);
+      const double so = -dot3(nrm, wi), sd = dot3(nrm, eo);
+      if (sd != 0.0 && so * sd >= 0.0) continue;
+      inside = false;
+      double lf[3], x[3];
+      tri_weights(wi, wj, wk, lf);
+      for (int k = 0; k < 3; ++k) x[k] = lf[0] * wi[k] + lf[1] * wj[k] + lf[2] * wk[k];
+      const double d = dot3(x, x);
+      if (best < 0.0 || d < best) {
+        best = d;
+        l[0] = l[1] = l[2] = l[3] = 0.0;
+        for (int k = 0; k < 3; ++k) l[F[f][k]] = lf[k];
+      }
+    }
+    if (inside) {
+      v[0] = v[1] = v[2] = 0.0;
+      return true;
+    }
+  }
+  // keep the points with positive weight
+  int kept = 0;
+  double lk[4];
+  for (int j = 0; j < m; ++j)
+    if (l[j] > 0.0) {
+      idx[kept] = j;
+      lk[kept] = l[j];
+      ++kept;
+    }
+  if (kept == 0) {   // cannot happen for weights summing to 1; keep the first point
+    idx[0] = 0;
+    lk[0] = 1.0;
+    kept = 1;
+  }
+  keep(s, idx, lk, kept);
+  v[0] = v[1] = v[2] = 0.0;
+  for (int j = 0; j < s.n; ++j)
+    for (int k = 0; k < 3; ++k) v[k] += s.lam[j] * s.w[j][k];
+  return false;
+}
+
+// Distance of the cores by GJK: returns true when they overlap (the origin in D, or a distance
+// below 1e-12); otherwise dist and the witness points pa (on A), pb (on B).
+DS_HDI bool gjk(const Core& A, const Core& B, double& dist, double* pa, double* pb) {
+  Simplex s;
+  s.n = 1;
+  s.ia[0] = 0;
+  s.ib[0] = 0;
+  s.lam[0] = 1.0;
+  sub3(A.v[0], B.v[0], s.w[0]);
+  double v[3];
+  copy3(s.w[0], v);
+  double vv = dot3(v, v);
+  bool overlap = false;
+  for (int it = 0; it < kGjkMaxIter; ++it) {
+    if (vv <= 1e-24) { overlap = true; break; }
+    const double nv[3] = {-v[0], -v[1], -v[2]};
+    const int ia = support(A, nv), ib = support(B, v);
+    bool dup = false;
+    for (int j = 0; j < s.n; ++j) dup = dup || (s.ia[j] == ia && s.ib[j] == ib);
+    double w[3];
+    sub3(A.v[ia], B.v[ib], w);
+    // stop when the new support point cannot bring the simplex closer to the origin
+    if (dup || vv - dot3(v, w) <= 1e-12 * vv) break;
+    Simplex prev = s;
+    copy3(w, s.w[s.n]);
+    s.ia[s.n] = ia;
+    s.ib[s.n] = ib;
+    ++s.n;
+    double vn[3];
+    if (closest_reduce(s, vn)) { overlap = true; break; }
+    const double vvn = dot3(vn, vn);
+    if (!(vvn < vv)) {   // no progress in floating point: keep the previous simplex
+      s = prev;
+      break;
+    }
+    copy3(vn, v);
+    vv = vvn;
+  }
+  for (int k = 0; k < 3; ++k) {
+    pa[k] = 0.0;
+    pb[k] = 0.0;
+    for (int j = 0; j < s.n; ++j) {
+      pa[k] += s.lam[j] * A.v[s.ia[j]][k];
+      pb[k] += s.lam[j] * B.v[s.ib[j]][k];
+    }
+  }
+  dist = sqrt(vv);
+  return overlap;
+}
+
+// ---------------------------------------------------------------------- overlapping cores
+// Closest points of segments [p1, q1] and [p2, q2] (the unconstrained minimiser of the squared
+// distance, clamped to the square; used for two support edges whose closest points are interior).
+DS_HDI void seg_seg(const double* p1, const double* q1, const double* p2, const double* q2,
+                    double* x1, double* x2) {
+  double d1[3], d2[3], r[3];
+  sub3(q1, p1, d1);
+  sub3(q2, p2, d2);
+  sub3(p1, p2, r);
+  const double a = dot3(d1, d1), b = dot3(d1, d2), e = dot3(d2, d2);
+  const double c = dot3(d1, r), f = dot3(d2, r);
+  const double den = a * e - b * b;
+  double s = den > 1e-14 * a * e ? (b * f - c * e) / den : 0.0;
+  s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+  double t = e > 0.0 ? (b * s + f) / e : 0.0;
+  t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  if (a > 0.0) {
+    s = (b * t - c) / a;
+    s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+  }
+  for (int k = 0; k < 3; ++k) {
+    x1[k] = p1[k] + s * d1[k];
+    x2[k] = p2[k] + t * d2[k];
+  }
+}
+
+// h_D(m) = max_a m.a - min_b m.b, with lo = min_b m.b and hi = max_a m.a.
+DS_HDI double support_gap(const Core& A, const Core& B, const double* m, double& hi, double& lo) {
+  hi = dot3(m, A.v[0]);
+  for (int i = 1; i < A.nv; ++i) hi = fmax(hi, dot3(m, A.v[i]));
+  lo = dot3(m, B.v[0]);
+  for (int j = 1; j < B.nv; ++j) lo = fmin(lo, dot3(m, B.v[j]));
+  return hi - lo;
+}
+
+// Penetration of overlapping cores (at least one a box): the depth, the unit axis m (from A to B:
+// moving A by -depth m separates them) and the witness points pa on A, pb on B with
+// pa - pb = depth m.
+DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, double* pa, double* pb) {
+  double cand[15][3];
+  int nc = 0;
+  if (A.nv == 8)
+    for (int i = 0; i < 3; ++i) copy3(A.axis[i], cand[nc++]);
+  if (B.nv == 8)
+    for (int j = 0; j < 3; ++j) copy3(B.axis[j], cand[nc++]);
+  for (int i = 0; i < A.naxis; ++i)
+    for (int j = 0; j < B.naxis; ++j) cross3(A.axis[i], B.axis[j], cand[nc++]);
+  depth = -1.0;
+  double hi_best = 0.0, lo_best = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double len2 = dot3(cand[c], cand[c]);
+    if (len2 < 1e-20) continue;   // parallel edges: no facet of their own
+    const double inv = 1.0 / sqrt(len2);
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const double s = sgn ? -inv : inv;
+      const double u[3] = {s * cand[c][0], s * cand[c][1], s * cand[c][2]};
+      double hi, lo;
+      const double h = support_gap(A, B, u, hi, lo);
+      if (depth < 0.0 || h < depth) {
+        depth = h;
+        copy3(u, m);
+        hi_best = hi;
+        lo_best = lo;
+      }
+    }
+  }
+  // the support features of A along m and of B along -m
+  const double tol = 1e-9 * (1.0 + fabs(hi_best) + fabs(lo_best));
+  int fa[8], fb[8], na = 0, nb = 0;
+  for (int i = 0; i < A.nv; ++i)
+    if (dot3(m, A.v[i]) >= hi_best - tol) fa[na++] = i;
+  for (int j = 0; j < B.nv; ++j)
+    if (dot3(m, B.v[j]) <= lo_best + tol) fb[nb++] = j;
+  if (na == 1) {
+    copy3(A.v[fa[0]], pa);
+    for (int k = 0; k < 3; ++k) pb[k] = pa[k] - depth * m[k];
+  } else if (nb == 1) {
+    copy3(B.v[fb[0]], pb);
+    for (int k = 0; k < 3; ++k) pa[k] = pb[k] + depth * m[k];
+  } else if (na == 2 && nb == 2) {
+    seg_seg(A.v[fa[0]], A.v[fa[1]], B.v[fb[0]], B.v[fb[1]], pa, pb);
+  } else {
+    // an edge or face against a face: the witness pairs form a set; take the centroid of B's
+    // feature and its partner on A
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < nb; ++j) s += B.v[fb[j]][k];
+      pb[k] = s / nb;
+      pa[k] = pb[k] + depth * m[k];
+    }
+  }
+}
+
+// Collision detection of shape A (type, size, pose) and shape B.  Writes DS_COLLIDE_OUT numbers:
+// phi, c[3], n[3], t1[3], t2[3], the witness points on the surfaces sa[3], sb[3].  An unknown type
+// gives NaN throughout.
+DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int type_b,
+                    const double* size_b, const double* pose_b, double* out) {
+  Core A, B;
+  if (!make_core(type_a, size_a, pose_a, pose_a + 9, A) || !make_core(type_b, size_b, pose_b, pose_b + 9, B)) {
+    for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
+    return;
+  }
+  double d, pa[3], pb[3], n[3];
+  const bool overlap = gjk(A, B, d, pa, pb);
+  if (!overlap) {
+    for (int k = 0; k < 3; ++k) n[k] = (pb[k] - pa[k]) / d;
+  } else if (A.nv == 8 || B.nv == 8) {
+    double depth;
+    penetration(A, B, depth, n, pa, pb);
+    d = -depth;
+  } else {
+    // touching or crossing point and segment cores have no normal: take the world z axis
+    d = 0.0;
+    n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+  }
+  double sa[3], sb[3];
+  for (int k = 0; k < 3; ++k) {
+    sa[k] = pa[k] + A.r * n[k];
+    sb[k] = pb[k] - B.r * n[k];
+  }
+  // tangent axes: t1 = normalize(e - (n.e) n), e = e_x (e_y when |n_x| > 0.9); t2 = n x t1
+  const bool use_y = fabs(n[0]) > 0.9;
+  const double e[3] = {use_y ? 0.0 : 1.0, use_y ? 1.0 : 0.0, 0.0};
+  const double ne = dot3(n, e);
+  double t1[3] = {e[0] - ne * n[0], e[1] - ne * n[1], e[2] - ne * n[2]};
+  const double it = 1.0 / sqrt(dot3(t1, t1));
+  for (int k = 0; k < 3; ++k) t1[k] *= it;
+  double t2[3];
+  cross3(n, t1, t2);
+  out[0] = d - A.r - B.r;
+  for (int k = 0; k < 3; ++k) {
+    out[1 + k] = 0.5 * (sa[k] + sb[k]);
+    out[4 + k] = n[k];
+    out[7 + k] = t1[k];
+    out[10 + k] = t2[k];
+    out[13 + k] = sa[k];
+    out[16 + k] = sb[k];
+  }
+}
+
+}  // namespace cd
+}  // namespace ds

@@ -90,3 +90,11 @@ def test_step_rejects_bad_arguments(L):
     b.ncmax = 99
     assert L.sim_step_vjp(models, 1, ctypes.byref(b), ctypes.byref(o), None, None, ctypes.byref(out), None, None,
                           None, None, 0, None) == ds.DS_EINVAL
+
+
+def test_collide_rejects_bad_arguments(L):
+    buf = ctypes.c_void_p(1)
+    assert L.ds_collide(-1, buf, buf, buf, buf, buf, buf, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide(4, None, buf, buf, buf, buf, buf, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide(4, buf, buf, buf, buf, buf, buf, None, None) == ds.DS_EINVAL
+    assert L.ds_collide(0, None, None, None, None, None, None, None, None) == ds.DS_OK
