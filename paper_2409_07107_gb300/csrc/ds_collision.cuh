@@ -16,7 +16,8 @@
 //   box, segment or point has as normal a face normal of a box or the cross product of an edge
 //   direction of each core, so the minimum over those (15 axes for two boxes, 6 for a segment and
 //   a box, 3 for a point and a box) is the depth (the separating-axis form; GJK/EPA's polytope
-//   expansion reaches the same facet).  The witness points are the projection of the origin on
+//   expansion reaches the same facet).  The same axes decide whether cores with a box overlap at
+//   all (a negative minimum is a separating axis), so GJK runs only on separated cores there.  The witness points are the projection of the origin on
 //   that facet, split over the two cores' support features.
 // * The contact point is the midpoint of the witness points moved to the surfaces (pA + rA n,
 //   pB - rB n); the tangent axes follow the plane contacts' rule: t1 = normalize(e_x - (n.e_x) n),
@@ -193,7 +194,9 @@ DS_HDI bool closest_reduce(Simplex& s, double* v) {
     tri_weights(s.w[0], s.w[1], s.w[2], l);
   } else if (s.n == 4) {
     // faces (i, j, k) with the opposite vertex o; the origin is outside a face when it lies on
-    // the other side of the face's plane from o (a flat tetrahedron has every face outside)
+    // the other side of the face's plane from o.  A flat tetrahedron (o within 1e-9 of the face's
+    // plane relative to the sizes) has no inside: every face counts as outside, so that rounding
+    // in the side tests cannot report the origin inside it
     const int F[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
     bool inside = true;
     double best = -1.0;
@@ -205,7 +208,8 @@ DS_HDI bool closest_reduce(Simplex& s, double* v) {
       cross3(e1, e2, nrm);
       sub3(wo, wi, eo);
       const double so = -dot3(nrm, wi), sd = dot3(nrm, eo);
-      if (sd != 0.0 && so * sd >= 0.0) continue;
+      const bool flat = fabs(sd) <= 1e-9 * sqrt(dot3(nrm, nrm) * dot3(eo, eo));
+      if (!flat && so * sd >= 0.0) continue;
       inside = false;
       double lf[3], x[3];
       tri_weights(wi, wj, wk, lf);
@@ -244,8 +248,9 @@ DS_HDI bool closest_reduce(Simplex& s, double* v) {
 }
 
 // Distance of the cores by GJK: returns true when they overlap (the origin in D, or a distance
-// below 1e-12); otherwise dist and the witness points pa (on A), pb (on B).
-DS_HDI bool gjk(const Core& A, const Core& B, double& dist, double* pa, double* pb) {
+// below 1e-12); the witness points pa (on A), pb (on B) are those of the last simplex that did
+// not contain the origin.
+DS_HDI bool gjk(const Core& A, const Core& B, double* pa, double* pb) {
   Simplex s;
   s.n = 1;
   s.ia[0] = 0;
@@ -272,7 +277,11 @@ DS_HDI bool gjk(const Core& A, const Core& B, double& dist, double* pa, double* 
     s.ib[s.n] = ib;
     ++s.n;
     double vn[3];
-    if (closest_reduce(s, vn)) { overlap = true; break; }
+    if (closest_reduce(s, vn)) {
+      s = prev;
+      overlap = true;
+      break;
+    }
     const double vvn = dot3(vn, vn);
     if (!(vvn < vv)) {   // no progress in floating point: keep the previous simplex
       s = prev;
@@ -289,7 +298,6 @@ DS_HDI bool gjk(const Core& A, const Core& B, double& dist, double* pa, double* 
       pb[k] += s.lam[j] * B.v[s.ib[j]][k];
     }
   }
-  dist = sqrt(vv);
   return overlap;
 }
 
@@ -319,18 +327,21 @@ DS_HDI void seg_seg(const double* p1, const double* q1, const double* p2, const 
   }
 }
 
-// h_D(m) = max_a m.a - min_b m.b, with lo = min_b m.b and hi = max_a m.a.
-DS_HDI double support_gap(const Core& A, const Core& B, const double* m, double& hi, double& lo) {
-  hi = dot3(m, A.v[0]);
-  for (int i = 1; i < A.nv; ++i) hi = fmax(hi, dot3(m, A.v[i]));
-  lo = dot3(m, B.v[0]);
-  for (int j = 1; j < B.nv; ++j) lo = fmin(lo, dot3(m, B.v[j]));
-  return hi - lo;
+// The range [lo, hi] of u . v over the vertices v of a core.
+DS_HDI void project(const Core& c, const double* u, double& lo, double& hi) {
+  lo = hi = dot3(u, c.v[0]);
+  for (int i = 1; i < c.nv; ++i) {
+    const double x = dot3(u, c.v[i]);
+    lo = fmin(lo, x);
+    hi = fmax(hi, x);
+  }
 }
 
-// Penetration of overlapping cores (at least one a box): the depth, the unit axis m (from A to B:
-// moving A by -depth m separates them) and the witness points pa on A, pb on B with
-// pa - pb = depth m.
+// Separating-axis test of two cores of which one is a box: depth = the minimum of h_D over the
+// candidate axes, with its unit axis m.  depth < 0: m separates the cores (they are apart).
+// depth >= 0: the cores overlap, depth is their penetration depth and m the axis from A to B
+// (moving A by -depth m separates them); then the witness points pa on A, pb on B with
+// pa - pb = depth m are written too.
 DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, double* pa, double* pb) {
   double cand[15][3];
   int nc = 0;
@@ -340,25 +351,30 @@ DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, 
     for (int j = 0; j < 3; ++j) copy3(B.axis[j], cand[nc++]);
   for (int i = 0; i < A.naxis; ++i)
     for (int j = 0; j < B.naxis; ++j) cross3(A.axis[i], B.axis[j], cand[nc++]);
+  bool found = false;
   depth = -1.0;
   double hi_best = 0.0, lo_best = 0.0;
   for (int c = 0; c < nc; ++c) {
     const double len2 = dot3(cand[c], cand[c]);
     if (len2 < 1e-20) continue;   // parallel edges: no facet of their own
     const double inv = 1.0 / sqrt(len2);
+    const double u[3] = {inv * cand[c][0], inv * cand[c][1], inv * cand[c][2]};
+    // h_D(u) = max_a u.a - min_b u.b and h_D(-u) = max_b u.b - min_a u.a from one projection
+    double alo, ahi, blo, bhi;
+    project(A, u, alo, ahi);
+    project(B, u, blo, bhi);
     for (int sgn = 0; sgn < 2; ++sgn) {
-      const double s = sgn ? -inv : inv;
-      const double u[3] = {s * cand[c][0], s * cand[c][1], s * cand[c][2]};
-      double hi, lo;
-      const double h = support_gap(A, B, u, hi, lo);
-      if (depth < 0.0 || h < depth) {
+      const double h = sgn ? bhi - alo : ahi - blo;
+      if (!found || h < depth) {
+        found = true;
         depth = h;
-        copy3(u, m);
-        hi_best = hi;
-        lo_best = lo;
+        for (int k = 0; k < 3; ++k) m[k] = sgn ? -u[k] : u[k];
+        hi_best = sgn ? -alo : ahi;   // max over A of m.a
+        lo_best = sgn ? -bhi : blo;   // min over B of m.b
       }
     }
   }
+  if (depth < 0.0) return;
   // the support features of A along m and of B along -m
   const double tol = 1e-9 * (1.0 + fabs(hi_best) + fabs(lo_best));
   int fa[8], fb[8], na = 0, nb = 0;
@@ -397,17 +413,31 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
     return;
   }
   double d, pa[3], pb[3], n[3];
-  const bool overlap = gjk(A, B, d, pa, pb);
-  if (!overlap) {
-    for (int k = 0; k < 3; ++k) n[k] = (pb[k] - pa[k]) / d;
-  } else if (A.nv == 8 || B.nv == 8) {
-    double depth;
-    penetration(A, B, depth, n, pa, pb);
+  const bool has_box = A.nv == 8 || B.nv == 8;
+  double depth = -1.0, m[3] = {0.0, 0.0, 1.0};
+  // with a box, the separating-axis test decides overlap exactly; GJK measures separated cores
+  if (has_box) penetration(A, B, depth, m, pa, pb);
+  if (has_box && depth >= 0.0) {
     d = -depth;
+    copy3(m, n);
   } else {
-    // touching or crossing point and segment cores have no normal: take the world z axis
-    d = 0.0;
-    n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+    const bool overlap = gjk(A, B, pa, pb);
+    double diff[3];
+    sub3(pb, pa, diff);
+    d = sqrt(dot3(diff, diff));
+    if (!overlap && d > 0.0) {
+      for (int k = 0; k < 3; ++k) n[k] = diff[k] / d;
+    } else if (has_box) {
+      // GJK met the origin although an axis separates the cores (rounding in a near-degenerate
+      // simplex): the separating axis and its gap stand in
+      d = -depth;
+      copy3(m, n);
+      for (int k = 0; k < 3; ++k) pb[k] = pa[k] + d * n[k];
+    } else {
+      // touching or crossing point and segment cores have no normal: take the world z axis
+      d = 0.0;
+      n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+    }
   }
   double sa[3], sb[3];
   for (int k = 0; k < 3; ++k) {

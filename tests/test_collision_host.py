@@ -8,8 +8,10 @@ witness points within 1e-10 (observed: 1e-16 for phi, 4e-13 for the normal).  Th
 the convex hull of the whole Minkowski difference (Qhull) and the device GJK or the separating
 axes, so a mistake in either one's region tests, support features or axis set shows up here.
 Random poses put no two faces or edges exactly parallel, where the witness points would not be
-unique."""
+unique.  Each check runs on a plain host build and on one with fused multiply-adds contracted (as
+on the device), whose rounding differs in the near-degenerate decisions."""
 import os
+import platform
 import shutil
 import subprocess
 
@@ -42,15 +44,19 @@ int main() {
 '''
 
 
-@pytest.fixture(scope="module")
-def host_collide(tmp_path_factory):
+def _host_build(tmp_path_factory, contracted):
     nvcc = build._nvcc()
     if not ((os.path.isabs(nvcc) and os.path.exists(nvcc)) or shutil.which(nvcc)):
         pytest.skip("nvcc not found")
     d = tmp_path_factory.mktemp("cd")
     src, exe = d / "cd.cu", d / "cd"
     src.write_text(PROG)
-    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-I" + build.INCLUDE, "-I" + build.CSRC, str(src), "-o", str(exe)],
+    flags = []
+    if contracted:
+        # fused multiply-adds wherever the compiler can form them, as the device code has: the
+        # rounding differs from the plain build's, which moves near-degenerate decisions
+        flags = ["-Xcompiler", "-ffp-contract=fast"] + (["-Xcompiler", "-mfma"] if platform.machine() == "x86_64" else [])
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", *flags, "-I" + build.INCLUDE, "-I" + build.CSRC, str(src), "-o", str(exe)],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
 
@@ -64,6 +70,11 @@ def host_collide(tmp_path_factory):
         assert out.returncode == 0
         return np.array([[float(x) for x in ln.split()] for ln in out.stdout.splitlines() if ln.strip()])
     return run
+
+
+@pytest.fixture(scope="module", params=["plain", "contracted"])
+def host_collide(request, tmp_path_factory):
+    return _host_build(tmp_path_factory, request.param == "contracted")
 
 
 def oracle_collide(P, k):
@@ -96,6 +107,16 @@ def test_host_collide_against_oracle(host_collide, types):
     got = host_collide(P)
     n_over, n_apart = compare(P, got)
     assert n_over >= 10 and n_apart >= 10
+
+
+def test_host_collide_witness_identity_large_batch(host_collide):
+    """On 20000 pairs: sb - sa = phi n and |n| = 1 for every pair (a false overlap from a flat
+    GJK simplex, seen once in 262144 pairs with contracted rounding, broke the first)."""
+    P = pairs(20000, seed=77)
+    got = host_collide(P)
+    phi, nrm, sa, sb = got[:, 0], got[:, 4:7], got[:, 13:16], got[:, 16:19]
+    assert np.abs(sb - sa - phi[:, None] * nrm).max() <= 1e-12
+    assert np.abs(np.einsum("ij,ij->i", nrm, nrm) - 1.0).max() <= 1e-12
 
 
 def test_host_collide_unknown_type_is_nan(host_collide):
