@@ -202,14 +202,15 @@ def cd_features(res):
     return np.concatenate([[res["phi"]], res["c"], res["n"]])
 
 
-def randomized_smoothing_jacobian(shape_a, Ra, pa, shape_b, Rb, pb, sigma, samples, rng):
+def randomized_smoothing_jacobian(shape_a, Ra, pa, shape_b, Rb, pb, sigma, samples, rng, eps_samples=None):
     """Zero-order randomized-smoothing estimate of the derivative of (phi, c, n) with respect to the
     world-frame twists of A's and B's poses (7 x 12; columns: A's (u, w), then B's): with eps ~
     N(0, sigma^2 I_12) the expectation of (f(eps) - f(-eps)) eps^T / (2 sigma^2), the gradient of
-    the Gaussian-smoothed f (antithetic pairs; unbiased for the smoothed function)."""
+    the Gaussian-smoothed f (antithetic pairs; unbiased for the smoothed function).  The samples are
+    drawn from rng, or taken from eps_samples (samples x 12, already scaled by sigma) when given."""
     acc = np.zeros((7, 12))
-    for _ in range(samples):
-        eps = rng.normal(0.0, sigma, size=12)
+    for s in range(samples):
+        eps = rng.normal(0.0, sigma, size=12) if eps_samples is None else np.asarray(eps_samples[s], float)
         fp = cd_features(collide(shape_a, *twist_pose(Ra, pa, eps[:6]), shape_b, *twist_pose(Rb, pb, eps[6:])))
         fm = cd_features(collide(shape_a, *twist_pose(Ra, pa, -eps[:6]), shape_b, *twist_pose(Rb, pb, -eps[6:])))
         acc += np.outer(fp - fm, eps)
