@@ -395,6 +395,22 @@ ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const double* size_
                      const int32_t* type_b, const double* size_b, const double* pose_b, double* out,
                      void* stream);
 
+/* The derivative App. C takes of the collision detection: its zero-order randomized-smoothing
+ * estimate.  For each pair, with the caller's samples eps_s = (u_A, w_A, u_B, w_B) (s < n_samples,
+ * 12 numbers each, drawn from N(0, sigma^2 I); the same samples serve every pair), the poses are
+ * moved by +-eps_s as world-frame twists (x -> exp([w]) x + V(w) u: R' = exp([w]) R,
+ * p' = exp([w]) p + V(w) u) and
+ *   J = 1 / (2 n_samples sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T,
+ * f = (phi, c[3], n[3]) the first 7 outputs of ds_collide.  J is the gradient estimate of the
+ * Gaussian-smoothed f with respect to the two twists: 7 x 12, row-major (columns: A's u, A's w,
+ * B's u, B's w), written to jac[84 k ...].  Shapes and poses as for ds_collide; eps (FP64,
+ * 12 n_samples) and jac (FP64, 84 n_pairs) are device pointers.  Errors: DS_EINVAL (n_pairs < 0,
+ * n_samples <= 0 with n_pairs > 0, sigma not positive and finite, a NULL pointer with
+ * n_pairs > 0), DS_ECUDA (launch failure). */
+ds_status ds_collide_smoothed(int32_t n_pairs, const int32_t* type_a, const double* size_a, const double* pose_a,
+                              const int32_t* type_b, const double* size_b, const double* pose_b,
+                              int32_t n_samples, const double* eps, double sigma, double* jac, void* stream);
+
 /* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
  * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per
  * thread to out[blocks*256] (device, FP64).  Used to measure the CUDA-core FMA peak that bounds

@@ -31,7 +31,7 @@ EXPORTS = ("ds_model_create", "ds_model_destroy", "ds_model_dims", "ds_options_d
            "ds_status_string", "sim_step", "sim_step_jac", "sim_step_vjp", "ds_fma_peak", "ds_workspace_size",
            "sim_step_jac_noalloc", "ds_profile", "ds_profile_read", "ds_cotangent_to_tangent",
            "ds_cotangent_to_raw", "ds_autotune", "sim_step_vjp_tape", "ds_set_schedule", "ds_check_bad_indices",
-           "ds_check_self_test", "ds_collide")
+           "ds_check_self_test", "ds_collide", "ds_collide_smoothed")
 
 
 class ds_model_desc(ctypes.Structure):
@@ -92,6 +92,7 @@ def lib():
         L.ds_profile_read.argtypes = [vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
         L.ds_collide.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ds_collide_smoothed.argtypes = [i32, vp, vp, vp, vp, vp, vp, i32, vp, ctypes.c_double, vp, vp]
         for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
@@ -324,6 +325,20 @@ def collide(type_a, size_a, pose_a, type_b, size_b, pose_b, out=None, stream=Non
         out = torch.empty((n, COLLIDE_OUT), dtype=torch.float64, device=type_a.device)
     _check(lib().ds_collide(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
                             _ptr(pose_b), _ptr(out), _stream(stream)))
+    return out
+
+
+def collide_smoothed(type_a, size_a, pose_a, type_b, size_b, pose_b, eps, sigma, out=None, stream=None):
+    """Randomized-smoothing derivative of the collision detection (ds_collide_smoothed): eps (FP64,
+    S x 12 CUDA tensor, samples of N(0, sigma^2 I)); returns (n x 7 x 12) d(phi, c, n)/d(twists of
+    A and B)."""
+    import torch
+    n = type_a.shape[0]
+    if out is None:
+        out = torch.empty((n, 7, 12), dtype=torch.float64, device=type_a.device)
+    _check(lib().ds_collide_smoothed(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
+                                     _ptr(pose_b), eps.shape[0], _ptr(eps), float(sigma), _ptr(out),
+                                     _stream(stream)))
     return out
 
 

@@ -464,5 +464,67 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
   }
 }
 
+// ------------------------------------------------------------- randomized-smoothing derivative
+// The pose (R row-major, p) moved by sgn times the world-frame twist xi = (u, w) (linear, then
+// angular about the world origin): x -> exp([w]) x + V(w) u, so R' = exp([w]) R and
+// p' = exp([w]) p + V(w) u, with exp([w]) = I + sin(t)/t W + (1 - cos t)/t^2 W^2 (Rodrigues) and
+// V(w) = I + (1 - cos t)/t^2 W + (t - sin t)/t^3 W^2, t = |w|, W = [w]x (I + W and I + W/2 below
+// t = 1e-12).
+DS_HDI void twist_pose(const double* pose, const double* xi, double sgn, double* out) {
+  const double u[3] = {sgn * xi[0], sgn * xi[1], sgn * xi[2]};
+  const double w[3] = {sgn * xi[3], sgn * xi[4], sgn * xi[5]};
+  const double t = sqrt(dot3(w, w));
+  const double W[3][3] = {{0.0, -w[2], w[1]}, {w[2], 0.0, -w[0]}, {-w[1], w[0], 0.0}};
+  double W2[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) W2[i][j] = W[i][0] * W[0][j] + W[i][1] * W[1][j] + W[i][2] * W[2][j];
+  double a = 1.0, b = 0.0, c = 0.5, d = 0.0;
+  if (t >= 1e-12) {
+    a = sin(t) / t;
+    b = (1.0 - cos(t)) / (t * t);
+    c = b;
+    d = (t - sin(t)) / (t * t * t);
+  }
+  double E[3][3], V[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double id = i == j ? 1.0 : 0.0;
+      E[i][j] = id + a * W[i][j] + b * W2[i][j];
+      V[i][j] = id + c * W[i][j] + d * W2[i][j];
+    }
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j)
+      out[3 * i + j] = E[i][0] * pose[j] + E[i][1] * pose[3 + j] + E[i][2] * pose[6 + j];
+    out[9 + i] = E[i][0] * pose[9] + E[i][1] * pose[10] + E[i][2] * pose[11] +
+                 V[i][0] * u[0] + V[i][1] * u[1] + V[i][2] * u[2];
+  }
+}
+
+// App. C's zero-order randomized-smoothing estimate of the derivative of f = (phi, c, n) (the
+// first 7 outputs of collide) with respect to the world-frame twists of A's and B's poses:
+// J = 1 / (2 S sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T, eps_s = (A's (u, w), B's (u, w))
+// the caller's samples (S x 12, drawn from N(0, sigma^2 I)).  J is 7 x 12, row-major.
+DS_HDI void smoothing_jacobian(int type_a, const double* size_a, const double* pose_a, int type_b,
+                               const double* size_b, const double* pose_b, int samples,
+                               const double* eps, double sigma, double* J) {
+  for (int k = 0; k < 84; ++k) J[k] = 0.0;
+  double qa[12], qb[12], fp[DS_COLLIDE_OUT], fm[DS_COLLIDE_OUT];
+  for (int s = 0; s < samples; ++s) {
+    const double* e = eps + 12 * s;
+    twist_pose(pose_a, e, 1.0, qa);
+    twist_pose(pose_b, e + 6, 1.0, qb);
+    collide(type_a, size_a, qa, type_b, size_b, qb, fp);
+    twist_pose(pose_a, e, -1.0, qa);
+    twist_pose(pose_b, e + 6, -1.0, qb);
+    collide(type_a, size_a, qa, type_b, size_b, qb, fm);
+    for (int i = 0; i < 7; ++i) {
+      const double df = fp[i] - fm[i];
+      for (int j = 0; j < 12; ++j) J[12 * i + j] += df * e[j];
+    }
+  }
+  const double scale = 1.0 / (2.0 * sigma * sigma * samples);
+  for (int k = 0; k < 84; ++k) J[k] *= scale;
+}
+
 }  // namespace cd
 }  // namespace ds

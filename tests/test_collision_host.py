@@ -124,3 +124,61 @@ def test_host_collide_unknown_type_is_nan(host_collide):
     P["type_b"][1] = 7
     got = host_collide(P)
     assert np.isfinite(got[0]).all() and np.isnan(got[1]).all()
+
+
+PROG_SMOOTH = r'''
+#include "ds_collision.cuh"
+#include <cstdio>
+#include <vector>
+int main() {
+  int ta, tb, S;
+  double sigma, sa[3], sb[3], pa[12], pb[12], J[84];
+  while (std::scanf("%d %lf", &S, &sigma) == 2) {
+    std::vector<double> eps(12 * S);
+    for (double& x : eps) std::scanf("%lf", &x);
+    std::scanf("%d", &ta);
+    for (double& x : sa) std::scanf("%lf", &x);
+    for (double& x : pa) std::scanf("%lf", &x);
+    std::scanf("%d", &tb);
+    for (double& x : sb) std::scanf("%lf", &x);
+    for (double& x : pb) std::scanf("%lf", &x);
+    ds::cd::smoothing_jacobian(ta, sa, pa, tb, sb, pb, S, eps.data(), sigma, J);
+    for (int k = 0; k < 84; ++k) std::printf("%.17g ", J[k]);
+    std::printf("\n");
+  }
+  return 0;
+}
+'''
+
+
+def test_host_smoothing_jacobian_against_oracle(tmp_path):
+    """App. C's randomized-smoothing derivative on the device side (the poses moved by the caller's
+    samples as world-frame twists, antithetic differences of (phi, c, n)) equals the oracle's
+    estimator fed the same samples, pair by pair."""
+    nvcc = build._nvcc()
+    if not ((os.path.isabs(nvcc) and os.path.exists(nvcc)) or shutil.which(nvcc)):
+        pytest.skip("nvcc not found")
+    src, exe = tmp_path / "sm.cu", tmp_path / "sm"
+    src.write_text(PROG_SMOOTH)
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-I" + build.INCLUDE, "-I" + build.CSRC, str(src), "-o", str(exe)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    P = pairs(48, seed=404)
+    rng = np.random.default_rng(5)
+    sigma, S = 2e-3, 6
+    eps = rng.normal(0.0, sigma, size=(S, 12))
+    head = "%d %.17g %s" % (S, sigma, " ".join("%.17g" % x for x in eps.ravel()))
+    lines = []
+    for k in range(len(P["type_a"])):
+        fa = " ".join("%.17g" % x for x in np.concatenate([P["size_a"][k], P["pose_a"][k]]))
+        fb = " ".join("%.17g" % x for x in np.concatenate([P["size_b"][k], P["pose_b"][k]]))
+        lines.append("%s %d %s %d %s" % (head, P["type_a"][k], fa, P["type_b"][k], fb))
+    out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300)
+    got = np.array([[float(x) for x in ln.split()] for ln in out.stdout.splitlines() if ln.strip()]).reshape(-1, 7, 12)
+    for k in range(len(P["type_a"])):
+        sa = oracle_shape(P["type_a"][k], P["size_a"][k])
+        sb = oracle_shape(P["type_b"][k], P["size_b"][k])
+        pa, pb = P["pose_a"][k], P["pose_b"][k]
+        ref = C.randomized_smoothing_jacobian(sa, pa[:9].reshape(3, 3), pa[9:], sb, pb[:9].reshape(3, 3), pb[9:],
+                                              sigma, S, None, eps_samples=eps)
+        assert np.abs(got[k] - ref).max() <= 1e-8 * max(1.0, np.abs(ref).max()), k

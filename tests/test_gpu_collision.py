@@ -7,7 +7,9 @@ oracle's collision detection by its definition (oracle/collision.py).
 * 262144 pairs (the size of a batch of 16384 humanoids with 16 candidate pairs each) with a
   ragged tail: 512 sampled pairs against the oracle, and every pair checked for what holds at any
   size: n unit, (t1, t2, n) orthonormal and right-handed, sb - sa = phi n;
-* an unknown shape type gives NaN for that pair only, and an empty batch launches nothing."""
+* an unknown shape type gives NaN for that pair only, and an empty batch launches nothing;
+* the randomized-smoothing derivative (ds_collide_smoothed) against the oracle's estimator fed the
+  same samples."""
 import numpy as np
 import pytest
 
@@ -70,3 +72,26 @@ def test_collide_unknown_type_and_empty_batch():
     f = torch.empty((0, 3), dtype=torch.float64, device="cuda")
     out = ds.collide(e, f, f, e, f, f)
     assert out.shape == (0, ds.COLLIDE_OUT)
+
+
+def test_collide_smoothed_against_oracle():
+    """App. C's randomized-smoothing derivative (ds_collide_smoothed) against the oracle's estimator
+    fed the same samples: 4096 pairs, 8 samples, every 64th pair compared (relative 1e-8)."""
+    import torch
+    from oracle import collision as C
+    from tests.convex_pairs import oracle_shape
+    P = pairs(4096, seed=31)
+    D = _device(P)
+    sigma, S = 2e-3, 8
+    eps = np.random.default_rng(6).normal(0.0, sigma, size=(S, 12))
+    J = ds.collide_smoothed(D["type_a"], D["size_a"], D["pose_a"], D["type_b"], D["size_b"], D["pose_b"],
+                            torch.from_numpy(eps).cuda(), sigma)
+    torch.cuda.synchronize()
+    J = J.cpu().numpy()
+    assert np.isfinite(J).all()
+    for k in range(0, 4096, 64):
+        pa, pb = P["pose_a"][k], P["pose_b"][k]
+        ref = C.randomized_smoothing_jacobian(oracle_shape(P["type_a"][k], P["size_a"][k]), pa[:9].reshape(3, 3), pa[9:],
+                                              oracle_shape(P["type_b"][k], P["size_b"][k]), pb[:9].reshape(3, 3), pb[9:],
+                                              sigma, S, None, eps_samples=eps)
+        assert np.abs(J[k] - ref).max() <= 1e-8 * max(1.0, np.abs(ref).max()), k
