@@ -134,14 +134,19 @@ def _hull_core_distance(ca, cb):
                 best = (err, simplex, w)
         _, simplex, w = best
         return -depth, w @ ca[ia[simplex]], w @ cb[ib[simplex]], m
-    best = None
+    # the closest point of conv(D) to the origin is unique, but where it lies on an edge shared by
+    # two hull triangles (a face of D triangulated through it) the two candidates tie in distance
+    # to rounding while the edge foot of the wrong one is off by the square root of it; among
+    # such ties the triangle that contains the projection (all weights > 0) gives the point
+    cands = []
     for simplex in hull.simplices:
         w = closest_on_triangle(*D[simplex])
         y = w @ D[simplex]
-        d2 = y @ y
-        if best is None or d2 < best[0]:
-            best = (d2, simplex, w, y)
-    d2, simplex, w, y = best
+        cands.append((y @ y, simplex, w, y))
+    d2min = min(c[0] for c in cands)
+    ties = [c for c in cands if c[0] <= d2min * (1.0 + 1e-12)]
+    interior = [c for c in ties if np.all(c[2] > 0.0)]
+    d2, simplex, w, y = min(interior or ties, key=lambda c: c[0])
     d = np.sqrt(d2)
     return d, w @ ca[ia[simplex]], w @ cb[ib[simplex]], -y / d
 

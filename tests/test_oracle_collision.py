@@ -238,3 +238,17 @@ def test_appc_transposed_terms(kind):
     dcd = (C.dcd_dbody(model, q, pair, 0), C.dcd_dbody(model, q, pair, 1))
     terms = C.appc_dJctlam_dq(model, q, lam, pair, dcd)
     assert np.abs(terms - (moving - held)).max() <= 1e-5 * max(1.0, np.abs(moving).max())
+
+
+def test_witness_on_a_triangulated_face_diagonal():
+    """A sphere straight above the centre of a box face: the closest point of the Minkowski
+    difference lies on the diagonal through which Qhull triangulates that face, where the two
+    triangles tie in distance to rounding.  The closed form (n = -e_z from the sphere to the box,
+    phi = height - r - half height, c straight below the centre) must hold to rounding, also for
+    lateral offsets of 1e-12 to 1e-9 (the edge foot of the wrong triangle is off by ~1e-10)."""
+    for dx in (0.0, 1e-12, -3e-11, 2e-10, 1e-9):
+        for h in (0.07, 0.1, 0.2):
+            r = C.collide(C.sphere(0.05), I3, np.array([dx, -dx, h]), C.box(0.3, 0.2, 0.04), I3, np.zeros(3))
+            assert np.abs(r["n"] - [0.0, 0.0, -1.0]).max() <= 1e-14
+            assert abs(r["phi"] - (h - 0.05 - 0.04)) <= 1e-14
+            assert np.abs(r["c"][:2] - [dx, -dx]).max() <= 1e-14

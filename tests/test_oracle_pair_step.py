@@ -8,8 +8,9 @@ and of its Jacobians with App. C's contact-placement terms, no GPU.
   the collision detection) equals central differences of the whole step -- contact frame, Delassus
   matrix and NCP solve recomputed at every perturbed q -- for a capsule on an arm link against a
   fixed box and a sphere on one link against a box on another, in each mode (breaking, sticking,
-  sliding).  Leaving out either placement term (the one in d(J_c v+)/dq or the one in
-  d(J_c^T lambda)/dq) misses by orders of magnitude more than the tolerance.
+  sliding), and for both pairs in contact at once.  Leaving out either placement term (the one in
+  d(J_c v+)/dq or the one in d(J_c^T lambda)/dq) misses by orders of magnitude more than the
+  tolerance.
 * With no pair in contact the step is the free step v + dt ABA(q, v, tau)."""
 import types
 
@@ -111,6 +112,34 @@ def test_pair_step_jacobian_needs_both_placement_terms(monkeypatch, dropped):
     monkeypatch.setattr(C, dropped, lambda *a: 0.0 * full(*a))
     st = PS.step_jac(model, env, pairs, OPT)
     assert np.abs(st["dv_dq"] - fd[:, :7]).max() > 1e-2
+
+
+def _two_pair_case(seed, vscale, mu):
+    """The capsule-against-fixed-box pair of _world_case and, on the same arm at the same q, a
+    sphere at link 7's origin against a box on link 3, both active."""
+    model, env, pairs = _world_case(seed, vscale, mu)
+    rng = np.random.default_rng(seed + 1000)
+    q = env["q"]
+    _, p7 = C.body_pose(model, q, 6)
+    R3, p3 = C.body_pose(model, q, 2)
+    Eb = Rotation.from_rotvec(rng.normal(size=3)).as_matrix()
+    box_ctr = p7 - (R3 @ Eb)[:, 2] * (0.05 - 0.004 + 0.06)
+    pairs = pairs + [(C.sphere(0.05), 6, (I3, np.zeros(3)), C.box(0.05, 0.08, 0.06), 2, (Eb, R3.T @ (box_ctr - p3)), mu)]
+    return model, env, pairs
+
+
+@pytest.mark.parametrize("seed,vscale,mu,modes", [(21, 0.3, 0.3, (SLD, BRK)), (21, 0.02, 3.0, (STK, STK)),
+                                                  (20, 0.02, 3.0, (SLD, SLD))])
+def test_two_pairs_against_central_differences(seed, vscale, mu, modes):
+    """Two pairs in contact at once, each with its own moving contact frame (at seed 21 the capsule's
+    contact point lies on the diagonal of the box face's triangulation, the case the collision pin
+    test_witness_on_a_triangulated_face_diagonal covers)."""
+    model, env, pairs = _two_pair_case(seed, vscale, mu)
+    st = PS.step_jac(model, env, pairs, OPT)
+    assert st["act"] == [0, 1] and tuple(int(m) for m in st["modes"]) == modes
+    fd = PS.jacobian_fd(model, env, pairs, OPT)
+    J = np.concatenate([st["dv_dq"], st["dv_dv"], st["dv_dtau"]], axis=1)
+    assert np.abs(J - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max())
 
 
 def test_pair_step_without_contact_is_the_free_step():
