@@ -371,15 +371,18 @@ ds_status ds_profile_read(double* ms, int32_t* launches);
  *
  * A shape is a type and three sizes: DS_CONVEX_SPHERE (radius, -, -), DS_CONVEX_CAPSULE (half
  * length, radius, -; the segment runs along the body z axis from -half length to +half length),
- * DS_CONVEX_BOX (half extents hx, hy, hz).  A pose is 12 numbers: the rotation R (row-major, body
- * to world) and the position p.  For each of n_pairs pairs (A, B) ds_collide writes DS_COLLIDE_OUT
+ * DS_CONVEX_BOX (half extents hx, hy, hz), DS_CONVEX_HULL (first vertex, vertex count, radius: the
+ * convex hull of vertices first .. first + count - 1 of the pool hull_vertices, in the body frame,
+ * swept by the radius; 4 <= count <= DS_CONVEX_HULL_MAX, both integral).  A pose is 12 numbers:
+ * the rotation R (row-major, body to world) and the position p.  For each of n_pairs pairs (A, B) ds_collide writes DS_COLLIDE_OUT
  * numbers to out[DS_COLLIDE_OUT * k ...]: the signed distance phi (< 0: penetration), the contact
  * point c[3] (the midpoint of the witness points), the unit normal n[3] from A to B, the tangent
  * axes t1[3], t2[3] of the contact frame (Z along n; t1 = normalize(e_x - (n.e_x) n), e_y in place
  * of e_x when |n_x| > 0.9; t2 = n x t1) and the witness points on A's and B's surfaces sa[3],
- * sb[3].  Separated shapes take the closest points of their cores (point, segment or box corners)
- * by GJK; overlapping ones the penetration depth of the cores along the nearest facet of their
- * Minkowski difference.  Touching or crossing point and segment cores (sphere and capsule cores)
+ * sb[3].  Separated shapes take the closest points of their cores (point, segment, box corners or
+ * hull vertices) by GJK; overlapping ones the penetration depth of the cores along the nearest
+ * facet of their Minkowski difference (separating axes for a box with a point, segment or box;
+ * the expanding polytope, EPA, with a hull).  Touching or crossing point and segment cores (sphere and capsule cores)
  * have no normal: n is the world z axis there.  Where the witness points are not unique (parallel
  * faces or edges in contact) one of them is returned.
  *
@@ -388,12 +391,15 @@ ds_status ds_profile_read(double* ms, int32_t* launches);
  * on `stream` (a cudaStream_t, NULL = the default stream); the call returns after the launch.
  * The caller owns every buffer.  Errors: DS_EINVAL (n_pairs < 0, or a NULL pointer with
  * n_pairs > 0), DS_ECUDA (launch failure).  A pair with an unknown type gets NaN in all its
- * outputs.  n_pairs = 0 launches nothing. */
-enum { DS_CONVEX_SPHERE = 0, DS_CONVEX_CAPSULE = 1, DS_CONVEX_BOX = 2 };
+ * outputs, and so does a hull whose range is not inside the pool or a hull penetration that the
+ * expanding polytope cannot resolve within 64 vertices and 128 faces.  hull_vertices (FP64,
+ * 3 n_hull_vertices, device) may be NULL when no pair has a hull.  n_pairs = 0 launches nothing. */
+enum { DS_CONVEX_SPHERE = 0, DS_CONVEX_CAPSULE = 1, DS_CONVEX_BOX = 2, DS_CONVEX_HULL = 3 };
 #define DS_COLLIDE_OUT 19
+#define DS_CONVEX_HULL_MAX 32
 ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const double* size_a, const double* pose_a,
-                     const int32_t* type_b, const double* size_b, const double* pose_b, double* out,
-                     void* stream);
+                     const int32_t* type_b, const double* size_b, const double* pose_b,
+                     const double* hull_vertices, int32_t n_hull_vertices, double* out, void* stream);
 
 /* The derivative App. C takes of the collision detection: its zero-order randomized-smoothing
  * estimate.  For each pair, with the caller's samples eps_s = (u_A, w_A, u_B, w_B) (s < n_samples,
@@ -403,13 +409,14 @@ ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const double* size_
  *   J = 1 / (2 n_samples sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T,
  * f = (phi, c[3], n[3]) the first 7 outputs of ds_collide.  J is the gradient estimate of the
  * Gaussian-smoothed f with respect to the two twists: 7 x 12, row-major (columns: A's u, A's w,
- * B's u, B's w), written to jac[84 k ...].  Shapes and poses as for ds_collide; eps (FP64,
+ * B's u, B's w), written to jac[84 k ...].  Shapes, poses and hulls as for ds_collide; eps (FP64,
  * 12 n_samples) and jac (FP64, 84 n_pairs) are device pointers.  Errors: DS_EINVAL (n_pairs < 0,
  * n_samples <= 0 with n_pairs > 0, sigma not positive and finite, a NULL pointer with
  * n_pairs > 0), DS_ECUDA (launch failure). */
 ds_status ds_collide_smoothed(int32_t n_pairs, const int32_t* type_a, const double* size_a, const double* pose_a,
                               const int32_t* type_b, const double* size_b, const double* pose_b,
-                              int32_t n_samples, const double* eps, double sigma, double* jac, void* stream);
+                              const double* hull_vertices, int32_t n_hull_vertices, int32_t n_samples,
+                              const double* eps, double sigma, double* jac, void* stream);
 
 /* Measurement helper (no counterpart in the paper): runs `blocks` x 256 threads, each doing `iters`
  * rounds of 8 independent fused multiply-adds in FP64 (fp64 != 0) or FP32 and writing one value per

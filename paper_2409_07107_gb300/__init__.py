@@ -91,8 +91,8 @@ def lib():
         L.ds_profile.argtypes = [i32]
         L.ds_profile_read.argtypes = [vp, vp]
         L.ds_fma_peak.argtypes = [vp, i32, i32, i32, vp]
-        L.ds_collide.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.ds_collide_smoothed.argtypes = [i32, vp, vp, vp, vp, vp, vp, i32, vp, ctypes.c_double, vp, vp]
+        L.ds_collide.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp]
+        L.ds_collide_smoothed.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, ctypes.c_double, vp, vp]
         for f in ("ds_cotangent_to_tangent", "ds_cotangent_to_raw"):
             getattr(L, f).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.ds_autotune.argtypes = common + [i32, vp, ctypes.POINTER(ds_step_out), vp, vp, vp, vp, sz, vp, vp]
@@ -311,24 +311,32 @@ def fma_peak(out, blocks, iters, fp64, stream=None):
     _check(lib().ds_fma_peak(_ptr(out), blocks, iters, 1 if fp64 else 0, _stream(stream)))
 
 
-CONVEX_SPHERE, CONVEX_CAPSULE, CONVEX_BOX = 0, 1, 2
+CONVEX_SPHERE, CONVEX_CAPSULE, CONVEX_BOX, CONVEX_HULL = 0, 1, 2, 3
+CONVEX_HULL_MAX = 32
 COLLIDE_OUT = 19
 
 
-def collide(type_a, size_a, pose_a, type_b, size_b, pose_b, out=None, stream=None):
+def _hull_pool(hull_vertices):
+    return (ctypes.c_void_p(0), 0) if hull_vertices is None else (_ptr(hull_vertices), hull_vertices.shape[0])
+
+
+def collide(type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices=None, out=None, stream=None):
     """Collision detection between convex shapes (ds_collide), one pair per row: type (int32, n),
-    size (FP64, n x 3), pose (FP64, n x 12: R row-major, then p), all CUDA tensors.  Returns out
-    (FP64, n x 19): phi, c, n, t1, t2, the witness points on A's and B's surfaces."""
+    size (FP64, n x 3; a hull's is (first vertex, count, radius)), pose (FP64, n x 12: R row-major,
+    then p), hull_vertices (FP64, V x 3, body frames), all CUDA tensors.  Returns out (FP64,
+    n x 19): phi, c, n, t1, t2, the witness points on A's and B's surfaces."""
     import torch
     n = type_a.shape[0]
     if out is None:
         out = torch.empty((n, COLLIDE_OUT), dtype=torch.float64, device=type_a.device)
+    hv, nhv = _hull_pool(hull_vertices)
     _check(lib().ds_collide(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
-                            _ptr(pose_b), _ptr(out), _stream(stream)))
+                            _ptr(pose_b), hv, nhv, _ptr(out), _stream(stream)))
     return out
 
 
-def collide_smoothed(type_a, size_a, pose_a, type_b, size_b, pose_b, eps, sigma, out=None, stream=None):
+def collide_smoothed(type_a, size_a, pose_a, type_b, size_b, pose_b, eps, sigma, hull_vertices=None, out=None,
+                     stream=None):
     """Randomized-smoothing derivative of the collision detection (ds_collide_smoothed): eps (FP64,
     S x 12 CUDA tensor, samples of N(0, sigma^2 I)); returns (n x 7 x 12) d(phi, c, n)/d(twists of
     A and B)."""
@@ -336,8 +344,9 @@ def collide_smoothed(type_a, size_a, pose_a, type_b, size_b, pose_b, eps, sigma,
     n = type_a.shape[0]
     if out is None:
         out = torch.empty((n, 7, 12), dtype=torch.float64, device=type_a.device)
+    hv, nhv = _hull_pool(hull_vertices)
     _check(lib().ds_collide_smoothed(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
-                                     _ptr(pose_b), eps.shape[0], _ptr(eps), float(sigma), _ptr(out),
+                                     _ptr(pose_b), hv, nhv, eps.shape[0], _ptr(eps), float(sigma), _ptr(out),
                                      _stream(stream)))
     return out
 

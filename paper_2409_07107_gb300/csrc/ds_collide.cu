@@ -10,6 +10,7 @@ __global__ void __launch_bounds__(128) collide_kernel(int n, const int32_t* __re
                                                       const int32_t* __restrict__ type_b,
                                                       const double* __restrict__ size_b,
                                                       const double* __restrict__ pose_b,
+                                                      const double* __restrict__ hv, int n_hv,
                                                       double* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -22,14 +23,15 @@ __global__ void __launch_bounds__(128) collide_kernel(int n, const int32_t* __re
     pa[i] = pose_a[12 * k + i];
     pb[i] = pose_b[12 * k + i];
   }
-  ds::cd::collide(type_a[k], sa, pa, type_b[k], sb, pb, o);
+  ds::cd::collide(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, o);
   for (int i = 0; i < DS_COLLIDE_OUT; ++i) out[static_cast<size_t>(DS_COLLIDE_OUT) * k + i] = o[i];
 }
 
 __global__ void __launch_bounds__(128) collide_smoothed_kernel(
     int n, const int32_t* __restrict__ type_a, const double* __restrict__ size_a,
     const double* __restrict__ pose_a, const int32_t* __restrict__ type_b, const double* __restrict__ size_b,
-    const double* __restrict__ pose_b, int samples, const double* __restrict__ eps, double sigma,
+    const double* __restrict__ pose_b, const double* __restrict__ hv, int n_hv, int samples,
+    const double* __restrict__ eps, double sigma,
     double* __restrict__ jac) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(128) collide_smoothed_kernel(
     pa[i] = pose_a[12 * k + i];
     pb[i] = pose_b[12 * k + i];
   }
-  ds::cd::smoothing_jacobian(type_a[k], sa, pa, type_b[k], sb, pb, samples, eps, sigma, J);
+  ds::cd::smoothing_jacobian(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, samples, eps, sigma, J);
   for (int i = 0; i < 84; ++i) jac[static_cast<size_t>(84) * k + i] = J[i];
 }
 
@@ -50,28 +52,31 @@ __global__ void __launch_bounds__(128) collide_smoothed_kernel(
 
 extern "C" ds_status ds_collide_smoothed(int32_t n_pairs, const int32_t* type_a, const double* size_a,
                                          const double* pose_a, const int32_t* type_b, const double* size_b,
-                                         const double* pose_b, int32_t n_samples, const double* eps,
+                                         const double* pose_b, const double* hull_vertices,
+                                         int32_t n_hull_vertices, int32_t n_samples, const double* eps,
                                          double sigma, double* jac, void* stream) {
-  if (n_pairs < 0) return DS_EINVAL;
+  if (n_pairs < 0 || n_hull_vertices < 0) return DS_EINVAL;
   if (n_pairs == 0) return DS_OK;
   if (!type_a || !size_a || !pose_a || !type_b || !size_b || !pose_b || !eps || !jac) return DS_EINVAL;
   if (n_samples <= 0 || !(sigma > 0.0) || !(sigma < 1e300)) return DS_EINVAL;
   const int threads = 128;
   const int blocks = (n_pairs + threads - 1) / threads;
   collide_smoothed_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
-      n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, n_samples, eps, sigma, jac);
+      n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, n_samples, eps,
+      sigma, jac);
   return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ECUDA;
 }
 
 extern "C" ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const double* size_a,
                                 const double* pose_a, const int32_t* type_b, const double* size_b,
-                                const double* pose_b, double* out, void* stream) {
-  if (n_pairs < 0) return DS_EINVAL;
+                                const double* pose_b, const double* hull_vertices, int32_t n_hull_vertices,
+                                double* out, void* stream) {
+  if (n_pairs < 0 || n_hull_vertices < 0) return DS_EINVAL;
   if (n_pairs == 0) return DS_OK;
   if (!type_a || !size_a || !pose_a || !type_b || !size_b || !pose_b || !out) return DS_EINVAL;
   const int threads = 128;
   const int blocks = (n_pairs + threads - 1) / threads;
-  collide_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(n_pairs, type_a, size_a, pose_a,
-                                                                              type_b, size_b, pose_b, out);
+  collide_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+      n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, out);
   return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ECUDA;
 }

@@ -3,7 +3,8 @@
 // world poses.  FP64, host- and device-callable, one pair per thread.
 //
 // Every shape is a core swept by a radius: a sphere is a point + r, a capsule a segment along its
-// body z axis (from -half_length to +half_length) + r, a box its 8 corners + 0.  The signed
+// body z axis (from -half_length to +half_length) + r, a box its 8 corners + 0, a hull the convex
+// hull of up to 32 vertices (a range of a shared vertex pool, body frame) + r.  The signed
 // distance is the distance of the cores minus rA + rB when the cores are apart, and minus
 // (penetration depth of the cores + rA + rB) when they overlap.
 //
@@ -17,7 +18,9 @@
 //   direction of each core, so the minimum over those (15 axes for two boxes, 6 for a segment and
 //   a box, 3 for a point and a box) is the depth (the separating-axis form; GJK/EPA's polytope
 //   expansion reaches the same facet).  The same axes decide whether cores with a box overlap at
-//   all (a negative minimum is a separating axis), so GJK runs only on separated cores there.  The witness points are the projection of the origin on
+//   all (a negative minimum is a separating axis), so GJK runs only on separated cores there.
+//   A hull has no such short axis list: overlapping cores with a hull take the expanding polytope
+//   (EPA, van den Bergen 2001) from GJK's tetrahedron around the origin.  The witness points are the projection of the origin on
 //   that facet, split over the two cores' support features.
 // * The contact point is the midpoint of the witness points moved to the surfaces (pA + rA n,
 //   pB - rB n); the tangent axes follow the plane contacts' rule: t1 = normalize(e_x - (n.e_x) n),
@@ -31,12 +34,15 @@ namespace ds {
 namespace cd {
 
 constexpr int kGjkMaxIter = 64;
+constexpr int kCoreMax = DS_CONVEX_HULL_MAX;   // vertices of a hull core (32)
+enum CoreKind { kPoint = 0, kSegment = 1, kBox = 2, kHull = 3 };
 
-// A core in world coordinates: 1 point, 2 segment end points, or 8 box corners, plus the radius
-// and (for a box) its axes, the directions of its faces and edges.
+// A core in world coordinates: 1 point, 2 segment end points, 8 box corners or up to 32 hull
+// vertices, plus the radius and (for a box) its axes, the directions of its faces and edges.
 struct Core {
+  int kind;
   int nv;
-  double v[8][3];
+  double v[kCoreMax][3];
   double r;
   double axis[3][3];   // box: the columns of R; segment: axis[0] = its direction
   int naxis;           // 3 for a box, 1 for a segment, 0 for a point
@@ -48,17 +54,31 @@ DS_HDI void sub3(const double* a, const double* b, double* o) {
 
 DS_HDI void copy3(const double* a, double* o) { o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; }
 
-// Build the world core of shape (type, size) at pose (R row-major, p).  Returns false for an
-// unknown type.
-DS_HDI bool make_core(int type, const double* size, const double* R, const double* p, Core& c) {
+// Build the world core of shape (type, size) at pose (R row-major, p); a hull's vertices come
+// from the pool hv (n_hv vertices, body frame).  Returns false for an unknown type or a hull whose
+// vertex range is not an integral range of 4..32 vertices inside the pool.
+DS_HDI bool make_core(int type, const double* size, const double* R, const double* p, const double* hv,
+                      int n_hv, Core& c) {
+  if (type == DS_CONVEX_HULL) {
+    const double f = size[0], n = size[1];
+    if (!(f >= 0.0 && n >= 4.0 && n <= kCoreMax && f == floor(f) && n == floor(n))) return false;
+    const int first = static_cast<int>(f), count = static_cast<int>(n);
+    if (hv == nullptr || first > n_hv - count) return false;
+    c.kind = kHull; c.nv = count; c.naxis = 0; c.r = size[2];
+    for (int i = 0; i < count; ++i) {
+      const double* x = hv + 3 * (first + i);
+      for (int k = 0; k < 3; ++k) c.v[i][k] = p[k] + R[3 * k] * x[0] + R[3 * k + 1] * x[1] + R[3 * k + 2] * x[2];
+    }
+    return true;
+  }
   if (type == DS_CONVEX_SPHERE) {
-    c.nv = 1; c.naxis = 0; c.r = size[0];
+    c.kind = kPoint; c.nv = 1; c.naxis = 0; c.r = size[0];
     copy3(p, c.v[0]);
     return true;
   }
   if (type == DS_CONVEX_CAPSULE) {
     const double h = size[0];
-    c.nv = 2; c.naxis = 1; c.r = size[1];
+    c.kind = kSegment; c.nv = 2; c.naxis = 1; c.r = size[1];
     for (int k = 0; k < 3; ++k) {
       const double z = R[3 * k + 2];
       c.v[0][k] = p[k] - h * z;
@@ -68,7 +88,7 @@ DS_HDI bool make_core(int type, const double* size, const double* R, const doubl
     return true;
   }
   if (type == DS_CONVEX_BOX) {
-    c.nv = 8; c.naxis = 3; c.r = 0.0;
+    c.kind = kBox; c.nv = 8; c.naxis = 3; c.r = 0.0;
     for (int i = 0; i < 8; ++i) {
       const double s0 = (i & 4) ? size[0] : -size[0];
       const double s1 = (i & 2) ? size[1] : -size[1];
@@ -249,8 +269,10 @@ DS_HDI bool closest_reduce(Simplex& s, double* v) {
 
 // Distance of the cores by GJK: returns true when they overlap (the origin in D, or a distance
 // below 1e-12); the witness points pa (on A), pb (on B) are those of the last simplex that did
-// not contain the origin.
-DS_HDI bool gjk(const Core& A, const Core& B, double* pa, double* pb) {
+// not contain the origin.  When the origin lies inside a tetrahedron of support points, that
+// tetrahedron is copied to *tet (if given) and tet->n = 4; otherwise tet->n = 0.
+DS_HDI bool gjk(const Core& A, const Core& B, double* pa, double* pb, Simplex* tet = nullptr) {
+  if (tet) tet->n = 0;
   Simplex s;
   s.n = 1;
   s.ia[0] = 0;
@@ -278,6 +300,7 @@ DS_HDI bool gjk(const Core& A, const Core& B, double* pa, double* pb) {
     ++s.n;
     double vn[3];
     if (closest_reduce(s, vn)) {
+      if (tet) *tet = s;
       s = prev;
       overlap = true;
       break;
@@ -345,9 +368,9 @@ DS_HDI void project(const Core& c, const double* u, double& lo, double& hi) {
 DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, double* pa, double* pb) {
   double cand[15][3];
   int nc = 0;
-  if (A.nv == 8)
+  if (A.kind == kBox)
     for (int i = 0; i < 3; ++i) copy3(A.axis[i], cand[nc++]);
-  if (B.nv == 8)
+  if (B.kind == kBox)
     for (int j = 0; j < 3; ++j) copy3(B.axis[j], cand[nc++]);
   for (int i = 0; i < A.naxis; ++i)
     for (int j = 0; j < B.naxis; ++j) cross3(A.axis[i], B.axis[j], cand[nc++]);
@@ -377,7 +400,7 @@ DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, 
   if (depth < 0.0) return;
   // the support features of A along m and of B along -m
   const double tol = 1e-9 * (1.0 + fabs(hi_best) + fabs(lo_best));
-  int fa[8], fb[8], na = 0, nb = 0;
+  int fa[kCoreMax], fb[kCoreMax], na = 0, nb = 0;
   for (int i = 0; i < A.nv; ++i)
     if (dot3(m, A.v[i]) >= hi_best - tol) fa[na++] = i;
   for (int j = 0; j < B.nv; ++j)
@@ -402,26 +425,190 @@ DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, 
   }
 }
 
-// Collision detection of shape A (type, size, pose) and shape B.  Writes DS_COLLIDE_OUT numbers:
-// phi, c[3], n[3], t1[3], t2[3], the witness points on the surfaces sa[3], sb[3].  An unknown type
-// gives NaN throughout.
+// ------------------------------------------------------------------------------------------ EPA
+// Overlapping cores with a hull on either side have no short list of candidate axes; their
+// nearest facet of D is found by the expanding polytope (van den Bergen 2001): start from GJK's
+// tetrahedron around the origin and repeatedly push out the face nearest the origin by the support
+// point along its normal, replacing the faces that point sees by a fan from it to their horizon.
+constexpr int kEpaMaxV = 64;
+constexpr int kEpaMaxF = 128;
+constexpr int kEpaMaxE = 96;
+constexpr int kEpaMaxIter = 64;
+
+struct Polytope {
+  int nv, nf;
+  double w[kEpaMaxV][3];
+  int ia[kEpaMaxV], ib[kEpaMaxV];
+  int f[kEpaMaxF][3];
+  double n[kEpaMaxF][3];   // unit outward normal
+  double d[kEpaMaxF];      // distance of the face's plane from the origin (>= 0 up to rounding)
+};
+
+// Face slot k = (i, j, l), counter-clockwise seen from outside; false for a face of zero area.
+DS_HDI bool epa_face(Polytope& P, int k, int i, int j, int l) {
+  double e1[3], e2[3], nr[3];
+  sub3(P.w[j], P.w[i], e1);
+  sub3(P.w[l], P.w[i], e2);
+  cross3(e1, e2, nr);
+  const double len = sqrt(dot3(nr, nr));
+  if (!(len > 1e-15 * sqrt(dot3(e1, e1) * dot3(e2, e2)))) return false;
+  P.f[k][0] = i;
+  P.f[k][1] = j;
+  P.f[k][2] = l;
+  for (int c = 0; c < 3; ++c) P.n[k][c] = nr[c] / len;
+  P.d[k] = dot3(P.n[k], P.w[i]);
+  return true;
+}
+
+DS_HDI int epa_nearest(const Polytope& P) {
+  int best = 0;
+  for (int k = 1; k < P.nf; ++k)
+    if (P.d[k] < P.d[best]) best = k;
+  return best;
+}
+
+// Penetration of overlapping cores from GJK's tetrahedron tet around the origin: depth, the unit
+// axis m from A to B (moving A by -depth m separates the cores) and the witness points pa, pb with
+// pa - pb = depth m (the projection of the origin on the nearest facet, in barycentric weights of
+// its triangle).  Stops when the support point along the nearest face's normal adds less than
+// 1e-12 (relative to the coordinates) to its distance.  Returns false when the polytope runs out
+// of its 64 vertices, 128 faces or 96 horizon edges, or a new face has zero area.
+DS_HDI bool epa(const Core& A, const Core& B, const Simplex& tet, double& depth, double* m, double* pa,
+                double* pb) {
+  Polytope P;
+  P.nv = 4;
+  P.nf = 0;
+  double scale = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    copy3(tet.w[i], P.w[i]);
+    P.ia[i] = tet.ia[i];
+    P.ib[i] = tet.ib[i];
+    scale = fmax(scale, sqrt(dot3(P.w[i], P.w[i])));
+  }
+  const double tol = 1e-12 * fmax(scale, 1e-300);
+  const int F[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
+  for (int f = 0; f < 4; ++f) {
+    int i = F[f][0], j = F[f][1], l = F[f][2];
+    double e1[3], e2[3], nr[3], eo[3];
+    sub3(P.w[j], P.w[i], e1);
+    sub3(P.w[l], P.w[i], e2);
+    cross3(e1, e2, nr);
+    sub3(P.w[F[f][3]], P.w[i], eo);
+    if (dot3(nr, eo) > 0.0) {   // make the normal point away from the opposite vertex
+      const int t = j;
+      j = l;
+      l = t;
+    }
+    if (!epa_face(P, P.nf, i, j, l)) return false;
+    ++P.nf;
+  }
+  int edges[kEpaMaxE][2];
+  for (int it = 0; it < kEpaMaxIter; ++it) {
+    const int best = epa_nearest(P);
+    const double* nb = P.n[best];
+    const double neg[3] = {-nb[0], -nb[1], -nb[2]};
+    const int ia = support(A, nb), ib = support(B, neg);
+    bool dup = false;
+    for (int v = 0; v < P.nv; ++v) dup = dup || (P.ia[v] == ia && P.ib[v] == ib);
+    double w[3];
+    sub3(A.v[ia], B.v[ib], w);
+    if (dup || dot3(nb, w) - P.d[best] <= tol) break;
+    if (P.nv == kEpaMaxV) return false;
+    const int nw = P.nv++;
+    copy3(w, P.w[nw]);
+    P.ia[nw] = ia;
+    P.ib[nw] = ib;
+    // remove the faces that see w; their edges not shared by two of them form the horizon
+    int ne = 0, kept = 0;
+    for (int k = 0; k < P.nf; ++k) {
+      double rel[3];
+      sub3(w, P.w[P.f[k][0]], rel);
+      if (dot3(P.n[k], rel) > 0.0) {
+        for (int e = 0; e < 3; ++e) {
+          const int a = P.f[k][e], b = P.f[k][(e + 1) % 3];
+          int found = -1;
+          for (int x = 0; x < ne; ++x)
+            if (edges[x][0] == b && edges[x][1] == a) found = x;
+          if (found >= 0) {
+            --ne;
+            edges[found][0] = edges[ne][0];
+            edges[found][1] = edges[ne][1];
+          } else {
+            if (ne == kEpaMaxE) return false;
+            edges[ne][0] = a;
+            edges[ne][1] = b;
+            ++ne;
+          }
+        }
+      } else {
+        if (kept != k) {
+          for (int c = 0; c < 3; ++c) {
+            P.f[kept][c] = P.f[k][c];
+            P.n[kept][c] = P.n[k][c];
+          }
+          P.d[kept] = P.d[k];
+        }
+        ++kept;
+      }
+    }
+    P.nf = kept;
+    if (ne < 3) return false;
+    for (int x = 0; x < ne; ++x) {
+      if (P.nf == kEpaMaxF) return false;
+      if (!epa_face(P, P.nf, edges[x][0], edges[x][1], nw)) return false;
+      ++P.nf;
+    }
+  }
+  const int best = epa_nearest(P);
+  depth = P.d[best];
+  copy3(P.n[best], m);
+  // barycentric weights of y = depth m in the face's triangle (a, b, c)
+  const int* fv = P.f[best];
+  double v0[3], v1[3], v2[3];
+  sub3(P.w[fv[1]], P.w[fv[0]], v0);
+  sub3(P.w[fv[2]], P.w[fv[0]], v1);
+  for (int c = 0; c < 3; ++c) v2[c] = depth * m[c] - P.w[fv[0]][c];
+  const double d00 = dot3(v0, v0), d01 = dot3(v0, v1), d11 = dot3(v1, v1);
+  const double d20 = dot3(v2, v0), d21 = dot3(v2, v1);
+  const double den = d00 * d11 - d01 * d01;
+  const double lb = (d11 * d20 - d01 * d21) / den, lc = (d00 * d21 - d01 * d20) / den;
+  const double l[3] = {1.0 - lb - lc, lb, lc};
+  for (int c = 0; c < 3; ++c) {
+    pa[c] = 0.0;
+    pb[c] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      pa[c] += l[k] * A.v[P.ia[fv[k]]][c];
+      pb[c] += l[k] * B.v[P.ib[fv[k]]][c];
+    }
+  }
+  return true;
+}
+
+// Collision detection of shape A (type, size, pose) and shape B (hull vertices from the pool hv
+// of n_hv vertices).  Writes DS_COLLIDE_OUT numbers: phi, c[3], n[3], t1[3], t2[3], the witness
+// points on the surfaces sa[3], sb[3].  An unknown type, a bad hull range, or a hull penetration
+// the expanding polytope cannot resolve gives NaN throughout.
 DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int type_b,
-                    const double* size_b, const double* pose_b, double* out) {
+                    const double* size_b, const double* pose_b, const double* hv, int n_hv, double* out) {
   Core A, B;
-  if (!make_core(type_a, size_a, pose_a, pose_a + 9, A) || !make_core(type_b, size_b, pose_b, pose_b + 9, B)) {
+  if (!make_core(type_a, size_a, pose_a, pose_a + 9, hv, n_hv, A) ||
+      !make_core(type_b, size_b, pose_b, pose_b + 9, hv, n_hv, B)) {
     for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
     return;
   }
   double d, pa[3], pb[3], n[3];
-  const bool has_box = A.nv == 8 || B.nv == 8;
+  const bool hull = A.kind == kHull || B.kind == kHull;
+  const bool has_box = !hull && (A.kind == kBox || B.kind == kBox);
   double depth = -1.0, m[3] = {0.0, 0.0, 1.0};
-  // with a box, the separating-axis test decides overlap exactly; GJK measures separated cores
+  // with a box (and no hull), the separating-axis test decides overlap exactly; GJK measures
+  // separated cores
   if (has_box) penetration(A, B, depth, m, pa, pb);
   if (has_box && depth >= 0.0) {
     d = -depth;
     copy3(m, n);
   } else {
-    const bool overlap = gjk(A, B, pa, pb);
+    Simplex tet;
+    const bool overlap = gjk(A, B, pa, pb, &tet);
     double diff[3];
     sub3(pb, pa, diff);
     d = sqrt(dot3(diff, diff));
@@ -433,8 +620,15 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
       d = -depth;
       copy3(m, n);
       for (int k = 0; k < 3; ++k) pb[k] = pa[k] + d * n[k];
+    } else if (hull && tet.n == 4) {
+      if (!epa(A, B, tet, depth, n, pa, pb)) {
+        for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
+        return;
+      }
+      d = -depth;
     } else {
-      // touching or crossing point and segment cores have no normal: take the world z axis
+      // touching cores (within 1e-12), or crossing point and segment cores: no normal; take the
+      // world z axis
       d = 0.0;
       n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
     }
@@ -505,18 +699,18 @@ DS_HDI void twist_pose(const double* pose, const double* xi, double sgn, double*
 // J = 1 / (2 S sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T, eps_s = (A's (u, w), B's (u, w))
 // the caller's samples (S x 12, drawn from N(0, sigma^2 I)).  J is 7 x 12, row-major.
 DS_HDI void smoothing_jacobian(int type_a, const double* size_a, const double* pose_a, int type_b,
-                               const double* size_b, const double* pose_b, int samples,
-                               const double* eps, double sigma, double* J) {
+                               const double* size_b, const double* pose_b, const double* hv, int n_hv,
+                               int samples, const double* eps, double sigma, double* J) {
   for (int k = 0; k < 84; ++k) J[k] = 0.0;
   double qa[12], qb[12], fp[DS_COLLIDE_OUT], fm[DS_COLLIDE_OUT];
   for (int s = 0; s < samples; ++s) {
     const double* e = eps + 12 * s;
     twist_pose(pose_a, e, 1.0, qa);
     twist_pose(pose_b, e + 6, 1.0, qb);
-    collide(type_a, size_a, qa, type_b, size_b, qb, fp);
+    collide(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fp);
     twist_pose(pose_a, e, -1.0, qa);
     twist_pose(pose_b, e + 6, -1.0, qb);
-    collide(type_a, size_a, qa, type_b, size_b, qb, fm);
+    collide(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fm);
     for (int i = 0; i < 7; ++i) {
       const double df = fp[i] - fm[i];
       for (int j = 0; j < 12; ++j) J[12 * i + j] += df * e[j];

@@ -94,18 +94,20 @@ def test_step_rejects_bad_arguments(L):
 
 def test_collide_rejects_bad_arguments(L):
     buf = ctypes.c_void_p(1)
-    assert L.ds_collide(-1, buf, buf, buf, buf, buf, buf, buf, None) == ds.DS_EINVAL
-    assert L.ds_collide(4, None, buf, buf, buf, buf, buf, buf, None) == ds.DS_EINVAL
-    assert L.ds_collide(4, buf, buf, buf, buf, buf, buf, None, None) == ds.DS_EINVAL
-    assert L.ds_collide(0, None, None, None, None, None, None, None, None) == ds.DS_OK
+    assert L.ds_collide(-1, buf, buf, buf, buf, buf, buf, None, 0, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide(4, None, buf, buf, buf, buf, buf, None, 0, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide(4, buf, buf, buf, buf, buf, buf, None, 0, None, None) == ds.DS_EINVAL
+    assert L.ds_collide(4, buf, buf, buf, buf, buf, buf, buf, -1, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide(0, None, None, None, None, None, None, None, 0, None, None) == ds.DS_OK
 
 
 def test_collide_smoothed_rejects_bad_arguments(L):
     buf = ctypes.c_void_p(1)
-    args = [buf] * 6
+    args = [buf] * 6 + [None, 0]
     assert L.ds_collide_smoothed(-1, *args, 4, buf, 1e-3, buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(4, *args, 0, buf, 1e-3, buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(4, *args, 4, buf, 0.0, buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(4, *args, 4, buf, float("nan"), buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(4, *args, 4, None, 1e-3, buf, None) == ds.DS_EINVAL
-    assert L.ds_collide_smoothed(0, *([None] * 6), 0, None, 0.0, None, None) == ds.DS_OK
+    assert L.ds_collide_smoothed(4, *([buf] * 6), buf, -2, 4, buf, 1e-3, buf, None) == ds.DS_EINVAL
+    assert L.ds_collide_smoothed(0, *([None] * 6), None, 0, 0, None, 0.0, None, None) == ds.DS_OK

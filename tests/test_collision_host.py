@@ -21,21 +21,25 @@ import pytest
 from oracle import collision as C
 from paper_2409_07107_gb300 import build
 
-from tests.convex_pairs import BOX, CAPSULE, SPHERE, oracle_shape, pairs
+from tests.convex_pairs import BOX, CAPSULE, HULL, SPHERE, oracle_shape, pairs
 
 PROG = r'''
 #include "ds_collision.cuh"
 #include <cstdio>
+#include <vector>
 int main() {
-  int ta, tb;
+  int ta, tb, nhv;
   double sa[3], sb[3], pa[12], pb[12], out[DS_COLLIDE_OUT];
+  if (std::scanf("%d", &nhv) != 1) return 1;
+  std::vector<double> hv(3 * nhv + 3);
+  for (int i = 0; i < 3 * nhv; ++i) std::scanf("%lf", &hv[i]);
   while (std::scanf("%d", &ta) == 1) {
     for (double& x : sa) std::scanf("%lf", &x);
     for (double& x : pa) std::scanf("%lf", &x);
     std::scanf("%d", &tb);
     for (double& x : sb) std::scanf("%lf", &x);
     for (double& x : pb) std::scanf("%lf", &x);
-    ds::cd::collide(ta, sa, pa, tb, sb, pb, out);
+    ds::cd::collide(ta, sa, pa, tb, sb, pb, hv.data(), nhv, out);
     for (int k = 0; k < DS_COLLIDE_OUT; ++k) std::printf("%.17g ", out[k]);
     std::printf("\n");
   }
@@ -61,7 +65,8 @@ def _host_build(tmp_path_factory, contracted):
     assert r.returncode == 0, r.stderr[-2000:]
 
     def run(P):
-        lines = []
+        hv = P.get("hull_vertices", np.zeros((0, 3)))
+        lines = ["%d %s" % (len(hv), " ".join("%.17g" % x for x in np.ravel(hv)))]
         for k in range(len(P["type_a"])):
             fa = " ".join("%.17g" % x for x in np.concatenate([P["size_a"][k], P["pose_a"][k]]))
             fb = " ".join("%.17g" % x for x in np.concatenate([P["size_b"][k], P["pose_b"][k]]))
@@ -78,8 +83,9 @@ def host_collide(request, tmp_path_factory):
 
 
 def oracle_collide(P, k):
-    sa = oracle_shape(P["type_a"][k], P["size_a"][k])
-    sb = oracle_shape(P["type_b"][k], P["size_b"][k])
+    pool = P.get("hull_vertices")
+    sa = oracle_shape(P["type_a"][k], P["size_a"][k], pool)
+    sb = oracle_shape(P["type_b"][k], P["size_b"][k], pool)
     pa, pb = P["pose_a"][k], P["pose_b"][k]
     return C.collide(sa, pa[:9].reshape(3, 3), pa[9:], sb, pb[:9].reshape(3, 3), pb[9:])
 
@@ -107,6 +113,24 @@ def test_host_collide_against_oracle(host_collide, types):
     got = host_collide(P)
     n_over, n_apart = compare(P, got)
     assert n_over >= 10 and n_apart >= 10
+
+
+@pytest.mark.parametrize("types", [[(HULL, HULL)], [(HULL, BOX), (BOX, HULL)], [(HULL, SPHERE), (CAPSULE, HULL)]])
+def test_host_collide_hulls_against_oracle(host_collide, types):
+    """Convex hulls (8 to 20 vertices, swept by a radius): GJK when apart, the expanding polytope
+    when the cores overlap, against the oracle's hull of the whole Minkowski difference."""
+    P = pairs(120, seed=300 + types[0][1] * 5 + len(types), types=types)
+    got = host_collide(P)
+    n_over, n_apart = compare(P, got)
+    assert n_over >= 10 and n_apart >= 10
+
+
+def test_host_collide_bad_hull_range_is_nan(host_collide):
+    P = pairs(3, seed=6, types=[(HULL, BOX)])
+    P["size_a"][1][1] = 40.0                              # more than 32 vertices
+    P["size_a"][2][0] = len(P["hull_vertices"]) - 2.0     # runs past the pool
+    got = host_collide(P)
+    assert np.isfinite(got[0]).all() and np.isnan(got[1]).all() and np.isnan(got[2]).all()
 
 
 def test_host_collide_witness_identity_large_batch(host_collide):
@@ -142,7 +166,7 @@ int main() {
     std::scanf("%d", &tb);
     for (double& x : sb) std::scanf("%lf", &x);
     for (double& x : pb) std::scanf("%lf", &x);
-    ds::cd::smoothing_jacobian(ta, sa, pa, tb, sb, pb, S, eps.data(), sigma, J);
+    ds::cd::smoothing_jacobian(ta, sa, pa, tb, sb, pb, nullptr, 0, S, eps.data(), sigma, J);
     for (int k = 0; k < 84; ++k) std::printf("%.17g ", J[k]);
     std::printf("\n");
   }

@@ -7,6 +7,8 @@ oracle's collision detection by its definition (oracle/collision.py).
 * 262144 pairs (the size of a batch of 16384 humanoids with 16 candidate pairs each) with a
   ragged tail: 512 sampled pairs against the oracle, and every pair checked for what holds at any
   size: n unit, (t1, t2, n) orthonormal and right-handed, sb - sa = phi n;
+* convex hulls against hulls, boxes, spheres and capsules (GJK and the expanding polytope), every
+  pair compared with the oracle;
 * an unknown shape type gives NaN for that pair only, and an empty batch launches nothing;
 * the randomized-smoothing derivative (ds_collide_smoothed) against the oracle's estimator fed the
   same samples."""
@@ -14,7 +16,7 @@ import numpy as np
 import pytest
 
 import paper_2409_07107_gb300 as ds
-from tests.convex_pairs import pairs
+from tests.convex_pairs import BOX, CAPSULE, HULL, SPHERE, pairs
 from tests.test_collision_host import compare, oracle_collide
 
 pytestmark = pytest.mark.gpu
@@ -28,7 +30,8 @@ def _device(P):
 def _run(P):
     import torch
     D = _device(P)
-    out = ds.collide(D["type_a"], D["size_a"], D["pose_a"], D["type_b"], D["size_b"], D["pose_b"])
+    hv = D["hull_vertices"] if P["hull_vertices"].size else None
+    out = ds.collide(D["type_a"], D["size_a"], D["pose_a"], D["type_b"], D["size_b"], D["pose_b"], hull_vertices=hv)
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -38,6 +41,17 @@ def test_collide_against_oracle():
     got = _run(P)
     n_over, n_apart = compare(P, got)
     assert n_over >= 200 and n_apart >= 200
+
+
+def test_collide_hulls_against_oracle():
+    """Convex hulls (8 to 20 vertices from a shared pool) against hulls, boxes, spheres and
+    capsules: GJK when apart, the expanding polytope when the cores overlap; 1536 pairs, every one
+    compared with the oracle."""
+    P = pairs(1536, seed=4242, types=[(HULL, HULL), (HULL, BOX), (SPHERE, HULL), (HULL, CAPSULE)])
+    got = _run(P)
+    assert np.isfinite(got).all()
+    n_over, n_apart = compare(P, got)
+    assert n_over >= 150 and n_apart >= 150
 
 
 def test_collide_large_batch_sampled_and_properties():
@@ -53,7 +67,7 @@ def test_collide_large_batch_sampled_and_properties():
     assert np.abs(sb - sa - phi[:, None] * nrm).max() <= 1e-12
     rng = np.random.default_rng(3)
     idx = np.concatenate([rng.choice(n, size=500, replace=False), np.arange(n - 12, n)])
-    sub = {k: v[idx] for k, v in P.items()}
+    sub = {k: (v if k == "hull_vertices" else v[idx]) for k, v in P.items()}
     compare(sub, got[idx])
 
 
