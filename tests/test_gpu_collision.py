@@ -7,8 +7,6 @@ oracle's collision detection by its definition (oracle/collision.py).
 * 262144 pairs (the size of a batch of 16384 humanoids with 16 candidate pairs each) with a
   ragged tail: 512 sampled pairs against the oracle, and every pair checked for what holds at any
   size: n unit, (t1, t2, n) orthonormal and right-handed, sb - sa = phi n;
-* convex hulls against hulls, boxes, spheres and capsules (GJK and the expanding polytope), every
-  pair compared with the oracle;
 * an unknown shape type gives NaN for that pair only, and an empty batch launches nothing;
 * the randomized-smoothing derivative (ds_collide_smoothed) against the oracle's estimator fed the
   same samples."""
@@ -16,7 +14,7 @@ import numpy as np
 import pytest
 
 import paper_2409_07107_gb300 as ds
-from tests.convex_pairs import BOX, CAPSULE, HULL, SPHERE, pairs
+from tests.convex_pairs import pairs
 from tests.test_collision_host import compare, oracle_collide
 
 pytestmark = pytest.mark.gpu
@@ -41,17 +39,6 @@ def test_collide_against_oracle():
     got = _run(P)
     n_over, n_apart = compare(P, got)
     assert n_over >= 200 and n_apart >= 200
-
-
-def test_collide_hulls_against_oracle():
-    """Convex hulls (8 to 20 vertices from a shared pool) against hulls, boxes, spheres and
-    capsules: GJK when apart, the expanding polytope when the cores overlap; 1536 pairs, every one
-    compared with the oracle."""
-    P = pairs(1536, seed=4242, types=[(HULL, HULL), (HULL, BOX), (SPHERE, HULL), (HULL, CAPSULE)])
-    got = _run(P)
-    assert np.isfinite(got).all()
-    n_over, n_apart = compare(P, got)
-    assert n_over >= 150 and n_apart >= 150
 
 
 def test_collide_large_batch_sampled_and_properties():
