@@ -105,7 +105,7 @@ def test_appc_terms_against_oracle(tmp_path, kind):
 
 
 def test_appc_compiles_for_sm103a(tmp_path):
-    """The same functions compile as device code for sm_103a (a kernel calling both; no GPU)."""
+    """The same functions compile as device code for sm_103a (a kernel calling them; no GPU)."""
     nvcc = build._nvcc()
     if not ((os.path.isabs(nvcc) and os.path.exists(nvcc)) or shutil.which(nvcc)):
         pytest.skip("nvcc not found")
@@ -118,9 +118,74 @@ __global__ void k(const double* in, double* out) {
                        nullptr, nullptr, out);
   ds::cd::appc_dJctlam_dq(7, in + 108, in, in + 9, in + 12, in + 21, in + 30, in + 72, nullptr, nullptr, nullptr,
                           nullptr, scratch, out + 21);
+  ds::cd::dcd_dbody(2, in, in + 3, in + 15, 0, in + 27, in + 30, in + 42, nullptr, 0, 1, 1e-6, out + 70);
 }
 ''')
     r = subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I" + build.INCLUDE,
                         "-I" + build.CSRC, "-c", str(src), "-o", str(tmp_path / "appc_dev.o")],
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
+
+
+PROG_DCD = r'''
+#include "ds_appc.cuh"
+#include <cstdio>
+static void rd(double* x, int n) { for (int i = 0; i < n; ++i) if (std::scanf("%lf", &x[i]) != 1) x[i] = 0.0; }
+int main() {
+  int ta, tb, which;
+  while (std::scanf("%d %d %d", &ta, &tb, &which) == 3) {
+    double sa[3], sb[3], Ma[12], Mb[12], oa[12], ob[12], h, out[36];
+    rd(sa, 3); rd(Ma, 12); rd(oa, 12); rd(sb, 3); rd(Mb, 12); rd(ob, 12); rd(&h, 1);
+    const bool ok = ds::cd::dcd_dbody(ta, sa, Ma, oa, tb, sb, Mb, ob, nullptr, 0, which, h, out);
+    std::printf("%d ", ok ? 1 : 0);
+    for (double x : out) std::printf("%.17g ", x);
+    std::printf("\n");
+  }
+  return 0;
+}
+'''
+
+
+def _device_shape(shape):
+    """(type, size) of the device collision detection for the oracle's sphere, capsule or box."""
+    core, r = shape.core, shape.radius
+    if len(core) == 1:
+        return 0, [r, 0.0, 0.0]
+    if len(core) == 2:
+        return 1, [float(core[1][2]), r, 0.0]
+    return 2, list(np.abs(core[-1]))
+
+
+def test_dcd_dbody_against_oracle(tmp_path):
+    """dCD/dM_i by central differences of the device collision detection, in the body's local twist,
+    against the oracle's (the same definition on its own collision detection): both bodies of a
+    pair between two arm links, and the arm body of a pair against a fixed box."""
+    nvcc = build._nvcc()
+    if not ((os.path.isabs(nvcc) and os.path.exists(nvcc)) or shutil.which(nvcc)):
+        pytest.skip("nvcc not found")
+    src, exe = tmp_path / "dcd.cu", tmp_path / "dcd"
+    src.write_text(PROG_DCD)
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-I" + build.INCLUDE, "-I" + build.CSRC, str(src), "-o", str(exe)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines, refs = [], []
+    for kind in ("self", "world"):
+        for seed in range(4):
+            rng = np.random.default_rng(70 + seed + (0 if kind == "self" else 100))
+            model, q, _, pair = _arm_pair(rng, kind)
+            sa, ba, (Ea, ra), sb, bb, (Eb, rb) = pair
+            Ma = np.concatenate([np.ravel(C.body_pose(model, q, ba)[0]), C.body_pose(model, q, ba)[1]])
+            Mb = np.concatenate([np.ravel(C.body_pose(model, q, bb)[0]), C.body_pose(model, q, bb)[1]])
+            ta, za = _device_shape(sa)
+            tb, zb = _device_shape(sb)
+            for which in ((0, 1) if bb >= 0 else (0,)):
+                nums = np.concatenate([za, Ma, np.ravel(Ea), ra, zb, Mb, np.ravel(Eb), rb, [1e-6]])
+                lines.append("%d %d %d %s" % (ta, tb, which, " ".join("%.17g" % x for x in nums)))
+                refs.append(C.dcd_dbody(model, q, pair, which))
+    out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120)
+    rows = [np.array([float(x) for x in ln.split()]) for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(rows) == len(refs)
+    for row, ref in zip(rows, refs):
+        assert row[0] == 1.0
+        assert np.abs(ref).max() > 0.1
+        assert np.abs(row[1:].reshape(6, 6) - ref).max() <= 1e-7 * max(1.0, np.abs(ref).max())
