@@ -44,6 +44,26 @@ DS_HDI void to_contact(const double* R, const double* p, const double* Rc, const
   }
 }
 
+// out (3 x nv, row-major) = J_c of the pair: column k is E (cX_B J_B[:, k] - cX_A J_A[:, k]).
+DS_HD inline void pair_jc(int nv, const double* Rc, const double* c, const double* Ra, const double* pa,
+                          const double* Ja, const double* Rb, const double* pb, const double* Jb, double* out) {
+  for (int k = 0; k < nv; ++k) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    const double* R[2] = {Ra, Rb};
+    const double* P[2] = {pa, pb};
+    const double* J[2] = {Ja, Jb};
+    for (int b = 0; b < 2; ++b) {
+      if (!R[b]) continue;
+      const double jk[6] = {J[b][0 * nv + k], J[b][1 * nv + k], J[b][2 * nv + k],
+                            J[b][3 * nv + k], J[b][4 * nv + k], J[b][5 * nv + k]};
+      double x[6];
+      to_contact(R[b], P[b], Rc, c, jk, x);
+      for (int i = 0; i < 3; ++i) acc[i] += (b == 0 ? -1.0 : 1.0) * x[i];
+    }
+    for (int i = 0; i < 3; ++i) out[i * nv + k] = acc[i];
+  }
+}
+
 // o = dCD/dM J[:, k] (6 x 6 times column k of a 6 x nv Jacobian).
 DS_HDI void dcd_column(const double* dcd, const double* J, int nv, int k, double* o) {
   for (int i = 0; i < 6; ++i) {

@@ -1,6 +1,6 @@
-"""App. C's contact-placement terms on the device side (ds_appc.cuh), compiled for the host with nvcc
-and run on the CPU, against the oracle's (oracle/collision.py appc_dJcv_dq, appc_dJctlam_dq), no
-GPU.  The inputs (contact placement, body poses, twists, Jacobians and dCD/dM_i) come from the
+"""App. C's contact rows J_c and contact-placement terms on the device side (ds_appc.cuh), compiled
+for the host with nvcc and run on the CPU, against the oracle's (oracle/collision.py pair_jc,
+appc_dJcv_dq, appc_dJctlam_dq, dcd_dbody), no GPU.  The inputs (contact placement, body poses, twists, Jacobians and dCD/dM_i) come from the
 oracle's kinematics and collision detection for a contact between two links of a random 7-dof arm
 and between an arm link and a fixed box; the expected values are the oracle's terms, which
 test_oracle_collision.py pins against central differences."""
@@ -27,13 +27,16 @@ int main() {
     std::vector<double> J[2] = {std::vector<double>(6 * nv), std::vector<double>(6 * nv)};
     rd(Rc, 9); rd(c, 3); rd(lam, 3);
     for (int b = 0; b < 2; ++b) { rd(R[b], 9); rd(p[b], 3); rd(V[b], 6); rd(J[b].data(), 6 * nv); rd(D[b], 36); }
-    std::vector<double> t1(3 * nv), t2(nv * nv), scratch(3 * nv);
+    std::vector<double> t1(3 * nv), t2(nv * nv), scratch(3 * nv), jc(3 * nv);
+    ds::cd::pair_jc(nv, Rc, c, has[0] ? R[0] : nullptr, p[0], J[0].data(), has[1] ? R[1] : nullptr, p[1],
+                    J[1].data(), jc.data());
     ds::cd::appc_dJcv_dq(nv, Rc, c, has[0] ? R[0] : nullptr, p[0], V[0], J[0].data(), D[0],
                          has[1] ? R[1] : nullptr, p[1], V[1], J[1].data(), D[1], t1.data());
     ds::cd::appc_dJctlam_dq(nv, lam, Rc, c, has[0] ? R[0] : nullptr, p[0], J[0].data(), D[0],
                             has[1] ? R[1] : nullptr, p[1], J[1].data(), D[1], scratch.data(), t2.data());
     for (double x : t1) std::printf("%.17g ", x);
     for (double x : t2) std::printf("%.17g ", x);
+    for (double x : jc) std::printf("%.17g ", x);
     std::printf("\n");
   }
   return 0;
@@ -73,7 +76,8 @@ def _line(model, q, v, pair, lam):
         nums += [R.ravel(), p, vel[body], Js[body].ravel(), dcd[which].ravel()]
     ref1 = C.appc_dJcv_dq(model, q, v, pair, dcd)
     ref2 = C.appc_dJctlam_dq(model, q, lam, pair, dcd)
-    return " ".join(str(x) for x in fields) + " " + " ".join("%.17g" % x for x in np.concatenate(nums)), ref1, ref2
+    ref3 = C.pair_jc(model, q, pair)
+    return " ".join(str(x) for x in fields) + " " + " ".join("%.17g" % x for x in np.concatenate(nums)), ref1, ref2, ref3
 
 
 @pytest.mark.parametrize("kind", ["self", "world"])
@@ -90,15 +94,17 @@ def test_appc_terms_against_oracle(tmp_path, kind):
     for seed in range(6):
         rng = np.random.default_rng(50 + seed + (0 if kind == "self" else 100))
         model, q, v, pair = _arm_pair(rng, kind)
-        ln, r1, r2 = _line(model, q, v, pair, rng.normal(size=3))
+        ln, r1, r2, r3 = _line(model, q, v, pair, rng.normal(size=3))
         lines.append(ln)
-        refs.append((r1, r2))
+        refs.append((r1, r2, r3))
     out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120)
     rows = [np.array([float(x) for x in ln.split()]) for ln in out.stdout.splitlines() if ln.strip()]
     assert len(rows) == len(refs)
-    for row, (r1, r2) in zip(rows, refs):
+    for row, (r1, r2, r3) in zip(rows, refs):
         nv = r1.shape[1]
-        g1, g2 = row[:3 * nv].reshape(3, nv), row[3 * nv:].reshape(nv, nv)
+        g1, g2 = row[:3 * nv].reshape(3, nv), row[3 * nv:3 * nv + nv * nv].reshape(nv, nv)
+        g3 = row[3 * nv + nv * nv:].reshape(3, nv)
+        assert np.abs(g3 - r3).max() <= 1e-13 * max(1.0, np.abs(r3).max())
         assert np.abs(r1).max() > 1e-3 and np.abs(r2).max() > 1e-3
         assert np.abs(g1 - r1).max() <= 1e-12 * max(1.0, np.abs(r1).max())
         assert np.abs(g2 - r2).max() <= 1e-12 * max(1.0, np.abs(r2).max())
