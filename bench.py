@@ -306,6 +306,47 @@ def collision_pairs_device(n, seed):
             t32[1].contiguous(), size[1].contiguous(), pose[1].contiguous()]
 
 
+def hull_pairs_device(n, seed, n_hulls=4096, verts=16):
+    """Seeded random hull pairs generated on the device (inputs only): a pool of n_hulls hulls of
+    verts points on ellipsoids with semi-axes in [0.03, 0.1], radius in [0, 0.02]; side A a random
+    hull, side B a random hull (even k) or box (odd k); rotations and positions as in
+    collision_pairs_device."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    f64 = dict(device="cuda", dtype=torch.float64)
+    x = torch.randn((n_hulls, verts, 3), generator=g, **f64)
+    axes = 0.03 + 0.07 * torch.rand((n_hulls, 1, 3), generator=g, **f64)
+    pool = (x / x.norm(dim=-1, keepdim=True) * axes).reshape(-1, 3).contiguous()
+    pick = torch.randint(0, n_hulls, (2, n), generator=g, device="cuda")
+    hull_size = torch.stack([(pick * verts).double(), torch.full((2, n), float(verts), **f64),
+                             0.02 * torch.rand((2, n), generator=g, **f64)], dim=-1)
+    ta, sa, pa, tb, sb, pb = collision_pairs_device(n, seed + 1)
+    box = (torch.arange(n, device="cuda") % 2) == 1
+    ta = torch.full_like(ta, 3)
+    tb = torch.where(box, torch.full_like(tb, 2), torch.full_like(tb, 3))
+    box_size = 0.03 + 0.09 * torch.rand((n, 3), generator=g, **f64)
+    sa = hull_size[0].contiguous()
+    sb = torch.where(box[:, None], box_size, hull_size[1]).contiguous()
+    return [ta.contiguous(), sa, pa, tb.contiguous(), sb, pb], pool
+
+
+def _time_launches(fn, steps, warmup, flush):
+    import torch
+    stream = torch.cuda.current_stream()
+    ms = []
+    for i in range(warmup + steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    return float(np.mean(ms))
+
+
 def collision_bench(n, steps, warmup, flush):
     """Time ds_collide (one pair per thread) on n random pairs: CUDA events on the launching
     stream around each launch, the L2 flushed before each."""
@@ -328,9 +369,28 @@ def collision_bench(n, steps, warmup, flush):
     overlap = float((out[:, 0] < 0).double().mean())
     bytes_per_pair = 2 * (4 + 3 * 8 + 12 * 8) + ds.COLLIDE_OUT * 8
     t = float(np.mean(ms))
+    # convex hulls (16 vertices) against hulls and boxes: GJK, and EPA for overlapping cores
+    nh = 65536
+    hargs, pool = hull_pairs_device(nh, seed=2410)
+    hout = torch.empty((nh, ds.COLLIDE_OUT), dtype=torch.float64, device="cuda")
+    th = _time_launches(lambda st: ds.collide(*hargs, hull_vertices=pool, out=hout, stream=st), steps, warmup, flush)
+    hulls = {"pairs": nh, "ms_per_launch": th, "pairs_per_s": nh / (th * 1e-3),
+             "overlap_fraction": float((hout[:, 0] < 0).double().mean()),
+             "nonfinite_pairs": int((~torch.isfinite(hout).all(dim=1)).sum()),
+             "note": "hull (16 vertices) against hull or box, every other pair; pool of 4096 hulls"}
+    # App. C's randomized-smoothing derivative, 8 antithetic samples (16 collision detections a pair)
+    ns, S, sigma = 65536, 8, 1e-3
+    sargs = [a[:ns].contiguous() for a in args]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2411)
+    eps = sigma * torch.randn((S, 12), generator=gen, device="cuda", dtype=torch.float64)
+    jac = torch.empty((ns, 7, 12), dtype=torch.float64, device="cuda")
+    tsm = _time_launches(lambda st: ds.collide_smoothed(*sargs, eps, sigma, out=jac, stream=st), steps, warmup, flush)
+    smoothed = {"pairs": ns, "samples": S, "sigma": sigma, "ms_per_launch": tsm, "pairs_per_s": ns / (tsm * 1e-3),
+                "nonfinite_pairs": int((~torch.isfinite(jac.reshape(ns, -1)).all(dim=1)).sum())}
     return {"pairs": n, "ms_per_launch": t, "pairs_per_s": n / (t * 1e-3),
             "hbm_gbs": n * bytes_per_pair / (t * 1e-3) / 1e9, "bytes_per_pair": bytes_per_pair,
-            "overlap_fraction": overlap, "launches": steps,
+            "overlap_fraction": overlap, "launches": steps, "hulls": hulls, "smoothing_derivative": smoothed,
             "note": "sphere / capsule / box pairs, FP64; GJK for separated cores, the nearest facet of "
                     "the Minkowski difference (separating axes) for overlapping ones; bound by FP64 "
                     "arithmetic, not HBM; not part of the step (its contacts are primitive versus plane)"}
