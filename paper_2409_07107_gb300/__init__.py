@@ -320,15 +320,34 @@ def _hull_pool(hull_vertices):
     return (ctypes.c_void_p(0), 0) if hull_vertices is None else (_ptr(hull_vertices), hull_vertices.shape[0])
 
 
+def _check_pairs(type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, extra=()):
+    """The kernels read n pairs from each buffer: reject a dtype, shape, device or layout that would
+    make them read past it."""
+    import torch
+    n = type_a.shape[0] if type_a.dim() == 1 else -1
+    want = [(type_a, torch.int32, (n,)), (type_b, torch.int32, (n,)), (size_a, torch.float64, (n, 3)),
+            (size_b, torch.float64, (n, 3)), (pose_a, torch.float64, (n, 12)), (pose_b, torch.float64, (n, 12))]
+    if hull_vertices is not None:
+        want.append((hull_vertices, torch.float64, (hull_vertices.shape[0], 3)))
+    want += list(extra)
+    for t, dtype, shape in want:
+        if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous() or t.device != type_a.device \
+                or (t.numel() and not t.is_cuda):
+            raise ValueError("diffsim: expected a contiguous CUDA %s tensor of shape %s, got %s %s on %s"
+                             % (dtype, tuple(shape), t.dtype, tuple(t.shape), t.device))
+    return n
+
+
 def collide(type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices=None, out=None, stream=None):
     """Collision detection between convex shapes (ds_collide), one pair per row: type (int32, n),
     size (FP64, n x 3; a hull's is (first vertex, count, radius)), pose (FP64, n x 12: R row-major,
     then p), hull_vertices (FP64, V x 3, body frames), all CUDA tensors.  Returns out (FP64,
     n x 19): phi, c, n, t1, t2, the witness points on A's and B's surfaces."""
     import torch
-    n = type_a.shape[0]
+    n = _check_pairs(type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices)
     if out is None:
         out = torch.empty((n, COLLIDE_OUT), dtype=torch.float64, device=type_a.device)
+    _check_pairs(type_a, size_a, pose_a, type_b, size_b, pose_b, None, [(out, torch.float64, (n, COLLIDE_OUT))])
     hv, nhv = _hull_pool(hull_vertices)
     _check(lib().ds_collide(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
                             _ptr(pose_b), hv, nhv, _ptr(out), _stream(stream)))
@@ -341,9 +360,11 @@ def collide_smoothed(type_a, size_a, pose_a, type_b, size_b, pose_b, eps, sigma,
     S x 12 CUDA tensor, samples of N(0, sigma^2 I)); returns (n x 7 x 12) d(phi, c, n)/d(twists of
     A and B)."""
     import torch
-    n = type_a.shape[0]
+    n = _check_pairs(type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices,
+                     [(eps, torch.float64, (eps.shape[0], 12))])
     if out is None:
         out = torch.empty((n, 7, 12), dtype=torch.float64, device=type_a.device)
+    _check_pairs(type_a, size_a, pose_a, type_b, size_b, pose_b, None, [(out, torch.float64, (n, 7, 12))])
     hv, nhv = _hull_pool(hull_vertices)
     _check(lib().ds_collide_smoothed(n, _ptr(type_a), _ptr(size_a), _ptr(pose_a), _ptr(type_b), _ptr(size_b),
                                      _ptr(pose_b), hv, nhv, eps.shape[0], _ptr(eps), float(sigma), _ptr(out),

@@ -111,3 +111,23 @@ def test_collide_smoothed_rejects_bad_arguments(L):
     assert L.ds_collide_smoothed(4, *args, 4, None, 1e-3, buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(4, *([buf] * 6), buf, -2, 4, buf, 1e-3, buf, None) == ds.DS_EINVAL
     assert L.ds_collide_smoothed(0, *([None] * 6), None, 0, 0, None, 0.0, None, None) == ds.DS_OK
+
+
+def test_collide_binding_rejects_bad_tensors():
+    """The binding checks dtype, shape and layout before any launch (a float32 size or a short pose
+    buffer would be read past its end); checked on CPU tensors, which it also rejects."""
+    torch = pytest.importorskip("torch")
+    n = 4
+    t = torch.zeros(n, dtype=torch.int32)
+    z = torch.zeros((n, 3), dtype=torch.float64)
+    p = torch.zeros((n, 12), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        ds.collide(t, z.float(), p, t, z, p)
+    with pytest.raises(ValueError):
+        ds.collide(t, z, p[:, :9].contiguous(), t, z, p)
+    with pytest.raises(ValueError):
+        ds.collide(t.long(), z, p, t, z, p)
+    with pytest.raises(ValueError):
+        ds.collide(t, z, p, t, z, p)                     # CPU tensors
+    with pytest.raises(ValueError):
+        ds.collide_smoothed(t, z, p, t, z, p, torch.zeros((2, 6), dtype=torch.float64), 1e-3)

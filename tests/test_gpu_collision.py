@@ -71,7 +71,8 @@ def test_collide_unknown_type_and_empty_batch():
     assert abs(got[16, 0] - ref["phi"]) <= 1e-12
     e = torch.empty(0, dtype=torch.int32, device="cuda")
     f = torch.empty((0, 3), dtype=torch.float64, device="cuda")
-    out = ds.collide(e, f, f, e, f, f)
+    g = torch.empty((0, 12), dtype=torch.float64, device="cuda")
+    out = ds.collide(e, f, g, e, f, g)
     assert out.shape == (0, ds.COLLIDE_OUT)
 
 
