@@ -308,6 +308,28 @@ def dcd_dbody(model, q, pair, which, h=1e-6):
     return out
 
 
+def dcd_dbody_smoothed(model, q, pair, which, sigma, eps_samples):
+    """dCD/dM_i (6 x 6) by App. C's zero-order randomized smoothing: with local twists eps_s of body
+    i's pose (the rows of eps_samples, S x 6, drawn from N(0, sigma^2 I)), the antithetic estimate
+    1 / (2 S sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T of the Gaussian-smoothed derivative of f,
+    the local twist of the contact placement (as in dcd_dbody) when body i moves to M_i exp(eps)."""
+    poses = [body_pose(model, q, pair[1]), body_pose(model, q, pair[4])]
+    Rc, c, _ = pair_placement(model, q, pair, poses)
+    eps_samples = np.asarray(eps_samples, float)
+    acc = np.zeros((6, 6))
+    for eps in eps_samples:
+        f = []
+        for s in (1.0, -1.0):
+            R, p = poses[which]
+            R2, p2 = twist_pose(np.eye(3), np.zeros(3), s * eps)
+            moved = list(poses)
+            moved[which] = (R @ R2, p + R @ p2)
+            Rc2, c2, _ = pair_placement(model, q, pair, moved)
+            f.append(local_twist(Rc, c, Rc2, c2))
+        acc += np.outer(f[0] - f[1], eps)
+    return acc / (2.0 * sigma ** 2 * len(eps_samples))
+
+
 def appc_dJcv_dq(model, q, v, pair, dcd):
     """App. C's contact-placement terms of d(J_c v)/dq at fixed v and fixed body velocities V_i:
     sum over the two bodies of the sign times E [ (cX_i V_i) x dCD/dM_i J_i - cX_i (V_i x J_i) ],

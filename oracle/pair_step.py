@@ -16,7 +16,7 @@ App. D's route 1 (step.route1_matrices): D = dv+/d(q, v, tau) at fixed lambda an
 at fixed v+, where the q-derivatives split into the part at fixed contact placement (complex steps
 through the rigid-body functions, the transforms X_i held) and App. C's placement terms
 (collision.appc_dJctlam_dq, collision.appc_dJcv_dq), with dCD/dM_i by central differences of the
-collision detection (the paper takes it from randomized smoothing)."""
+collision detection or, as the paper takes it, by randomized smoothing (dcd_fn)."""
 import numpy as np
 
 from . import collision as Co
@@ -85,8 +85,10 @@ def step(model, env, pairs, opt):
                 Jc=Jc, Y=Y, G=G, g=g, mu=mu, M=M, converged=conv)
 
 
-def partials(model, env, pairs, opt, st):
-    """D = dv+/d(q, v, tau) at fixed lambda (nv x 3 nv) and F = d(J_c v+)/dq at fixed v+."""
+def partials(model, env, pairs, opt, st, dcd_fn=None):
+    """D = dv+/d(q, v, tau) at fixed lambda (nv x 3 nv) and F = d(J_c v+)/dq at fixed v+.
+    dcd_fn(model, q, pair, which) gives dCD/dM_i (default: central differences, Co.dcd_dbody)."""
+    dcd_fn = dcd_fn or (lambda m, qq, pr, w: Co.dcd_dbody(m, qq, pr, w))
     q, v, tau = env["q"], env["v"], env["tau"]
     nv, dt = len(v), opt.dt
     act, transforms, lam, v_next = st["act"], st["transforms"], st["lam"], st["v_next"]
@@ -114,7 +116,7 @@ def partials(model, env, pairs, opt, st):
             Fq[:, j] = np.imag(Jh @ v_next) / H_CS
     for jj, k in enumerate(act):
         pr = pairs[k][:6]
-        dcd = (Co.dcd_dbody(model, q, pr, 0), Co.dcd_dbody(model, q, pr, 1))
+        dcd = (dcd_fn(model, q, pr, 0), dcd_fn(model, q, pr, 1))
         dJl += Co.appc_dJctlam_dq(model, q, lam[3 * jj:3 * jj + 3], pr, dcd)
         Fq[3 * jj:3 * jj + 3] += Co.appc_dJcv_dq(model, q, v_next, pr, dcd)
     Dq = -dt * rigid.chol_solve(rigid.cholesky(st["M"]), dRq - dJl / dt)
@@ -122,11 +124,12 @@ def partials(model, env, pairs, opt, st):
     return D, Fq
 
 
-def step_jac(model, env, pairs, opt):
+def step_jac(model, env, pairs, opt, dcd_fn=None):
     """The step and dv+/d(q, v, tau) by route 1 (App. B, D): dv = D + Y C X with
-    X = -A^- B (J_c D + [F, 0, 0])."""
+    X = -A^- B (J_c D + [F, 0, 0]).  dcd_fn as for partials (e.g. App. C's randomized smoothing,
+    Co.dcd_dbody_smoothed with the caller's samples)."""
     st = step(model, env, pairs, opt)
-    D, F = partials(model, env, pairs, opt, st)
+    D, F = partials(model, env, pairs, opt, st, dcd_fn)
     nv = len(env["v"])
     if st["act"]:
         A, Bm, C = route1_matrices(st["G"], st["g"], st["mu"], st["lam"], st["modes"])

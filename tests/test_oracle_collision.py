@@ -252,3 +252,23 @@ def test_witness_on_a_triangulated_face_diagonal():
             assert np.abs(r["n"] - [0.0, 0.0, -1.0]).max() <= 1e-14
             assert abs(r["phi"] - (h - 0.05 - 0.04)) <= 1e-14
             assert np.abs(r["c"][:2] - [dx, -dx]).max() <= 1e-14
+
+
+@pytest.mark.parametrize("kind", ["self", "world"])
+def test_smoothed_dcd_with_orthogonal_samples_is_central_differences(kind):
+    """App. C's randomized-smoothing estimate of dCD/dM_i, 1/(2 S sigma^2) sum (f(+e) - f(-e)) e^T,
+    fed the orthogonal design e = +-sigma sqrt(6) e_j (sum e e^T = S sigma^2 I, as for Gaussian
+    samples in expectation) is exactly the central difference at step sigma sqrt(6); a wrong
+    normalisation, sign or twist convention in the estimator breaks it.  With Gaussian samples it
+    approaches the derivative as the samples grow (checked loosely: 20 % at 300 samples)."""
+    rng = np.random.default_rng(12 if kind == "self" else 13)
+    model, q, v, pair = _arm_pair(rng, kind)
+    sigma = 1e-6
+    design = np.sqrt(6.0) * sigma * np.eye(6)
+    for which in ((0, 1) if kind == "self" else (0,)):
+        est = C.dcd_dbody_smoothed(model, q, pair, which, sigma, design)
+        ref = C.dcd_dbody(model, q, pair, which, h=np.sqrt(6.0) * sigma)
+        assert np.abs(est - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    gauss = C.dcd_dbody_smoothed(model, q, pair, 0, 1e-4, rng.normal(0.0, 1e-4, size=(300, 6)))
+    ref = C.dcd_dbody(model, q, pair, 0)
+    assert np.abs(gauss - ref).max() <= 0.2 * np.abs(ref).max()

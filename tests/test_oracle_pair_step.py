@@ -142,6 +142,19 @@ def test_two_pairs_against_central_differences(seed, vscale, mu, modes):
     assert np.abs(J - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max())
 
 
+def test_pair_step_takes_the_smoothed_placement_derivative():
+    """The step Jacobian with dCD/dM_i from App. C's smoothing estimator (the paper's route) fed
+    the orthogonal samples +-sigma sqrt(6) e_j equals the one with central differences at that
+    step (the estimator is then exactly those differences)."""
+    model, env, pairs = _two_pair_case(21, 0.3, 0.3)
+    sigma = 1e-6 / np.sqrt(6.0)
+    design = np.sqrt(6.0) * sigma * np.eye(6)
+    st = PS.step_jac(model, env, pairs, OPT,
+                     dcd_fn=lambda m, q, pr, w: C.dcd_dbody_smoothed(m, q, pr, w, sigma, design))
+    ref = PS.step_jac(model, env, pairs, OPT)
+    assert np.abs(st["dv_dq"] - ref["dv_dq"]).max() <= 1e-9 * max(1.0, np.abs(ref["dv_dq"]).max())
+
+
 def test_pair_step_without_contact_is_the_free_step():
     model, env, pairs = _world_case(3, 0.5, 0.5, pen=-0.05)     # the box 5 cm below the capsule
     st = PS.step_jac(model, env, pairs, OPT)
