@@ -17,7 +17,8 @@
 // Vectors are (linear, angular); a body is given by its world pose (R row-major, p), its twist V
 // and Jacobian J (6 x nv, row-major) in its own coordinates and dCD/dM (6 x 6, row-major); R ==
 // nullptr stands for the fixed world (no twist, no Jacobian).  dCD/dM_i itself comes from
-// dcd_dbody (central differences of the collision detection in the body's local twist).
+// dcd_dbody (central differences of the collision detection in the body's local twist) or, as the
+// paper takes it, dcd_dbody_smoothed (its randomized-smoothing estimate).
 #pragma once
 #include "ds_collision.cuh"
 #include "ds_common.cuh"
@@ -147,57 +148,85 @@ DS_HDI void shape_pose(const double* M, const double* off, double* o) {
   }
 }
 
-// dCD/dM_i (6 x 6, row-major) by central differences of the collision detection: column j is the
-// local twist of the contact placement, (Rc^T (c' - c), vee of the antisymmetric part of
-// Rc^T Rc' - I), per unit of the j-th component of a local twist delta of body i's pose
-// (M_i -> M_i exp(delta): R' = R exp([w]), p' = p + R V(w) u), step h, which = 0 for A, 1 for B.
-// Ma, Mb are the bodies' world poses (the identity for the fixed world), oa, ob the shapes'
-// offsets on them; shapes, hulls as for collide.  Returns false when a collision result is not
-// finite.
+// f = the local twist of the contact placement when body i (which = 0: A, 1: B) moves by the local
+// twist xi (M_i -> M_i exp(xi): R' = R exp([w]), p' = p + R V(w) u): (Rc^T (c' - c), vee of the
+// antisymmetric part of Rc^T Rc' - I), with (Rc, c) the placement read from base (collide's
+// outputs at the unmoved poses).  Returns false when the moved result is not finite.
+DS_HD inline bool placement_twist(int type_a, const double* size_a, const double* Ma, const double* oa,
+                                  int type_b, const double* size_b, const double* Mb, const double* ob,
+                                  const double* hv, int n_hv, int which, const double* base, const double* xi,
+                                  double* f) {
+  const double ident[12] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+  double ex[12], Mm[12], moved[12], other[12], r[DS_COLLIDE_OUT];
+  twist_pose(ident, xi, 1.0, ex);
+  shape_pose(which == 0 ? Ma : Mb, ex, Mm);   // (R E_x, p + R p_x)
+  shape_pose(Mm, which == 0 ? oa : ob, moved);
+  shape_pose(which == 0 ? Mb : Ma, which == 0 ? ob : oa, other);
+  if (which == 0) collide(type_a, size_a, moved, type_b, size_b, other, hv, n_hv, r);
+  else collide(type_a, size_a, other, type_b, size_b, moved, hv, n_hv, r);
+  const double* axes[3] = {base + 7, base + 10, base + 4};   // rows of Rc^T: t1, t2, n
+  const double* ax2[3] = {r + 7, r + 10, r + 4};
+  const double dc[3] = {r[1] - base[1], r[2] - base[2], r[3] - base[3]};
+  double W[3][3];   // Rc^T Rc' - I
+  for (int a = 0; a < 3; ++a) {
+    f[a] = dot3(axes[a], dc);
+    for (int b = 0; b < 3; ++b) W[a][b] = dot3(axes[a], ax2[b]) - (a == b ? 1.0 : 0.0);
+  }
+  f[3] = 0.5 * (W[2][1] - W[1][2]);
+  f[4] = 0.5 * (W[0][2] - W[2][0]);
+  f[5] = 0.5 * (W[1][0] - W[0][1]);
+  for (int k = 0; k < 6; ++k)
+    if (!(f[k] - f[k] == 0.0)) return false;
+  return true;
+}
+
+// dCD/dM_i (6 x 6, row-major) by central differences of the collision detection: column j is
+// (f(+h e_j) - f(-h e_j)) / (2 h) for f of placement_twist, which = 0 for A, 1 for B.  Ma, Mb are
+// the bodies' world poses (the identity for the fixed world), oa, ob the shapes' offsets on them;
+// shapes, hulls as for collide.  Returns false when a collision result is not finite.
 DS_HD inline bool dcd_dbody(int type_a, const double* size_a, const double* Ma, const double* oa, int type_b,
                             const double* size_b, const double* Mb, const double* ob, const double* hv, int n_hv,
                             int which, double h, double* out) {
-  double pa[12], pb[12], base[DS_COLLIDE_OUT], res[2][DS_COLLIDE_OUT];
+  double pa[12], pb[12], base[DS_COLLIDE_OUT];
   shape_pose(Ma, oa, pa);
   shape_pose(Mb, ob, pb);
   collide(type_a, size_a, pa, type_b, size_b, pb, hv, n_hv, base);
-  // Rc^T (row i of Rc^T = column i of Rc: t1, t2, n)
-  const double* axes[3] = {base + 7, base + 10, base + 4};
-  const double* M = which == 0 ? Ma : Mb;
-  const double* off = which == 0 ? oa : ob;
   for (int j = 0; j < 6; ++j) {
-    for (int sgn = 0; sgn < 2; ++sgn) {
-      double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      xi[j] = sgn ? -h : h;
-      // the body moved by its local twist: M exp(xi), with exp(xi) = twist_pose of the identity
-      const double ident[12] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
-      double ex[12], Mm[12], moved[12];
-      twist_pose(ident, xi, 1.0, ex);
-      shape_pose(M, ex, Mm);   // (R E_x, p + R p_x)
-      shape_pose(Mm, off, moved);
-      if (which == 0) collide(type_a, size_a, moved, type_b, size_b, pb, hv, n_hv, res[sgn]);
-      else collide(type_a, size_a, pa, type_b, size_b, moved, hv, n_hv, res[sgn]);
-    }
-    double col[2][6];
-    for (int sgn = 0; sgn < 2; ++sgn) {
-      const double* r = res[sgn];
-      const double* ax2[3] = {r + 7, r + 10, r + 4};
-      double dc[3] = {r[1] - base[1], r[2] - base[2], r[3] - base[3]};
-      double W[3][3];   // Rc^T Rc' - I
-      for (int a = 0; a < 3; ++a) {
-        col[sgn][a] = dot3(axes[a], dc);
-        for (int b = 0; b < 3; ++b) W[a][b] = dot3(axes[a], ax2[b]) - (a == b ? 1.0 : 0.0);
-      }
-      col[sgn][3] = 0.5 * (W[2][1] - W[1][2]);
-      col[sgn][4] = 0.5 * (W[0][2] - W[2][0]);
-      col[sgn][5] = 0.5 * (W[1][0] - W[0][1]);
-    }
-    for (int i = 0; i < 6; ++i) {
-      const double v = (col[0][i] - col[1][i]) / (2.0 * h);
-      if (!(v == v) || v - v != 0.0) return false;
-      out[6 * i + j] = v;
-    }
+    double xp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, xm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, fp[6], fm[6];
+    xp[j] = h;
+    xm[j] = -h;
+    if (!placement_twist(type_a, size_a, Ma, oa, type_b, size_b, Mb, ob, hv, n_hv, which, base, xp, fp) ||
+        !placement_twist(type_a, size_a, Ma, oa, type_b, size_b, Mb, ob, hv, n_hv, which, base, xm, fm))
+      return false;
+    for (int i = 0; i < 6; ++i) out[6 * i + j] = (fp[i] - fm[i]) / (2.0 * h);
   }
+  return true;
+}
+
+// dCD/dM_i by App. C's zero-order randomized smoothing: with the caller's local twists eps_s of
+// body i (samples x 6, drawn from N(0, sigma^2 I)), 1 / (2 S sigma^2) sum_s (f(+eps_s) - f(-eps_s))
+// eps_s^T for f of placement_twist.  Returns false when a collision result is not finite.
+DS_HD inline bool dcd_dbody_smoothed(int type_a, const double* size_a, const double* Ma, const double* oa,
+                                     int type_b, const double* size_b, const double* Mb, const double* ob,
+                                     const double* hv, int n_hv, int which, int samples, const double* eps,
+                                     double sigma, double* out) {
+  double pa[12], pb[12], base[DS_COLLIDE_OUT];
+  shape_pose(Ma, oa, pa);
+  shape_pose(Mb, ob, pb);
+  collide(type_a, size_a, pa, type_b, size_b, pb, hv, n_hv, base);
+  for (int k = 0; k < 36; ++k) out[k] = 0.0;
+  for (int s = 0; s < samples; ++s) {
+    const double* e = eps + 6 * s;
+    const double em[6] = {-e[0], -e[1], -e[2], -e[3], -e[4], -e[5]};
+    double fp[6], fm[6];
+    if (!placement_twist(type_a, size_a, Ma, oa, type_b, size_b, Mb, ob, hv, n_hv, which, base, e, fp) ||
+        !placement_twist(type_a, size_a, Ma, oa, type_b, size_b, Mb, ob, hv, n_hv, which, base, em, fm))
+      return false;
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) out[6 * i + j] += (fp[i] - fm[i]) * e[j];
+  }
+  const double scale = 1.0 / (2.0 * sigma * sigma * samples);
+  for (int k = 0; k < 36; ++k) out[k] *= scale;
   return true;
 }
 

@@ -125,6 +125,8 @@ __global__ void k(const double* in, double* out) {
   ds::cd::appc_dJctlam_dq(7, in + 108, in, in + 9, in + 12, in + 21, in + 30, in + 72, nullptr, nullptr, nullptr,
                           nullptr, scratch, out + 21);
   ds::cd::dcd_dbody(2, in, in + 3, in + 15, 0, in + 27, in + 30, in + 42, nullptr, 0, 1, 1e-6, out + 70);
+  ds::cd::dcd_dbody_smoothed(2, in, in + 3, in + 15, 0, in + 27, in + 30, in + 42, nullptr, 0, 0, 4, in + 54, 1e-4,
+                             out + 106);
 }
 ''')
     r = subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I" + build.INCLUDE,
@@ -136,13 +138,19 @@ __global__ void k(const double* in, double* out) {
 PROG_DCD = r'''
 #include "ds_appc.cuh"
 #include <cstdio>
+#include <vector>
 static void rd(double* x, int n) { for (int i = 0; i < n; ++i) if (std::scanf("%lf", &x[i]) != 1) x[i] = 0.0; }
 int main() {
-  int ta, tb, which;
-  while (std::scanf("%d %d %d", &ta, &tb, &which) == 3) {
+  int ta, tb, which, S;
+  while (std::scanf("%d %d %d %d", &ta, &tb, &which, &S) == 4) {
     double sa[3], sb[3], Ma[12], Mb[12], oa[12], ob[12], h, out[36];
     rd(sa, 3); rd(Ma, 12); rd(oa, 12); rd(sb, 3); rd(Mb, 12); rd(ob, 12); rd(&h, 1);
-    const bool ok = ds::cd::dcd_dbody(ta, sa, Ma, oa, tb, sb, Mb, ob, nullptr, 0, which, h, out);
+    std::vector<double> eps(6 * S + 6);
+    rd(eps.data(), 6 * S);
+    // S = 0: central differences with step h; S > 0: the smoothing estimate with sigma = h
+    const bool ok = S == 0 ? ds::cd::dcd_dbody(ta, sa, Ma, oa, tb, sb, Mb, ob, nullptr, 0, which, h, out)
+                           : ds::cd::dcd_dbody_smoothed(ta, sa, Ma, oa, tb, sb, Mb, ob, nullptr, 0, which, S,
+                                                        eps.data(), h, out);
     std::printf("%d ", ok ? 1 : 0);
     for (double x : out) std::printf("%.17g ", x);
     std::printf("\n");
@@ -164,8 +172,9 @@ def _device_shape(shape):
 
 def test_dcd_dbody_against_oracle(tmp_path):
     """dCD/dM_i by central differences of the device collision detection, in the body's local twist,
-    against the oracle's (the same definition on its own collision detection): both bodies of a
-    pair between two arm links, and the arm body of a pair against a fixed box."""
+    and by App. C's randomized smoothing fed the same samples, against the oracle's (the same
+    definitions on its own collision detection): both bodies of a pair between two arm links, and
+    the arm body of a pair against a fixed box."""
     nvcc = build._nvcc()
     if not ((os.path.isabs(nvcc) and os.path.exists(nvcc)) or shutil.which(nvcc)):
         pytest.skip("nvcc not found")
@@ -186,8 +195,14 @@ def test_dcd_dbody_against_oracle(tmp_path):
             tb, zb = _device_shape(sb)
             for which in ((0, 1) if bb >= 0 else (0,)):
                 nums = np.concatenate([za, Ma, np.ravel(Ea), ra, zb, Mb, np.ravel(Eb), rb, [1e-6]])
-                lines.append("%d %d %d %s" % (ta, tb, which, " ".join("%.17g" % x for x in nums)))
+                lines.append("%d %d %d 0 %s" % (ta, tb, which, " ".join("%.17g" % x for x in nums)))
                 refs.append(C.dcd_dbody(model, q, pair, which))
+                # App. C's smoothing estimate with 8 Gaussian samples, the same on both sides
+                sig = 1e-4
+                eps = rng.normal(0.0, sig, size=(8, 6))
+                nums = np.concatenate([za, Ma, np.ravel(Ea), ra, zb, Mb, np.ravel(Eb), rb, [sig], eps.ravel()])
+                lines.append("%d %d %d 8 %s" % (ta, tb, which, " ".join("%.17g" % x for x in nums)))
+                refs.append(C.dcd_dbody_smoothed(model, q, pair, which, sig, eps))
     out = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120)
     rows = [np.array([float(x) for x in ln.split()]) for ln in out.stdout.splitlines() if ln.strip()]
     assert len(rows) == len(refs)
