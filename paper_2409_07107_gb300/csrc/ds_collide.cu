@@ -4,6 +4,7 @@
 
 namespace {
 
+template <bool kHulls>
 __global__ void __launch_bounds__(128) collide_kernel(int n, const int32_t* __restrict__ type_a,
                                                       const double* __restrict__ size_a,
                                                       const double* __restrict__ pose_a,
@@ -23,10 +24,11 @@ __global__ void __launch_bounds__(128) collide_kernel(int n, const int32_t* __re
     pa[i] = pose_a[12 * k + i];
     pb[i] = pose_b[12 * k + i];
   }
-  ds::cd::collide(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, o);
+  ds::cd::collide<kHulls>(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, o);
   for (int i = 0; i < DS_COLLIDE_OUT; ++i) out[static_cast<size_t>(DS_COLLIDE_OUT) * k + i] = o[i];
 }
 
+template <bool kHulls>
 __global__ void __launch_bounds__(128) collide_smoothed_kernel(
     int n, const int32_t* __restrict__ type_a, const double* __restrict__ size_a,
     const double* __restrict__ pose_a, const int32_t* __restrict__ type_b, const double* __restrict__ size_b,
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(128) collide_smoothed_kernel(
     pa[i] = pose_a[12 * k + i];
     pb[i] = pose_b[12 * k + i];
   }
-  ds::cd::smoothing_jacobian(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, samples, eps, sigma, J);
+  ds::cd::smoothing_jacobian<kHulls>(type_a[k], sa, pa, type_b[k], sb, pb, hv, n_hv, samples, eps, sigma, J);
   for (int i = 0; i < 84; ++i) jac[static_cast<size_t>(84) * k + i] = J[i];
 }
 
@@ -61,9 +63,14 @@ extern "C" ds_status ds_collide_smoothed(int32_t n_pairs, const int32_t* type_a,
   if (n_samples <= 0 || !(sigma > 0.0) || !(sigma < 1e300)) return DS_EINVAL;
   const int threads = 128;
   const int blocks = (n_pairs + threads - 1) / threads;
-  collide_smoothed_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
-      n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, n_samples, eps,
-      sigma, jac);
+  // without a hull pool no pair can be a valid hull: the form without hulls (a tenth of the state)
+  if (hull_vertices && n_hull_vertices > 0)
+    collide_smoothed_kernel<true><<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, n_samples, eps,
+        sigma, jac);
+  else
+    collide_smoothed_kernel<false><<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, nullptr, 0, n_samples, eps, sigma, jac);
   return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ECUDA;
 }
 
@@ -76,7 +83,12 @@ extern "C" ds_status ds_collide(int32_t n_pairs, const int32_t* type_a, const do
   if (!type_a || !size_a || !pose_a || !type_b || !size_b || !pose_b || !out) return DS_EINVAL;
   const int threads = 128;
   const int blocks = (n_pairs + threads - 1) / threads;
-  collide_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
-      n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, out);
+  // without a hull pool no pair can be a valid hull: the form without hulls (a tenth of the state)
+  if (hull_vertices && n_hull_vertices > 0)
+    collide_kernel<true><<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, hull_vertices, n_hull_vertices, out);
+  else
+    collide_kernel<false><<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n_pairs, type_a, size_a, pose_a, type_b, size_b, pose_b, nullptr, 0, out);
   return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ECUDA;
 }

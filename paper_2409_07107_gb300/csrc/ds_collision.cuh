@@ -37,16 +37,22 @@ constexpr int kGjkMaxIter = 64;
 constexpr int kCoreMax = DS_CONVEX_HULL_MAX;   // vertices of a hull core (32)
 enum CoreKind { kPoint = 0, kSegment = 1, kBox = 2, kHull = 3 };
 
-// A core in world coordinates: 1 point, 2 segment end points, 8 box corners or up to 32 hull
+// A core in world coordinates: 1 point, 2 segment end points, 8 box corners or up to NMAX hull
 // vertices, plus the radius and (for a box) its axes, the directions of its faces and edges.
-struct Core {
+// Code that may meet hulls uses Core (32 vertices); code that rules them out uses BoxCore (8),
+// which keeps its per-thread state small.
+template <int NMAX>
+struct CoreT {
+  static constexpr int kMax = NMAX;
   int kind;
   int nv;
-  double v[kCoreMax][3];
+  double v[NMAX][3];
   double r;
   double axis[3][3];   // box: the columns of R; segment: axis[0] = its direction
   int naxis;           // 3 for a box, 1 for a segment, 0 for a point
 };
+using Core = CoreT<kCoreMax>;
+using BoxCore = CoreT<8>;
 
 DS_HDI void sub3(const double* a, const double* b, double* o) {
   o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
@@ -56,12 +62,14 @@ DS_HDI void copy3(const double* a, double* o) { o[0] = a[0]; o[1] = a[1]; o[2] =
 
 // Build the world core of shape (type, size) at pose (R row-major, p); a hull's vertices come
 // from the pool hv (n_hv vertices, body frame).  Returns false for an unknown type or a hull whose
-// vertex range is not an integral range of 4..32 vertices inside the pool.
+// vertex range is not an integral range of 4..32 vertices inside the pool (always for a BoxCore).
+template <class C>
 DS_HDI bool make_core(int type, const double* size, const double* R, const double* p, const double* hv,
-                      int n_hv, Core& c) {
+                      int n_hv, C& c) {
   if (type == DS_CONVEX_HULL) {
+    if (C::kMax < kCoreMax) return false;
     const double f = size[0], n = size[1];
-    if (!(f >= 0.0 && n >= 4.0 && n <= kCoreMax && f == floor(f) && n == floor(n))) return false;
+    if (!(f >= 0.0 && n >= 4.0 && n <= C::kMax && f == floor(f) && n == floor(n))) return false;
     const int first = static_cast<int>(f), count = static_cast<int>(n);
     if (hv == nullptr || first > n_hv - count) return false;
     c.kind = kHull; c.nv = count; c.naxis = 0; c.r = size[2];
@@ -103,7 +111,8 @@ DS_HDI bool make_core(int type, const double* size, const double* R, const doubl
 }
 
 // Index of the core vertex with the largest d . v (the first of equals).
-DS_HDI int support(const Core& c, const double* d) {
+template <class C>
+DS_HDI int support(const C& c, const double* d) {
   int best = 0;
   double bv = dot3(d, c.v[0]);
   for (int i = 1; i < c.nv; ++i) {
@@ -271,7 +280,8 @@ DS_HDI bool closest_reduce(Simplex& s, double* v) {
 // below 1e-12); the witness points pa (on A), pb (on B) are those of the last simplex that did
 // not contain the origin.  When the origin lies inside a tetrahedron of support points, that
 // tetrahedron is copied to *tet (if given) and tet->n = 4; otherwise tet->n = 0.
-DS_HDI bool gjk(const Core& A, const Core& B, double* pa, double* pb, Simplex* tet = nullptr) {
+template <class C>
+DS_HDI bool gjk(const C& A, const C& B, double* pa, double* pb, Simplex* tet = nullptr) {
   if (tet) tet->n = 0;
   Simplex s;
   s.n = 1;
@@ -351,7 +361,8 @@ DS_HDI void seg_seg(const double* p1, const double* q1, const double* p2, const 
 }
 
 // The range [lo, hi] of u . v over the vertices v of a core.
-DS_HDI void project(const Core& c, const double* u, double& lo, double& hi) {
+template <class C>
+DS_HDI void project(const C& c, const double* u, double& lo, double& hi) {
   lo = hi = dot3(u, c.v[0]);
   for (int i = 1; i < c.nv; ++i) {
     const double x = dot3(u, c.v[i]);
@@ -365,7 +376,8 @@ DS_HDI void project(const Core& c, const double* u, double& lo, double& hi) {
 // depth >= 0: the cores overlap, depth is their penetration depth and m the axis from A to B
 // (moving A by -depth m separates them); then the witness points pa on A, pb on B with
 // pa - pb = depth m are written too.
-DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, double* pa, double* pb) {
+template <class C>
+DS_HDI void penetration(const C& A, const C& B, double& depth, double* m, double* pa, double* pb) {
   double cand[15][3];
   int nc = 0;
   if (A.kind == kBox)
@@ -400,7 +412,7 @@ DS_HDI void penetration(const Core& A, const Core& B, double& depth, double* m, 
   if (depth < 0.0) return;
   // the support features of A along m and of B along -m
   const double tol = 1e-9 * (1.0 + fabs(hi_best) + fabs(lo_best));
-  int fa[kCoreMax], fb[kCoreMax], na = 0, nb = 0;
+  int fa[C::kMax], fb[C::kMax], na = 0, nb = 0;
   for (int i = 0; i < A.nv; ++i)
     if (dot3(m, A.v[i]) >= hi_best - tol) fa[na++] = i;
   for (int j = 0; j < B.nv; ++j)
@@ -473,7 +485,8 @@ DS_HDI int epa_nearest(const Polytope& P) {
 // its triangle).  Stops when the support point along the nearest face's normal adds less than
 // 1e-12 (relative to the coordinates) to its distance.  Returns false when the polytope runs out
 // of its 64 vertices, 128 faces or 96 horizon edges, or a new face has zero area.
-DS_HDI bool epa(const Core& A, const Core& B, const Simplex& tet, double& depth, double* m, double* pa,
+template <class C>
+DS_HDI bool epa(const C& A, const C& B, const Simplex& tet, double& depth, double* m, double* pa,
                 double* pb) {
   Polytope P;
   P.nv = 4;
@@ -587,10 +600,13 @@ DS_HDI bool epa(const Core& A, const Core& B, const Simplex& tet, double& depth,
 // Collision detection of shape A (type, size, pose) and shape B (hull vertices from the pool hv
 // of n_hv vertices).  Writes DS_COLLIDE_OUT numbers: phi, c[3], n[3], t1[3], t2[3], the witness
 // points on the surfaces sa[3], sb[3].  An unknown type, a bad hull range, or a hull penetration
-// the expanding polytope cannot resolve gives NaN throughout.
+// the expanding polytope cannot resolve gives NaN throughout.  kHulls = false compiles the form
+// without hulls (a hull is then a bad range), whose per-thread state is a tenth of the other's.
+template <bool kHulls = true>
 DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int type_b,
                     const double* size_b, const double* pose_b, const double* hv, int n_hv, double* out) {
-  Core A, B;
+  using C = typename std::conditional<kHulls, Core, BoxCore>::type;
+  C A, B;
   if (!make_core(type_a, size_a, pose_a, pose_a + 9, hv, n_hv, A) ||
       !make_core(type_b, size_b, pose_b, pose_b + 9, hv, n_hv, B)) {
     for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
@@ -620,10 +636,12 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
       d = -depth;
       copy3(m, n);
       for (int k = 0; k < 3; ++k) pb[k] = pa[k] + d * n[k];
-    } else if (hull && tet.n == 4) {
-      if (!epa(A, B, tet, depth, n, pa, pb)) {
-        for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
-        return;
+    } else if (kHulls && hull && tet.n == 4) {
+      if constexpr (kHulls) {
+        if (!epa(A, B, tet, depth, n, pa, pb)) {
+          for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
+          return;
+        }
       }
       d = -depth;
     } else {
@@ -698,6 +716,7 @@ DS_HDI void twist_pose(const double* pose, const double* xi, double sgn, double*
 // first 7 outputs of collide) with respect to the world-frame twists of A's and B's poses:
 // J = 1 / (2 S sigma^2) sum_s (f(+eps_s) - f(-eps_s)) eps_s^T, eps_s = (A's (u, w), B's (u, w))
 // the caller's samples (S x 12, drawn from N(0, sigma^2 I)).  J is 7 x 12, row-major.
+template <bool kHulls = true>
 DS_HDI void smoothing_jacobian(int type_a, const double* size_a, const double* pose_a, int type_b,
                                const double* size_b, const double* pose_b, const double* hv, int n_hv,
                                int samples, const double* eps, double sigma, double* J) {
@@ -707,10 +726,10 @@ DS_HDI void smoothing_jacobian(int type_a, const double* size_a, const double* p
     const double* e = eps + 12 * s;
     twist_pose(pose_a, e, 1.0, qa);
     twist_pose(pose_b, e + 6, 1.0, qb);
-    collide(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fp);
+    collide<kHulls>(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fp);
     twist_pose(pose_a, e, -1.0, qa);
     twist_pose(pose_b, e + 6, -1.0, qb);
-    collide(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fm);
+    collide<kHulls>(type_a, size_a, qa, type_b, size_b, qb, hv, n_hv, fm);
     for (int i = 0; i < 7; ++i) {
       const double df = fp[i] - fm[i];
       for (int j = 0; j < 12; ++j) J[12 * i + j] += df * e[j];

@@ -40,6 +40,14 @@ int main() {
     for (double& x : sb) std::scanf("%lf", &x);
     for (double& x : pb) std::scanf("%lf", &x);
     ds::cd::collide(ta, sa, pa, tb, sb, pb, hv.data(), nhv, out);
+    if (nhv == 0) {
+      // the form without hulls (what the device runs for a batch without a hull pool) must give
+      // the same numbers, bit for bit
+      double o2[DS_COLLIDE_OUT];
+      ds::cd::collide<false>(ta, sa, pa, tb, sb, pb, nullptr, 0, o2);
+      for (int k = 0; k < DS_COLLIDE_OUT; ++k)
+        if (!(o2[k] == out[k]) && !(o2[k] != o2[k] && out[k] != out[k])) return 3;
+    }
     for (int k = 0; k < DS_COLLIDE_OUT; ++k) std::printf("%.17g ", out[k]);
     std::printf("\n");
   }
