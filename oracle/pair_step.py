@@ -10,8 +10,10 @@ sigma = J_c v+ follows Eq. 1's convention (sigma_N > 0 separates).  The impulse 
 and -lambda on A: body i receives the wrench +-X_i^T [lambda; 0] / dt in its own coordinates (X_i
 the motion transform from body i to the contact frame).
 
-The step is Eq. 3-6 with these rows: v_f = v + dt ABA(q, v, tau), G = J_c M^-1 J_c^T, g = J_c v_f,
-the staged NCP solve of ncp.py, v+ = v + dt ABA(q, v, tau, f_ext(lambda)).  Its Jacobians take
+The step is Eq. 3-6 with these rows: v_f = v + dt ABA(q, v, tau), G = J_c M^-1 J_c^T,
+g = J_c v_f (+ App. D's Baumgarte term with the options baumgarte_kp, baumgarte_kd and the
+activation margin contact_margin, as for the plane contacts), the staged NCP solve of ncp.py,
+v+ = v + dt ABA(q, v, tau, f_ext(lambda)).  Its Jacobians take
 App. D's route 1 (step.route1_matrices): D = dv+/d(q, v, tau) at fixed lambda and F = d(J_c v+)/dq
 at fixed v+, where the q-derivatives split into the part at fixed contact placement (complex steps
 through the rigid-body functions, the transforms X_i held) and App. C's placement terms
@@ -25,14 +27,35 @@ from .ncp import classify, solve_ncp
 from .step import H_CS, pinv_solve, route1_matrices
 
 
-def active_pairs(model, q, pairs):
-    """Indices of the pairs whose signed distance is <= 0 (decided on the real part)."""
-    out = []
+def active_pairs(model, q, pairs, margin=0.0):
+    """Indices of the pairs whose signed distance is <= margin (decided on the real part) and
+    their signed distances."""
+    out, phis = [], []
     for k, pr in enumerate(pairs):
         _, _, res = Co.pair_placement(model, np.real(q), pr[:6])
-        if res["phi"] <= 0.0:
+        if res["phi"] <= margin:
             out.append(k)
-    return out
+            phis.append(res["phi"])
+    return out, np.array(phis)
+
+
+def _gains(opt):
+    kp, kd = getattr(opt, "baumgarte_kp", 1.0), getattr(opt, "baumgarte_kd", 0.0)
+    margin = getattr(opt, "contact_margin", 0.0)
+    return kp, kd, margin, not (kp == 1.0 and kd == 0.0 and margin == 0.0)
+
+
+def baumgarte(opt, phis, Jc, v):
+    """App. D's term of g on the active pairs: zero on the tangent rows, and on the normal row
+    phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N ([x]_- = min(x, 0)); identically zero for K_p = 1,
+    K_d = 0 and no margin (every active pair then has phi <= 0)."""
+    kp, kd, _, on = _gains(opt)
+    b = np.zeros(Jc.shape[0])
+    if not on or len(phis) == 0:
+        return b
+    x = phis / opt.dt
+    b[2::3] = x - kp * np.minimum(x, 0.0) - kd * (Jc @ v)[2::3]
+    return b
 
 
 def pair_rows(model, q, pairs, act, transforms=None):
@@ -70,23 +93,27 @@ def step(model, env, pairs, opt):
     M = rigid.crba(model, q)
     L = rigid.cholesky(M)
     v_f = ufd_velocity(model, q, v, tau, opt, None)
-    act = active_pairs(model, q, pairs)
+    act, phis = active_pairs(model, q, pairs, _gains(opt)[2])
     transforms = [Co.pair_transforms(model, q, pairs[k][:6]) for k in act]
     Jc = pair_rows(model, q, pairs, act, transforms)
     mu = np.array([pairs[k][6] for k in act])
     Y = rigid.chol_solve(L, Jc.T) if act else np.zeros((len(v), 0))
-    G, g = Jc @ Y, Jc @ v_f
+    G, g = Jc @ Y, Jc @ v_f + baumgarte(opt, phis, Jc, v)
     es, el = getattr(opt, "eps_sigma", 1e-8), getattr(opt, "eps_lambda", 1e-8)
     lam, iters, conv = solve_ncp(G, g, mu, es, el) if act else (np.zeros(0), 0, True)
     modes, margin = classify(G, g, mu, lam, es, el)
     fext = pair_wrenches(model, q, pairs, act, transforms, lam, dt) if act else None
     v_next = ufd_velocity(model, q, v, tau, opt, fext)
     return dict(v_next=v_next, lam=lam, modes=modes, margin=margin, act=act, transforms=transforms,
-                Jc=Jc, Y=Y, G=G, g=g, mu=mu, M=M, converged=conv)
+                Jc=Jc, Y=Y, G=G, g=g, mu=mu, M=M, converged=conv, phis=phis)
 
 
 def partials(model, env, pairs, opt, st, dcd_fn=None):
-    """D = dv+/d(q, v, tau) at fixed lambda (nv x 3 nv) and F = d(J_c v+)/dq at fixed v+.
+    """D = dv+/d(q, v, tau) at fixed lambda (nv x 3 nv), F = d(J_c v+)/dq at fixed v+ and Bt, the
+    derivative of the Baumgarte term (None when it is identically zero): on the normal rows
+    d(phi/dt - K_p [phi/dt]_-)/dq = (1 - K_p [phi < 0]) (J_c)_N / dt, since the signed distance
+    changes at the normal relative velocity of the witness points (d phi = (J_c dq)_N), and
+    -K_d d(J_c v)_N/d(q, v) with the same placement terms as F.
     dcd_fn(model, q, pair, which) gives dCD/dM_i (default: central differences, Co.dcd_dbody)."""
     dcd_fn = dcd_fn or (lambda m, qq, pr, w: Co.dcd_dbody(m, qq, pr, w))
     q, v, tau = env["q"], env["v"], env["tau"]
@@ -105,6 +132,7 @@ def partials(model, env, pairs, opt, st, dcd_fn=None):
     a_star = (v_next - v) / dt
     grav = np.asarray(opt.gravity, float)
     dRq, dJl, Fq = np.zeros((nv, nv)), np.zeros((nv, nv)), np.zeros((3 * len(act), nv))
+    Kq = np.zeros((3 * len(act), nv))                             # d(J_c v)/dq at fixed v
     for j in range(nv):
         e = np.zeros(nv, dtype=complex)
         e[j] = 1j * H_CS
@@ -114,14 +142,24 @@ def partials(model, env, pairs, opt, st, dcd_fn=None):
             Jh = pair_rows(model, qj, pairs, act, transforms)      # the transforms held
             dJl[:, j] = np.imag(Jh.T @ lam) / H_CS
             Fq[:, j] = np.imag(Jh @ v_next) / H_CS
+            Kq[:, j] = np.imag(Jh @ v) / H_CS
     for jj, k in enumerate(act):
         pr = pairs[k][:6]
         dcd = (dcd_fn(model, q, pr, 0), dcd_fn(model, q, pr, 1))
         dJl += Co.appc_dJctlam_dq(model, q, lam[3 * jj:3 * jj + 3], pr, dcd)
         Fq[3 * jj:3 * jj + 3] += Co.appc_dJcv_dq(model, q, v_next, pr, dcd)
+        Kq[3 * jj:3 * jj + 3] += Co.appc_dJcv_dq(model, q, v, pr, dcd)
     Dq = -dt * rigid.chol_solve(rigid.cholesky(st["M"]), dRq - dJl / dt)
     D = np.concatenate([Dq, np.stack(Dv, 1), np.stack(Dt, 1)], axis=1)
-    return D, Fq
+    kp, kd, _, on = _gains(opt)
+    Bt = None
+    if act and on:
+        Bt = np.zeros((3 * len(act), 3 * nv))
+        Jc = st["Jc"]
+        neg = np.real(st["phis"]) < 0.0
+        Bt[2::3, :nv] = (1.0 - kp * neg)[:, None] * Jc[2::3] / dt - kd * Kq[2::3]
+        Bt[2::3, nv:2 * nv] = -kd * Jc[2::3]
+    return D, Fq, Bt
 
 
 def step_jac(model, env, pairs, opt, dcd_fn=None):
@@ -129,12 +167,14 @@ def step_jac(model, env, pairs, opt, dcd_fn=None):
     X = -A^- B (J_c D + [F, 0, 0]).  dcd_fn as for partials (e.g. App. C's randomized smoothing,
     Co.dcd_dbody_smoothed with the caller's samples)."""
     st = step(model, env, pairs, opt)
-    D, F = partials(model, env, pairs, opt, st, dcd_fn)
+    D, F, Bt = partials(model, env, pairs, opt, st, dcd_fn)
     nv = len(env["v"])
     if st["act"]:
         A, Bm, C = route1_matrices(st["G"], st["g"], st["mu"], st["lam"], st["modes"])
         RHS = st["Jc"] @ D
         RHS[:, :nv] += F
+        if Bt is not None:
+            RHS = RHS + Bt
         X = -pinv_solve(A, Bm @ RHS)
         J = D + st["Y"] @ (C @ X)
     else:

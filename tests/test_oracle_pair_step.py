@@ -11,6 +11,8 @@ and of its Jacobians with App. C's contact-placement terms, no GPU.
   sliding), and for both pairs in contact at once.  Leaving out either placement term (the one in
   d(J_c v+)/dq or the one in d(J_c^T lambda)/dq) misses by orders of magnitude more than the
   tolerance.
+* App. D's Baumgarte term and activation margin on pair contacts: the Jacobian against central
+  differences, with a pair inside the margin but apart; without the term's derivative it misses.
 * With no pair in contact the step is the free step v + dt ABA(q, v, tau)."""
 import types
 
@@ -153,6 +155,49 @@ def test_pair_step_takes_the_smoothed_placement_derivative():
                      dcd_fn=lambda m, q, pr, w: C.dcd_dbody_smoothed(m, q, pr, w, sigma, design))
     ref = PS.step_jac(model, env, pairs, OPT)
     assert np.abs(st["dv_dq"] - ref["dv_dq"]).max() <= 1e-9 * max(1.0, np.abs(ref["dv_dq"]).max())
+
+
+def _opt(kp, kd, margin):
+    return types.SimpleNamespace(dt=0.01, gravity=(0.0, 0.0, -9.81), baumgarte_kp=kp, baumgarte_kd=kd,
+                                 contact_margin=margin)
+
+
+BAUMGARTE_CASES = [
+    ("world", 2, 1.0, 0.2, 0.004, (0.3, 0.2, 0.01), [SLD]),
+    ("world", 34, 1.0, 0.6, -0.0005, (0.3, 0.2, 0.01), [SLD]),      # apart by 0.5 mm, inside the margin
+    ("two", 21, 0.3, 0.3, None, (0.5, 0.0, 0.0), [SLD, BRK]),
+    ("two", 20, 0.02, 3.0, None, (0.3, 0.2, 0.01), [STK, BRK]),
+]
+
+
+def _baumgarte_case(kind, seed, vscale, mu, pen):
+    return _world_case(seed, vscale, mu, pen=pen) if kind == "world" else _two_pair_case(seed, vscale, mu)
+
+
+@pytest.mark.parametrize("kind,seed,vscale,mu,pen,gains,modes", BAUMGARTE_CASES)
+def test_pair_step_baumgarte_against_central_differences(kind, seed, vscale, mu, pen, gains, modes):
+    """App. D's Baumgarte term phi/dt - K_p [phi/dt]_- - K_d (J_c v)_N on pair contacts, with the
+    activation margin (a pair 0.5 mm apart is active and slides): the route-1 Jacobian, whose
+    Baumgarte derivative takes d phi/dq = (J_c)_N and the placement terms for d(J_c v)_N/dq,
+    equals central differences of the whole step."""
+    model, env, pairs = _baumgarte_case(kind, seed, vscale, mu, pen)
+    opt = _opt(*gains)
+    st = PS.step_jac(model, env, pairs, opt)
+    assert [int(m) for m in st["modes"]] == modes
+    fd = PS.jacobian_fd(model, env, pairs, opt)
+    J = np.concatenate([st["dv_dq"], st["dv_dv"], st["dv_dtau"]], axis=1)
+    assert np.abs(J - fd).max() <= 1e-6 * max(1.0, np.abs(fd).max())
+
+
+def test_pair_step_baumgarte_derivative_matters(monkeypatch):
+    model, env, pairs = _world_case(34, 1.0, 0.6, pen=-0.0005)
+    opt = _opt(0.3, 0.2, 0.01)
+    fd = PS.jacobian_fd(model, env, pairs, opt)
+    full = PS.partials
+    monkeypatch.setattr(PS, "partials", lambda *a, **k: full(*a, **k)[:2] + (None,))
+    st = PS.step_jac(model, env, pairs, opt)
+    J = np.concatenate([st["dv_dq"], st["dv_dv"], st["dv_dtau"]], axis=1)
+    assert np.abs(J - fd).max() > 1e-2 * np.abs(fd).max()
 
 
 def test_pair_step_without_contact_is_the_free_step():
