@@ -20,8 +20,10 @@
 //   expansion reaches the same facet).  The same axes decide whether cores with a box overlap at
 //   all (a negative minimum is a separating axis), so GJK runs only on separated cores there.
 //   A hull has no such short axis list: overlapping cores with a hull take the expanding polytope
-//   (EPA, van den Bergen 2001) from GJK's tetrahedron around the origin.  The witness points are the projection of the origin on
-//   that facet, split over the two cores' support features.
+//   (EPA, van den Bergen 2001) from GJK's tetrahedron around the origin (or, where GJK stopped on
+//   the origin before forming one, a tetrahedron built by GJK's intersection iteration).  The
+//   witness points are the projection of the origin on that facet, split over the two cores'
+//   support features.
 // * The contact point is the midpoint of the witness points moved to the surfaces (pA + rA n,
 //   pB - rB n); the tangent axes follow the plane contacts' rule: t1 = normalize(e_x - (n.e_x) n),
 //   e_y in place of e_x when |n_x| > 0.9, t2 = n x t1.
@@ -479,6 +481,64 @@ DS_HDI int epa_nearest(const Polytope& P) {
   return best;
 }
 
+// A tetrahedron of support points around the origin, for overlapping cores where GJK stopped on
+// the origin before forming one (e.g. identical cores at one pose, whose first support difference
+// is the origin itself): support points along the four tetrahedral directions, then, while a face
+// separates the origin from the opposite vertex, that vertex replaced by the support point along
+// the face's outward normal (GJK's intersection iteration).  Returns false when D is flat, the
+// origin is not strictly inside it, or 64 replacements do not enclose it.
+template <class C>
+DS_HDI bool enclose_origin(const C& A, const C& B, Simplex& t) {
+  const double dirs[4][3] = {{1.0, 1.0, 1.0}, {1.0, -1.0, -1.0}, {-1.0, 1.0, -1.0}, {-1.0, -1.0, 1.0}};
+  double scale = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    const double neg[3] = {-dirs[i][0], -dirs[i][1], -dirs[i][2]};
+    t.ia[i] = support(A, dirs[i]);
+    t.ib[i] = support(B, neg);
+    sub3(A.v[t.ia[i]], B.v[t.ib[i]], t.w[i]);
+    scale = fmax(scale, sqrt(dot3(t.w[i], t.w[i])));
+  }
+  t.n = 4;
+  const int F[4][4] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 3, 1}, {1, 2, 3, 0}};
+  for (int it = 0; it < kEpaMaxIter; ++it) {
+    int out_face = -1;
+    double dir[3] = {0.0, 0.0, 0.0};
+    for (int f = 0; f < 4 && out_face < 0; ++f) {
+      const double *wi = t.w[F[f][0]], *wj = t.w[F[f][1]], *wk = t.w[F[f][2]], *wo = t.w[F[f][3]];
+      double e1[3], e2[3], nrm[3], eo[3];
+      sub3(wj, wi, e1);
+      sub3(wk, wi, e2);
+      cross3(e1, e2, nrm);
+      sub3(wo, wi, eo);
+      const double sd = dot3(nrm, eo), so = -dot3(nrm, wi);
+      if (fabs(sd) <= 1e-9 * sqrt(dot3(nrm, nrm) * dot3(eo, eo))) {   // flat
+        t.n = 0;
+        return false;
+      }
+      if (so * sd < 0.0) {   // the origin lies beyond face f
+        out_face = f;
+        for (int c = 0; c < 3; ++c) dir[c] = sd > 0.0 ? -nrm[c] : nrm[c];
+      }
+    }
+    if (out_face < 0) return true;
+    const double neg[3] = {-dir[0], -dir[1], -dir[2]};
+    const int ia = support(A, dir), ib = support(B, neg);
+    double w[3];
+    sub3(A.v[ia], B.v[ib], w);
+    // the origin is beyond the face: unless the support point passes it, D misses the origin
+    if (dot3(dir, w) <= 1e-12 * scale * sqrt(dot3(dir, dir))) {
+      t.n = 0;
+      return false;
+    }
+    const int o = F[out_face][3];
+    copy3(w, t.w[o]);
+    t.ia[o] = ia;
+    t.ib[o] = ib;
+  }
+  t.n = 0;
+  return false;
+}
+
 // Penetration of overlapping cores from GJK's tetrahedron tet around the origin: depth, the unit
 // axis m from A to B (moving A by -depth m separates the cores) and the witness points pa, pb with
 // pa - pb = depth m (the projection of the origin on the nearest facet, in barycentric weights of
@@ -636,7 +696,7 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
       d = -depth;
       copy3(m, n);
       for (int k = 0; k < 3; ++k) pb[k] = pa[k] + d * n[k];
-    } else if (kHulls && hull && tet.n == 4) {
+    } else if (kHulls && hull && (tet.n == 4 || enclose_origin(A, B, tet))) {
       if constexpr (kHulls) {
         if (!epa(A, B, tet, depth, n, pa, pb)) {
           for (int k = 0; k < DS_COLLIDE_OUT; ++k) out[k] = nan("");
@@ -645,8 +705,8 @@ DS_HDI void collide(int type_a, const double* size_a, const double* pose_a, int 
       }
       d = -depth;
     } else {
-      // touching cores (within 1e-12), or crossing point and segment cores: no normal; take the
-      // world z axis
+      // touching cores (within 1e-12, no tetrahedron of D strictly around the origin), or
+      // crossing point and segment cores: no normal; take the world z axis
       d = 0.0;
       n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
     }

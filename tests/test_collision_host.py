@@ -133,6 +133,24 @@ def test_host_collide_hulls_against_oracle(host_collide, types):
     assert n_over >= 10 and n_apart >= 10
 
 
+def test_host_collide_identical_shapes_at_one_pose(host_collide):
+    """The degenerate overlap of a shape with its copy at the same pose: for boxes phi = -2 x the
+    smallest half extent (the separating axes); for hulls, where GJK's first support difference is
+    the origin itself, the enclosing tetrahedron is built by GJK's intersection iteration and EPA
+    gives the oracle's phi (its normal is one of a +-m pair, as D = A - A is symmetric), with
+    sb - sa = phi n."""
+    P = pairs(8, seed=3, types=[(BOX, BOX), (HULL, HULL)])
+    for k in range(8):
+        P["type_b"][k], P["size_b"][k], P["pose_b"][k] = P["type_a"][k], P["size_a"][k], P["pose_a"][k]
+    got = host_collide(P)
+    assert np.isfinite(got).all()
+    for k in range(8):
+        phi, n, sa, sb = got[k][0], got[k][4:7], got[k][13:16], got[k][16:19]
+        ref = -2.0 * P["size_a"][k].min() if P["type_a"][k] == BOX else oracle_collide(P, k)["phi"]
+        assert abs(phi - ref) <= 1e-12
+        assert abs(n @ n - 1.0) <= 1e-12 and np.abs(sb - sa - phi * n).max() <= 1e-12
+
+
 def test_host_collide_bad_hull_range_is_nan(host_collide):
     P = pairs(3, seed=6, types=[(HULL, BOX)])
     P["size_a"][1][1] = 40.0                              # more than 32 vertices
